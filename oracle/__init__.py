@@ -1,0 +1,261 @@
+"""CPU oracle for the localization path -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, ``__graft_entry__.smoke()`` and bench.py's CPU-baseline leg may import this
+package.  The product library never calls it and shares no code with it: the oracle has
+its own net-spec and weight-blob parser (below), its own C implementation
+(``sml_oracle.c``) and its own record type.
+
+What it computes (each function cites the passage it follows):
+  * ``forward``        -- float64 forward of the plain dilated 3x3 stack (Sec. 3.2.1) with
+                          DECODE-style per-pixel heads (Sec. 3.2);
+  * ``maps_f32``       -- per-pixel maps handed to the decode: p = sigmoid(logit), dx, dy,
+                          zhat, Nhat, rounded once to float32;
+  * ``decode``         -- float32 decode of maps into (frame, x, y, z, photons, p) records
+                          (post-processing on the device, Sec. 2.2 and Sec. 4.2.1);
+  * ``localize``       -- forward, maps, decode;
+  * ``forward_window`` -- exact heads of an interior block of a large frame from a crop
+                          that covers the receptive field (for sampled parity checks);
+  * ``loss_grad``      -- BCE (Sec. 3.3) + masked L2 training loss and its gradient.
+Pins for each of these live in tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+import struct
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_SRC = os.path.join(_HERE, "sml_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+NH = 5
+RECORD_DTYPE = np.dtype(
+    [("frame", "<i4"), ("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("photons", "<f4"), ("p", "<f4")]
+)
+
+
+def build(force: bool = False) -> str:
+    """Compile sml_oracle.c with gcc (float64 forward, float32 decode without FMA contraction)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            D = ctypes.c_double
+            F = ctypes.c_float
+            lib.orc_forward_x.argtypes = [P, I, I, I, I, I, I, P, P, P, P, D, P, P, P, P]
+            lib.orc_forward_x.restype = None
+            lib.orc_ingest.argtypes = [P, I, I, I, P, P, D, D, D, P]
+            lib.orc_ingest.restype = None
+            lib.orc_decode.argtypes = [P, I, I, I, F, F, F, P, ctypes.c_long]
+            lib.orc_decode.restype = ctypes.c_long
+            lib.orc_loss.argtypes = [P, P, I, I, I, P]
+            lib.orc_loss.restype = D
+            lib.orc_loss_grad.argtypes = [P, P, I, I, I, I, I, I, P, P, P, P, P, P, P, P, P, P]
+            lib.orc_loss_grad.restype = D
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ----------------------------------------------------------------------------- parsing
+
+
+class Net:
+    """Network description parsed from a JSON net spec and an SMLW weight blob."""
+
+    def __init__(self, spec_json: str, blob: bytes):
+        s = json.loads(spec_json)
+        self.in_ch = int(s.get("in_ch", 1))
+        self.C = int(s["channels"])
+        self.dil = [int(d) for d in s["dilations"]]
+        self.L = len(self.dil)
+        self.in_scale = float(s.get("in_scale", 1e-3))
+        self.z_scale = float(s.get("z_scale", 1000.0))
+        self.ph_scale = float(s.get("ph_scale", 10000.0))
+        fmt = "<8s7I16i"
+        hdr = struct.unpack_from(fmt, blob, 0)
+        if hdr[0] != b"SMLW0001":
+            raise ValueError("weight blob: bad magic")
+        _, _ver, L, C, in_ch, nh, has_bn, _, *dil = hdr
+        if (L, C, in_ch, nh, list(dil[:L])) != (self.L, self.C, self.in_ch, NH, self.dil):
+            raise ValueError("weight blob does not match net spec")
+        off = struct.calcsize(fmt)
+
+        def take(n):
+            nonlocal off
+            a = np.frombuffer(blob, dtype="<f4", count=n, offset=off).astype(np.float64)
+            off += 4 * n
+            return a
+
+        ws, bs, bns = [], [], []
+        self.bn_eps = 0.0
+        for layer in range(L):
+            cin = in_ch if layer == 0 else C
+            ws.append(take(C * cin * 9))
+            bs.append(take(C))
+            if has_bn:
+                bns.append(take(4 * C))
+                self.bn_eps = float(take(1)[0])
+        self.conv_w = np.ascontiguousarray(np.concatenate(ws))
+        self.conv_b = np.ascontiguousarray(np.concatenate(bs))
+        self.bn = np.ascontiguousarray(np.concatenate(bns)) if has_bn else None
+        self.head_w = np.ascontiguousarray(take(NH * C))
+        self.head_b = np.ascontiguousarray(take(NH))
+        if off != len(blob):
+            raise ValueError("weight blob: trailing bytes")
+
+    @property
+    def R(self) -> int:
+        return sum(self.dil)
+
+
+# ----------------------------------------------------------------------------- forward
+
+
+def ingest(frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None, in_scale=1e-3):
+    """Network input x = (adu - offset) / gain * in_scale, float64 [T,H,W]."""
+    lib = _load()
+    f = np.ascontiguousarray(frames, dtype=np.uint16)
+    T, H, W = f.shape
+    gm = None if gain_map is None else np.ascontiguousarray(gain_map, dtype=np.float64)
+    om = None if offset_map is None else np.ascontiguousarray(offset_map, dtype=np.float64)
+    x0 = np.empty((T, H, W), dtype=np.float64)
+    lib.orc_ingest(_ptr(f), T, H, W, _ptr(gm), _ptr(om), gain, offset, in_scale, _ptr(x0))
+    return x0
+
+
+def forward_x(net: Net, x0, acts=False):
+    """Raw heads [T,5,H,W] (float64) of the dilated stack on inputs x0 [T,in_ch,H,W]
+    (Sec. 3.2.1 dilated convolution, zero padding at every layer; Sec. 3.2 heads)."""
+    lib = _load()
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    if x0.ndim == 3:
+        x0 = x0[:, None]
+    T, cin, H, W = x0.shape
+    assert cin == net.in_ch
+    heads = np.empty((T, NH, H, W), dtype=np.float64)
+    a = np.empty((T, net.L, net.C, H, W), dtype=np.float64) if acts else None
+    dil = np.asarray(net.dil, dtype=np.int32)
+    lib.orc_forward_x(_ptr(x0), T, H, W, net.L, net.C, net.in_ch, _ptr(dil), _ptr(net.conv_w),
+                      _ptr(net.conv_b), _ptr(net.bn), net.bn_eps, _ptr(net.head_w), _ptr(net.head_b),
+                      _ptr(heads), _ptr(a))
+    return (heads, a) if acts else heads
+
+
+def forward(net: Net, frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None):
+    """Raw heads [T,5,H,W] float64 from uint16 frames through the camera transform."""
+    x0 = ingest(frames, gain, offset, gain_map, offset_map, net.in_scale)
+    return forward_x(net, x0)
+
+
+def sigmoid(h):
+    """p = 1 / (1 + exp(-h)) in float64."""
+    return 1.0 / (1.0 + np.exp(-np.asarray(h, dtype=np.float64)))
+
+
+def maps_f32(heads):
+    """Decode input [T,5,H,W] float32: channel 0 = sigmoid(logit), channels 1-4 unchanged."""
+    m = np.array(heads, dtype=np.float64, copy=True)
+    m[:, 0] = sigmoid(m[:, 0])
+    return m.astype(np.float32)
+
+
+def decode(maps, p_min, z_scale, ph_scale, cap=None):
+    """Float32 decode (Sec. 2.2 post-processing): records ordered by (frame, row, col)."""
+    lib = _load()
+    m = np.ascontiguousarray(maps, dtype=np.float32)
+    T, nh, H, W = m.shape
+    assert nh == NH
+    n = lib.orc_decode(_ptr(m), T, H, W, p_min, z_scale, ph_scale, None, 0)
+    out = np.zeros(n if cap is None else min(n, cap), dtype=RECORD_DTYPE)
+    lib.orc_decode(_ptr(m), T, H, W, p_min, z_scale, ph_scale, _ptr(out), out.size)
+    return out
+
+
+def localize(net: Net, frames, p_min, gain=1.0, offset=100.0, gain_map=None, offset_map=None):
+    heads = forward(net, frames, gain, offset, gain_map, offset_map)
+    maps = maps_f32(heads)
+    return decode(maps, p_min, net.z_scale, net.ph_scale), heads, maps
+
+
+def forward_window(net: Net, frames, i0, i1, j0, j1, gain=1.0, offset=100.0, gain_map=None,
+                   offset_map=None):
+    """Exact heads [T,5,i1-i0,j1-j0] of the block [i0,i1) x [j0,j1) of full frames.
+
+    The crop extends the block by the receptive radius R = sum of dilations (clipped at the
+    frame border).  Every output inside the block depends only on inputs within R of it,
+    and layer l's outputs are wrong only within sum_{k<=l} d_k of a crop edge that is not
+    a frame edge, so the block's values equal those of the whole-frame forward.
+    """
+    T, H, W = frames.shape
+    R = net.R
+    ci0, ci1 = max(0, i0 - R), min(H, i1 + R)
+    cj0, cj1 = max(0, j0 - R), min(W, j1 + R)
+    crop = np.ascontiguousarray(frames[:, ci0:ci1, cj0:cj1])
+    gm = None if gain_map is None else gain_map[ci0:ci1, cj0:cj1]
+    om = None if offset_map is None else offset_map[ci0:ci1, cj0:cj1]
+    h = forward(net, crop, gain, offset, gm, om)
+    return h[:, :, i0 - ci0 : i1 - ci0, j0 - cj0 : j1 - cj0]
+
+
+# ----------------------------------------------------------------------------- training
+
+
+def loss(heads, targets):
+    lib = _load()
+    h = np.ascontiguousarray(heads, dtype=np.float64)
+    y = np.ascontiguousarray(targets, dtype=np.float64)
+    B, _, H, W = h.shape
+    dh = np.empty_like(h)
+    val = lib.orc_loss(_ptr(h), _ptr(y), B, H, W, _ptr(dh))
+    return val, dh
+
+
+def loss_grad(net: Net, x0, targets):
+    """Loss (BCE on p, Sec. 3.3, + masked L2) and its exact gradient w.r.t. every weight.
+
+    Returns (loss, g_conv_w (flat, blob order), g_conv_b [L*C], g_head_w [5*C], g_head_b [5],
+    heads)."""
+    if net.bn is not None:
+        raise ValueError("training gradient is defined for nets without BatchNorm")
+    lib = _load()
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    if x0.ndim == 3:
+        x0 = x0[:, None]
+    B, cin, H, W = x0.shape
+    y = np.ascontiguousarray(targets, dtype=np.float64)
+    gw = np.empty_like(net.conv_w)
+    gb = np.empty_like(net.conv_b)
+    ghw = np.empty_like(net.head_w)
+    ghb = np.empty_like(net.head_b)
+    heads = np.empty((B, NH, H, W), dtype=np.float64)
+    dil = np.asarray(net.dil, dtype=np.int32)
+    val = lib.orc_loss_grad(_ptr(x0), _ptr(y), B, H, W, net.L, net.C, net.in_ch, _ptr(dil),
+                            _ptr(net.conv_w), _ptr(net.conv_b), _ptr(net.head_w), _ptr(net.head_b),
+                            _ptr(gw), _ptr(gb), _ptr(ghw), _ptr(ghb), _ptr(heads))
+    return val, gw, gb, ghw, ghb, heads
