@@ -1,0 +1,375 @@
+"""Benchmark: localization throughput of the dilated-conv localization path on one GB300.
+
+Workload (the batched-inference configuration): 256 frames of 256x256 uint16, 1 emitter per
+um^2 at 100 nm pixels, sigma 1.3 px, photons LogNormal(ln 3000, 0.5), background U(50,200);
+48-channel 8-layer dilated net (dilations 1,2,4,8,16,8,4,1), random-init weights from a seed.
+One step = the whole path (camera transform, 8 conv layers, heads, decode into records) over
+the 256-frame batch.  `value` is frames/s with inputs resident in HBM; `e2e` is the same
+metric through the synchronous C-ABI call with host buffers (H2D of the frames and D2H of
+the records inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp8] [--impl reference]
+
+With N > 1 (launched by torchrun) every rank processes its own batch: replicas with no
+collective on the data path ("weak" scaling); rank 0 prints the max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+T_FRAMES, H, W = 256, 256, 256
+P_MIN = 0.5
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def conv_flops_per_px(C):
+    return 2 * 9 * C * C
+
+
+def algorithmic_flops_per_px(spec):
+    C, L = spec.channels, spec.L
+    return 2 * (9 * C + (L - 1) * 9 * C * C + 5 * C)
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2410_02314_gb300", "csrc", "k_tc.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(precision):
+    """DRAM bytes per launch of the middle-layer conv kernel from the committed ncu summary,
+    valid only if the kernel source hash recorded there matches the current source."""
+    p = os.path.join(ROOT, "profiles", f"dconv_tc_{precision}_batched256.md")
+    if not os.path.exists(p):
+        return None
+    text = open(p).read()
+    m_hash = re.search(r"k_tc\.cu sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    m_bytes = re.search(r"dram bytes per full launch:\s*([0-9.e+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+def cpu_baseline(w, budget_s=12.0):
+    """The oracle as it stands (forward + decode) on whole frames of the workload, on the host
+    cores; as many frames as fit the time budget (at least one)."""
+    import oracle
+
+    net = oracle.Net(w.spec.to_json(), w.blob)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        f = w.frames[done : done + 1]
+        oracle.localize(net, f, P_MIN, w.cam.gain, w.cam.offset)
+        done += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or done >= 16:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": done / el, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} of the {w.frames.shape[0]} frames ({w.frames.shape[1]}x{w.frames.shape[2]}), "
+                      f"float64 forward + float32 decode, {el:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, timed on bounded samples of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2410_02314_gb300 import synth
+    import oracle
+
+    w = synth.workload_batched(T=T_FRAMES, H=H, W=W, precision=args.precision)
+    net = oracle.Net(w.spec.to_json(), w.blob)
+    frames_per_step = 1
+    for k in range(args.warmup):
+        oracle.localize(net, w.frames[k % T_FRAMES : k % T_FRAMES + 1], P_MIN)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.localize(net, w.frames[k % T_FRAMES : k % T_FRAMES + 1], P_MIN)
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * statistics.mean(times)
+    val = frames_per_step / (ms / 1000)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": "frames/s", "value": val, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batched_{T_FRAMES}x{H}x{W}_48ch_8layer", "frames_per_step": frames_per_step,
+                       "note": "CPU oracle, one whole frame per step"},
+            "cpu_baseline": {"value": val, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{frames_per_step} frame per step, {args.steps} steps"},
+            "e2e": {"value": val, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chunk-px", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import paper_2410_02314_gb300 as sml
+    from paper_2410_02314_gb300 import synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if rank == 0:
+        __graft_entry__.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+        dist.barrier()
+        __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def workload(prec):
+        w = synth.workload_batched(T=T_FRAMES, H=H, W=W, precision=prec, seed=3 + rank)
+        spec = json.loads(w.spec.to_json())
+        if args.chunk_px:
+            spec["chunk_px"] = args.chunk_px
+        return w, json.dumps(spec)
+
+    w, spec_json = workload(args.precision)
+    loc = sml.Localizer(spec_json, w.blob)
+    d_frames = torch.from_numpy(w.frames).to(dev)
+    cap = T_FRAMES * H * W // 4
+    d_out = torch.empty(cap * 24, dtype=torch.uint8, device=dev)
+    d_n = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        loc.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream)
+
+    def timed(steps, profile=False):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if profile:
+            sml.sml_profile_enable(loc.ctx, True)
+        for a, b in evs:
+            flush.zero_()  # L2 flushed between steps, outside the timed events
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        if profile:
+            sml.sml_profile_enable(loc.ctx, False)
+        return [a.elapsed_time(b) for a, b in evs]
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = loc.last_launch_count
+    n_rec = int(d_n.item())
+
+    clk = ClockSampler(local)
+    clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = timed(args.steps, profile=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = statistics.mean(times)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * T_FRAMES / (ms / 1000.0)
+
+    # dominant kernel: the middle-layer tensor-core (or FP32) conv, timed on its stream
+    conv_ms, conv_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_CONV)
+    heads_ms, heads_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_CONV_HEADS)
+    l1_ms, l1_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_LAYER1)
+    dec_ms, dec_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_DECODE)
+    C = w.spec.channels
+    chunk_px = json.loads(spec_json).get("chunk_px", 1 << 20)
+    frames_per_chunk = max(1, chunk_px // (H * W))
+    px_per_launch = min(frames_per_chunk, T_FRAMES) * H * W
+    pk, pk_kind = peaks()
+    flops_launch = conv_flops_per_px(C) * px_per_launch
+    avg_conv_s = conv_ms / max(conv_n, 1) / 1000.0
+    achieved = flops_launch / avg_conv_s / 1e12
+    if args.precision == "bf16":
+        peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+        peak_note = f"bf16 dense sustained ({pk_kind})"
+    elif args.precision == "fp8":
+        peak = 2.0 * pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+        peak_note = f"fp8 = 2 x bf16 sustained ({pk_kind}) by the nominal 4.5/2.25 ratio"
+    else:
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        peak_note = "fp32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz (derived, not measured)"
+    traffic = profiled_traffic(args.precision)
+    roofline = {"bound": "tensor" if args.precision != "fp32" else "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "kernel": "k_dconv_tc (middle layers)"
+                if args.precision != "fp32" else "k_dconv_f32 (middle layers)", "peak_kind": peak_note,
+                "flops_per_launch": flops_launch, "launches": conv_n, "avg_launch_ms": avg_conv_s * 1000}
+    breakdown = {"layer1_ms": l1_ms / args.steps, "conv_ms": conv_ms / args.steps,
+                 "conv_heads_ms": heads_ms / args.steps, "decode_ms": dec_ms / args.steps}
+
+    # end to end through the synchronous C-ABI call with host buffers
+    host_frames = torch.from_numpy(w.frames).pin_memory()
+    host_out = torch.empty(cap * 24, dtype=torch.uint8).pin_memory()
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        recs = sml.sml_localize(loc.ctx, host_frames, P_MIN, gain=w.cam.gain, offset=w.cam.offset, out=host_out)
+        el = time.perf_counter() - t0
+        if k >= args.warmup:
+            e2e_times.append(el)
+    e2e_s = statistics.mean(e2e_times)
+    e2e = {"value": world * T_FRAMES / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": int(w.frames.nbytes),
+           "d2h_bytes_per_step": int(recs.numel() + 8)}
+
+    extra = {}
+    if not args.no_fp32 and args.precision != "fp32":
+        w32, js32 = workload("fp32")
+        loc32 = sml.Localizer(js32, w32.blob)
+        for _ in range(2):
+            loc32.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            loc32.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms32 = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        extra["fp32_frames_per_s"] = T_FRAMES / (ms32 / 1000)
+        extra["speedup_vs_fp32"] = (T_FRAMES / (ms / 1000)) / extra["fp32_frames_per_s"]
+        loc32.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(w)
+    line = {
+        "metric": "frames/s",
+        "value": value,
+        "unit": "frames/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": args.precision,
+        "data": "synthetic",
+        "config": {"workload": f"batched_{T_FRAMES}x{H}x{W}_48ch_8layer", "frames_per_step": T_FRAMES,
+                   "precision": args.precision, "chunk_px": chunk_px, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas{world}"},
+        "mpix_per_s": value * H * W / 1e6,
+        "records_per_step": n_rec,
+        "gpu_launches": launches_per_step * args.steps,
+        "e2e": e2e,
+        "roofline": roofline,
+        "kernel_ms_per_step": breakdown,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        **extra,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * sml.h -- C ABI of the GB300 single-molecule localization library.
+ *
+ * The library runs the hot path of the DilatedLoc-style method on one GPU: a stack of
+ * dilated 3x3 convolutions (dilated convolution, Sec. 3.2.1) over uint16 camera frames,
+ * DECODE-style per-pixel output heads (probability p and sub-pixel offsets, Sec. 3.2),
+ * and the post-processing of those maps into a list of localizations on the device
+ * (Sec. 2.2: post-processing kept in GPU memory; Sec. 4.2.1: post-processing cost).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: SML_OK (0) or a negative SML_ERR_* code.  sml_last_error() gives a
+ *    one-line message for the most recent failure of a context (or of sml_create when
+ *    called with NULL).
+ *  - Frames are uint16 ADU, layout [T][H][W] (row-major, W fastest).  1 <= H, W <= 16384.
+ *  - The camera transform is e = (adu - offset) / gain (photo-electrons), and the network
+ *    input is e * in_scale (in_scale from the net spec).
+ *  - Pixel (i, j) covers [j-1/2, j+1/2) x [i-1/2, i+1/2): its centre is the integer index.
+ *    x and y are reported in pixels, z in nm (z_scale * zhat), photons in e- (ph_scale * Nhat).
+ *  - A pixel is a detection iff p > p_min, p > p of every in-frame 8-neighbour that comes
+ *    earlier in raster order and p >= p of every in-frame 8-neighbour that comes later.
+ *    Records are ordered by (frame, row, column); results are deterministic and do not
+ *    depend on batch composition or chunking.
+ *  - A context is bound to the CUDA device that was current at sml_create.  It is not
+ *    thread safe: use one context per host thread.
+ *  - No entry point falls back to the CPU.  Without a usable sm_103 device, sml_create
+ *    fails with SML_ERR_CUDA.
+ */
+#ifndef SML_H
+#define SML_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SML_OK 0
+#define SML_ERR_BAD_ARG -1     /* a NULL pointer, a size out of range, a bad threshold */
+#define SML_ERR_BAD_SPEC -2    /* the JSON net spec is malformed or unsupported */
+#define SML_ERR_BAD_WEIGHTS -3 /* the weight blob is malformed or does not match the spec */
+#define SML_ERR_OOM -4         /* a device or pinned-host allocation failed */
+#define SML_ERR_CUDA -5        /* a CUDA runtime or driver call failed */
+#define SML_ERR_CAPACITY -6    /* more detections than the output capacity (see below) */
+#define SML_ERR_UNSUPPORTED -7 /* valid request the build does not support */
+
+typedef struct sml_ctx sml_ctx;
+
+/* One localization, 24 bytes.  frame is the index within the T frames of the call. */
+typedef struct {
+  int32_t frame;
+  float x, y;    /* pixels */
+  float z;       /* nm */
+  float photons; /* photo-electrons */
+  float p;       /* detection probability at the peak pixel */
+} sml_record;
+
+/* Camera model.  If gain_map / offset_map are non-NULL they hold per-pixel values [H][W]
+ * (float32) and override the scalars.  Their memory space must match the call: host or
+ * device for sml_localize, device for the *_async entry points. */
+typedef struct {
+  float gain;   /* ADU per photo-electron, > 0 */
+  float offset; /* ADU */
+  const float* gain_map;
+  const float* offset_map;
+} sml_camera;
+
+typedef struct {
+  float p_min; /* detection threshold on p, in [0, 1) */
+} sml_thresholds;
+
+/*
+ * sml_create -- parse a net spec and a weight blob and upload the network.
+ *
+ * net_spec: NUL-terminated JSON object, e.g.
+ *   {"in_ch":1,"channels":48,"dilations":[1,2,4,8,16,8,4,1],"precision":"bf16",
+ *    "in_scale":0.001,"z_scale":1000,"ph_scale":10000}
+ *   in_ch must be 1; channels in {16,32,48,64}; 2..16 layers with dilations 1..64;
+ *   precision "fp32" (SIMT FP32 FMA), "bf16" (tensor cores, FP32 accumulation) or
+ *   "fp8" (e4m3 activations and weights, FP32 accumulation; needs "act_scales": one
+ *   positive float per conv layer, the scale of that layer's input activations).
+ *   Optional "chunk_px": pixels per device chunk (default 2^20).
+ * weights: an SMLW blob (host memory, read during the call only):
+ *   header "<8s7I16i": magic "SMLW0001", version 1, L, C, in_ch, n_heads (5), has_bn,
+ *   reserved, dilations[16]; then per layer l: W[C][Cin_l][3][3] f32, b[C] f32 and, if
+ *   has_bn, gamma[C], beta[C], mean[C], var[C] f32 and eps f32; then the heads
+ *   Wh[5][C] f32 and bh[5] f32 (head order: p logit, dx, dy, zhat, Nhat).
+ *   BatchNorm is folded into the conv weights here.
+ * out: receives the context (owned by the caller, freed with sml_destroy).
+ * Errors: SML_ERR_BAD_SPEC, SML_ERR_BAD_WEIGHTS, SML_ERR_OOM, SML_ERR_CUDA.
+ */
+int sml_create(const char* net_spec, const void* weights, size_t weights_bytes, sml_ctx** out);
+
+/* Release every device and host resource of the context.  NULL is ignored. */
+void sml_destroy(sml_ctx* ctx);
+
+/* Message for the last failure of ctx (or of sml_create if ctx is NULL).  Owned by the
+ * library, valid until the next call on the same context. */
+const char* sml_last_error(const sml_ctx* ctx);
+
+/*
+ * sml_localize -- frames in, localizations out; synchronous.
+ *
+ * frames: [T][H][W] uint16, host (pageable or pinned) or device memory (detected).
+ * cam, thr: host structs; the camera maps may be host or device pointers.
+ * out: host or device array of capacity records (detected).  n_out: host.
+ * Work is split into chunks of whole frames; records keep (frame, row, column) order.
+ * On SML_OK, *n_out records were written.  If the detections exceed capacity, the call
+ * returns SML_ERR_CAPACITY, sets *n_out to the number needed and leaves out unspecified.
+ * T = 0 is valid and yields *n_out = 0.
+ */
+int sml_localize(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, const sml_camera* cam,
+                 const sml_thresholds* thr, sml_record* out, size_t capacity, size_t* n_out);
+
+/*
+ * sml_localize_async -- device-resident variant, stream ordered, no host synchronisation.
+ *
+ * d_frames: device [T][H][W] uint16.  cam maps (if any) are device pointers.
+ * d_out: device array of capacity records.  d_n_out: device uint64, overwritten with the
+ * number of detections (records beyond capacity are not written; compare on the host).
+ * stream: a cudaStream_t (NULL = the legacy default stream).  Every buffer must stay valid
+ * until the stream reaches the end of this call's work.  One call at a time per context:
+ * calls on different streams that overlap on the GPU would share the context's workspace.
+ */
+int sml_localize_async(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam,
+                       const sml_thresholds* thr, sml_record* d_out, size_t capacity,
+                       unsigned long long* d_n_out, void* stream);
+
+/*
+ * sml_forward_maps -- the network alone (no decode), device-resident, stream ordered.
+ *
+ * d_maps: device float32 [T][5][H][W]: channel 0 = p = sigmoid(logit), channels 1..4 =
+ * dx, dy, zhat, Nhat (raw head outputs).  d_logits: device float32 [T][H][W] or NULL.
+ * These are exactly the maps that sml_localize decodes.
+ */
+int sml_forward_maps(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam,
+                     float* d_maps, float* d_logits, void* stream);
+
+/*
+ * sml_decode_maps -- decode caller-supplied maps [T][5][H][W] (device float32, layout of
+ * sml_forward_maps) into records, stream ordered; the decode half of sml_localize.
+ * z_scale and ph_scale come from the context's net spec.  d_out / d_n_out as in
+ * sml_localize_async.
+ */
+int sml_decode_maps(sml_ctx* ctx, const float* d_maps, int T, int H, int W, const sml_thresholds* thr,
+                    sml_record* d_out, size_t capacity, unsigned long long* d_n_out, void* stream);
+
+/* Number of kernels the last localize / forward / decode call launched (for profiling). */
+int sml_last_launch_count(const sml_ctx* ctx);
+
+/*
+ * Kernel timing.  sml_profile_enable(ctx, 1) clears the counters and makes every later call
+ * bracket each kernel launch with a pair of CUDA events recorded on the launching stream;
+ * sml_profile_enable(ctx, 0) stops recording.  sml_profile_read synchronises the recorded
+ * events and returns, for one kernel class, the summed device time in milliseconds and the
+ * number of timed launches since the last enable.  Classes: SML_KERNEL_LAYER1 (camera
+ * transform + first conv), SML_KERNEL_CONV (middle dilated conv layers), SML_KERNEL_CONV_HEADS
+ * (last conv layer with the fused heads), SML_KERNEL_DECODE (count + scan + write, timed as
+ * one interval).  Timing adds one event pair per launch; leave it off outside profiling.
+ */
+#define SML_KERNEL_LAYER1 0
+#define SML_KERNEL_CONV 1
+#define SML_KERNEL_CONV_HEADS 2
+#define SML_KERNEL_DECODE 3
+int sml_profile_enable(sml_ctx* ctx, int on);
+int sml_profile_read(sml_ctx* ctx, int kernel_class, double* total_ms, int* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SML_H */

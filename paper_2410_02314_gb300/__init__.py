@@ -1,0 +1,271 @@
+"""GB300 single-molecule localization: Python binding of the C ABI in include/sml.h.
+
+The functions below carry the C names and only marshal arguments (ctypes); every step of
+the path runs in the CUDA library ``_lib/libsml.so``.  There is no CPU fallback: if the
+library is missing or the device is not an sm_103 GPU, calls raise.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA memory); device
+entry points (``*_async``, ``sml_forward_maps``, ``sml_decode_maps``) need CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsml.so")
+
+SML_OK = 0
+SML_ERR_BAD_ARG = -1
+SML_ERR_BAD_SPEC = -2
+SML_ERR_BAD_WEIGHTS = -3
+SML_ERR_OOM = -4
+SML_ERR_CUDA = -5
+SML_ERR_CAPACITY = -6
+SML_ERR_UNSUPPORTED = -7
+
+RECORD_DTYPE = np.dtype(
+    [("frame", "<i4"), ("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("photons", "<f4"), ("p", "<f4")]
+)
+
+# every symbol the headers in include/ declare
+EXPORTS = (
+    "sml_create",
+    "sml_destroy",
+    "sml_last_error",
+    "sml_localize",
+    "sml_localize_async",
+    "sml_forward_maps",
+    "sml_decode_maps",
+    "sml_last_launch_count",
+    "sml_profile_enable",
+    "sml_profile_read",
+    "sml_debug_umma",
+)
+SML_KERNEL_LAYER1, SML_KERNEL_CONV, SML_KERNEL_CONV_HEADS, SML_KERNEL_DECODE = 0, 1, 2, 3
+
+
+class SmlError(RuntimeError):
+    def __init__(self, code, msg, needed=None):
+        super().__init__(f"sml error {code}: {msg}")
+        self.code = code
+        self.needed = needed
+
+
+class _Camera(ctypes.Structure):
+    _fields_ = [("gain", ctypes.c_float), ("offset", ctypes.c_float), ("gain_map", ctypes.c_void_p),
+                ("offset_map", ctypes.c_void_p)]
+
+
+class _Thresholds(ctypes.Structure):
+    _fields_ = [("p_min", ctypes.c_float)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsml.so (built in-tree by ``__graft_entry__.build()`` / ``_build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, F, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+        L.sml_create.argtypes = [ctypes.c_char_p, P, S, ctypes.POINTER(P)]
+        L.sml_create.restype = I
+        L.sml_destroy.argtypes = [P]
+        L.sml_destroy.restype = None
+        L.sml_last_error.argtypes = [P]
+        L.sml_last_error.restype = ctypes.c_char_p
+        L.sml_localize.argtypes = [P, P, I, I, I, ctypes.POINTER(_Camera), ctypes.POINTER(_Thresholds), P, S,
+                                   ctypes.POINTER(S)]
+        L.sml_localize.restype = I
+        L.sml_localize_async.argtypes = [P, P, I, I, I, ctypes.POINTER(_Camera), ctypes.POINTER(_Thresholds), P, S,
+                                         P, P]
+        L.sml_localize_async.restype = I
+        L.sml_forward_maps.argtypes = [P, P, I, I, I, ctypes.POINTER(_Camera), P, P, P]
+        L.sml_forward_maps.restype = I
+        L.sml_decode_maps.argtypes = [P, P, I, I, I, ctypes.POINTER(_Thresholds), P, S, P, P]
+        L.sml_decode_maps.restype = I
+        L.sml_last_launch_count.argtypes = [P]
+        L.sml_last_launch_count.restype = I
+        L.sml_profile_enable.argtypes = [P, I]
+        L.sml_profile_enable.restype = I
+        L.sml_profile_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]
+        L.sml_profile_read.restype = I
+        L.sml_debug_umma.argtypes = [P, P, P, I, I, I, P]
+        L.sml_debug_umma.restype = I
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _camera(gain=1.0, offset=100.0, gain_map=None, offset_map=None):
+    return _Camera(float(gain), float(offset), _ptr(gain_map), _ptr(offset_map))
+
+
+def _check(ctx, code):
+    if code != SML_OK:
+        raise SmlError(code, sml_last_error(ctx))
+
+
+# ----------------------------------------------------------------------------- C names
+
+
+def sml_create(net_spec: str, weights: bytes):
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(weights, len(weights))
+    code = lib().sml_create(net_spec.encode(), buf, len(weights), ctypes.byref(h))
+    if code != SML_OK:
+        raise SmlError(code, sml_last_error(None))
+    return h
+
+
+def sml_destroy(ctx):
+    lib().sml_destroy(ctx)
+
+
+def sml_last_error(ctx) -> str:
+    m = lib().sml_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def sml_last_launch_count(ctx) -> int:
+    return lib().sml_last_launch_count(ctx)
+
+
+def sml_localize(ctx, frames, p_min, gain=1.0, offset=100.0, gain_map=None, offset_map=None, capacity=None,
+                 out=None):
+    """Synchronous localization.  frames: uint16 [T,H,W] (numpy, or torch host/CUDA tensor).
+    Returns a numpy record array (RECORD_DTYPE); when ``out`` is a torch byte tensor (host,
+    pinned or CUDA) the records are written there and its first n*24 bytes are returned."""
+    T, H, W = (int(s) for s in frames.shape)
+    if isinstance(frames, np.ndarray):
+        frames = np.ascontiguousarray(frames, dtype=np.uint16)
+    if out is None:
+        cap = int(capacity if capacity is not None else max(16, T * H * W // 9 + 16))
+        out_arr = np.empty(cap, dtype=RECORD_DTYPE)
+    elif hasattr(out, "data_ptr"):  # torch byte tensor (host, pinned or CUDA)
+        out_arr = out
+        cap = int(out.numel() * out.element_size() // RECORD_DTYPE.itemsize)
+    else:
+        out_arr = out
+        cap = len(out)
+    n = ctypes.c_size_t(0)
+    cam = _camera(gain, offset, gain_map, offset_map)
+    thr = _Thresholds(float(p_min))
+    code = lib().sml_localize(ctx, _ptr(frames), T, H, W, ctypes.byref(cam), ctypes.byref(thr), _ptr(out_arr), cap,
+                              ctypes.byref(n))
+    if code == SML_ERR_CAPACITY:
+        raise SmlError(code, sml_last_error(ctx), needed=int(n.value))
+    _check(ctx, code)
+    if hasattr(out_arr, "data_ptr"):
+        return out_arr[: n.value * RECORD_DTYPE.itemsize]
+    return out_arr[: n.value]
+
+
+def sml_localize_async(ctx, d_frames, p_min, d_out, d_n, gain=1.0, offset=100.0, gain_map=None, offset_map=None,
+                       stream=None):
+    """Device-resident localization on a stream.  d_out: CUDA uint8 tensor holding records;
+    d_n: CUDA int64 tensor (1 element) receiving the detection count."""
+    T, H, W = (int(s) for s in d_frames.shape)
+    cap = int(d_out.numel() * d_out.element_size() // RECORD_DTYPE.itemsize)
+    cam = _camera(gain, offset, gain_map, offset_map)
+    thr = _Thresholds(float(p_min))
+    _check(ctx, lib().sml_localize_async(ctx, _ptr(d_frames), T, H, W, ctypes.byref(cam), ctypes.byref(thr),
+                                         _ptr(d_out), cap, _ptr(d_n), _stream(stream)))
+
+
+def sml_forward_maps(ctx, d_frames, d_maps, d_logits=None, gain=1.0, offset=100.0, gain_map=None, offset_map=None,
+                     stream=None):
+    T, H, W = (int(s) for s in d_frames.shape)
+    cam = _camera(gain, offset, gain_map, offset_map)
+    _check(ctx, lib().sml_forward_maps(ctx, _ptr(d_frames), T, H, W, ctypes.byref(cam), _ptr(d_maps),
+                                       _ptr(d_logits), _stream(stream)))
+
+
+def sml_decode_maps(ctx, d_maps, p_min, d_out, d_n, stream=None):
+    T, _, H, W = (int(s) for s in d_maps.shape)
+    cap = int(d_out.numel() * d_out.element_size() // RECORD_DTYPE.itemsize)
+    thr = _Thresholds(float(p_min))
+    _check(ctx, lib().sml_decode_maps(ctx, _ptr(d_maps), T, H, W, ctypes.byref(thr), _ptr(d_out), cap, _ptr(d_n),
+                                      _stream(stream)))
+
+
+def sml_profile_enable(ctx, on: bool):
+    _check(ctx, lib().sml_profile_enable(ctx, int(bool(on))))
+
+
+def sml_profile_read(ctx, kernel_class: int):
+    """(summed device milliseconds, number of timed launches) for one kernel class."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int(0)
+    _check(ctx, lib().sml_profile_read(ctx, int(kernel_class), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def sml_debug_umma(d_a, d_b, d_d, n, k, fp8=False, stream=None):
+    code = lib().sml_debug_umma(_ptr(d_a), _ptr(d_b), _ptr(d_d), int(n), int(k), int(bool(fp8)), _stream(stream))
+    if code != SML_OK:
+        raise SmlError(code, "umma self-test failed")
+
+
+# ----------------------------------------------------------------------------- helpers
+
+
+def records_from_bytes(t, n):
+    """View the first n records of a CUDA/CPU uint8 tensor as a numpy record array."""
+    raw = t[: n * RECORD_DTYPE.itemsize].cpu().numpy()
+    return raw.view(RECORD_DTYPE).copy()
+
+
+class Localizer:
+    """Owns one context: ``Localizer(spec_json, blob).localize(frames, p_min)``."""
+
+    def __init__(self, net_spec: str, weights: bytes):
+        self.ctx = sml_create(net_spec, weights)
+
+    def close(self):
+        if self.ctx is not None:
+            sml_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def localize(self, frames, p_min, **kw):
+        return sml_localize(self.ctx, frames, p_min, **kw)
+
+    def forward_maps(self, d_frames, d_maps, d_logits=None, **kw):
+        sml_forward_maps(self.ctx, d_frames, d_maps, d_logits, **kw)
+
+    def decode_maps(self, d_maps, p_min, d_out, d_n, **kw):
+        sml_decode_maps(self.ctx, d_maps, p_min, d_out, d_n, **kw)
+
+    def localize_async(self, d_frames, p_min, d_out, d_n, **kw):
+        sml_localize_async(self.ctx, d_frames, p_min, d_out, d_n, **kw)
+
+    @property
+    def last_launch_count(self):
+        return sml_last_launch_count(self.ctx)

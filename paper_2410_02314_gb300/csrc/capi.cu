@@ -1,0 +1,813 @@
+// C ABI and host runtime: net-spec parsing, weight upload (BatchNorm folding, layout packing,
+// FP8 scaling), per-frame-size plans (workspace, TMA descriptors), chunked execution and
+// the host <-> device boundary.  The entry points are documented in include/sml.h.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cctype>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "sml_internal.h"
+
+using namespace sml;
+
+namespace {
+
+// ------------------------------------------------------------------ tiny JSON reader
+struct JVal {
+  enum Kind { kNull, kNum, kStr, kArr, kObj, kBool } kind = kNull;
+  double num = 0;
+  std::string str;
+  std::vector<JVal> arr;
+  std::map<std::string, JVal> obj;
+};
+
+struct JParser {
+  const char* p;
+  bool ok = true;
+  void ws() {
+    while (*p && isspace((unsigned char)*p)) ++p;
+  }
+  bool lit(const char* s) {
+    size_t n = strlen(s);
+    if (strncmp(p, s, n) == 0) {
+      p += n;
+      return true;
+    }
+    return false;
+  }
+  JVal value() {
+    JVal v;
+    ws();
+    if (*p == '{') {
+      ++p;
+      v.kind = JVal::kObj;
+      ws();
+      if (*p == '}') {
+        ++p;
+        return v;
+      }
+      while (ok) {
+        ws();
+        JVal k = value();
+        if (!ok || k.kind != JVal::kStr) {
+          ok = false;
+          break;
+        }
+        ws();
+        if (*p != ':') {
+          ok = false;
+          break;
+        }
+        ++p;
+        v.obj[k.str] = value();
+        ws();
+        if (*p == ',') {
+          ++p;
+          continue;
+        }
+        if (*p == '}') {
+          ++p;
+          break;
+        }
+        ok = false;
+      }
+    } else if (*p == '[') {
+      ++p;
+      v.kind = JVal::kArr;
+      ws();
+      if (*p == ']') {
+        ++p;
+        return v;
+      }
+      while (ok) {
+        v.arr.push_back(value());
+        ws();
+        if (*p == ',') {
+          ++p;
+          continue;
+        }
+        if (*p == ']') {
+          ++p;
+          break;
+        }
+        ok = false;
+      }
+    } else if (*p == '"') {
+      ++p;
+      v.kind = JVal::kStr;
+      while (*p && *p != '"') {
+        if (*p == '\\' && p[1]) ++p;
+        v.str.push_back(*p++);
+      }
+      if (*p != '"') ok = false;
+      else ++p;
+    } else if (lit("true")) {
+      v.kind = JVal::kBool;
+      v.num = 1;
+    } else if (lit("false")) {
+      v.kind = JVal::kBool;
+    } else if (lit("null")) {
+      v.kind = JVal::kNull;
+    } else {
+      char* end = nullptr;
+      v.num = strtod(p, &end);
+      if (end == p) ok = false;
+      else {
+        v.kind = JVal::kNum;
+        p = end;
+      }
+    }
+    return v;
+  }
+};
+
+// ------------------------------------------------------------------ tensor map encoder
+typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                      const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                      CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled_t get_encoder() {
+  static PFN_encodeTiled_t fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_encodeTiled_t>(p);
+  }
+  return fn;
+}
+
+std::string g_create_error;
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct Plan {
+  int H = 0, W = 0, Tc = 0;
+  void* act[2] = {nullptr, nullptr};
+  float* maps = nullptr;
+  unsigned* block_counts = nullptr;
+  unsigned long long* block_offsets = nullptr;
+  uint16_t* frames = nullptr;  // staging for host frames
+  float* cam_maps = nullptr;   // staging for host camera maps [2][H][W]
+  CUtensorMap tmap[2][kMaxLayers];
+};
+
+struct sml_ctx {
+  int device = 0, num_sms = 0;
+  // spec
+  int in_ch = 1, C = 0, L = 0, dil[kMaxLayers] = {0};
+  int prec = kFP32;
+  float in_scale = 1e-3f, z_scale = 1000.f, ph_scale = 10000.f;
+  float act_scale[kMaxLayers] = {0};
+  long long chunk_px = 1 << 20;
+  // device weights
+  float* w1 = nullptr;  // [C][9]
+  float* b1 = nullptr;
+  float* wf32[kMaxLayers] = {nullptr};  // [9][C][C]
+  float* bias[kMaxLayers] = {nullptr};
+  void* bimg[kMaxLayers] = {nullptr};
+  float* deq[kMaxLayers] = {nullptr};
+  float* head_w = nullptr;
+  float* head_b = nullptr;
+  // runtime
+  Plan plan;
+  cudaStream_t stream = nullptr;
+  unsigned long long* d_total = nullptr;
+  int* d_err = nullptr;
+  sml_record* d_rec = nullptr;
+  size_t d_rec_cap = 0;
+  std::vector<void*> owned;
+  std::string err;
+  int launches = 0;
+  // kernel timing (sml_profile_enable)
+  bool prof_on = false;
+  struct ProfEv {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfEv> prof_events;
+  size_t prof_used = 0;
+};
+
+namespace {
+
+int fail(sml_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+int cuda_fail(sml_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, e == cudaErrorMemoryAllocation ? SML_ERR_OOM : SML_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define SML_CUDA(call, where)                  \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+template <typename T>
+int dev_alloc(sml_ctx* ctx, T** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+  *p = static_cast<T*>(q);
+  return SML_OK;
+}
+
+template <typename T>
+int upload(sml_ctx* ctx, T** dst, const void* src, size_t bytes) {
+  int r = dev_alloc(ctx, dst, bytes);
+  if (r) return r;
+  ctx->owned.push_back(*dst);
+  SML_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), "upload");
+  return SML_OK;
+}
+
+void free_plan(Plan& p) {
+  cudaFree(p.act[0]);
+  cudaFree(p.act[1]);
+  cudaFree(p.maps);
+  cudaFree(p.block_counts);
+  cudaFree(p.block_offsets);
+  cudaFree(p.frames);
+  cudaFree(p.cam_maps);
+  p = Plan();
+}
+
+size_t act_elem_bytes(int prec) { return prec == kFP32 ? 4 : (prec == kBF16 ? 2 : 1); }
+
+int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W, int d) {
+  PFN_encodeTiled_t enc = get_encoder();
+  if (!enc) return fail(ctx, SML_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const int epg = ctx->prec == kBF16 ? 8 : 16;
+  const int G = tc_groups(ctx->C, ctx->prec);
+  cuuint64_t dims[5] = {(cuuint64_t)epg, (cuuint64_t)W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)Tc};
+  cuuint64_t strides[4] = {16ull, 16ull * W, 16ull * W * G, 16ull * W * G * H};
+  cuuint32_t box[5] = {(cuuint32_t)epg, (cuuint32_t)tc_box_width(d), (cuuint32_t)G, 1u, 1u};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = enc(m, ctx->prec == kBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 5, base,
+                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, SML_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return SML_OK;
+}
+
+// Brackets the launches issued in its scope with an event pair when profiling is on.
+struct ProfScope {
+  sml_ctx* ctx;
+  sml_ctx::ProfEv* ev = nullptr;
+  cudaStream_t s;
+  ProfScope(sml_ctx* c, int cls, cudaStream_t st) : ctx(c), s(st) {
+    if (!ctx->prof_on) return;
+    if (ctx->prof_used == ctx->prof_events.size()) {
+      sml_ctx::ProfEv e{cls, nullptr, nullptr};
+      if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return;
+      ctx->prof_events.push_back(e);
+    }
+    ev = &ctx->prof_events[ctx->prof_used++];
+    ev->cls = cls;
+    cudaEventRecord(ev->a, s);
+  }
+  ~ProfScope() {
+    if (ev) cudaEventRecord(ev->b, s);
+  }
+};
+
+int get_plan(sml_ctx* ctx, int H, int W) {
+  Plan& p = ctx->plan;
+  if (p.H == H && p.W == W) return SML_OK;
+  free_plan(p);
+  long long hw = (long long)H * W;
+  int Tc = (int)std::max(1LL, ctx->chunk_px / hw);
+  size_t npx = (size_t)Tc * hw;
+  size_t ab = npx * ctx->C * act_elem_bytes(ctx->prec);
+  int r;
+  if ((r = dev_alloc(ctx, &p.act[0], ab)) || (r = dev_alloc(ctx, &p.act[1], ab)) ||
+      (r = dev_alloc(ctx, &p.maps, npx * kHeads * sizeof(float))) ||
+      (r = dev_alloc(ctx, &p.block_counts, decode_blocks(npx) * sizeof(unsigned))) ||
+      (r = dev_alloc(ctx, &p.block_offsets, decode_blocks(npx) * sizeof(unsigned long long))) ||
+      (r = dev_alloc(ctx, &p.frames, npx * sizeof(uint16_t))) ||
+      (r = dev_alloc(ctx, &p.cam_maps, 2 * hw * sizeof(float)))) {
+    free_plan(p);
+    return r;
+  }
+  if (ctx->prec != kFP32) {
+    for (int b = 0; b < 2; ++b)
+      for (int l = 1; l < ctx->L; ++l)
+        if ((r = encode_act_map(ctx, &p.tmap[b][l], p.act[b], Tc, H, W, ctx->dil[l]))) {
+          free_plan(p);
+          return r;
+        }
+  }
+  p.H = H;
+  p.W = W;
+  p.Tc = Tc;
+  return SML_OK;
+}
+
+// One chunk of frames through the network: maps [tc][5][H][W] (+ optional logits).
+int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, int H, int W, const CamArgs& cam, float* maps,
+                  float* logits, cudaStream_t s) {
+  Plan& p = ctx->plan;
+  const int L = ctx->L, C = ctx->C;
+  float l1_scale = ctx->prec == kFP8 ? 1.0f / ctx->act_scale[1] : 1.0f;
+  {
+    ProfScope ps(ctx, SML_KERNEL_LAYER1, s);
+    SML_CUDA(launch_ingest_l1(d_frames, tc, H, W, ctx->dil[0], cam, ctx->w1, ctx->b1, C, ctx->prec, l1_scale, p.act[0], s),
+             "layer 1");
+  }
+  ++ctx->launches;
+  for (int l = 1; l < L; ++l) {
+    const bool last = (l == L - 1);
+    void* in = p.act[(l - 1) & 1];
+    void* out = p.act[l & 1];
+    ProfScope ps(ctx, last ? SML_KERNEL_CONV_HEADS : SML_KERNEL_CONV, s);
+    if (ctx->prec == kFP32) {
+      if (last)
+        SML_CUDA(launch_dconv_f32_heads(static_cast<float*>(in), ctx->wf32[l], ctx->bias[l], ctx->head_w, ctx->head_b, tc,
+                                        H, W, C, ctx->dil[l], maps, logits, s),
+                 "fp32 conv+heads");
+      else
+        SML_CUDA(launch_dconv_f32(static_cast<float*>(in), static_cast<float*>(out), ctx->wf32[l], ctx->bias[l], tc, H, W,
+                                  C, ctx->dil[l], s),
+                 "fp32 conv");
+    } else {
+      TcLayerArgs a{};
+      a.tmap = &p.tmap[(l - 1) & 1][l];
+      a.bimg = ctx->bimg[l];
+      a.bias = ctx->bias[l];
+      a.deq = ctx->deq[l];
+      a.out_inv_scale = (ctx->prec == kFP8 && !last) ? 1.0f / ctx->act_scale[l + 1] : 1.0f;
+      a.out = out;
+      a.head_w = ctx->head_w;
+      a.head_b = ctx->head_b;
+      a.maps = maps;
+      a.logits = logits;
+      a.T = tc;
+      a.H = H;
+      a.W = W;
+      a.C = C;
+      a.d = ctx->dil[l];
+      a.prec = ctx->prec;
+      a.err = ctx->d_err;
+      SML_CUDA(launch_dconv_tc(a, last, ctx->num_sms, s), "tensor-core conv");
+    }
+    ++ctx->launches;
+  }
+  return SML_OK;
+}
+
+int check_device_error(sml_ctx* ctx) {
+  int h = 0;
+  SML_CUDA(cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+  if (h) {
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    return fail(ctx, SML_ERR_CUDA, "a device-side wait timed out (kernel gave up and returned)");
+  }
+  return SML_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int check_dims(sml_ctx* ctx, int T, int H, int W) {
+  if (T < 0 || H < 1 || W < 1 || H > 16384 || W > 16384) return fail(ctx, SML_ERR_BAD_ARG, "bad frame dims T=%d H=%d W=%d", T, H, W);
+  return SML_OK;
+}
+
+int check_thr(sml_ctx* ctx, const sml_thresholds* thr) {
+  if (!thr || !(thr->p_min >= 0.0f && thr->p_min < 1.0f)) return fail(ctx, SML_ERR_BAD_ARG, "p_min must be in [0,1)");
+  return SML_OK;
+}
+
+int make_cam(sml_ctx* ctx, const sml_camera* cam, CamArgs* out) {
+  if (!cam) return fail(ctx, SML_ERR_BAD_ARG, "camera is NULL");
+  if (!cam->gain_map && !(cam->gain > 0.0f)) return fail(ctx, SML_ERR_BAD_ARG, "gain must be > 0");
+  out->gain = cam->gain;
+  out->offset = cam->offset;
+  out->in_scale = ctx->in_scale;
+  out->gain_map = cam->gain_map;
+  out->offset_map = cam->offset_map;
+  return SML_OK;
+}
+
+// Whole call on device-resident frames: chunks of whole frames, one running record count.
+int localize_device(sml_ctx* ctx, const uint16_t* d_frames, bool frames_on_host, int T, int H, int W, const CamArgs& cam,
+                    float p_min, sml_record* d_out, size_t capacity, unsigned long long* d_n, cudaStream_t s) {
+  int r = get_plan(ctx, H, W);
+  if (r) return r;
+  Plan& p = ctx->plan;
+  SML_CUDA(cudaMemsetAsync(d_n, 0, sizeof(unsigned long long), s), "memset count");
+  const size_t fpx = (size_t)H * W;
+  for (int t0 = 0; t0 < T; t0 += p.Tc) {
+    int tc = std::min(p.Tc, T - t0);
+    const uint16_t* f = d_frames + (size_t)t0 * fpx;
+    if (frames_on_host) {
+      SML_CUDA(cudaMemcpyAsync(p.frames, f, (size_t)tc * fpx * sizeof(uint16_t), cudaMemcpyHostToDevice, s), "H2D frames");
+      f = p.frames;
+    }
+    if ((r = forward_chunk(ctx, f, tc, H, W, cam, p.maps, nullptr, s))) return r;
+    DecodeArgs da{};
+    da.maps = p.maps;
+    da.T = tc;
+    da.H = H;
+    da.W = W;
+    da.frame0 = t0;
+    da.p_min = p_min;
+    da.z_scale = ctx->z_scale;
+    da.ph_scale = ctx->ph_scale;
+    da.out = d_out;
+    da.capacity = capacity;
+    da.total = d_n;
+    da.block_counts = p.block_counts;
+    da.block_offsets = p.block_offsets;
+    ProfScope ps(ctx, SML_KERNEL_DECODE, s);
+    SML_CUDA(launch_decode(da, s, &ctx->launches), "decode");
+  }
+  return SML_OK;
+}
+
+int parse_spec(sml_ctx* ctx, const char* spec) {
+  JParser jp{spec};
+  JVal root = jp.value();
+  if (!jp.ok || root.kind != JVal::kObj) return fail(nullptr, SML_ERR_BAD_SPEC, "net spec is not a JSON object");
+  auto num = [&](const char* k, double def) {
+    auto it = root.obj.find(k);
+    return (it != root.obj.end() && it->second.kind == JVal::kNum) ? it->second.num : def;
+  };
+  ctx->in_ch = (int)num("in_ch", 1);
+  ctx->C = (int)num("channels", 0);
+  ctx->in_scale = (float)num("in_scale", 1e-3);
+  ctx->z_scale = (float)num("z_scale", 1000.0);
+  ctx->ph_scale = (float)num("ph_scale", 10000.0);
+  ctx->chunk_px = (long long)num("chunk_px", (double)(1 << 20));
+  if (ctx->in_ch != 1) return fail(nullptr, SML_ERR_BAD_SPEC, "in_ch must be 1");
+  if (ctx->C != 16 && ctx->C != 32 && ctx->C != 48 && ctx->C != 64)
+    return fail(nullptr, SML_ERR_BAD_SPEC, "channels must be 16, 32, 48 or 64");
+  if (ctx->chunk_px < 1) return fail(nullptr, SML_ERR_BAD_SPEC, "chunk_px must be >= 1");
+  auto it = root.obj.find("dilations");
+  if (it == root.obj.end() || it->second.kind != JVal::kArr) return fail(nullptr, SML_ERR_BAD_SPEC, "dilations missing");
+  ctx->L = (int)it->second.arr.size();
+  if (ctx->L < 2 || ctx->L > kMaxLayers) return fail(nullptr, SML_ERR_BAD_SPEC, "need 2..16 layers");
+  for (int l = 0; l < ctx->L; ++l) {
+    const JVal& v = it->second.arr[l];
+    if (v.kind != JVal::kNum || v.num < 1 || v.num > 64 || v.num != floor(v.num))
+      return fail(nullptr, SML_ERR_BAD_SPEC, "dilation %d must be an integer in 1..64", l);
+    ctx->dil[l] = (int)v.num;
+  }
+  auto pr = root.obj.find("precision");
+  std::string prec = (pr != root.obj.end() && pr->second.kind == JVal::kStr) ? pr->second.str : "fp32";
+  if (prec == "fp32") ctx->prec = kFP32;
+  else if (prec == "bf16") ctx->prec = kBF16;
+  else if (prec == "fp8") ctx->prec = kFP8;
+  else return fail(nullptr, SML_ERR_BAD_SPEC, "precision must be fp32, bf16 or fp8");
+  if (ctx->prec == kFP8) {
+    auto as = root.obj.find("act_scales");
+    if (as == root.obj.end() || as->second.kind != JVal::kArr || (int)as->second.arr.size() != ctx->L)
+      return fail(nullptr, SML_ERR_BAD_SPEC, "fp8 needs act_scales with one entry per layer");
+    for (int l = 0; l < ctx->L; ++l) {
+      const JVal& v = as->second.arr[l];
+      if (v.kind != JVal::kNum || !(v.num > 0)) return fail(nullptr, SML_ERR_BAD_SPEC, "act_scales must be > 0");
+      ctx->act_scale[l] = (float)v.num;
+    }
+  }
+  auto hd = root.obj.find("heads");
+  if (hd != root.obj.end() && (hd->second.kind != JVal::kArr || hd->second.arr.size() != kHeads))
+    return fail(nullptr, SML_ERR_BAD_SPEC, "heads must list 5 outputs");
+  return SML_OK;
+}
+
+int load_weights(sml_ctx* ctx, const void* blob, size_t bytes) {
+  const uint8_t* b = static_cast<const uint8_t*>(blob);
+  const size_t hdr_bytes = 8 + 7 * 4 + 16 * 4;
+  if (!blob || bytes < hdr_bytes || memcmp(b, "SMLW0001", 8) != 0)
+    return fail(nullptr, SML_ERR_BAD_WEIGHTS, "weight blob: bad magic or too short");
+  uint32_t h[7];
+  int32_t dil[16];
+  memcpy(h, b + 8, sizeof(h));
+  memcpy(dil, b + 8 + sizeof(h), sizeof(dil));
+  const int L = (int)h[1], C = (int)h[2], in_ch = (int)h[3], nh = (int)h[4], has_bn = (int)h[5];
+  if (h[0] != 1 || L != ctx->L || C != ctx->C || in_ch != ctx->in_ch || nh != kHeads)
+    return fail(nullptr, SML_ERR_BAD_WEIGHTS, "weight blob header does not match the net spec");
+  for (int l = 0; l < L; ++l)
+    if (dil[l] != ctx->dil[l]) return fail(nullptr, SML_ERR_BAD_WEIGHTS, "weight blob dilations do not match the net spec");
+  size_t need = hdr_bytes;
+  for (int l = 0; l < L; ++l) need += 4 * ((size_t)C * (l ? C : in_ch) * 9 + C + (has_bn ? 4 * C + 1 : 0));
+  need += 4 * ((size_t)kHeads * C + kHeads);
+  if (bytes != need) return fail(nullptr, SML_ERR_BAD_WEIGHTS, "weight blob has %zu bytes, expected %zu", bytes, need);
+  const float* f = reinterpret_cast<const float*>(b + hdr_bytes);  // blob offsets are 4-byte aligned
+  std::vector<float> tmp;
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    tmp.assign(n, 0.f);
+    memcpy(tmp.data(), reinterpret_cast<const uint8_t*>(f) + off * 4, n * 4);
+    off += n;
+    return tmp;
+  };
+  int r;
+  for (int l = 0; l < L; ++l) {
+    const int cin = l ? C : in_ch;
+    std::vector<float> w = take((size_t)C * cin * 9);
+    std::vector<float> bias = take(C);
+    if (has_bn) {
+      std::vector<float> bn = take(4 * (size_t)C);
+      float eps = take(1)[0];
+      for (int co = 0; co < C; ++co) {  // fold: W' = W g/sqrt(v+e); b' = (b-m) g/sqrt(v+e) + beta
+        double sc = (double)bn[co] / sqrt((double)bn[3 * C + co] + (double)eps);
+        for (int k = 0; k < cin * 9; ++k) w[(size_t)co * cin * 9 + k] = (float)(w[(size_t)co * cin * 9 + k] * sc);
+        bias[co] = (float)(((double)bias[co] - bn[2 * C + co]) * sc + bn[C + co]);
+      }
+    }
+    if (!std::all_of(w.begin(), w.end(), [](float x) { return std::isfinite(x); }) ||
+        !std::all_of(bias.begin(), bias.end(), [](float x) { return std::isfinite(x); }))
+      return fail(nullptr, SML_ERR_BAD_WEIGHTS, "layer %d has non-finite weights", l);
+    if (l == 0) {
+      if ((r = upload(ctx, &ctx->w1, w.data(), w.size() * 4)) || (r = upload(ctx, &ctx->b1, bias.data(), C * 4))) return r;
+      continue;
+    }
+    // [co][ci][ky][kx] -> [tap][ci][co]
+    std::vector<float> t((size_t)9 * C * C);
+    for (int co = 0; co < C; ++co)
+      for (int ci = 0; ci < C; ++ci)
+        for (int tap = 0; tap < 9; ++tap) t[((size_t)tap * C + ci) * C + co] = w[((size_t)co * C + ci) * 9 + tap];
+    if (ctx->prec == kFP32) {
+      if ((r = upload(ctx, &ctx->wf32[l], t.data(), t.size() * 4)) || (r = upload(ctx, &ctx->bias[l], bias.data(), C * 4)))
+        return r;
+    } else {
+      std::vector<float> wscale(C, 1.0f), deq(C, 1.0f);
+      if (ctx->prec == kFP8) {
+        for (int co = 0; co < C; ++co) {
+          float amax = 0.f;
+          for (int k = 0; k < 9 * C; ++k) amax = std::max(amax, fabsf(t[(size_t)k * C + co]));
+          wscale[co] = amax > 0.f ? amax / 448.0f : 1.0f;
+          deq[co] = ctx->act_scale[l] * wscale[co];
+        }
+      }
+      std::vector<uint8_t> img(tc_bimg_bytes(C, ctx->prec));
+      tc_pack_bimg(t.data(), C, ctx->prec, wscale.data(), img.data());
+      if ((r = upload(ctx, &ctx->bimg[l], img.data(), img.size())) || (r = upload(ctx, &ctx->bias[l], bias.data(), C * 4)))
+        return r;
+      if (ctx->prec == kFP8 && (r = upload(ctx, &ctx->deq[l], deq.data(), C * 4))) return r;
+    }
+  }
+  std::vector<float> hw = take((size_t)kHeads * C);
+  if ((r = upload(ctx, &ctx->head_w, hw.data(), hw.size() * 4))) return r;
+  std::vector<float> hb = take(kHeads);
+  if ((r = upload(ctx, &ctx->head_b, hb.data(), hb.size() * 4))) return r;
+  return SML_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ entry points
+extern "C" {
+
+int sml_create(const char* net_spec, const void* weights, size_t weights_bytes, sml_ctx** out) {
+  g_create_error.clear();
+  if (!net_spec || !out) return fail(nullptr, SML_ERR_BAD_ARG, "net_spec and out must be non-NULL");
+  *out = nullptr;
+  std::unique_ptr<sml_ctx> ctx(new sml_ctx());
+  int r = parse_spec(ctx.get(), net_spec);
+  if (r) return r;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, SML_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess)
+    return fail(nullptr, SML_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(nullptr, SML_ERR_CUDA, "device %d is sm_%d%d; this build targets sm_103a", dev, prop.major, prop.minor);
+  ctx->device = dev;
+  ctx->num_sms = prop.multiProcessorCount;
+  r = load_weights(ctx.get(), weights, weights_bytes);
+  if (r) {
+    if (g_create_error.empty()) g_create_error = ctx->err;
+    for (void* p : ctx->owned) cudaFree(p);
+    return r;
+  }
+  sml_ctx* c = ctx.get();
+  if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_total, sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) {
+    for (void* p : c->owned) cudaFree(p);
+    return fail(nullptr, SML_ERR_CUDA, "context set-up: %s", cudaGetErrorString(e));
+  }
+  *out = ctx.release();
+  return SML_OK;
+}
+
+void sml_destroy(sml_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_plan(ctx->plan);
+  for (void* p : ctx->owned) cudaFree(p);
+  cudaFree(ctx->d_total);
+  cudaFree(ctx->d_err);
+  cudaFree(ctx->d_rec);
+  for (auto& e : ctx->prof_events) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* sml_last_error(const sml_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int sml_last_launch_count(const sml_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int sml_localize(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, const sml_camera* cam,
+                 const sml_thresholds* thr, sml_record* out, size_t capacity, size_t* n_out) {
+  if (!ctx) return SML_ERR_BAD_ARG;
+  ctx->launches = 0;
+  int r;
+  if (!n_out || (T > 0 && !frames) || (capacity > 0 && !out)) return fail(ctx, SML_ERR_BAD_ARG, "NULL argument");
+  if ((r = check_dims(ctx, T, H, W)) || (r = check_thr(ctx, thr))) return r;
+  CamArgs ca;
+  if ((r = make_cam(ctx, cam, &ca))) return r;
+  *n_out = 0;
+  if (T == 0) return SML_OK;
+  SML_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if ((r = get_plan(ctx, H, W))) return r;
+  cudaStream_t s = ctx->stream;
+  const size_t hw = (size_t)H * W;
+  // camera maps given in host memory are staged once per call
+  if (ca.gain_map && !is_device_ptr(ca.gain_map)) {
+    SML_CUDA(cudaMemcpyAsync(ctx->plan.cam_maps, ca.gain_map, hw * 4, cudaMemcpyHostToDevice, s), "H2D gain map");
+    ca.gain_map = ctx->plan.cam_maps;
+  }
+  if (ca.offset_map && !is_device_ptr(ca.offset_map)) {
+    SML_CUDA(cudaMemcpyAsync(ctx->plan.cam_maps + hw, ca.offset_map, hw * 4, cudaMemcpyHostToDevice, s), "H2D offset map");
+    ca.offset_map = ctx->plan.cam_maps + hw;
+  }
+  const bool out_dev = capacity > 0 && is_device_ptr(out);
+  sml_record* d_out = out;
+  if (!out_dev) {
+    if (ctx->d_rec_cap < capacity || !ctx->d_rec) {
+      cudaFree(ctx->d_rec);
+      ctx->d_rec = nullptr;
+      ctx->d_rec_cap = 0;
+      if ((r = dev_alloc(ctx, &ctx->d_rec, std::max<size_t>(capacity, 1) * sizeof(sml_record)))) return r;
+      ctx->d_rec_cap = std::max<size_t>(capacity, 1);
+    }
+    d_out = ctx->d_rec;
+  }
+  const bool host_frames = !is_device_ptr(frames);
+  if ((r = localize_device(ctx, frames, host_frames, T, H, W, ca, thr->p_min, d_out, capacity, ctx->d_total, s))) return r;
+  unsigned long long total = 0;
+  SML_CUDA(cudaMemcpyAsync(&total, ctx->d_total, sizeof(total), cudaMemcpyDeviceToHost, s), "D2H count");
+  SML_CUDA(cudaStreamSynchronize(s), "localize");
+  if ((r = check_device_error(ctx))) return r;
+  *n_out = (size_t)total;
+  if (total > capacity) return fail(ctx, SML_ERR_CAPACITY, "%llu detections exceed capacity %zu", total, capacity);
+  if (!out_dev && total > 0) {
+    SML_CUDA(cudaMemcpyAsync(out, d_out, (size_t)total * sizeof(sml_record), cudaMemcpyDeviceToHost, s), "D2H records");
+    SML_CUDA(cudaStreamSynchronize(s), "D2H records");
+  }
+  return SML_OK;
+}
+
+int sml_localize_async(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam,
+                       const sml_thresholds* thr, sml_record* d_out, size_t capacity, unsigned long long* d_n_out,
+                       void* stream) {
+  if (!ctx) return SML_ERR_BAD_ARG;
+  ctx->launches = 0;
+  int r;
+  if (!d_n_out || (T > 0 && !d_frames) || (capacity > 0 && !d_out)) return fail(ctx, SML_ERR_BAD_ARG, "NULL argument");
+  if ((r = check_dims(ctx, T, H, W)) || (r = check_thr(ctx, thr))) return r;
+  CamArgs ca;
+  if ((r = make_cam(ctx, cam, &ca))) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (T == 0) {
+    SML_CUDA(cudaMemsetAsync(d_n_out, 0, sizeof(unsigned long long), s), "memset count");
+    return SML_OK;
+  }
+  return localize_device(ctx, d_frames, false, T, H, W, ca, thr->p_min, d_out, capacity, d_n_out, s);
+}
+
+int sml_forward_maps(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam, float* d_maps,
+                     float* d_logits, void* stream) {
+  if (!ctx) return SML_ERR_BAD_ARG;
+  ctx->launches = 0;
+  int r;
+  if ((T > 0 && (!d_frames || !d_maps))) return fail(ctx, SML_ERR_BAD_ARG, "NULL argument");
+  if ((r = check_dims(ctx, T, H, W))) return r;
+  CamArgs ca;
+  if ((r = make_cam(ctx, cam, &ca))) return r;
+  if (T == 0) return SML_OK;
+  if ((r = get_plan(ctx, H, W))) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t fpx = (size_t)H * W;
+  for (int t0 = 0; t0 < T; t0 += ctx->plan.Tc) {
+    int tc = std::min(ctx->plan.Tc, T - t0);
+    if ((r = forward_chunk(ctx, d_frames + (size_t)t0 * fpx, tc, H, W, ca, d_maps + (size_t)t0 * kHeads * fpx,
+                           d_logits ? d_logits + (size_t)t0 * fpx : nullptr, s)))
+      return r;
+  }
+  return SML_OK;
+}
+
+int sml_decode_maps(sml_ctx* ctx, const float* d_maps, int T, int H, int W, const sml_thresholds* thr, sml_record* d_out,
+                    size_t capacity, unsigned long long* d_n_out, void* stream) {
+  if (!ctx) return SML_ERR_BAD_ARG;
+  ctx->launches = 0;
+  int r;
+  if (!d_n_out || (T > 0 && !d_maps) || (capacity > 0 && !d_out)) return fail(ctx, SML_ERR_BAD_ARG, "NULL argument");
+  if ((r = check_dims(ctx, T, H, W)) || (r = check_thr(ctx, thr))) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SML_CUDA(cudaMemsetAsync(d_n_out, 0, sizeof(unsigned long long), s), "memset count");
+  if (T == 0) return SML_OK;
+  if ((r = get_plan(ctx, H, W))) return r;
+  Plan& p = ctx->plan;
+  const size_t fpx = (size_t)H * W;
+  for (int t0 = 0; t0 < T; t0 += p.Tc) {
+    int tc = std::min(p.Tc, T - t0);
+    DecodeArgs da{};
+    da.maps = d_maps + (size_t)t0 * kHeads * fpx;
+    da.T = tc;
+    da.H = H;
+    da.W = W;
+    da.frame0 = t0;
+    da.p_min = thr->p_min;
+    da.z_scale = ctx->z_scale;
+    da.ph_scale = ctx->ph_scale;
+    da.out = d_out;
+    da.capacity = capacity;
+    da.total = d_n_out;
+    da.block_counts = p.block_counts;
+    da.block_offsets = p.block_offsets;
+    ProfScope ps(ctx, SML_KERNEL_DECODE, s);
+    SML_CUDA(launch_decode(da, s, &ctx->launches), "decode");
+  }
+  return SML_OK;
+}
+
+int sml_profile_enable(sml_ctx* ctx, int on) {
+  if (!ctx) return SML_ERR_BAD_ARG;
+  if (on) {
+    for (size_t k = 0; k < ctx->prof_used; ++k) cudaEventSynchronize(ctx->prof_events[k].b);
+    ctx->prof_used = 0;
+  }
+  ctx->prof_on = on != 0;
+  return SML_OK;
+}
+
+int sml_profile_read(sml_ctx* ctx, int kernel_class, double* total_ms, int* launches) {
+  if (!ctx || !total_ms || !launches) return SML_ERR_BAD_ARG;
+  double sum = 0.0;
+  int n = 0;
+  for (size_t k = 0; k < ctx->prof_used; ++k) {
+    sml_ctx::ProfEv& e = ctx->prof_events[k];
+    if (e.cls != kernel_class) continue;
+    float ms = 0.f;
+    SML_CUDA(cudaEventSynchronize(e.b), "profile sync");
+    SML_CUDA(cudaEventElapsedTime(&ms, e.a, e.b), "profile elapsed");
+    sum += ms;
+    ++n;
+  }
+  *total_ms = sum;
+  *launches = n;
+  return SML_OK;
+}
+
+// Debug entry (include/sml_debug.h): one UMMA tile through the conv kernel's descriptor helpers.
+int sml_debug_umma(const void* d_a, const void* d_b, float* d_d, int n, int k, int fp8, void* stream) {
+  static int* d_err = nullptr;
+  if (!d_err && cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) return SML_ERR_OOM;
+  cudaMemset(d_err, 0, sizeof(int));
+  if (n % 16 || n < 16 || n > 256 || k % 32 || k < 32) return SML_ERR_BAD_ARG;
+  cudaError_t e = launch_umma_selftest(d_a, d_b, d_d, n, k, fp8 ? kFP8 : kBF16, d_err, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return SML_ERR_CUDA;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return SML_ERR_CUDA;
+  int h = 0;
+  cudaMemcpy(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  return h ? SML_ERR_CUDA : SML_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+// SIMT kernels: first layer (camera transform fused with the Cin=1 dilated 3x3 conv) and
+// the FP32 dilated 3x3 conv layers (plain FP32 FMA; the FP32 precision mode).
+//
+// Layer semantics (dilated convolution, Sec. 3.2.1), per frame and output channel co:
+//   a_out[i,j,co] = ReLU(b[co] + sum_{ci,ky,kx} w[co,ci,ky,kx] a_in[i+(ky-1)d, j+(kx-1)d, ci])
+// with a_in = 0 outside the frame, at every layer.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "sml_internal.h"
+
+namespace sml {
+
+namespace {
+
+constexpr int kSimtThreads = 128;
+
+__device__ __forceinline__ float cam_input(const uint16_t* __restrict__ f, int H, int W, int i, int j,
+                                           const CamArgs& cam) {
+  if (i < 0 || i >= H || j < 0 || j >= W) return 0.0f;
+  size_t px = (size_t)i * W + j;
+  float g = cam.gain_map ? cam.gain_map[px] : cam.gain;
+  float o = cam.offset_map ? cam.offset_map[px] : cam.offset;
+  return __fmul_rn(__fdiv_rn(__fsub_rn((float)f[px], o), g), cam.in_scale);
+}
+
+// OUT: 0 = float NHWC, 1 = bf16 row-planar (8 ch / 16 B), 2 = e4m3 row-planar (16 ch / 16 B)
+template <int C, int OUT>
+__global__ void __launch_bounds__(kSimtThreads) k_ingest_l1(const uint16_t* __restrict__ frames, int T, int H, int W,
+                                                            int d, CamArgs cam, const float* __restrict__ w1,
+                                                            const float* __restrict__ b1, float out_scale,
+                                                            void* __restrict__ out) {
+  __shared__ float sw[C * 9];
+  __shared__ float sb[C];
+  for (int k = threadIdx.x; k < C * 9; k += blockDim.x) sw[k] = w1[k];
+  for (int k = threadIdx.x; k < C; k += blockDim.x) sb[k] = b1[k];
+  __syncthreads();
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long npx = (long long)T * H * W;
+  if (q >= npx) return;
+  int j = (int)(q % W);
+  int i = (int)((q / W) % H);
+  int t = (int)(q / ((long long)H * W));
+  const uint16_t* f = frames + (size_t)t * H * W;
+  float x[9];
+#pragma unroll
+  for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = cam_input(f, H, W, i + (ky - 1) * d, j + (kx - 1) * d, cam);
+  float a[C];
+#pragma unroll
+  for (int co = 0; co < C; ++co) {
+    float s = sb[co];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s = fmaf(sw[co * 9 + k], x[k], s);
+    a[co] = fmaxf(s, 0.0f);
+  }
+  if (OUT == 0) {
+    float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + (size_t)q * C);
+#pragma unroll
+    for (int c4 = 0; c4 < C / 4; ++c4) dst[c4] = make_float4(a[4 * c4], a[4 * c4 + 1], a[4 * c4 + 2], a[4 * c4 + 3]);
+  } else if (OUT == 1) {
+    constexpr int G = C / 8;
+    uint8_t* base = static_cast<uint8_t*>(out);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      uint4 v;
+      uint32_t* vw = reinterpret_cast<uint32_t*>(&v);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(a[8 * g + 2 * e], a[8 * g + 2 * e + 1]);
+        vw[e] = *reinterpret_cast<uint32_t*>(&h2);
+      }
+      size_t off = ((((size_t)t * H + i) * G + g) * W + j) * 16;
+      *reinterpret_cast<uint4*>(base + off) = v;
+    }
+  } else {
+    constexpr int G = C / 16;
+    uint8_t* base = static_cast<uint8_t*>(out);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      uint4 v;
+      uint16_t* vh = reinterpret_cast<uint16_t*>(&v);
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        vh[e] = __nv_cvt_float2_to_fp8x2(make_float2(a[16 * g + 2 * e] * out_scale, a[16 * g + 2 * e + 1] * out_scale),
+                                         __NV_SATFINITE, __NV_E4M3);
+      size_t off = ((((size_t)t * H + i) * G + g) * W + j) * 16;
+      *reinterpret_cast<uint4*>(base + off) = v;
+    }
+  }
+}
+
+// FP32 dilated conv: one thread per pixel, all C output channels in registers.
+// Weights in shared memory as [tap][ci][co]; each float4 read is a warp-wide broadcast.
+template <int C, bool HEADS>
+__global__ void __launch_bounds__(kSimtThreads) k_dconv_f32(const float* __restrict__ in, float* __restrict__ out,
+                                                            const float* __restrict__ w, const float* __restrict__ b,
+                                                            const float* __restrict__ hw, const float* __restrict__ hb,
+                                                            int T, int H, int W, int d, float* __restrict__ maps,
+                                                            float* __restrict__ logits) {
+  extern __shared__ float4 smem4[];
+  float* sw = reinterpret_cast<float*>(smem4);
+  for (int k = threadIdx.x; k < 9 * C * C / 4; k += blockDim.x) smem4[k] = reinterpret_cast<const float4*>(w)[k];
+  __syncthreads();
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long npx = (long long)T * H * W;
+  if (q >= npx) return;
+  int j = (int)(q % W);
+  int i = (int)((q / W) % H);
+  int t = (int)(q / ((long long)H * W));
+  float acc[C];
+#pragma unroll
+  for (int co = 0; co < C; ++co) acc[co] = b[co];
+  for (int ky = 0; ky < 3; ++ky) {
+    int ii = i + (ky - 1) * d;
+    if (ii < 0 || ii >= H) continue;
+    for (int kx = 0; kx < 3; ++kx) {
+      int jj = j + (kx - 1) * d;
+      if (jj < 0 || jj >= W) continue;
+      const float4* src = reinterpret_cast<const float4*>(in + (((size_t)t * H + ii) * W + jj) * C);
+      const float* wt = sw + (ky * 3 + kx) * C * C;
+#pragma unroll 2
+      for (int c4 = 0; c4 < C / 4; ++c4) {
+        float4 v = __ldg(src + c4);
+        float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float4* wr = reinterpret_cast<const float4*>(wt + (4 * c4 + e) * C);
+#pragma unroll
+          for (int o4 = 0; o4 < C / 4; ++o4) {
+            float4 ww = wr[o4];
+            acc[4 * o4 + 0] = fmaf(vv[e], ww.x, acc[4 * o4 + 0]);
+            acc[4 * o4 + 1] = fmaf(vv[e], ww.y, acc[4 * o4 + 1]);
+            acc[4 * o4 + 2] = fmaf(vv[e], ww.z, acc[4 * o4 + 2]);
+            acc[4 * o4 + 3] = fmaf(vv[e], ww.w, acc[4 * o4 + 3]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int co = 0; co < C; ++co) acc[co] = fmaxf(acc[co], 0.0f);
+  if (!HEADS) {
+    float4* dst = reinterpret_cast<float4*>(out + (size_t)q * C);
+#pragma unroll
+    for (int c4 = 0; c4 < C / 4; ++c4)
+      dst[c4] = make_float4(acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]);
+  } else {
+    // 1x1 heads (Sec. 3.2): h_k = hb[k] + sum_c hw[k,c] a[c]; p = sigmoid(h_0)
+    size_t plane = (size_t)H * W;
+    size_t px = (size_t)i * W + j;
+#pragma unroll
+    for (int k = 0; k < kHeads; ++k) {
+      float h = hb[k];
+#pragma unroll
+      for (int c = 0; c < C; ++c) h = fmaf(hw[k * C + c], acc[c], h);
+      if (k == 0) {
+        if (logits) logits[(size_t)t * plane + px] = h;
+        h = 1.0f / (1.0f + expf(-h));
+      }
+      maps[((size_t)t * kHeads + k) * plane + px] = h;
+    }
+  }
+}
+
+inline unsigned grid_for(long long npx) { return (unsigned)((npx + kSimtThreads - 1) / kSimtThreads); }
+
+}  // namespace
+
+cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1,
+                             const float* b1, int C, int prec, float out_scale, void* out, cudaStream_t s) {
+  long long npx = (long long)T * H * W;
+  if (npx == 0) return cudaSuccess;
+  dim3 grid(grid_for(npx)), block(kSimtThreads);
+#define SML_L1(CC)                                                                                       \
+  case CC:                                                                                               \
+    if (prec == kFP32)                                                                                   \
+      k_ingest_l1<CC, 0><<<grid, block, 0, s>>>(frames, T, H, W, d, cam, w1, b1, out_scale, out);        \
+    else if (prec == kBF16)                                                                              \
+      k_ingest_l1<CC, 1><<<grid, block, 0, s>>>(frames, T, H, W, d, cam, w1, b1, out_scale, out);        \
+    else                                                                                                 \
+      k_ingest_l1<CC, 2><<<grid, block, 0, s>>>(frames, T, H, W, d, cam, w1, b1, out_scale, out);        \
+    break;
+  switch (C) {
+    SML_L1(16)
+    SML_L1(32)
+    SML_L1(48)
+    SML_L1(64)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SML_L1
+  return cudaGetLastError();
+}
+
+template <int C, bool HEADS>
+static cudaError_t launch_f32_impl(const float* in, float* out, const float* w, const float* b, const float* hw,
+                                   const float* hb, int T, int H, int W, int d, float* maps, float* logits,
+                                   cudaStream_t s) {
+  size_t smem = sizeof(float) * 9 * C * C;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_dconv_f32<C, HEADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  long long npx = (long long)T * H * W;
+  if (npx == 0) return cudaSuccess;
+  k_dconv_f32<C, HEADS><<<grid_for(npx), kSimtThreads, smem, s>>>(in, out, w, b, hw, hb, T, H, W, d, maps, logits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dconv_f32(const float* in, float* out, const float* w, const float* b, int T, int H, int W,
+                             int C, int d, cudaStream_t s) {
+  switch (C) {
+    case 16: return launch_f32_impl<16, false>(in, out, w, b, nullptr, nullptr, T, H, W, d, nullptr, nullptr, s);
+    case 32: return launch_f32_impl<32, false>(in, out, w, b, nullptr, nullptr, T, H, W, d, nullptr, nullptr, s);
+    case 48: return launch_f32_impl<48, false>(in, out, w, b, nullptr, nullptr, T, H, W, d, nullptr, nullptr, s);
+    case 64: return launch_f32_impl<64, false>(in, out, w, b, nullptr, nullptr, T, H, W, d, nullptr, nullptr, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_dconv_f32_heads(const float* in, const float* w, const float* b, const float* hw,
+                                   const float* hb, int T, int H, int W, int C, int d, float* maps, float* logits,
+                                   cudaStream_t s) {
+  switch (C) {
+    case 16: return launch_f32_impl<16, true>(in, nullptr, w, b, hw, hb, T, H, W, d, maps, logits, s);
+    case 32: return launch_f32_impl<32, true>(in, nullptr, w, b, hw, hb, T, H, W, d, maps, logits, s);
+    case 48: return launch_f32_impl<48, true>(in, nullptr, w, b, hw, hb, T, H, W, d, maps, logits, s);
+    case 64: return launch_f32_impl<64, true>(in, nullptr, w, b, hw, hb, T, H, W, d, maps, logits, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace sml

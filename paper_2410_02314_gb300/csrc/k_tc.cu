@@ -1,0 +1,616 @@
+// Tensor-core dilated 3x3 conv for sm_103a: implicit GEMM on tcgen05 with TMEM accumulators,
+// activations staged by TMA (dilated convolution, Sec. 3.2.1; heads of Sec. 3.2 fused into
+// the last layer's epilogue).
+//
+// GEMM view of one output row segment: D[m, co] = sum_{ky,kx,ci} A[m + kx*d, ci | row ky] W[ky,kx,ci,co]
+// with M = 128 pixels of one image row, N = C output channels, K = 9 taps x C input channels.
+//
+// Activation layout in HBM ("row-planar"): [T][H][G][W][16 bytes], G = C / (channels per
+// 16 bytes) -- 8 channels for BF16, 16 for FP8 e4m3.  One TMA box (elements of a group x
+// (128 + 2d) pixels x G groups) of one image row lands in shared memory as G planes of
+// [pixel][16 bytes]: exactly the no-swizzle K-major canonical layout of a UMMA operand with
+// 16-byte core-matrix rows, so the operand of tap kx is the same buffer started kx*d rows
+// later (SBO = 128 B between 8-pixel groups, LBO = plane stride between 8/16-channel
+// groups).  The TMA zero fill of out-of-frame pixels and rows is the "same" zero padding.
+//
+// Work decomposition ("row classes"): the three input rows of output row i are i-d, i, i+d,
+// so rows with the same residue mod d form independent chains.  A work unit is
+// (frame, 128-pixel column strip, residue phi, segment of S consecutive rows of the chain).
+// Its S+2 input rows stream through a ring of TMA stages, each loaded once, and each input
+// row feeds up to three output rows (ky = 2, 1, 0) whose accumulators live in a ring of 4
+// TMEM slots.  Accumulation order inside a row is fixed (ky, kx, k-step ascending), so the
+// result does not depend on scheduling, grid size or batch composition.
+//
+// Warp roles (192 threads): warps 0-3 epilogue (TMEM lane quarter = warp index), warp 4 TMA
+// producer, warp 5 TMEM allocator and MMA issuer.  Every mbarrier wait is bounded: on
+// timeout the kernel sets *err, stops issuing, drains its own MMAs and TMA loads (bounded),
+// frees TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "sml_internal.h"
+
+namespace sml {
+
+namespace {
+
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = 192;
+constexpr int kAccSlots = 4;
+constexpr int kSlotCols = 64;
+constexpr int kTmemCols = 256;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr int kSegRows = 8;                                 // S: output rows per work unit
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the phase with the given parity.  Fails fast once any role of the CTA
+// has given up (abort flag in shared memory).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  unsigned long long t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 0) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > kWaitLimitNs) {
+        *abort_flag = 1;
+        atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: no swizzle, K-major.
+//   bits 0-13 start >> 4, 16-29 LBO >> 4 (K-direction core-matrix stride),
+//   32-45 SBO >> 4 (M/N-direction 8-row-group stride), 46-48 = 0b001, 61-63 swizzle = 0.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: D = F32, A/B K-major, dense.  kind::f16 with BF16 inputs
+// (a/b format 1) or kind::f8f6f4 with E4M3 inputs (format 0).
+__host__ __device__ constexpr uint32_t instr_desc(int prec, int M, int N) {
+  return (1u << 4) | ((prec == kBF16 ? 1u : 0u) << 7) | ((prec == kBF16 ? 1u : 0u) << 10) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int PREC>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (PREC == kBF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+// 32 lanes x 32 bits, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+struct TcKArgs {
+  const uint8_t* bimg;
+  const float* bias;
+  const float* deq;
+  float out_inv_scale;
+  uint8_t* out;
+  const float* head_w;
+  const float* head_b;
+  float* maps;
+  float* logits;
+  int T, H, W, d;
+  int NS, NQ;          // column strips, segments per residue class
+  long long units;     // T * NS * d * NQ
+  uint32_t stage_bytes, plane_stride, tx_bytes;
+  int nstages;
+  int* err;
+};
+
+template <int C, int PREC>
+struct TcCfg {
+  static constexpr int EPG = PREC == kBF16 ? 8 : 16;     // elements per 16-byte group
+  static constexpr int G = C / EPG;                       // groups stored in HBM
+  static constexpr int KSTEP = PREC == kBF16 ? 16 : 32;   // K per MMA instruction
+  static constexpr int NKS = (C + KSTEP - 1) / KSTEP;     // MMAs per tap
+  static constexpr int GP = 2 * NKS;                      // planes in shared memory (FP8: zero pad)
+  static constexpr int BBLK = (C / 8) * 256;              // bytes of one (tap, k-step) B block
+  static constexpr int BIMG = 9 * NKS * BBLK;
+  static constexpr uint32_t IDESC = instr_desc(PREC, kTileM, C);
+};
+
+// Unit -> (t, strip, phi, q); returns the number of valid output rows.
+__device__ __forceinline__ int unit_rows(const TcKArgs& a, long long u, int& t, int& j0, int& phi, int& q) {
+  q = (int)(u % a.NQ);
+  long long r = u / a.NQ;
+  phi = (int)(r % a.d);
+  r /= a.d;
+  int s = (int)(r % a.NS);
+  t = (int)(r / a.NS);
+  j0 = s * kTileM;
+  int n_class = phi < a.H ? (a.H - phi + a.d - 1) / a.d : 0;
+  int n = n_class - q * kSegRows;
+  return n < 0 ? 0 : (n > kSegRows ? kSegRows : n);
+}
+
+template <int C, int PREC, bool LAST>
+__global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant__ CUtensorMap tmap, const TcKArgs a) {
+  using Cfg = TcCfg<C, PREC>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // carve shared memory (1024-aligned base)
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* s_bimg = smem;
+  uint8_t* s_stage = smem + ((Cfg::BIMG + 1023) & ~1023);
+  float* s_bias = reinterpret_cast<float*>(s_stage + (size_t)a.nstages * a.stage_bytes);
+  float* s_deq = s_bias + C;
+  float* s_hw = s_deq + C;
+  float* s_hb = s_hw + kHeads * C;
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uintptr_t>(s_hb + 8 + 1) & ~uintptr_t(7));
+  // barriers: full[nst], empty[nst], acc_full[4], acc_empty[4], drain
+  uint64_t* full_bar = s_bar;
+  uint64_t* empty_bar = s_bar + a.nstages;
+  uint64_t* accf_bar = empty_bar + a.nstages;
+  uint64_t* acce_bar = accf_bar + kAccSlots;
+  uint64_t* drain_bar = acce_bar + kAccSlots;
+  volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(drain_bar + 1);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  // ---- set-up: weights -> shared, zero pad planes, barriers, TMEM
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.bimg);
+    uint4* dst = reinterpret_cast<uint4*>(s_bimg);
+    for (int k = threadIdx.x; k < Cfg::BIMG / 16; k += kThreads) dst[k] = src[k];
+    for (int k = threadIdx.x; k < C; k += kThreads) {
+      s_bias[k] = a.bias[k];
+      s_deq[k] = a.deq ? a.deq[k] : 1.0f;
+    }
+    if (LAST)
+      for (int k = threadIdx.x; k < kHeads * C + kHeads; k += kThreads)
+        (k < kHeads * C ? s_hw[k] : s_hb[k - kHeads * C]) = (k < kHeads * C ? a.head_w[k] : a.head_b[k - kHeads * C]);
+    if (Cfg::GP > Cfg::G) {  // planes beyond the stored groups stay zero (K padding)
+      for (int s = 0; s < a.nstages; ++s) {
+        uint4* z = reinterpret_cast<uint4*>(s_stage + (size_t)s * a.stage_bytes + (size_t)Cfg::G * a.plane_stride);
+        int n16 = (Cfg::GP - Cfg::G) * a.plane_stride / 16;
+        for (int k = threadIdx.x; k < n16; k += kThreads) z[k] = make_uint4(0, 0, 0, 0);
+      }
+    }
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < a.nstages; ++s) {
+        mbar_init(smem_u32(&full_bar[s]), 1);
+        mbar_init(smem_u32(&empty_bar[s]), 1);
+      }
+      for (int s = 0; s < kAccSlots; ++s) {
+        mbar_init(smem_u32(&accf_bar[s]), 1);
+        mbar_init(smem_u32(&acce_bar[s]), kEpiWarps * 32);
+      }
+      mbar_init(smem_u32(&drain_bar[0]), 1);
+      *s_abort = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void*)s_tmem)),
+                   "r"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_proxy_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  }
+  const uint32_t tmem = *s_tmem;
+
+  if (warp == 4) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+      uint32_t stc = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+        int t, j0, phi, q;
+        int n_out = unit_rows(a, u, t, j0, phi, q);
+        for (int kk = 0; kk < n_out + 2 && n_out > 0; ++kk, ++stc) {
+          uint32_t st = stc % a.nstages, use = stc / a.nstages;
+          if (use > 0 && !mbar_wait(smem_u32(&empty_bar[st]), (use - 1) & 1, a.err, s_abort)) {
+            ok = false;
+            break;
+          }
+          uint32_t fb = smem_u32(&full_bar[st]);
+          mbar_expect_tx(fb, a.tx_bytes);
+          int row = phi + (q * kSegRows + kk - 1) * a.d;
+          tma_load_5d(smem_u32(s_stage + (size_t)st * a.stage_bytes), &tmap, 0, j0 - a.d, 0, row, t, fb);
+        }
+      }
+      // drain: make sure no load of ours is still landing in shared memory
+      uint32_t first = stc > (uint32_t)a.nstages ? stc - a.nstages : 0;
+      for (uint32_t k = first; k < stc; ++k)
+        mbar_wait(smem_u32(&full_bar[k % a.nstages]), (k / a.nstages) & 1, a.err, s_abort);
+    }
+  } else if (warp == 5) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t s_stage_u = smem_u32(s_stage);
+      const uint32_t s_bimg_u = smem_u32(s_bimg);
+      uint32_t stc = 0, rowc = 0;
+      bool ok = true, issued = false;
+      for (long long u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+        int t, j0, phi, q;
+        int n_out = unit_rows(a, u, t, j0, phi, q);
+        if (n_out == 0) continue;
+        for (int kk = 0; kk < n_out + 2 && ok; ++kk, ++stc) {
+          uint32_t st = stc % a.nstages;
+          if (!mbar_wait(smem_u32(&full_bar[st]), (stc / a.nstages) & 1, a.err, s_abort)) {
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          const uint32_t a_base = s_stage_u + st * a.stage_bytes;
+#pragma unroll 1
+          for (int ky = 2; ky >= 0; --ky) {
+            int k = kk - ky;  // output row fed by this input row through tap ky
+            if (k < 0 || k >= n_out) continue;
+            uint32_t g = rowc + k, slot = g % kAccSlots, use = g / kAccSlots;
+            if (ky == 0 && use > 0) {
+              if (!mbar_wait(smem_u32(&acce_bar[slot]), (use - 1) & 1, a.err, s_abort)) {
+                ok = false;
+                break;
+              }
+              fence_after_sync();
+            }
+            const uint32_t d_tmem = tmem + slot * kSlotCols;
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+              for (int ks = 0; ks < Cfg::NKS; ++ks) {
+                uint64_t ad = smem_desc(a_base + (uint32_t)(2 * ks) * a.plane_stride + (uint32_t)(kx * a.d) * 16u,
+                                        a.plane_stride, 128u);
+                uint64_t bd = smem_desc(s_bimg_u + (uint32_t)(((ky * 3 + kx) * Cfg::NKS + ks) * Cfg::BBLK), 128u, 256u);
+                umma<PREC>(d_tmem, ad, bd, Cfg::IDESC, (ky == 0 && kx == 0 && ks == 0) ? 0u : 1u);
+                issued = true;
+              }
+            if (ky == 2) umma_commit(smem_u32(&accf_bar[slot]));
+          }
+          if (ok) umma_commit(smem_u32(&empty_bar[st]));
+        }
+        rowc += n_out;
+      }
+      if (issued) {  // all MMAs of this CTA complete before TMEM is released
+        umma_commit(smem_u32(&drain_bar[0]));
+        mbar_wait(smem_u32(&drain_bar[0]), 0, a.err, s_abort);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 0-3)
+    const int m = warp * 32 + lane;  // TMEM lane = pixel within the strip
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t rowc = 0;
+    bool ok = true;
+    const size_t plane = (size_t)a.H * a.W;
+    for (long long u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+      int t, j0, phi, q;
+      int n_out = unit_rows(a, u, t, j0, phi, q);
+      for (int k = 0; k < n_out; ++k) {
+        uint32_t g = rowc + k, slot = g % kAccSlots, use = g / kAccSlots;
+        if (!mbar_wait(smem_u32(&accf_bar[slot]), use & 1, a.err, s_abort)) {
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+        float v[C];
+#pragma unroll
+        for (int c = 0; c < C; c += 16) tmem_ld16(lane_addr + slot * kSlotCols + c, v + c);
+        tmem_ld_wait();
+        fence_before_sync();
+        mbar_arrive(smem_u32(&acce_bar[slot]));
+        const int i = phi + (q * kSegRows + k) * a.d;
+        const int j = j0 + m;
+        if (j >= a.W) continue;
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[c] = fmaxf(fmaf(v[c], s_deq[c], s_bias[c]), 0.0f);
+        if (LAST) {
+          const size_t px = (size_t)i * a.W + j;
+#pragma unroll
+          for (int h = 0; h < kHeads; ++h) {
+            float acc = s_hb[h];
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc = fmaf(s_hw[h * C + c], v[c], acc);
+            if (h == 0) {
+              if (a.logits) a.logits[(size_t)t * plane + px] = acc;
+              acc = 1.0f / (1.0f + expf(-acc));
+            }
+            a.maps[((size_t)t * kHeads + h) * plane + px] = acc;
+          }
+        } else if (PREC == kBF16) {
+#pragma unroll
+          for (int gq = 0; gq < Cfg::G; ++gq) {
+            uint4 o;
+            uint32_t* ow = reinterpret_cast<uint32_t*>(&o);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * gq + 2 * e], v[8 * gq + 2 * e + 1]);
+              ow[e] = *reinterpret_cast<uint32_t*>(&h2);
+            }
+            *reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 16) = o;
+          }
+        } else {
+#pragma unroll
+          for (int gq = 0; gq < Cfg::G; ++gq) {
+            uint4 o;
+            uint16_t* oh = reinterpret_cast<uint16_t*>(&o);
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              oh[e] = __nv_cvt_float2_to_fp8x2(
+                  make_float2(v[16 * gq + 2 * e] * a.out_inv_scale, v[16 * gq + 2 * e + 1] * a.out_inv_scale),
+                  __NV_SATFINITE, __NV_E4M3);
+            *reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 16) = o;
+          }
+        }
+      }
+      rowc += n_out;
+    }
+  }
+
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 5) {
+    fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ UMMA self-test
+// One 128 x N x K product: A [128][K] and B [N][K] pre-packed by the host in the same
+// layouts the conv uses (A: planes of [128 rows][16 bytes]; B: the per-block image).
+template <int PREC>
+__global__ void __launch_bounds__(128, 1) k_umma_selftest(const uint8_t* A, const uint8_t* B, float* D, int N, int K,
+                                                          int* err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int ES = PREC == kBF16 ? 2 : 1;
+  constexpr int KSTEP = PREC == kBF16 ? 16 : 32;
+  const int a_bytes = 128 * K * ES, b_bytes = N * K * ES;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + a_bytes;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + b_bytes);
+  volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(bar + 1);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
+  for (int k = threadIdx.x; k < a_bytes / 16; k += 128) reinterpret_cast<uint4*>(sA)[k] = reinterpret_cast<const uint4*>(A)[k];
+  for (int k = threadIdx.x; k < b_bytes / 16; k += 128) reinterpret_cast<uint4*>(sB)[k] = reinterpret_cast<const uint4*>(B)[k];
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(bar), 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void*)s_tmem)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t plane = 128 * 16;  // A plane stride: 128 rows x 16 bytes
+  const uint32_t bblk = (N / 8) * 256;
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = instr_desc(PREC, 128, N);
+    for (int ks = 0; ks < K / KSTEP; ++ks) {
+      uint64_t ad = smem_desc(smem_u32(sA) + 2 * ks * plane, plane, 128);
+      uint64_t bd = smem_desc(smem_u32(sB) + ks * bblk, 128, 256);
+      umma<PREC>(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+    }
+    umma_commit(smem_u32(bar));
+  }
+  __syncwarp();
+  bool ok = mbar_wait(smem_u32(bar), 0, err, s_abort);
+  fence_after_sync();
+  const int warp = threadIdx.x >> 5;
+  if (ok) {
+    for (int c = 0; c < N; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+      tmem_ld_wait();
+      for (int k = 0; k < 16; ++k) D[(size_t)threadIdx.x * N + c + k] = v[k];
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+  }
+}
+
+template <int C, int PREC>
+size_t tc_smem_bytes(int nstages, uint32_t stage_bytes) {
+  using Cfg = TcCfg<C, PREC>;
+  size_t b = 1024;                            // alignment slack
+  b += (Cfg::BIMG + 1023) & ~1023;            // weights
+  b += (size_t)nstages * stage_bytes;         // stages
+  b += sizeof(float) * (2 * C + kHeads * C + 8) + 16;  // bias, deq, heads
+  b += 8 * (2 * nstages + 2 * kAccSlots + 1) + 16;     // barriers, tmem addr, abort flag
+  return b;
+}
+
+template <int C, int PREC, bool LAST>
+cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
+  using Cfg = TcCfg<C, PREC>;
+  TcKArgs a{};
+  a.bimg = static_cast<const uint8_t*>(la.bimg);
+  a.bias = la.bias;
+  a.deq = la.deq;
+  a.out_inv_scale = la.out_inv_scale;
+  a.out = static_cast<uint8_t*>(la.out);
+  a.head_w = la.head_w;
+  a.head_b = la.head_b;
+  a.maps = la.maps;
+  a.logits = la.logits;
+  a.T = la.T;
+  a.H = la.H;
+  a.W = la.W;
+  a.d = la.d;
+  a.NS = (la.W + kTileM - 1) / kTileM;
+  int rows0 = (la.H + la.d - 1) / la.d;
+  a.NQ = (rows0 + kSegRows - 1) / kSegRows;
+  a.units = (long long)la.T * a.NS * la.d * a.NQ;
+  const int boxw = tc_box_width(la.d);
+  a.plane_stride = (uint32_t)boxw * 16u;
+  a.tx_bytes = (uint32_t)Cfg::G * a.plane_stride;
+  a.stage_bytes = ((uint32_t)Cfg::GP * a.plane_stride + 1023u) & ~1023u;
+  a.err = la.err;
+  if (a.units == 0) return cudaSuccess;
+  const size_t budget = 227 * 1024;
+  int nst = 6;
+  while (nst > 2 && tc_smem_bytes<C, PREC>(nst, a.stage_bytes) > budget) --nst;
+  a.nstages = nst;
+  size_t smem = tc_smem_bytes<C, PREC>(nst, a.stage_bytes);
+  if (smem > budget) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_dconv_tc<C, PREC, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  long long grid = a.units < (long long)num_sms ? a.units : (long long)num_sms;
+  k_dconv_tc<C, PREC, LAST><<<(unsigned)grid, kThreads, smem, s>>>(*la.tmap, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_box_width(int d) { return kTileM + 2 * d; }
+
+int tc_groups(int C, int prec) { return C / (prec == kBF16 ? 8 : 16); }
+
+size_t tc_bimg_bytes(int C, int prec) {
+  const int kstep = prec == kBF16 ? 16 : 32;
+  const int nks = (C + kstep - 1) / kstep;
+  return (size_t)9 * nks * (C / 8) * 256;
+}
+
+// B image: for tap (ky*3+kx) and k-step ks, the [N = C][K = kstep] block in no-swizzle
+// K-major core-matrix order: byte (n/8)*256 + (k/EPG)*128 + (n%8)*16 + (k%EPG)*esize.
+// Input channels beyond C (FP8 padding) are zero.  FP8 weights are divided by w_scale[co].
+void tc_pack_bimg(const float* w /*[9][C][C] tap, ci, co*/, int C, int prec, const float* w_scale, void* dst) {
+  const int kstep = prec == kBF16 ? 16 : 32;
+  const int epg = prec == kBF16 ? 8 : 16;
+  const int es = prec == kBF16 ? 2 : 1;
+  const int nks = (C + kstep - 1) / kstep;
+  const size_t bblk = (size_t)(C / 8) * 256;
+  uint8_t* out = static_cast<uint8_t*>(dst);
+  for (int tap = 0; tap < 9; ++tap)
+    for (int ks = 0; ks < nks; ++ks) {
+      uint8_t* blk = out + ((size_t)tap * nks + ks) * bblk;
+      for (int n = 0; n < C; ++n)
+        for (int k = 0; k < kstep; ++k) {
+          int ci = ks * kstep + k;
+          float v = ci < C ? w[((size_t)tap * C + ci) * C + n] : 0.0f;
+          size_t off = (size_t)(n / 8) * 256 + (size_t)(k / epg) * 128 + (size_t)(n % 8) * 16 + (size_t)(k % epg) * es;
+          if (prec == kBF16) {
+            __nv_bfloat16 h = __float2bfloat16_rn(v);
+            memcpy(blk + off, &h, 2);
+          } else {
+            float sv = v / w_scale[n];
+            blk[off] = (uint8_t)__nv_cvt_float_to_fp8(sv, __NV_SATFINITE, __NV_E4M3);
+          }
+        }
+    }
+}
+
+cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaStream_t s) {
+#define SML_TC(CC)                                                                               \
+  case CC:                                                                                       \
+    if (a.prec == kBF16)                                                                         \
+      return last ? launch_tc_impl<CC, kBF16, true>(a, num_sms, s) : launch_tc_impl<CC, kBF16, false>(a, num_sms, s); \
+    else                                                                                         \
+      return last ? launch_tc_impl<CC, kFP8, true>(a, num_sms, s) : launch_tc_impl<CC, kFP8, false>(a, num_sms, s);
+  switch (a.C) {
+    SML_TC(16)
+    SML_TC(32)
+    SML_TC(48)
+    SML_TC(64)
+  }
+#undef SML_TC
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_umma_selftest(const void* A, const void* B, float* D, int N, int K, int prec, int* err,
+                                 cudaStream_t s) {
+  const int es = prec == kBF16 ? 2 : 1;
+  size_t smem = 1024 + (size_t)128 * K * es + (size_t)N * K * es + 64;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  if (prec == kBF16) {
+    cudaError_t e = cudaFuncSetAttribute(k_umma_selftest<kBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_umma_selftest<kBF16><<<1, 128, smem, s>>>(static_cast<const uint8_t*>(A), static_cast<const uint8_t*>(B), D, N, K, err);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_umma_selftest<kFP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_umma_selftest<kFP8><<<1, 128, smem, s>>>(static_cast<const uint8_t*>(A), static_cast<const uint8_t*>(B), D, N, K, err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sml

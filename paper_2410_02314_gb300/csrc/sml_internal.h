@@ -1,0 +1,85 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sml.h"
+
+namespace sml {
+
+constexpr int kHeads = 5;
+constexpr int kMaxLayers = 16;
+constexpr int kTileM = 128;  // pixels per MMA tile (one row segment)
+
+enum Precision { kFP32 = 0, kBF16 = 1, kFP8 = 2 };
+
+// Decode parameters shared by the fused path and sml_decode_maps.
+struct DecodeArgs {
+  const float* maps;  // [Tc][5][H][W]
+  int T, H, W;
+  int frame0;  // frame index of the chunk's first frame
+  float p_min, z_scale, ph_scale;
+  sml_record* out;
+  unsigned long long capacity;
+  unsigned long long* total;  // running count (device); updated by the scan kernel
+  unsigned int* block_counts;  // [nblocks]
+  unsigned long long* block_offsets;  // [nblocks]
+};
+
+constexpr int kDecodeThreads = 256;
+constexpr int kDecodePxPerBlock = 1024;
+
+inline long long decode_blocks(long long npx) { return (npx + kDecodePxPerBlock - 1) / kDecodePxPerBlock; }
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int* launches);
+
+// Camera parameters for the first layer (device pointers or NULL maps).
+struct CamArgs {
+  float gain, offset, in_scale;
+  const float* gain_map;
+  const float* offset_map;
+};
+
+// --- layer 1: camera transform + Cin=1 dilated 3x3 conv, bias, ReLU -------------------
+// prec kFP32 writes float NHWC [T][H][W][C]; kBF16 / kFP8 write row-planar activations
+// [T][H][C/g][W][16 bytes] (g = 8 bf16 or 16 e4m3 channels per group).  out_scale
+// multiplies the FP8 output before rounding (1 / activation scale).
+cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1,
+                             const float* b1, int C, int prec, float out_scale, void* out, cudaStream_t s);
+
+// --- SIMT FP32 path (NHWC float activations) ------------------------------------------
+cudaError_t launch_dconv_f32(const float* in, float* out, const float* w, const float* b, int T, int H, int W,
+                             int C, int d, cudaStream_t s);
+cudaError_t launch_dconv_f32_heads(const float* in, const float* w, const float* b, const float* hw,
+                                   const float* hb, int T, int H, int W, int C, int d, float* maps, float* logits,
+                                   cudaStream_t s);
+
+// --- tensor-core path (row-planar activations) -------------------------------------
+struct TcLayerArgs {
+  const CUtensorMap* tmap;  // input activations (host copy, passed by value to the kernel)
+  const void* bimg;         // device: packed B operand image for this layer
+  const float* bias;        // device [C] (FP8: already in the output scale domain)
+  const float* deq;         // device [C] per-output-channel dequant factor (FP8) or NULL
+  float out_inv_scale;      // FP8: 1 / scale of the output activations
+  void* out;                // row-planar output activations (middle layers)
+  const float* head_w;      // last layer: device [5][C]
+  const float* head_b;      // last layer: device [5]
+  float* maps;              // last layer: [T][5][H][W]
+  float* logits;            // last layer: optional [T][H][W]
+  int T, H, W, C, d, prec;
+  int* err;                 // device error word (wait timeouts)
+};
+cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaStream_t s);
+size_t tc_bimg_bytes(int C, int prec);
+void tc_pack_bimg(const float* w_tap_ci_co /*[9][C][C]*/, int C, int prec, const float* w_scale, void* dst);
+int tc_box_width(int d);
+int tc_groups(int C, int prec);
+
+// Debug: one 128 x N x K UMMA through the same descriptor helpers (exposed for tests).
+cudaError_t launch_umma_selftest(const void* a, const void* b, float* d, int N, int K, int prec, int* err,
+                                 cudaStream_t s);
+
+}  // namespace sml

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (derived in the design doc):
+  * FP32 maps: max|gpu - oracle| <= 1e-4 * max|oracle| per map (p compared as logits);
+  * BF16 maps: the same normalised max error <= 3e-2;
+  * decode: bit-exact (same bytes) when both sides decode the same float32 maps;
+  * the fused localize call equals the decode of the maps the same network produced.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2410_02314_gb300 as sml
+from paper_2410_02314_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-4, "bf16": 3e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def with_precision(w, prec, **extra):
+    spec = synth.NetSpec(**{**w.spec.__dict__, "precision": prec})
+    js = spec.to_json()
+    if extra:
+        import json
+
+        d = json.loads(js)
+        d.update(extra)
+        js = json.dumps(d)
+    return js
+
+
+def gpu_maps(spec_json, blob, frames, cam):
+    loc = sml.Localizer(spec_json, blob)
+    fr = torch.from_numpy(np.ascontiguousarray(frames)).cuda()
+    T, H, W = frames.shape
+    maps = torch.empty((T, 5, H, W), dtype=torch.float32, device="cuda")
+    logits = torch.empty((T, H, W), dtype=torch.float32, device="cuda")
+    gm = None if cam.gain_map is None else torch.from_numpy(cam.gain_map).cuda()
+    om = None if cam.offset_map is None else torch.from_numpy(cam.offset_map).cuda()
+    loc.forward_maps(fr, maps, logits, gain=cam.gain, offset=cam.offset, gain_map=gm, offset_map=om)
+    torch.cuda.synchronize()
+    return loc, maps, logits
+
+
+def map_errors(maps, logits, ref):
+    got = maps.cpu().numpy().astype(np.float64)
+    got[:, 0] = logits.cpu().numpy()
+    return [float(np.abs(got[:, k] - ref[:, k]).max() / max(np.abs(ref[:, k]).max(), 1e-6)) for k in range(5)]
+
+
+def cam_kwargs(cam):
+    return dict(gain=cam.gain, offset=cam.offset, gain_map=cam.gain_map, offset_map=cam.offset_map)
+
+
+# ----------------------------------------------------------------------------- UMMA unit
+
+
+def _bf16_bits(x):
+    return torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("fp8", [False, True])
+def test_umma_selftest_matches_matmul(fp8):
+    rng = np.random.default_rng(0)
+    N, K = 48, 64
+    a = rng.normal(0, 1, (128, K)).astype(np.float32)
+    b = rng.normal(0, 1, (N, K)).astype(np.float32)
+    if fp8:
+        at = torch.from_numpy(a).to(torch.float8_e4m3fn)
+        bt = torch.from_numpy(b).to(torch.float8_e4m3fn)
+        e, s = 16, 32
+    else:
+        at, bt = _bf16_bits(a), _bf16_bits(b)
+        e, s = 8, 16
+    af, bf = at.float().numpy().astype(np.float64), bt.float().numpy().astype(np.float64)
+    a_img = at.reshape(128, K // e, e).permute(1, 0, 2).contiguous()
+    b_img = bt.reshape(N // 8, 8, K // s, s // e, e).permute(2, 0, 3, 1, 4).contiguous()
+    da, db = a_img.view(torch.uint8).cuda(), b_img.view(torch.uint8).cuda()
+    dd = torch.zeros((128, N), dtype=torch.float32, device="cuda")
+    sml.sml_debug_umma(da, db, dd, N, K, fp8=fp8)
+    ref = af @ bf.T
+    got = dd.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+# ----------------------------------------------------------------------------- maps
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_small_workload_maps_match_oracle(prec):
+    w = synth.workload_small()
+    js = with_precision(w, prec)
+    loc, maps, logits = gpu_maps(js, w.blob, w.frames, w.cam)
+    ref = oracle.forward(oracle.Net(js, w.blob), w.frames, w.cam.gain, w.cam.offset)
+    errs = map_errors(maps, logits, ref)
+    print(prec, "normalised max map errors", errs)
+    assert max(errs) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_ragged_frames_multi_chunk_and_scmos(prec):
+    """W not a multiple of the 128-pixel tile, odd H, several chunks, per-pixel camera maps."""
+    rng = np.random.default_rng(7)
+    T, H, W = 5, 37, 150
+    cam = synth.scmos_camera(rng, H, W)
+    em = synth.emitters_density(rng, T, H, W, 2.0, astig=True)
+    frames = synth.simulate(em, T, H, W, cam, True, rng)
+    spec = synth.spec_48(prec)
+    blob = synth.pack_blob(spec, synth.init_weights(spec, 17))
+    js = with_precision(synth.Workload("r", frames, cam, em, spec, blob, True), prec, chunk_px=2 * H * W)
+    loc, maps, logits = gpu_maps(js, blob, frames, cam)
+    net = oracle.Net(js, blob)
+    ref = oracle.forward(net, frames, cam.gain, cam.offset, cam.gain_map.astype(np.float64),
+                         cam.offset_map.astype(np.float64))
+    errs = map_errors(maps, logits, ref)
+    print(prec, "ragged errors", errs)
+    assert max(errs) <= TOL[prec]
+    # fused path (host frames + host camera maps) decodes exactly the maps above
+    recs = loc.localize(frames, 0.5, **cam_kwargs(cam))
+    want = oracle.decode(maps.cpu().numpy(), 0.5, net.z_scale, net.ph_scale)
+    assert recs.tobytes() == want.tobytes()
+
+
+def test_dilation_larger_than_tile_margin():
+    """Dilations up to 64 (TMA box 256 pixels) and a frame narrower than the dilation."""
+    rng = np.random.default_rng(8)
+    spec = synth.NetSpec(in_ch=1, channels=32, dilations=(1, 64, 3, 17), precision="bf16")
+    blob = synth.pack_blob(spec, synth.init_weights(spec, 5))
+    frames = rng.integers(100, 600, (2, 90, 40)).astype(np.uint16)
+    cam = synth.Camera(1.0, 100.0)
+    loc, maps, logits = gpu_maps(spec.to_json(), blob, frames, cam)
+    ref = oracle.forward(oracle.Net(spec.to_json(), blob), frames, 1.0, 100.0)
+    assert max(map_errors(maps, logits, ref)) <= TOL["bf16"]
+
+
+# ----------------------------------------------------------------------------- decode
+
+
+def test_decode_bit_exact_on_gpu_maps():
+    w = synth.workload_small()
+    js = w.spec.to_json()
+    loc, maps, _ = gpu_maps(js, w.blob, w.frames, w.cam)
+    T, _, H, W = maps.shape
+    cap = T * H * W
+    d_out = torch.empty(cap * 24, dtype=torch.uint8, device="cuda")
+    d_n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    loc.decode_maps(maps, 0.5, d_out, d_n)
+    torch.cuda.synchronize()
+    n = int(d_n.item())
+    got = sml.records_from_bytes(d_out, n)
+    net = oracle.Net(js, w.blob)
+    want = oracle.decode(maps.cpu().numpy(), 0.5, net.z_scale, net.ph_scale)
+    assert n == len(want) and n > 0
+    assert got.tobytes() == want.tobytes()
+
+
+def test_decode_golden_cases_on_gpu():
+    import json
+    import os
+
+    cases = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "decode_cases.json")))["cases"]
+    for case in cases:
+        spec = synth.NetSpec(in_ch=1, channels=16, dilations=(1, 1), z_scale=case["z_scale"],
+                             ph_scale=case["ph_scale"])
+        loc = sml.Localizer(spec.to_json(), synth.pack_blob(spec, synth.init_weights(spec, 1)))
+        p = np.asarray(case["p"], dtype=np.float32)
+        T, H, W = p.shape
+        m = np.zeros((T, 5, H, W), dtype=np.float32)
+        m[:, 0] = p
+        m[:, 1], m[:, 2], m[:, 3], m[:, 4] = case["dx"], case["dy"], case["zhat"], case["nhat"]
+        d_out = torch.empty(64 * 24, dtype=torch.uint8, device="cuda")
+        d_n = torch.zeros(1, dtype=torch.int64, device="cuda")
+        loc.decode_maps(torch.from_numpy(m).cuda(), case["p_min"], d_out, d_n)
+        torch.cuda.synchronize()
+        got = sml.records_from_bytes(d_out, int(d_n.item()))
+        rows = [[int(r["frame"])] + [float(r[k]) for k in ("x", "y", "z", "photons", "p")] for r in got]
+        want = [[int(e[0])] + [float(np.float32(v)) for v in e[1:]] for e in case["expected"]]
+        assert rows == want, case["name"]
+
+
+def test_empty_input_and_capacity_overflow():
+    w = synth.workload_small()
+    loc = sml.Localizer(w.spec.to_json(), w.blob)
+    assert len(loc.localize(w.frames[:0], 0.5)) == 0
+    full = loc.localize(w.frames, 0.5, gain=w.cam.gain, offset=w.cam.offset)
+    assert len(full) > 2
+    with pytest.raises(sml.SmlError) as e:
+        loc.localize(w.frames, 0.5, gain=w.cam.gain, offset=w.cam.offset, capacity=len(full) - 1)
+    assert e.value.code == sml.SML_ERR_CAPACITY and e.value.needed == len(full)
+    exact = loc.localize(w.frames, 0.5, gain=w.cam.gain, offset=w.cam.offset, capacity=len(full))
+    assert exact.tobytes() == full.tobytes()
+
+
+def test_device_and_host_frames_agree_and_async_path():
+    w = synth.workload_small(precision="bf16")
+    js = with_precision(w, "bf16")
+    loc = sml.Localizer(js, w.blob)
+    host = loc.localize(w.frames, 0.5, gain=w.cam.gain, offset=w.cam.offset)
+    dev = loc.localize(torch.from_numpy(w.frames).cuda(), 0.5, gain=w.cam.gain, offset=w.cam.offset)
+    assert host.tobytes() == dev.tobytes()
+    d_out = torch.empty(len(host) * 24 + 24, dtype=torch.uint8, device="cuda")
+    d_n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    loc.localize_async(torch.from_numpy(w.frames).cuda(), 0.5, d_out, d_n, gain=w.cam.gain, offset=w.cam.offset)
+    torch.cuda.synchronize()
+    assert sml.records_from_bytes(d_out, int(d_n.item())).tobytes() == host.tobytes()
+
+
+def test_result_independent_of_chunking_and_batch():
+    """A frame's records are the same alone, inside a batch, and across chunk sizes."""
+    w = synth.workload_batched(T=6, H=128, W=192, precision="bf16")
+    a = sml.Localizer(with_precision(w, "bf16"), w.blob).localize(w.frames, 0.5)
+    b = sml.Localizer(with_precision(w, "bf16", chunk_px=128 * 192), w.blob).localize(w.frames, 0.5)
+    assert a.tobytes() == b.tobytes()
+    alone = sml.Localizer(with_precision(w, "bf16"), w.blob).localize(w.frames[3:4], 0.5)
+    sub = a[a["frame"] == 3].copy()
+    sub["frame"] = 0
+    assert alone.tobytes() == sub.tobytes()
+
+
+# ----------------------------------------------------------------------------- full size
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_batched_256_full_size_sampled(prec):
+    """256 frames of 256x256 with the 48-channel net (the benchmark workload): the maps of
+    sampled interior and border blocks match the oracle's exact windowed forward, and the
+    decode of all 16.8 Mpixel of GPU maps is bit-exact."""
+    w = synth.workload_batched(precision=prec)
+    js = with_precision(w, prec)
+    loc, maps, logits = gpu_maps(js, w.blob, w.frames, w.cam)
+    net = oracle.Net(js, w.blob)
+    m = maps.cpu().numpy()
+    lg = logits.cpu().numpy()
+    worst = 0.0
+    for t, (i0, j0) in [(0, (0, 0)), (77, (100, 120)), (255, (232, 232)), (130, (0, 200))]:
+        ref = oracle.forward_window(net, w.frames[t : t + 1], i0, i0 + 24, j0, j0 + 24)
+        got = m[t : t + 1, :, i0 : i0 + 24, j0 : j0 + 24].astype(np.float64)
+        got[:, 0] = lg[t : t + 1, i0 : i0 + 24, j0 : j0 + 24]
+        for k in range(5):
+            e = np.abs(got[:, k] - ref[:, k]).max() / max(np.abs(ref[:, k]).max(), 1e-6)
+            worst = max(worst, e)
+    print(prec, "full-size sampled worst normalised error", worst)
+    assert worst <= TOL[prec]
+    recs = loc.localize(w.frames, 0.5, capacity=4_000_000)
+    want = oracle.decode(m, 0.5, net.z_scale, net.ph_scale)
+    assert recs.tobytes() == want.tobytes()
