@@ -178,7 +178,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -212,12 +212,17 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    def workload(prec):
-        w = synth.workload_batched(T=T_FRAMES, H=H, W=W, precision=prec, seed=3 + rank)
+    def workload(prec, d_frames=None):
+        w = synth.workload_batched(T=T_FRAMES, H=H, W=W, precision="bf16" if prec == "fp8" else prec, seed=3 + rank)
         spec = json.loads(w.spec.to_json())
         if args.chunk_px:
             spec["chunk_px"] = args.chunk_px
-        return w, json.dumps(spec)
+        js = json.dumps(spec)
+        if prec == "fp8":  # per-layer activation scales from a bf16 pass over the first 16 frames
+            if d_frames is None:
+                d_frames = torch.from_numpy(w.frames).to(dev)
+            js = sml.calibrate_fp8(js, w.blob, d_frames[:16], gain=w.cam.gain, offset=w.cam.offset)
+        return w, js
 
     w, spec_json = workload(args.precision)
     loc = sml.Localizer(spec_json, w.blob)
@@ -315,23 +320,25 @@ def main():
            "d2h_bytes_per_step": int(recs.numel() + 8)}
 
     extra = {}
-    if not args.no_fp32 and args.precision != "fp32":
-        w32, js32 = workload("fp32")
-        loc32 = sml.Localizer(js32, w32.blob)
+    others = [] if args.no_fp32 else [p for p in ("fp32", "bf16", "fp8") if p != args.precision]
+    for prec in others:  # the same batch at the other precisions, same timing method
+        wo, jso = workload(prec, d_frames)
+        loco = sml.Localizer(jso, wo.blob)
         for _ in range(2):
-            loc32.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream)
+            loco.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream)
         torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
         for a, b in ev:
             flush.zero_()
             a.record(stream)
-            loc32.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream)
+            loco.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream)
             b.record(stream)
         torch.cuda.synchronize()
-        ms32 = statistics.mean(a.elapsed_time(b) for a, b in ev)
-        extra["fp32_frames_per_s"] = T_FRAMES / (ms32 / 1000)
-        extra["speedup_vs_fp32"] = (T_FRAMES / (ms / 1000)) / extra["fp32_frames_per_s"]
-        loc32.close()
+        mso = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        extra[f"{prec}_frames_per_s"] = world * T_FRAMES / (mso / 1000)
+        loco.close()
+    if "fp32_frames_per_s" in extra:
+        extra["speedup_vs_fp32"] = value / extra["fp32_frames_per_s"]
 
     if rank != 0:
         if dist:

@@ -146,6 +146,17 @@ int sml_forward_maps(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W
 int sml_decode_maps(sml_ctx* ctx, const float* d_maps, int T, int H, int W, const sml_thresholds* thr,
                     sml_record* d_out, size_t capacity, unsigned long long* d_n_out, void* stream);
 
+/*
+ * sml_activation_amax -- calibration for the "fp8" precision.  Runs the network of an fp32 or
+ * bf16 context over d_frames (device [T][H][W] uint16, camera as in sml_localize with device
+ * maps) and writes to amax (host float[L]): amax[l], l = 1..L-1, is the largest activation
+ * that enters conv layer l (the ReLU output of layer l-1); amax[0] = 0.  An fp8 net spec
+ * then uses act_scales[l] = amax[l] / 448 (the largest finite e4m3 value).  Synchronous.
+ * Errors: SML_ERR_UNSUPPORTED on an fp8 context, SML_ERR_BAD_ARG, SML_ERR_CUDA.
+ */
+int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam,
+                        float* amax);
+
 /* Number of kernels the last localize / forward / decode call launched (for profiling). */
 int sml_last_launch_count(const sml_ctx* ctx);
 

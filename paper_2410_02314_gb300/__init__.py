@@ -40,6 +40,7 @@ EXPORTS = (
     "sml_forward_maps",
     "sml_decode_maps",
     "sml_last_launch_count",
+    "sml_activation_amax",
     "sml_profile_enable",
     "sml_profile_read",
     "sml_debug_umma",
@@ -92,6 +93,8 @@ def lib():
         L.sml_decode_maps.restype = I
         L.sml_last_launch_count.argtypes = [P]
         L.sml_last_launch_count.restype = I
+        L.sml_activation_amax.argtypes = [P, P, I, I, I, ctypes.POINTER(_Camera), P]
+        L.sml_activation_amax.restype = I
         L.sml_profile_enable.argtypes = [P, I]
         L.sml_profile_enable.restype = I
         L.sml_profile_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]
@@ -208,6 +211,31 @@ def sml_decode_maps(ctx, d_maps, p_min, d_out, d_n, stream=None):
     thr = _Thresholds(float(p_min))
     _check(ctx, lib().sml_decode_maps(ctx, _ptr(d_maps), T, H, W, ctypes.byref(thr), _ptr(d_out), cap, _ptr(d_n),
                                       _stream(stream)))
+
+
+def sml_activation_amax(ctx, d_frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None):
+    """Per-layer maxima of the activations entering each conv layer (numpy float32 [L])."""
+    T, H, W = (int(s) for s in d_frames.shape)
+    out = np.zeros(64, dtype=np.float32)
+    cam = _camera(gain, offset, gain_map, offset_map)
+    _check(ctx, lib().sml_activation_amax(ctx, _ptr(d_frames), T, H, W, ctypes.byref(cam), out.ctypes.data))
+    return out
+
+
+def calibrate_fp8(net_spec: str, weights: bytes, d_frames, margin=1.0, **cam):
+    """FP8 net spec from a bf16 calibration pass: act_scales[l] = margin * amax[l] / 448."""
+    import json
+
+    spec = json.loads(net_spec)
+    L = len(spec["dilations"])
+    cal = dict(spec, precision="bf16")
+    ctx = sml_create(json.dumps(cal), weights)
+    try:
+        amax = sml_activation_amax(ctx, d_frames, **cam)[:L]
+    finally:
+        sml_destroy(ctx)
+    scales = [1.0] + [max(float(a), 1e-6) * margin / 448.0 for a in amax[1:]]
+    return json.dumps(dict(spec, precision="fp8", act_scales=scales))
 
 
 def sml_profile_enable(ctx, on: bool):

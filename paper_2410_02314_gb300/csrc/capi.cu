@@ -173,8 +173,7 @@ struct sml_ctx {
   float act_scale[kMaxLayers] = {0};
   long long chunk_px = 1 << 20;
   // device weights
-  float* w1 = nullptr;  // [C][9]
-  float* b1 = nullptr;
+  std::vector<float> w1, b1;  // layer 1 [C][9], [C] (host: passed to the kernel by value)
   float* wf32[kMaxLayers] = {nullptr};  // [9][C][C]
   float* bias[kMaxLayers] = {nullptr};
   void* bimg[kMaxLayers] = {nullptr};
@@ -326,16 +325,18 @@ int get_plan(sml_ctx* ctx, int H, int W) {
 
 // One chunk of frames through the network: maps [tc][5][H][W] (+ optional logits).
 int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, int H, int W, const CamArgs& cam, float* maps,
-                  float* logits, cudaStream_t s) {
+                  float* logits, cudaStream_t s, unsigned* d_amax = nullptr) {
   Plan& p = ctx->plan;
   const int L = ctx->L, C = ctx->C;
   float l1_scale = ctx->prec == kFP8 ? 1.0f / ctx->act_scale[1] : 1.0f;
   {
     ProfScope ps(ctx, SML_KERNEL_LAYER1, s);
-    SML_CUDA(launch_ingest_l1(d_frames, tc, H, W, ctx->dil[0], cam, ctx->w1, ctx->b1, C, ctx->prec, l1_scale, p.act[0], s),
+    SML_CUDA(launch_ingest_l1(d_frames, tc, H, W, ctx->dil[0], cam, ctx->w1.data(), ctx->b1.data(), C, ctx->prec, l1_scale, p.act[0], s),
              "layer 1");
   }
   ++ctx->launches;
+  const size_t n_act = (size_t)tc * H * W * C;
+  if (d_amax) SML_CUDA(launch_amax(p.act[0], n_act, ctx->prec, d_amax + 1, s), "amax");
   for (int l = 1; l < L; ++l) {
     const bool last = (l == L - 1);
     void* in = p.act[(l - 1) & 1];
@@ -372,6 +373,7 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, int H, int W, 
       SML_CUDA(launch_dconv_tc(a, last, ctx->num_sms, s), "tensor-core conv");
     }
     ++ctx->launches;
+    if (d_amax && !last) SML_CUDA(launch_amax(out, n_act, ctx->prec, d_amax + l + 1, s), "amax");
   }
   return SML_OK;
 }
@@ -547,7 +549,8 @@ int load_weights(sml_ctx* ctx, const void* blob, size_t bytes) {
         !std::all_of(bias.begin(), bias.end(), [](float x) { return std::isfinite(x); }))
       return fail(nullptr, SML_ERR_BAD_WEIGHTS, "layer %d has non-finite weights", l);
     if (l == 0) {
-      if ((r = upload(ctx, &ctx->w1, w.data(), w.size() * 4)) || (r = upload(ctx, &ctx->b1, bias.data(), C * 4))) return r;
+      ctx->w1 = w;
+      ctx->b1 = bias;
       continue;
     }
     // [co][ci][ky][kx] -> [tap][ci][co]
@@ -794,6 +797,36 @@ int sml_profile_read(sml_ctx* ctx, int kernel_class, double* total_ms, int* laun
   *total_ms = sum;
   *launches = n;
   return SML_OK;
+}
+
+int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam,
+                        float* amax) {
+  if (!ctx) return SML_ERR_BAD_ARG;
+  ctx->launches = 0;
+  int r;
+  if (!amax || (T > 0 && !d_frames)) return fail(ctx, SML_ERR_BAD_ARG, "NULL argument");
+  if (ctx->prec == kFP8) return fail(ctx, SML_ERR_UNSUPPORTED, "activation maxima need an fp32 or bf16 context");
+  if ((r = check_dims(ctx, T, H, W))) return r;
+  CamArgs ca;
+  if ((r = make_cam(ctx, cam, &ca))) return r;
+  for (int l = 0; l < ctx->L; ++l) amax[l] = 0.0f;
+  if (T == 0) return SML_OK;
+  if ((r = get_plan(ctx, H, W))) return r;
+  cudaStream_t s = ctx->stream;
+  unsigned* d_amax = nullptr;
+  if ((r = dev_alloc(ctx, &d_amax, kMaxLayers * sizeof(unsigned)))) return r;
+  std::unique_ptr<unsigned, decltype(&cudaFree)> guard(d_amax, &cudaFree);
+  SML_CUDA(cudaMemsetAsync(d_amax, 0, kMaxLayers * sizeof(unsigned), s), "memset amax");
+  const size_t fpx = (size_t)H * W;
+  for (int t0 = 0; t0 < T; t0 += ctx->plan.Tc) {
+    int tc = std::min(ctx->plan.Tc, T - t0);
+    if ((r = forward_chunk(ctx, d_frames + (size_t)t0 * fpx, tc, H, W, ca, ctx->plan.maps, nullptr, s, d_amax))) return r;
+  }
+  unsigned h[kMaxLayers];
+  SML_CUDA(cudaMemcpyAsync(h, d_amax, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H amax");
+  SML_CUDA(cudaStreamSynchronize(s), "amax");
+  for (int l = 1; l < ctx->L; ++l) memcpy(&amax[l], &h[l], sizeof(float));
+  return check_device_error(ctx);
 }
 
 // Debug entry (include/sml_debug.h): one UMMA tile through the conv kernel's descriptor helpers.

@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <cstring>
+
 #include "sml_internal.h"
 
 namespace sml {
@@ -24,39 +26,48 @@ __device__ __forceinline__ float cam_input(const uint16_t* __restrict__ f, int H
   return __fmul_rn(__fdiv_rn(__fsub_rn((float)f[px], o), g), cam.in_scale);
 }
 
-// OUT: 0 = float NHWC, 1 = bf16 row-planar (8 ch / 16 B), 2 = e4m3 row-planar (16 ch / 16 B)
+// Layer-1 weights by value: the FMAs read them straight from the constant bank.
+struct L1Params {
+  float w[64 * 9];  // [co][ky*3+kx]
+  float b[64];
+};
+
+constexpr int kL1Tile = 128;  // pixels of one image row per block
+
+// OUT: 0 = float NHWC, 1 = bf16 row-planar (8 ch / 16 B), 2 = e4m3 row-planar (16 ch / 16 B).
+// One block = 128 consecutive pixels of one row; the three dilated input rows (with a d-pixel
+// margin) are converted to network inputs once, into shared memory.
 template <int C, int OUT>
-__global__ void __launch_bounds__(kSimtThreads) k_ingest_l1(const uint16_t* __restrict__ frames, int T, int H, int W,
-                                                            int d, CamArgs cam, const float* __restrict__ w1,
-                                                            const float* __restrict__ b1, float out_scale,
-                                                            void* __restrict__ out) {
-  __shared__ float sw[C * 9];
-  __shared__ float sb[C];
-  for (int k = threadIdx.x; k < C * 9; k += blockDim.x) sw[k] = w1[k];
-  for (int k = threadIdx.x; k < C; k += blockDim.x) sb[k] = b1[k];
-  __syncthreads();
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long npx = (long long)T * H * W;
-  if (q >= npx) return;
-  int j = (int)(q % W);
-  int i = (int)((q / W) % H);
-  int t = (int)(q / ((long long)H * W));
+__global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restrict__ frames, int H, int W, int d,
+                                                       int t0, CamArgs cam, const __grid_constant__ L1Params prm,
+                                                       float out_scale, void* __restrict__ out) {
+  __shared__ float xs[3][kL1Tile + 2 * 64];
+  const int j0 = blockIdx.x * kL1Tile, i = blockIdx.y, t = t0 + blockIdx.z;
+  const int span = kL1Tile + 2 * d;
   const uint16_t* f = frames + (size_t)t * H * W;
+  for (int k = threadIdx.x; k < 3 * span; k += kL1Tile) {
+    int r = k / span, c = k - r * span;
+    xs[r][c] = cam_input(f, H, W, i + (r - 1) * d, j0 - d + c, cam);
+  }
+  __syncthreads();
+  const int j = j0 + threadIdx.x;
+  if (j >= W) return;
   float x[9];
 #pragma unroll
   for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-    for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = cam_input(f, H, W, i + (ky - 1) * d, j + (kx - 1) * d, cam);
+    for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xs[ky][threadIdx.x + kx * d];
   float a[C];
 #pragma unroll
   for (int co = 0; co < C; ++co) {
-    float s = sb[co];
+    float s = prm.b[co];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) s = fmaf(sw[co * 9 + k], x[k], s);
+    for (int k = 0; k < 9; ++k) s = fmaf(prm.w[co * 9 + k], x[k], s);
     a[co] = fmaxf(s, 0.0f);
   }
+  const size_t q = ((size_t)t * H + i) * W + j;
   if (OUT == 0) {
-    float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + (size_t)q * C);
+    float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + q * C);
 #pragma unroll
     for (int c4 = 0; c4 < C / 4; ++c4) dst[c4] = make_float4(a[4 * c4], a[4 * c4 + 1], a[4 * c4 + 2], a[4 * c4 + 3]);
   } else if (OUT == 1) {
@@ -164,33 +175,61 @@ __global__ void __launch_bounds__(kSimtThreads) k_dconv_f32(const float* __restr
   }
 }
 
+// Maximum of post-ReLU activations (all >= 0, so float bit patterns order like unsigned).
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_amax(const void* __restrict__ x, size_t n, unsigned* __restrict__ out) {
+  float m = 0.0f;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    float v = BF16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(x)[k]) : static_cast<const float*>(x)[k];
+    m = fmaxf(m, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
 inline unsigned grid_for(long long npx) { return (unsigned)((npx + kSimtThreads - 1) / kSimtThreads); }
 
 }  // namespace
 
 cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1,
                              const float* b1, int C, int prec, float out_scale, void* out, cudaStream_t s) {
-  long long npx = (long long)T * H * W;
-  if (npx == 0) return cudaSuccess;
-  dim3 grid(grid_for(npx)), block(kSimtThreads);
+  if ((long long)T * H * W == 0) return cudaSuccess;
+  if (d > 64 || C > 64) return cudaErrorInvalidValue;
+  // w1/b1 are host copies here: they travel as a kernel parameter
+  L1Params prm;
+  memset(&prm, 0, sizeof(prm));
+  memcpy(prm.w, w1, sizeof(float) * C * 9);
+  memcpy(prm.b, b1, sizeof(float) * C);
+  for (int t0 = 0; t0 < T; t0 += 65535) {
+    dim3 grid((W + kL1Tile - 1) / kL1Tile, H, (unsigned)(T - t0 < 65535 ? T - t0 : 65535)), block(kL1Tile);
 #define SML_L1(CC)                                                                                       \
   case CC:                                                                                               \
     if (prec == kFP32)                                                                                   \
-      k_ingest_l1<CC, 0><<<grid, block, 0, s>>>(frames, T, H, W, d, cam, w1, b1, out_scale, out);        \
+      k_ingest_l1<CC, 0><<<grid, block, 0, s>>>(frames, H, W, d, t0, cam, prm, out_scale, out);          \
     else if (prec == kBF16)                                                                              \
-      k_ingest_l1<CC, 1><<<grid, block, 0, s>>>(frames, T, H, W, d, cam, w1, b1, out_scale, out);        \
+      k_ingest_l1<CC, 1><<<grid, block, 0, s>>>(frames, H, W, d, t0, cam, prm, out_scale, out);          \
     else                                                                                                 \
-      k_ingest_l1<CC, 2><<<grid, block, 0, s>>>(frames, T, H, W, d, cam, w1, b1, out_scale, out);        \
+      k_ingest_l1<CC, 2><<<grid, block, 0, s>>>(frames, H, W, d, t0, cam, prm, out_scale, out);          \
     break;
-  switch (C) {
-    SML_L1(16)
-    SML_L1(32)
-    SML_L1(48)
-    SML_L1(64)
-    default:
-      return cudaErrorInvalidValue;
-  }
+    switch (C) {
+      SML_L1(16)
+      SML_L1(32)
+      SML_L1(48)
+      SML_L1(64)
+      default:
+        return cudaErrorInvalidValue;
+    }
 #undef SML_L1
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_amax(const void* x, size_t n, int prec, unsigned* out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (prec == kFP32) k_amax<false><<<1024, 256, 0, s>>>(x, n, out);
+  else if (prec == kBF16) k_amax<true><<<1024, 256, 0, s>>>(x, n, out);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -293,8 +293,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
   } else if (warp == 5) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t s_stage_u = smem_u32(s_stage);
-      const uint32_t s_bimg_u = smem_u32(s_bimg);
+      // Descriptors are computed once: the start-address field (bits 0-13, 16-byte units)
+      // is advanced by plain addition, which cannot carry out of the field because every
+      // shared-memory address is below 256 KB.
+      const uint64_t a_desc0 = smem_desc(smem_u32(s_stage), a.plane_stride, 128u);
+      const uint64_t b_desc0 = smem_desc(smem_u32(s_bimg), 128u, 256u);
+      uint32_t a_off[3 * Cfg::NKS];
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+        for (int ks = 0; ks < Cfg::NKS; ++ks) a_off[kx * Cfg::NKS + ks] = (uint32_t)(kx * a.d) + (uint32_t)ks * (a.plane_stride >> 3);
+      const uint32_t stage16 = a.stage_bytes >> 4;
       uint32_t stc = 0, rowc = 0;
       bool ok = true, issued = false;
       for (long long u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
@@ -308,8 +317,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
             break;
           }
           fence_after_sync();
-          const uint32_t a_base = s_stage_u + st * a.stage_bytes;
-#pragma unroll 1
+          const uint64_t a_st = a_desc0 + (uint64_t)(st * stage16);
+#pragma unroll
           for (int ky = 2; ky >= 0; --ky) {
             int k = kk - ky;  // output row fed by this input row through tap ky
             if (k < 0 || k >= n_out) continue;
@@ -326,12 +335,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
             for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
               for (int ks = 0; ks < Cfg::NKS; ++ks) {
-                uint64_t ad = smem_desc(a_base + (uint32_t)(2 * ks) * a.plane_stride + (uint32_t)(kx * a.d) * 16u,
-                                        a.plane_stride, 128u);
-                uint64_t bd = smem_desc(s_bimg_u + (uint32_t)(((ky * 3 + kx) * Cfg::NKS + ks) * Cfg::BBLK), 128u, 256u);
-                umma<PREC>(d_tmem, ad, bd, Cfg::IDESC, (ky == 0 && kx == 0 && ks == 0) ? 0u : 1u);
-                issued = true;
+                const uint64_t bd = b_desc0 + (uint64_t)((((ky * 3 + kx) * Cfg::NKS + ks) * Cfg::BBLK) >> 4);
+                umma<PREC>(d_tmem, a_st + a_off[kx * Cfg::NKS + ks], bd, Cfg::IDESC,
+                           (ky == 0 && kx == 0 && ks == 0) ? 0u : 1u);
               }
+            issued = true;
             if (ky == 2) umma_commit(smem_u32(&accf_bar[slot]));
           }
           if (ok) umma_commit(smem_u32(&empty_bar[st]));

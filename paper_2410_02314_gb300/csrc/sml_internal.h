@@ -46,9 +46,13 @@ struct CamArgs {
 // --- layer 1: camera transform + Cin=1 dilated 3x3 conv, bias, ReLU -------------------
 // prec kFP32 writes float NHWC [T][H][W][C]; kBF16 / kFP8 write row-planar activations
 // [T][H][C/g][W][16 bytes] (g = 8 bf16 or 16 e4m3 channels per group).  out_scale
-// multiplies the FP8 output before rounding (1 / activation scale).
+// multiplies the FP8 output before rounding (1 / activation scale).  w1 [C][9] and b1 [C]
+// are HOST pointers (the weights are passed to the kernel by value).
 cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1,
                              const float* b1, int C, int prec, float out_scale, void* out, cudaStream_t s);
+
+// Max of n post-ReLU activations (fp32 or bf16 buffer) into *out (float bits, atomicMax).
+cudaError_t launch_amax(const void* x, size_t n, int prec, unsigned* out, cudaStream_t s);
 
 // --- SIMT FP32 path (NHWC float activations) ------------------------------------------
 cudaError_t launch_dconv_f32(const float* in, float* out, const float* w, const float* b, int T, int H, int W,

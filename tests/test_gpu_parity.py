@@ -16,7 +16,7 @@ from paper_2410_02314_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-4, "bf16": 3e-2}
+TOL = {"fp32": 1e-4, "bf16": 3e-2, "fp8": 1.5e-1}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -254,3 +254,43 @@ def test_batched_256_full_size_sampled(prec):
     recs = loc.localize(w.frames, 0.5, capacity=4_000_000)
     want = oracle.decode(m, 0.5, net.z_scale, net.ph_scale)
     assert recs.tobytes() == want.tobytes()
+
+
+# ----------------------------------------------------------------------------- FP8
+
+
+@pytest.mark.parametrize("which", ["small", "batched"])
+def test_fp8_maps_within_gate(which):
+    """FP8 e4m3 activations and weights (per-output-channel weight scales, per-layer activation
+    scales from a bf16 calibration pass), FP32 accumulation, FP32 heads: maps within 1.5e-1."""
+    if which == "small":
+        w = synth.workload_small(precision="bf16")
+    else:
+        w = synth.workload_batched(T=6, H=256, W=256, precision="bf16")
+    d = torch.from_numpy(w.frames).cuda()
+    js8 = sml.calibrate_fp8(w.spec.to_json(), w.blob, d, gain=w.cam.gain, offset=w.cam.offset)
+    loc, maps, logits = gpu_maps(js8, w.blob, w.frames, w.cam)
+    ref = oracle.forward(oracle.Net(js8, w.blob), w.frames, w.cam.gain, w.cam.offset)
+    errs = map_errors(maps, logits, ref)
+    got = logits.cpu().numpy().astype(np.float64)
+    p999 = float(np.quantile(np.abs(got - ref[:, 0]), 0.999) / np.abs(ref[:, 0]).max())
+    print(which, "fp8 normalised max map errors", errs, "logit p99.9", p999)
+    assert max(errs) <= TOL["fp8"]
+    recs = loc.localize(w.frames, 0.5, gain=w.cam.gain, offset=w.cam.offset)
+    net = oracle.Net(js8, w.blob)
+    assert recs.tobytes() == oracle.decode(maps.cpu().numpy(), 0.5, net.z_scale, net.ph_scale).tobytes()
+
+
+def test_activation_amax_matches_oracle_activations():
+    """The calibration maxima equal the maxima of the oracle's per-layer activations (FP32
+    context, within the FP32 map tolerance)."""
+    w = synth.workload_small()
+    ctx = sml.sml_create(w.spec.to_json(), w.blob)
+    amax = sml.sml_activation_amax(ctx, torch.from_numpy(w.frames).cuda(), gain=w.cam.gain, offset=w.cam.offset)
+    sml.sml_destroy(ctx)
+    net = oracle.Net(w.spec.to_json(), w.blob)
+    x0 = oracle.ingest(w.frames, w.cam.gain, w.cam.offset, in_scale=net.in_scale)
+    _, acts = oracle.forward_x(net, x0, acts=True)
+    for l in range(1, net.L):
+        ref = acts[:, l - 1].max()
+        assert abs(amax[l] - ref) <= 1e-4 * ref, (l, amax[l], ref)
