@@ -66,6 +66,10 @@ def _load():
             F = ctypes.c_float
             lib.orc_forward_x.argtypes = [P, I, I, I, I, I, I, P, P, P, P, D, P, P, P, P]
             lib.orc_forward_x.restype = None
+            lib.orc_forward_xq.argtypes = [P, I, I, I, I, I, I, P, P, P, P, D, P, P, P, P, I, P]
+            lib.orc_forward_xq.restype = None
+            lib.orc_round_array.argtypes = [P, ctypes.c_size_t, I]
+            lib.orc_round_array.restype = None
             lib.orc_ingest.argtypes = [P, I, I, I, P, P, D, D, D, P]
             lib.orc_ingest.restype = None
             lib.orc_decode.argtypes = [P, I, I, I, F, F, F, P, ctypes.c_long]
@@ -149,9 +153,58 @@ def ingest(frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None, in_sc
     return x0
 
 
-def forward_x(net: Net, x0, acts=False):
+QUANT = {None: 0, "fp32": 0, "bf16": 1, "fp8": 2}
+
+
+def round_to(a, fmt):
+    """Round float64 values through float32 to bf16 or e4m3 (saturating at +-448), both
+    round-to-nearest-even; returns float64."""
+    lib = _load()
+    out = np.array(a, dtype=np.float64, copy=True, order="C")
+    lib.orc_round_array(_ptr(out), out.size, {"bf16": 1, "fp8": 2}[fmt])
+    return out
+
+
+def quantized(net: Net, fmt):
+    """Copy of net whose conv weights of layers 1..L-1 are rounded as the tensor-core path
+    stores them: bf16, or e4m3 of w / s[co] times s[co] with s[co] = max |w[co,:,:,:]| / 448
+    (float32).  Layer 0 (the SIMT first layer) and the heads keep their float32 weights."""
+    import copy
+
+    if net.bn is not None:
+        raise ValueError("quantized oracle modes need a net without BatchNorm")
+    q = copy.copy(net)
+    w = net.conv_w.copy()
+    off = net.C * net.in_ch * 9
+    n = net.C * net.C * 9
+    for layer in range(1, net.L):
+        blk = w[off : off + n].reshape(net.C, net.C * 9)
+        if fmt == "bf16":
+            blk[:] = round_to(blk, "bf16")
+        elif fmt == "fp8":
+            amax = np.abs(blk.astype(np.float32)).max(axis=1)
+            s = np.where(amax > 0, amax / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+            blk[:] = round_to((blk.astype(np.float32) / s[:, None]).astype(np.float64), "fp8") * s[:, None].astype(np.float64)
+        w[off : off + n] = blk.ravel()
+        off += n
+    q.conv_w = w
+    return q
+
+
+def act_scales(net: Net, frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None):
+    """FP8 activation scales from this oracle's own float64 activations: [1] + [amax_l / 448]
+    for the inputs of layers 1..L-1 (amax over the given frames)."""
+    x0 = ingest(frames, gain, offset, gain_map, offset_map, net.in_scale)
+    _, a = forward_x(net, x0, acts=True)
+    return [1.0] + [float(a[:, l - 1].max()) / 448.0 for l in range(1, net.L)]
+
+
+def forward_x(net: Net, x0, acts=False, quant=None, scales=None):
     """Raw heads [T,5,H,W] (float64) of the dilated stack on inputs x0 [T,in_ch,H,W]
-    (Sec. 3.2.1 dilated convolution, zero padding at every layer; Sec. 3.2 heads)."""
+    (Sec. 3.2.1 dilated convolution, zero padding at every layer; Sec. 3.2 heads).
+    quant "bf16" / "fp8" rounds the input activations of layers 1..L-1 to that format
+    (fp8: of a / scales[l]) before the layer, as the tensor-core path stores them; pass a
+    net from quantized() to round the weights too."""
     lib = _load()
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     if x0.ndim == 3:
@@ -161,16 +214,17 @@ def forward_x(net: Net, x0, acts=False):
     heads = np.empty((T, NH, H, W), dtype=np.float64)
     a = np.empty((T, net.L, net.C, H, W), dtype=np.float64) if acts else None
     dil = np.asarray(net.dil, dtype=np.int32)
-    lib.orc_forward_x(_ptr(x0), T, H, W, net.L, net.C, net.in_ch, _ptr(dil), _ptr(net.conv_w),
-                      _ptr(net.conv_b), _ptr(net.bn), net.bn_eps, _ptr(net.head_w), _ptr(net.head_b),
-                      _ptr(heads), _ptr(a))
+    sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float64)
+    lib.orc_forward_xq(_ptr(x0), T, H, W, net.L, net.C, net.in_ch, _ptr(dil), _ptr(net.conv_w),
+                       _ptr(net.conv_b), _ptr(net.bn), net.bn_eps, _ptr(net.head_w), _ptr(net.head_b),
+                       _ptr(heads), _ptr(a), QUANT[quant], _ptr(sc))
     return (heads, a) if acts else heads
 
 
-def forward(net: Net, frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None):
+def forward(net: Net, frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None, quant=None, scales=None):
     """Raw heads [T,5,H,W] float64 from uint16 frames through the camera transform."""
     x0 = ingest(frames, gain, offset, gain_map, offset_map, net.in_scale)
-    return forward_x(net, x0)
+    return forward_x(net, x0, quant=quant, scales=scales)
 
 
 def sigmoid(h):
@@ -204,7 +258,7 @@ def localize(net: Net, frames, p_min, gain=1.0, offset=100.0, gain_map=None, off
 
 
 def forward_window(net: Net, frames, i0, i1, j0, j1, gain=1.0, offset=100.0, gain_map=None,
-                   offset_map=None):
+                   offset_map=None, quant=None, scales=None):
     """Exact heads [T,5,i1-i0,j1-j0] of the block [i0,i1) x [j0,j1) of full frames.
 
     The crop extends the block by the receptive radius R = sum of dilations (clipped at the
@@ -219,7 +273,7 @@ def forward_window(net: Net, frames, i0, i1, j0, j1, gain=1.0, offset=100.0, gai
     crop = np.ascontiguousarray(frames[:, ci0:ci1, cj0:cj1])
     gm = None if gain_map is None else gain_map[ci0:ci1, cj0:cj1]
     om = None if offset_map is None else offset_map[ci0:ci1, cj0:cj1]
-    h = forward(net, crop, gain, offset, gm, om)
+    h = forward(net, crop, gain, offset, gm, om, quant=quant, scales=scales)
     return h[:, :, i0 - ci0 : i1 - ci0, j0 - cj0 : j1 - cj0]
 
 

@@ -31,6 +31,56 @@ typedef struct {
   float x, y, z, photons, p;
 } orc_record; /* 24 bytes */
 
+/* ------------------------------------------------------------------ rounding to narrow formats */
+
+/* float32 -> bfloat16 (8 significant bits), round to nearest, ties to even; returned as double. */
+double orc_round_bf16(double v) {
+  float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (double)f; /* inf / nan unchanged */
+  uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  u &= 0xffff0000u;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+/* float32 -> e4m3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits, no infinities;
+ * largest finite 448, smallest normal 2^-6, subnormal spacing 2^-9), round to nearest even,
+ * values beyond the largest finite saturate to +-448.  Returned as double. */
+double orc_round_e4m3(double v) {
+  float f = (float)v;
+  double a = fabs((double)f);
+  if (a != a) return (double)f;
+  double sgn = f < 0 ? -1.0 : 1.0;
+  if (a >= 448.0) return sgn * 448.0;
+  int e;
+  frexp(a, &e); /* a = m * 2^e, m in [0.5, 1) */
+  int ex = e - 1; /* a in [2^ex, 2^(ex+1)) */
+  if (ex < -6) ex = -6; /* subnormal range shares the spacing of the smallest binade */
+  double spacing = ldexp(1.0, ex - 3);
+  double q = nearbyint(a / spacing) * spacing; /* default rounding mode: ties to even */
+  if (q > 448.0) q = 448.0;
+  return sgn * q;
+}
+
+/* Round activations the way the tensor-core path stores them: quant 1 = bf16,
+ * quant 2 = e4m3 of a / scale (then multiplied back by scale). */
+static void round_acts(double* a, size_t n, int quant, double scale) {
+  if (quant == 1)
+    for (size_t k = 0; k < n; ++k) a[k] = orc_round_bf16(a[k]);
+  else if (quant == 2) {
+    float inv = (float)(1.0 / scale);
+    for (size_t k = 0; k < n; ++k) a[k] = orc_round_e4m3((double)((float)a[k] * inv)) * scale;
+  }
+}
+
+/* Round every element of a (fmt 1 = bf16, 2 = e4m3) in place. */
+void orc_round_array(double* a, size_t n, int fmt) {
+  for (size_t k = 0; k < n; ++k) a[k] = fmt == 1 ? orc_round_bf16(a[k]) : orc_round_e4m3(a[k]);
+}
+
 /* ------------------------------------------------------------------ helpers */
 
 static size_t conv_w_count(int layer, int in_ch, int C) {
@@ -98,9 +148,10 @@ static void conv_layer(const double* a, int cin, int H, int W, const double* w, 
  *   heads out: [T,5,H,W] raw head values (logit of p, dx, dy, z/z_scale, N/ph_scale).
  *   acts (optional): [T][L][C][H][W] post-ReLU activations of every layer.
  */
-void orc_forward_x(const double* x0, int T, int H, int W, int L, int C, int in_ch, const int* dil,
-                   const double* conv_w, const double* conv_b, const double* bn, double bn_eps,
-                   const double* head_w, const double* head_b, double* heads, double* acts) {
+void orc_forward_xq(const double* x0, int T, int H, int W, int L, int C, int in_ch, const int* dil,
+                    const double* conv_w, const double* conv_b, const double* bn, double bn_eps,
+                    const double* head_w, const double* head_b, double* heads, double* acts, int quant,
+                    const double* act_scales) {
   size_t plane = (size_t)H * W;
   double* bufA = (double*)malloc(sizeof(double) * C * plane);
   double* bufB = (double*)malloc(sizeof(double) * C * plane);
@@ -111,6 +162,7 @@ void orc_forward_x(const double* x0, int T, int H, int W, int L, int C, int in_c
     for (int l = 0; l < L; ++l) {
       const double* w = conv_w + conv_w_offset(l, in_ch, C);
       const double* bnl = bn ? bn + (size_t)l * 4 * C : NULL;
+      if (l > 0 && quant) round_acts((double*)in, (size_t)C * plane, quant, act_scales ? act_scales[l] : 1.0);
       conv_layer(in, cin, H, W, w, conv_b + (size_t)l * C, bnl, bn_eps, C, dil[l], NULL, cur);
       if (acts) memcpy(acts + ((size_t)t * L + l) * C * plane, cur, sizeof(double) * C * plane);
       in = cur;
@@ -127,6 +179,12 @@ void orc_forward_x(const double* x0, int T, int H, int W, int L, int C, int in_c
   }
   free(bufA);
   free(bufB);
+}
+
+void orc_forward_x(const double* x0, int T, int H, int W, int L, int C, int in_ch, const int* dil,
+                   const double* conv_w, const double* conv_b, const double* bn, double bn_eps,
+                   const double* head_w, const double* head_b, double* heads, double* acts) {
+  orc_forward_xq(x0, T, H, W, L, C, in_ch, dil, conv_w, conv_b, bn, bn_eps, head_w, head_b, heads, acts, 0, NULL);
 }
 
 /* Ingest + forward from uint16 frames. */

@@ -44,6 +44,12 @@ EXPORTS = (
     "sml_profile_enable",
     "sml_profile_read",
     "sml_debug_umma",
+    "sml_train_ingest",
+    "sml_train_conv_fwd",
+    "sml_train_conv_bwd_work_bytes",
+    "sml_train_conv_bwd",
+    "sml_train_heads_work_bytes",
+    "sml_train_heads_loss",
 )
 SML_KERNEL_LAYER1, SML_KERNEL_CONV, SML_KERNEL_CONV_HEADS, SML_KERNEL_DECODE = 0, 1, 2, 3
 

@@ -16,6 +16,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/sml_train.h"
 #include "sml_internal.h"
 
 using namespace sml;
@@ -827,6 +828,45 @@ int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, in
   SML_CUDA(cudaStreamSynchronize(s), "amax");
   for (int l = 1; l < ctx->L; ++l) memcpy(&amax[l], &h[l], sizeof(float));
   return check_device_error(ctx);
+}
+
+// ------------------------------------------------------------------ training (sml_train.h)
+static int train_status(cudaError_t e) { return e == cudaSuccess ? SML_OK : (e == cudaErrorInvalidValue ? SML_ERR_BAD_ARG : SML_ERR_CUDA); }
+
+int sml_train_ingest(const uint16_t* frames, long long n, float gain, float offset, float in_scale, float* x0,
+                     void* stream) {
+  if (n < 0 || (n > 0 && (!frames || !x0)) || !(gain > 0.0f)) return SML_ERR_BAD_ARG;
+  return train_status(train_ingest(frames, n, gain, offset, in_scale, x0, static_cast<cudaStream_t>(stream)));
+}
+
+int sml_train_conv_fwd(const float* x, int B, int H, int W, int cin, int cout, int d, const float* w, const float* b,
+                       float* y, void* stream) {
+  if (B < 0 || H < 1 || W < 1 || d < 1 || !x || !w || !b || !y) return SML_ERR_BAD_ARG;
+  return train_status(train_conv_fwd(x, B, H, W, cin, cout, d, w, b, y, static_cast<cudaStream_t>(stream)));
+}
+
+size_t sml_train_conv_bwd_work_bytes(int B, int H, int W, int cin, int cout) {
+  return train_conv_work_bytes(B, H, W, cin, cout);
+}
+
+int sml_train_conv_bwd(const float* x, const float* y, const float* dy, int B, int H, int W, int cin, int cout, int d,
+                       const float* w, float* dx, float* dw, float* db, void* work, size_t work_bytes, void* stream) {
+  if (B < 0 || H < 1 || W < 1 || d < 1 || !x || !y || !dy || !w || !dw || !db || !work) return SML_ERR_BAD_ARG;
+  if (work_bytes < train_conv_work_bytes(B, H, W, cin, cout)) return SML_ERR_BAD_ARG;
+  return train_status(train_conv_bwd(x, y, dy, B, H, W, cin, cout, d, w, dx, dw, db, work,
+                                     static_cast<cudaStream_t>(stream)));
+}
+
+size_t sml_train_heads_work_bytes(int B, int H, int W, int C) { return train_heads_work_bytes(B, H, W, C); }
+
+int sml_train_heads_loss(const float* a, const float* tgt, int B, int H, int W, int C, const float* hw,
+                         const float* hb, float* h, float* loss, const float* grad_scale, float* da, float* dhw,
+                         float* dhb, void* work, size_t work_bytes, void* stream) {
+  if (B < 1 || H < 1 || W < 1 || !a || !tgt || !hw || !hb || !h || !loss || !work) return SML_ERR_BAD_ARG;
+  if (da && (!grad_scale || !dhw || !dhb)) return SML_ERR_BAD_ARG;
+  if (work_bytes < train_heads_work_bytes(B, H, W, C)) return SML_ERR_BAD_ARG;
+  return train_status(train_heads_loss(a, tgt, B, H, W, C, hw, hb, h, loss, da ? grad_scale : nullptr, da, dhw, dhb,
+                                       work, static_cast<cudaStream_t>(stream)));
 }
 
 // Debug entry (include/sml_debug.h): one UMMA tile through the conv kernel's descriptor helpers.

@@ -82,6 +82,19 @@ void tc_pack_bimg(const float* w_tap_ci_co /*[9][C][C]*/, int C, int prec, const
 int tc_box_width(int d);
 int tc_groups(int C, int prec);
 
+// --- training (k_train.cu) -------------------------------------------------------------
+size_t train_conv_work_bytes(int B, int H, int W, int cin, int cout);
+size_t train_heads_work_bytes(int B, int H, int W, int C);
+cudaError_t train_conv_fwd(const float* x, int B, int H, int W, int cin, int cout, int d, const float* w,
+                           const float* b, float* y, cudaStream_t s);
+cudaError_t train_conv_bwd(const float* x, const float* y, const float* dy, int B, int H, int W, int cin, int cout,
+                           int d, const float* w, float* dx, float* dw, float* db, void* work, cudaStream_t s);
+cudaError_t train_heads_loss(const float* a, const float* tgt, int B, int H, int W, int C, const float* hw,
+                             const float* hb, float* h, float* loss, const float* gscale, float* da, float* dhw,
+                             float* dhb, void* work, cudaStream_t s);
+cudaError_t train_ingest(const uint16_t* f, long long n, float gain, float offset, float in_scale, float* x0,
+                         cudaStream_t s);
+
 // Debug: one 128 x N x K UMMA through the same descriptor helpers (exposed for tests).
 cudaError_t launch_umma_selftest(const void* a, const void* b, float* d, int N, int K, int prec, int* err,
                                  cudaStream_t s);

@@ -214,3 +214,58 @@ def test_analytic_network_recovers_emitter_grid():
     want = sorted(zip(em.frame.tolist(), em.y.tolist(), em.x.tolist()))
     assert got == want
     assert np.all(recs["z"] == 0.0) and np.all(recs["photons"] == 0.0)
+
+
+# ----------------------------------------------------------------------------- narrow formats
+
+
+def test_bf16_rounding_matches_torch_cast():
+    rng = np.random.default_rng(1)
+    v = np.concatenate([rng.normal(0, 1, 20000), rng.normal(0, 1e-3, 5000), rng.normal(0, 1e4, 5000),
+                        [0.0, 1.0, -1.0, 1.00390625, 1.01171875, 3.0e38]])
+    got = oracle.round_to(v, "bf16")
+    ref = torch.from_numpy(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_e4m3_rounding_matches_torch_cast_and_saturates():
+    rng = np.random.default_rng(2)
+    v = np.concatenate([rng.uniform(-448, 448, 20000), rng.normal(0, 1e-2, 5000), rng.normal(0, 3e-3, 5000),
+                        [0.0, 2.0 ** -9, 3 * 2.0 ** -10, 2.0 ** -6, 448.0, -448.0, 17.0, 18.0, 19.0]])
+    got = oracle.round_to(v, "fp8")
+    ref = torch.from_numpy(v.astype(np.float32)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(got, ref)
+    # beyond the largest finite value: saturate (by the definition of the format's finite range)
+    np.testing.assert_array_equal(oracle.round_to(np.array([460.0, 1e6, -500.0]), "fp8"), [448.0, 448.0, -448.0])
+    # ties go to the even mantissa: 3*2^-10 lies halfway between 2^-9 and 2^-8
+    assert oracle.round_to(np.array([3 * 2.0 ** -10]), "fp8")[0] == 2.0 ** -8
+
+
+def test_quantized_forward_matches_torch_emulation():
+    """The quantized oracle equals an independent torch emulation: e4m3 / bf16 casts at the
+    same points, torch conv2d in float64."""
+    spec = synth.spec_small()
+    blob = synth.pack_blob(spec, synth.init_weights(spec, 4))
+    net = oracle.Net(spec.to_json(), blob)
+    w = synth.blob_f32_weights(blob)
+    frames = np.random.default_rng(3).integers(100, 900, (2, 30, 34)).astype(np.uint16)
+    x0 = oracle.ingest(frames, 1.0, 100.0, in_scale=net.in_scale)[:, None]
+    scales = oracle.act_scales(net, frames)
+    for fmt in ("bf16", "fp8"):
+        got = oracle.forward_x(oracle.quantized(net, fmt), x0, quant=fmt, scales=scales)
+        a = torch.from_numpy(x0)
+        for layer, d in enumerate(net.dil):
+            wl = torch.from_numpy(w.conv_w[layer])
+            if layer > 0:
+                if fmt == "bf16":
+                    a = a.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+                    wl = wl.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+                else:
+                    inv = np.float32(1.0 / scales[layer])
+                    a = (a.to(torch.float32) * inv).to(torch.float8_e4m3fn).to(torch.float64) * scales[layer]
+                    s = (wl.abs().amax(dim=(1, 2, 3)).to(torch.float32) / 448.0)
+                    wl = (wl.to(torch.float32) / s[:, None, None, None]).to(torch.float8_e4m3fn).to(torch.float64) \
+                        * s.to(torch.float64)[:, None, None, None]
+            a = torch.relu(F.conv2d(a, wl, torch.from_numpy(w.conv_b[layer]), padding=d, dilation=d))
+        ref = F.conv2d(a, torch.from_numpy(w.head_w)[:, :, None, None], torch.from_numpy(w.head_b)).numpy()
+        assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max(), fmt
