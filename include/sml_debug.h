@@ -11,7 +11,8 @@
  *   d_b: k/s blocks (s = 16 for bf16, 32 for fp8) of (n/8)*256 bytes: element (nn, kk) of
  *        block kk/s at byte (nn/8)*256 + ((kk%s)/e)*128 + (nn%8)*16 + (kk%e)*size;
  *   d_d: float32 [128][n] output (row-major).
- * n in 16..256 (multiple of 16); k a positive multiple of 32; fp8 selects e4m3 inputs.
+ * n in 16..256 (multiple of 16); k a positive multiple of 32; fp8 selects e4m3 inputs;
+ * d_col: first TMEM column of the accumulator (multiple of 16, d_col + n <= 512).
  * Synchronises the stream.  Returns SML_OK, SML_ERR_BAD_ARG or SML_ERR_CUDA (also when the
  * kernel's bounded wait for the MMA gave up).
  */
@@ -22,7 +23,7 @@
 extern "C" {
 #endif
 
-int sml_debug_umma(const void* d_a, const void* d_b, float* d_d, int n, int k, int fp8, void* stream);
+int sml_debug_umma(const void* d_a, const void* d_b, float* d_d, int n, int k, int fp8, int d_col, void* stream);
 
 #ifdef __cplusplus
 }

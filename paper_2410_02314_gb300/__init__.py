@@ -105,7 +105,7 @@ def lib():
         L.sml_profile_enable.restype = I
         L.sml_profile_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]
         L.sml_profile_read.restype = I
-        L.sml_debug_umma.argtypes = [P, P, P, I, I, I, P]
+        L.sml_debug_umma.argtypes = [P, P, P, I, I, I, I, P]
         L.sml_debug_umma.restype = I
         _lib = L
     return _lib
@@ -256,8 +256,9 @@ def sml_profile_read(ctx, kernel_class: int):
     return ms.value, n.value
 
 
-def sml_debug_umma(d_a, d_b, d_d, n, k, fp8=False, stream=None):
-    code = lib().sml_debug_umma(_ptr(d_a), _ptr(d_b), _ptr(d_d), int(n), int(k), int(bool(fp8)), _stream(stream))
+def sml_debug_umma(d_a, d_b, d_d, n, k, fp8=False, d_col=0, stream=None):
+    code = lib().sml_debug_umma(_ptr(d_a), _ptr(d_b), _ptr(d_d), int(n), int(k), int(bool(fp8)), int(d_col),
+                                _stream(stream))
     if code != SML_OK:
         raise SmlError(code, "umma self-test failed")
 

@@ -16,10 +16,16 @@
 // Work decomposition ("row classes"): the three input rows of output row i are i-d, i, i+d,
 // so rows with the same residue mod d form independent chains.  A work unit is
 // (frame, 128-pixel column strip, residue phi, segment of S consecutive rows of the chain).
-// Its S+2 input rows stream through a ring of TMA stages, each loaded once, and each input
-// row feeds up to three output rows (ky = 2, 1, 0) whose accumulators live in a ring of 4
-// TMEM slots.  Accumulation order inside a row is fixed (ky, kx, k-step ascending), so the
-// result does not depend on scheduling, grid size or batch composition.
+// Its S+2 input rows stream through a ring of TMA stages, each loaded once.  Input row k'
+// feeds output rows k', k'-1, k'-2 through the vertical taps ky = 0, 1, 2; those three
+// contributions are ONE MMA with N = 3C (B = the three taps' weights side by side) whose
+// D columns are the three rows' accumulators: output row k of a unit accumulates at TMEM
+// column base0 - C*k, a window that slides down by C columns per input row.  Blocks that
+// would belong to rows outside the unit are not issued (N shrinks to C or 2C at the unit's
+// edges), and the first MMA of a row is split so that its own block starts from zero while
+// the older rows keep accumulating.  Accumulation order inside a row is fixed (ky, kx,
+// k-step ascending), so the result does not depend on scheduling, grid size or batch
+// composition.
 //
 // Warp roles (192 threads): warps 0-3 epilogue (TMEM lane quarter = warp index), warp 4 TMA
 // producer, warp 5 TMEM allocator and MMA issuer.  Every mbarrier wait is bounded: on
@@ -36,11 +42,9 @@ namespace {
 
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = 192;
-constexpr int kAccSlots = 4;
-constexpr int kSlotCols = 64;
-constexpr int kTmemCols = 256;
+constexpr int kTmemCols = 512;
+constexpr int kMaxSeg = 6;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
-constexpr int kSegRows = 8;                                 // S: output rows per work unit
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -175,13 +179,18 @@ struct TcCfg {
   static constexpr int KSTEP = PREC == kBF16 ? 16 : 32;   // K per MMA instruction
   static constexpr int NKS = (C + KSTEP - 1) / KSTEP;     // MMAs per tap
   static constexpr int GP = 2 * NKS;                      // planes in shared memory (FP8: zero pad)
-  static constexpr int BBLK = (C / 8) * 256;              // bytes of one (tap, k-step) B block
-  static constexpr int BIMG = 9 * NKS * BBLK;
-  static constexpr uint32_t IDESC = instr_desc(PREC, kTileM, C);
+  static constexpr int BBLK = 3 * (C / 8) * 256;          // bytes of one (kx, k-step) B block: N = 3C
+  static constexpr int BIMG = 3 * NKS * BBLK;
+  // S = output rows per unit: the window of S+2 input rows needs (S+1)*C + 3C <= 512 columns
+  static constexpr int SEG = (512 / C - 4) < kMaxSeg ? (512 / C - 4) : kMaxSeg;
+  static constexpr uint32_t BASE0 = (uint32_t)(SEG + 1) * C;  // TMEM column of output row 0
+  static constexpr uint32_t IDESC1 = instr_desc(PREC, kTileM, C);
+  static constexpr uint32_t IDESC2 = instr_desc(PREC, kTileM, 2 * C);
+  static constexpr uint32_t IDESC3 = instr_desc(PREC, kTileM, 3 * C);
 };
 
-// Unit -> (t, strip, phi, q); returns the number of valid output rows.
-__device__ __forceinline__ int unit_rows(const TcKArgs& a, long long u, int& t, int& j0, int& phi, int& q) {
+// Unit -> (t, strip, phi, q); returns the number of valid output rows (<= seg).
+__device__ __forceinline__ int unit_rows(const TcKArgs& a, long long u, int seg, int& t, int& j0, int& phi, int& q) {
   q = (int)(u % a.NQ);
   long long r = u / a.NQ;
   phi = (int)(r % a.d);
@@ -190,8 +199,8 @@ __device__ __forceinline__ int unit_rows(const TcKArgs& a, long long u, int& t, 
   t = (int)(r / a.NS);
   j0 = s * kTileM;
   int n_class = phi < a.H ? (a.H - phi + a.d - 1) / a.d : 0;
-  int n = n_class - q * kSegRows;
-  return n < 0 ? 0 : (n > kSegRows ? kSegRows : n);
+  int n = n_class - q * seg;
+  return n < 0 ? 0 : (n > seg ? seg : n);
 }
 
 template <int C, int PREC, bool LAST>
@@ -207,12 +216,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
   float* s_hw = s_deq + C;
   float* s_hb = s_hw + kHeads * C;
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uintptr_t>(s_hb + 8 + 1) & ~uintptr_t(7));
-  // barriers: full[nst], empty[nst], acc_full[4], acc_empty[4], drain
+  // barriers: full[nst], empty[nst], acc_full[SEG], acc_empty[SEG], drain
+  constexpr int SEG = Cfg::SEG;
   uint64_t* full_bar = s_bar;
   uint64_t* empty_bar = s_bar + a.nstages;
   uint64_t* accf_bar = empty_bar + a.nstages;
-  uint64_t* acce_bar = accf_bar + kAccSlots;
-  uint64_t* drain_bar = acce_bar + kAccSlots;
+  uint64_t* acce_bar = accf_bar + SEG;
+  uint64_t* drain_bar = acce_bar + SEG;
   volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(drain_bar + 1);
   volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
 
@@ -243,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         mbar_init(smem_u32(&full_bar[s]), 1);
         mbar_init(smem_u32(&empty_bar[s]), 1);
       }
-      for (int s = 0; s < kAccSlots; ++s) {
+      for (int s = 0; s < SEG; ++s) {
         mbar_init(smem_u32(&accf_bar[s]), 1);
         mbar_init(smem_u32(&acce_bar[s]), kEpiWarps * 32);
       }
@@ -272,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       bool ok = true;
       for (long long u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
         int t, j0, phi, q;
-        int n_out = unit_rows(a, u, t, j0, phi, q);
+        int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
         for (int kk = 0; kk < n_out + 2 && n_out > 0; ++kk, ++stc) {
           uint32_t st = stc % a.nstages, use = stc / a.nstages;
           if (use > 0 && !mbar_wait(smem_u32(&empty_bar[st]), (use - 1) & 1, a.err, s_abort)) {
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           }
           uint32_t fb = smem_u32(&full_bar[st]);
           mbar_expect_tx(fb, a.tx_bytes);
-          int row = phi + (q * kSegRows + kk - 1) * a.d;
+          int row = phi + (q * SEG + kk - 1) * a.d;
           tma_load_5d(smem_u32(s_stage + (size_t)st * a.stage_bytes), &tmap, 0, j0 - a.d, 0, row, t, fb);
         }
       }
@@ -304,11 +314,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
 #pragma unroll
         for (int ks = 0; ks < Cfg::NKS; ++ks) a_off[kx * Cfg::NKS + ks] = (uint32_t)(kx * a.d) + (uint32_t)ks * (a.plane_stride >> 3);
       const uint32_t stage16 = a.stage_bytes >> 4;
-      uint32_t stc = 0, rowc = 0;
+      uint32_t stc = 0;
+      uint32_t uses[SEG];
+#pragma unroll
+      for (int k = 0; k < SEG; ++k) uses[k] = 0;
       bool ok = true, issued = false;
       for (long long u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
         int t, j0, phi, q;
-        int n_out = unit_rows(a, u, t, j0, phi, q);
+        int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
         if (n_out == 0) continue;
         for (int kk = 0; kk < n_out + 2 && ok; ++kk, ++stc) {
           uint32_t st = stc % a.nstages;
@@ -317,34 +330,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
             break;
           }
           fence_after_sync();
-          const uint64_t a_st = a_desc0 + (uint64_t)(st * stage16);
+          // blocks b (output rows kk-b) of this input row that belong to the unit
+          const int b_lo = kk - n_out + 1 > 0 ? kk - n_out + 1 : 0;
+          const int b_hi = kk < 2 ? kk : 2;
+          const int nb = b_hi - b_lo + 1;
+          if (b_lo == 0) {  // this input row starts output row kk: its columns must be drained
+            uint32_t use = 0;
 #pragma unroll
-          for (int ky = 2; ky >= 0; --ky) {
-            int k = kk - ky;  // output row fed by this input row through tap ky
-            if (k < 0 || k >= n_out) continue;
-            uint32_t g = rowc + k, slot = g % kAccSlots, use = g / kAccSlots;
-            if (ky == 0 && use > 0) {
-              if (!mbar_wait(smem_u32(&acce_bar[slot]), (use - 1) & 1, a.err, s_abort)) {
+            for (int k = 0; k < SEG; ++k) use = (k == kk) ? uses[k] : use;
+            if (use > 0) {
+              if (!mbar_wait(smem_u32(&acce_bar[kk]), (use - 1) & 1, a.err, s_abort)) {
                 ok = false;
                 break;
               }
               fence_after_sync();
             }
-            const uint32_t d_tmem = tmem + slot * kSlotCols;
-#pragma unroll
-            for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-              for (int ks = 0; ks < Cfg::NKS; ++ks) {
-                const uint64_t bd = b_desc0 + (uint64_t)((((ky * 3 + kx) * Cfg::NKS + ks) * Cfg::BBLK) >> 4);
-                umma<PREC>(d_tmem, a_st + a_off[kx * Cfg::NKS + ks], bd, Cfg::IDESC,
-                           (ky == 0 && kx == 0 && ks == 0) ? 0u : 1u);
-              }
-            issued = true;
-            if (ky == 2) umma_commit(smem_u32(&accf_bar[slot]));
           }
-          if (ok) umma_commit(smem_u32(&empty_bar[st]));
+          const uint64_t a_st = a_desc0 + (uint64_t)(st * stage16);
+          const uint32_t d_col = tmem + Cfg::BASE0 - (uint32_t)(C * kk) + (uint32_t)(C * b_lo);
+          const uint32_t b_sub = (uint32_t)(2 * C * b_lo);  // 32*C*b_lo bytes in 16-byte units
+          const uint32_t idesc_n = nb == 3 ? Cfg::IDESC3 : (nb == 2 ? Cfg::IDESC2 : Cfg::IDESC1);
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+            for (int ks = 0; ks < Cfg::NKS; ++ks) {
+              const uint64_t ad = a_st + a_off[kx * Cfg::NKS + ks];
+              const uint64_t bd = b_desc0 + (uint64_t)(((kx * Cfg::NKS + ks) * Cfg::BBLK) >> 4) + b_sub;
+              if (kx == 0 && ks == 0 && b_lo == 0) {
+                umma<PREC>(d_col, ad, bd, Cfg::IDESC1, 0u);  // own block starts from zero
+                if (nb > 1)                                  // older rows keep accumulating
+                  umma<PREC>(d_col + C, ad, bd + (uint64_t)(2 * C), nb == 3 ? Cfg::IDESC2 : Cfg::IDESC1, 1u);
+              } else {
+                umma<PREC>(d_col, ad, bd, idesc_n, 1u);
+              }
+            }
+          issued = true;
+          if (kk >= 2 && kk - 2 < n_out) umma_commit(smem_u32(&accf_bar[kk - 2]));
+          umma_commit(smem_u32(&empty_bar[st]));
         }
-        rowc += n_out;
+#pragma unroll
+        for (int k = 0; k < SEG; ++k) uses[k] += (k < n_out) ? 1u : 0u;
       }
       if (issued) {  // all MMAs of this CTA complete before TMEM is released
         umma_commit(smem_u32(&drain_bar[0]));
@@ -355,26 +380,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     // ------------------------------------------------------------ epilogue (warps 0-3)
     const int m = warp * 32 + lane;  // TMEM lane = pixel within the strip
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    uint32_t rowc = 0;
+    uint32_t uses[SEG];
+#pragma unroll
+    for (int k = 0; k < SEG; ++k) uses[k] = 0;
     bool ok = true;
     const size_t plane = (size_t)a.H * a.W;
     for (long long u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
       int t, j0, phi, q;
-      int n_out = unit_rows(a, u, t, j0, phi, q);
+      int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
+#pragma unroll 1
       for (int k = 0; k < n_out; ++k) {
-        uint32_t g = rowc + k, slot = g % kAccSlots, use = g / kAccSlots;
-        if (!mbar_wait(smem_u32(&accf_bar[slot]), use & 1, a.err, s_abort)) {
+        uint32_t use = 0;
+#pragma unroll
+        for (int kq = 0; kq < SEG; ++kq) use = (kq == k) ? uses[kq] : use;
+        if (!mbar_wait(smem_u32(&accf_bar[k]), use & 1, a.err, s_abort)) {
           ok = false;
           break;
         }
         fence_after_sync();
         float v[C];
+        const uint32_t col = Cfg::BASE0 - (uint32_t)(C * k);
 #pragma unroll
-        for (int c = 0; c < C; c += 16) tmem_ld16(lane_addr + slot * kSlotCols + c, v + c);
+        for (int c = 0; c < C; c += 16) tmem_ld16(lane_addr + col + c, v + c);
         tmem_ld_wait();
         fence_before_sync();
-        mbar_arrive(smem_u32(&acce_bar[slot]));
-        const int i = phi + (q * kSegRows + k) * a.d;
+        mbar_arrive(smem_u32(&acce_bar[k]));
+        const int i = phi + (q * SEG + k) * a.d;
         const int j = j0 + m;
         if (j >= a.W) continue;
 #pragma unroll
@@ -418,7 +449,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           }
         }
       }
-      rowc += n_out;
+#pragma unroll
+      for (int k = 0; k < SEG; ++k) uses[k] += (k < n_out) ? 1u : 0u;
     }
   }
 
@@ -435,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
 // layouts the conv uses (A: planes of [128 rows][16 bytes]; B: the per-block image).
 template <int PREC>
 __global__ void __launch_bounds__(128, 1) k_umma_selftest(const uint8_t* A, const uint8_t* B, float* D, int N, int K,
-                                                          int* err) {
+                                                          int d_col, int* err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int ES = PREC == kBF16 ? 2 : 1;
@@ -455,7 +487,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_selftest(const uint8_t* A, cons
   }
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void*)s_tmem)),
-                 "r"(256)
+                 "r"(512)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -463,7 +495,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_selftest(const uint8_t* A, cons
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  const uint32_t tmem = *s_tmem;
+  const uint32_t tmem = *s_tmem + (uint32_t)d_col;
   const uint32_t plane = 128 * 16;  // A plane stride: 128 rows x 16 bytes
   const uint32_t bblk = (N / 8) * 256;
   if (threadIdx.x == 0) {
@@ -491,7 +523,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_selftest(const uint8_t* A, cons
   __syncthreads();
   if (threadIdx.x < 32) {
     fence_after_sync();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem - (uint32_t)d_col), "r"(512) : "memory");
   }
 }
 
@@ -502,7 +534,7 @@ size_t tc_smem_bytes(int nstages, uint32_t stage_bytes) {
   b += (Cfg::BIMG + 1023) & ~1023;            // weights
   b += (size_t)nstages * stage_bytes;         // stages
   b += sizeof(float) * (2 * C + kHeads * C + 8) + 16;  // bias, deq, heads
-  b += 8 * (2 * nstages + 2 * kAccSlots + 1) + 16;     // barriers, tmem addr, abort flag
+  b += 8 * (2 * nstages + 2 * Cfg::SEG + 1) + 16;      // barriers, tmem addr, abort flag
   return b;
 }
 
@@ -525,7 +557,7 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   a.d = la.d;
   a.NS = (la.W + kTileM - 1) / kTileM;
   int rows0 = (la.H + la.d - 1) / la.d;
-  a.NQ = (rows0 + kSegRows - 1) / kSegRows;
+  a.NQ = (rows0 + Cfg::SEG - 1) / Cfg::SEG;
   a.units = (long long)la.T * a.NS * la.d * a.NQ;
   const int boxw = tc_box_width(la.d);
   a.plane_stride = (uint32_t)boxw * 16u;
@@ -555,35 +587,38 @@ int tc_groups(int C, int prec) { return C / (prec == kBF16 ? 8 : 16); }
 size_t tc_bimg_bytes(int C, int prec) {
   const int kstep = prec == kBF16 ? 16 : 32;
   const int nks = (C + kstep - 1) / kstep;
-  return (size_t)9 * nks * (C / 8) * 256;
+  return (size_t)3 * nks * 3 * (C / 8) * 256;
 }
 
-// B image: for tap (ky*3+kx) and k-step ks, the [N = C][K = kstep] block in no-swizzle
-// K-major core-matrix order: byte (n/8)*256 + (k/EPG)*128 + (n%8)*16 + (k%EPG)*esize.
-// Input channels beyond C (FP8 padding) are zero.  FP8 weights are divided by w_scale[co].
+// B image: for horizontal tap kx and k-step ks, one [N = 3C][K = kstep] block whose rows are
+// n = ky*C + co (the three vertical taps side by side), in no-swizzle K-major core-matrix
+// order: byte (n/8)*256 + (k/EPG)*128 + (n%8)*16 + (k%EPG)*esize.  Input channels beyond C
+// (FP8 padding) are zero.  FP8 weights are divided by w_scale[co].
 void tc_pack_bimg(const float* w /*[9][C][C] tap, ci, co*/, int C, int prec, const float* w_scale, void* dst) {
   const int kstep = prec == kBF16 ? 16 : 32;
   const int epg = prec == kBF16 ? 8 : 16;
   const int es = prec == kBF16 ? 2 : 1;
   const int nks = (C + kstep - 1) / kstep;
-  const size_t bblk = (size_t)(C / 8) * 256;
+  const size_t bblk = (size_t)3 * (C / 8) * 256;
   uint8_t* out = static_cast<uint8_t*>(dst);
-  for (int tap = 0; tap < 9; ++tap)
+  for (int kx = 0; kx < 3; ++kx)
     for (int ks = 0; ks < nks; ++ks) {
-      uint8_t* blk = out + ((size_t)tap * nks + ks) * bblk;
-      for (int n = 0; n < C; ++n)
+      uint8_t* blk = out + ((size_t)kx * nks + ks) * bblk;
+      for (int n = 0; n < 3 * C; ++n) {
+        const int ky = n / C, co = n % C, tap = ky * 3 + kx;
         for (int k = 0; k < kstep; ++k) {
           int ci = ks * kstep + k;
-          float v = ci < C ? w[((size_t)tap * C + ci) * C + n] : 0.0f;
+          float v = ci < C ? w[((size_t)tap * C + ci) * C + co] : 0.0f;
           size_t off = (size_t)(n / 8) * 256 + (size_t)(k / epg) * 128 + (size_t)(n % 8) * 16 + (size_t)(k % epg) * es;
           if (prec == kBF16) {
             __nv_bfloat16 h = __float2bfloat16_rn(v);
             memcpy(blk + off, &h, 2);
           } else {
-            float sv = v / w_scale[n];
+            float sv = v / w_scale[co];
             blk[off] = (uint8_t)__nv_cvt_float_to_fp8(sv, __NV_SATFINITE, __NV_E4M3);
           }
         }
+      }
     }
 }
 
@@ -604,7 +639,7 @@ cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaSt
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_umma_selftest(const void* A, const void* B, float* D, int N, int K, int prec, int* err,
+cudaError_t launch_umma_selftest(const void* A, const void* B, float* D, int N, int K, int prec, int d_col, int* err,
                                  cudaStream_t s) {
   const int es = prec == kBF16 ? 2 : 1;
   size_t smem = 1024 + (size_t)128 * K * es + (size_t)N * K * es + 64;
@@ -612,11 +647,11 @@ cudaError_t launch_umma_selftest(const void* A, const void* B, float* D, int N, 
   if (prec == kBF16) {
     cudaError_t e = cudaFuncSetAttribute(k_umma_selftest<kBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_umma_selftest<kBF16><<<1, 128, smem, s>>>(static_cast<const uint8_t*>(A), static_cast<const uint8_t*>(B), D, N, K, err);
+    k_umma_selftest<kBF16><<<1, 128, smem, s>>>(static_cast<const uint8_t*>(A), static_cast<const uint8_t*>(B), D, N, K, d_col, err);
   } else {
     cudaError_t e = cudaFuncSetAttribute(k_umma_selftest<kFP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_umma_selftest<kFP8><<<1, 128, smem, s>>>(static_cast<const uint8_t*>(A), static_cast<const uint8_t*>(B), D, N, K, err);
+    k_umma_selftest<kFP8><<<1, 128, smem, s>>>(static_cast<const uint8_t*>(A), static_cast<const uint8_t*>(B), D, N, K, d_col, err);
   }
   return cudaGetLastError();
 }

@@ -96,7 +96,7 @@ cudaError_t train_ingest(const uint16_t* f, long long n, float gain, float offse
                          cudaStream_t s);
 
 // Debug: one 128 x N x K UMMA through the same descriptor helpers (exposed for tests).
-cudaError_t launch_umma_selftest(const void* a, const void* b, float* d, int N, int K, int prec, int* err,
+cudaError_t launch_umma_selftest(const void* a, const void* b, float* d, int N, int K, int prec, int d_col, int* err,
                                  cudaStream_t s);
 
 }  // namespace sml

@@ -100,10 +100,13 @@ def _bf16_bits(x):
     return torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16)
 
 
-@pytest.mark.parametrize("fp8", [False, True])
-def test_umma_selftest_matches_matmul(fp8):
+@pytest.mark.parametrize("fp8,N,d_col", [(False, 48, 0), (True, 48, 0), (False, 144, 48), (False, 48, 336),
+                                          (True, 144, 192), (False, 96, 288)])
+def test_umma_selftest_matches_matmul(fp8, N, d_col):
+    """One tcgen05 MMA chain: N = 48/96/144 accumulators at offset TMEM columns, as the
+    sliding-window conv uses them."""
     rng = np.random.default_rng(0)
-    N, K = 48, 64
+    K = 64
     a = rng.normal(0, 1, (128, K)).astype(np.float32)
     b = rng.normal(0, 1, (N, K)).astype(np.float32)
     if fp8:
@@ -118,7 +121,7 @@ def test_umma_selftest_matches_matmul(fp8):
     b_img = bt.reshape(N // 8, 8, K // s, s // e, e).permute(2, 0, 3, 1, 4).contiguous()
     da, db = a_img.view(torch.uint8).cuda(), b_img.view(torch.uint8).cuda()
     dd = torch.zeros((128, N), dtype=torch.float32, device="cuda")
-    sml.sml_debug_umma(da, db, dd, N, K, fp8=fp8)
+    sml.sml_debug_umma(da, db, dd, N, K, fp8=fp8, d_col=d_col)
     ref = af @ bf.T
     got = dd.cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
