@@ -156,13 +156,14 @@ std::string g_create_error;
 // ------------------------------------------------------------------ context
 struct Plan {
   int H = 0, W = 0, Tc = 0;
+  unsigned long long last_use = 0;
   void* act[2] = {nullptr, nullptr};
   float* maps = nullptr;
   unsigned* block_counts = nullptr;
   unsigned long long* block_offsets = nullptr;
   uint16_t* frames = nullptr;  // staging for host frames
   float* cam_maps = nullptr;   // staging for host camera maps [2][H][W]
-  CUtensorMap tmap[2][kMaxLayers];
+  CUtensorMap tmap[2];  // one per activation buffer
 };
 
 struct sml_ctx {
@@ -181,8 +182,11 @@ struct sml_ctx {
   float* deq[kMaxLayers] = {nullptr};
   float* head_w = nullptr;
   float* head_b = nullptr;
-  // runtime
-  Plan plan;
+  // runtime: plans (workspace + TMA maps) for up to kMaxPlans frame sizes, least recently
+  // used evicted first; plan points at the one in use
+  std::vector<std::unique_ptr<Plan>> plans;
+  Plan* plan = nullptr;
+  unsigned long long plan_clock = 0;
   cudaStream_t stream = nullptr;
   unsigned long long* d_total = nullptr;
   int* d_err = nullptr;
@@ -255,18 +259,21 @@ void free_plan(Plan& p) {
 
 size_t act_elem_bytes(int prec) { return prec == kFP32 ? 4 : (prec == kBF16 ? 2 : 1); }
 
-int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W, int d) {
+// Row-planar activations [Tc][H][G][W][16 B] described as 16-bit elements: dim0 runs over
+// the W*8 elements of one (row, group) plane-row, so a box of 256 elements is one contiguous
+// 512-byte run (32 pixels x 16 B).  The conv kernel loads each input row as G x ceil((128+2d)/32)
+// such boxes; elements left of pixel 0 or right of pixel W-1, and rows outside [0,H), are
+// filled with zeros by the TMA unit.
+int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W) {
   PFN_encodeTiled_t enc = get_encoder();
   if (!enc) return fail(ctx, SML_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  const int epg = ctx->prec == kBF16 ? 8 : 16;
   const int G = tc_groups(ctx->C, ctx->prec);
-  cuuint64_t dims[5] = {(cuuint64_t)epg, (cuuint64_t)W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)Tc};
-  cuuint64_t strides[4] = {16ull, 16ull * W, 16ull * W * G, 16ull * W * G * H};
-  cuuint32_t box[5] = {(cuuint32_t)epg, (cuuint32_t)tc_box_width(d), (cuuint32_t)G, 1u, 1u};
-  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  CUresult r = enc(m, ctx->prec == kBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 5, base,
-                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  cuuint64_t dims[4] = {8ull * W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)Tc};
+  cuuint64_t strides[3] = {16ull * W, 16ull * W * G, 16ull * W * G * H};
+  cuuint32_t box[4] = {256u, 1u, 1u, 1u};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ctx, SML_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return SML_OK;
 }
@@ -292,10 +299,27 @@ struct ProfScope {
   }
 };
 
+constexpr size_t kMaxPlans = 4;
+
 int get_plan(sml_ctx* ctx, int H, int W) {
-  Plan& p = ctx->plan;
-  if (p.H == H && p.W == W) return SML_OK;
-  free_plan(p);
+  ++ctx->plan_clock;
+  for (auto& q : ctx->plans)
+    if (q->H == H && q->W == W) {
+      q->last_use = ctx->plan_clock;
+      ctx->plan = q.get();
+      return SML_OK;
+    }
+  if (ctx->plans.size() >= kMaxPlans) {  // evict the least recently used plan
+    size_t victim = 0;
+    for (size_t k = 1; k < ctx->plans.size(); ++k)
+      if (ctx->plans[k]->last_use < ctx->plans[victim]->last_use) victim = k;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    cudaDeviceSynchronize();  // the plan's buffers may still be in use by async calls
+    free_plan(*ctx->plans[victim]);
+    ctx->plans.erase(ctx->plans.begin() + victim);
+  }
+  std::unique_ptr<Plan> np(new Plan());
+  Plan& p = *np;
   long long hw = (long long)H * W;
   int Tc = (int)std::max(1LL, ctx->chunk_px / hw);
   size_t npx = (size_t)Tc * hw;
@@ -312,22 +336,24 @@ int get_plan(sml_ctx* ctx, int H, int W) {
   }
   if (ctx->prec != kFP32) {
     for (int b = 0; b < 2; ++b)
-      for (int l = 1; l < ctx->L; ++l)
-        if ((r = encode_act_map(ctx, &p.tmap[b][l], p.act[b], Tc, H, W, ctx->dil[l]))) {
-          free_plan(p);
-          return r;
-        }
+      if ((r = encode_act_map(ctx, &p.tmap[b], p.act[b], Tc, H, W))) {
+        free_plan(p);
+        return r;
+      }
   }
   p.H = H;
   p.W = W;
   p.Tc = Tc;
+  p.last_use = ctx->plan_clock;
+  ctx->plan = np.get();
+  ctx->plans.push_back(std::move(np));
   return SML_OK;
 }
 
 // One chunk of frames through the network: maps [tc][5][H][W] (+ optional logits).
 int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, int H, int W, const CamArgs& cam, float* maps,
                   float* logits, cudaStream_t s, unsigned* d_amax = nullptr) {
-  Plan& p = ctx->plan;
+  Plan& p = *ctx->plan;
   const int L = ctx->L, C = ctx->C;
   float l1_scale = ctx->prec == kFP8 ? 1.0f / ctx->act_scale[1] : 1.0f;
   {
@@ -354,7 +380,7 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, int H, int W, 
                  "fp32 conv");
     } else {
       TcLayerArgs a{};
-      a.tmap = &p.tmap[(l - 1) & 1][l];
+      a.tmap = &p.tmap[(l - 1) & 1];
       a.bimg = ctx->bimg[l];
       a.bias = ctx->bias[l];
       a.deq = ctx->deq[l];
@@ -424,7 +450,7 @@ int localize_device(sml_ctx* ctx, const uint16_t* d_frames, bool frames_on_host,
                     float p_min, sml_record* d_out, size_t capacity, unsigned long long* d_n, cudaStream_t s) {
   int r = get_plan(ctx, H, W);
   if (r) return r;
-  Plan& p = ctx->plan;
+  Plan& p = *ctx->plan;
   SML_CUDA(cudaMemsetAsync(d_n, 0, sizeof(unsigned long long), s), "memset count");
   const size_t fpx = (size_t)H * W;
   for (int t0 = 0; t0 < T; t0 += p.Tc) {
@@ -629,7 +655,8 @@ void sml_destroy(sml_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  free_plan(ctx->plan);
+  for (auto& q : ctx->plans) free_plan(*q);
+  ctx->plans.clear();
   for (void* p : ctx->owned) cudaFree(p);
   cudaFree(ctx->d_total);
   cudaFree(ctx->d_err);
@@ -663,12 +690,12 @@ int sml_localize(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, cons
   const size_t hw = (size_t)H * W;
   // camera maps given in host memory are staged once per call
   if (ca.gain_map && !is_device_ptr(ca.gain_map)) {
-    SML_CUDA(cudaMemcpyAsync(ctx->plan.cam_maps, ca.gain_map, hw * 4, cudaMemcpyHostToDevice, s), "H2D gain map");
-    ca.gain_map = ctx->plan.cam_maps;
+    SML_CUDA(cudaMemcpyAsync(ctx->plan->cam_maps, ca.gain_map, hw * 4, cudaMemcpyHostToDevice, s), "H2D gain map");
+    ca.gain_map = ctx->plan->cam_maps;
   }
   if (ca.offset_map && !is_device_ptr(ca.offset_map)) {
-    SML_CUDA(cudaMemcpyAsync(ctx->plan.cam_maps + hw, ca.offset_map, hw * 4, cudaMemcpyHostToDevice, s), "H2D offset map");
-    ca.offset_map = ctx->plan.cam_maps + hw;
+    SML_CUDA(cudaMemcpyAsync(ctx->plan->cam_maps + hw, ca.offset_map, hw * 4, cudaMemcpyHostToDevice, s), "H2D offset map");
+    ca.offset_map = ctx->plan->cam_maps + hw;
   }
   const bool out_dev = capacity > 0 && is_device_ptr(out);
   sml_record* d_out = out;
@@ -728,8 +755,8 @@ int sml_forward_maps(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W
   if ((r = get_plan(ctx, H, W))) return r;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t fpx = (size_t)H * W;
-  for (int t0 = 0; t0 < T; t0 += ctx->plan.Tc) {
-    int tc = std::min(ctx->plan.Tc, T - t0);
+  for (int t0 = 0; t0 < T; t0 += ctx->plan->Tc) {
+    int tc = std::min(ctx->plan->Tc, T - t0);
     if ((r = forward_chunk(ctx, d_frames + (size_t)t0 * fpx, tc, H, W, ca, d_maps + (size_t)t0 * kHeads * fpx,
                            d_logits ? d_logits + (size_t)t0 * fpx : nullptr, s)))
       return r;
@@ -748,7 +775,7 @@ int sml_decode_maps(sml_ctx* ctx, const float* d_maps, int T, int H, int W, cons
   SML_CUDA(cudaMemsetAsync(d_n_out, 0, sizeof(unsigned long long), s), "memset count");
   if (T == 0) return SML_OK;
   if ((r = get_plan(ctx, H, W))) return r;
-  Plan& p = ctx->plan;
+  Plan& p = *ctx->plan;
   const size_t fpx = (size_t)H * W;
   for (int t0 = 0; t0 < T; t0 += p.Tc) {
     int tc = std::min(p.Tc, T - t0);
@@ -819,9 +846,9 @@ int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, in
   std::unique_ptr<unsigned, decltype(&cudaFree)> guard(d_amax, &cudaFree);
   SML_CUDA(cudaMemsetAsync(d_amax, 0, kMaxLayers * sizeof(unsigned), s), "memset amax");
   const size_t fpx = (size_t)H * W;
-  for (int t0 = 0; t0 < T; t0 += ctx->plan.Tc) {
-    int tc = std::min(ctx->plan.Tc, T - t0);
-    if ((r = forward_chunk(ctx, d_frames + (size_t)t0 * fpx, tc, H, W, ca, ctx->plan.maps, nullptr, s, d_amax))) return r;
+  for (int t0 = 0; t0 < T; t0 += ctx->plan->Tc) {
+    int tc = std::min(ctx->plan->Tc, T - t0);
+    if ((r = forward_chunk(ctx, d_frames + (size_t)t0 * fpx, tc, H, W, ca, ctx->plan->maps, nullptr, s, d_amax))) return r;
   }
   unsigned h[kMaxLayers];
   SML_CUDA(cudaMemcpyAsync(h, d_amax, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H amax");

@@ -6,8 +6,9 @@
 // with M = 128 pixels of one image row, N = C output channels, K = 9 taps x C input channels.
 //
 // Activation layout in HBM ("row-planar"): [T][H][G][W][16 bytes], G = C / (channels per
-// 16 bytes) -- 8 channels for BF16, 16 for FP8 e4m3.  One TMA box (elements of a group x
-// (128 + 2d) pixels x G groups) of one image row lands in shared memory as G planes of
+// 16 bytes) -- 8 channels for BF16, 16 for FP8 e4m3.  An input row segment of 128 + 2d
+// pixels is loaded as G x ceil((128 + 2d) / 32) TMA boxes, each one contiguous 512-byte run
+// (32 pixels of one channel group), and lands in shared memory as G planes of
 // [pixel][16 bytes]: exactly the no-swizzle K-major canonical layout of a UMMA operand with
 // 16-byte core-matrix rows, so the operand of tap kx is the same buffer started kx*d rows
 // later (SBO = 128 B between 8-pixel groups, LBO = plane stride between 8/16-channel
@@ -132,12 +133,12 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
           dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
       : "memory");
 }
 
@@ -168,6 +169,7 @@ struct TcKArgs {
   int NS, NQ;          // column strips, segments per residue class
   long long units;     // T * NS * d * NQ
   uint32_t stage_bytes, plane_stride, tx_bytes;
+  int nbx;  // 512-byte boxes per plane of one input row
   int nstages;
   int* err;
 };
@@ -291,8 +293,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           }
           uint32_t fb = smem_u32(&full_bar[st]);
           mbar_expect_tx(fb, a.tx_bytes);
-          int row = phi + (q * SEG + kk - 1) * a.d;
-          tma_load_5d(smem_u32(s_stage + (size_t)st * a.stage_bytes), &tmap, 0, j0 - a.d, 0, row, t, fb);
+          const int row = phi + (q * SEG + kk - 1) * a.d;
+          const uint32_t dst = smem_u32(s_stage + (size_t)st * a.stage_bytes);
+          const int x0 = 8 * (j0 - a.d);  // 16-bit elements; 16-byte aligned for any j0, d
+          for (int g = 0; g < Cfg::G; ++g)
+            for (int bx = 0; bx < a.nbx; ++bx)
+              tma_load_4d(dst + (uint32_t)g * a.plane_stride + (uint32_t)bx * 512u, &tmap, x0 + 256 * bx, g, row, t, fb);
         }
       }
       // drain: make sure no load of ours is still landing in shared memory
@@ -559,7 +565,8 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   int rows0 = (la.H + la.d - 1) / la.d;
   a.NQ = (rows0 + Cfg::SEG - 1) / Cfg::SEG;
   a.units = (long long)la.T * a.NS * la.d * a.NQ;
-  const int boxw = tc_box_width(la.d);
+  const int boxw = tc_box_width(la.d);  // pixels per plane, a multiple of 32
+  a.nbx = boxw / 32;
   a.plane_stride = (uint32_t)boxw * 16u;
   a.tx_bytes = (uint32_t)Cfg::G * a.plane_stride;
   a.stage_bytes = ((uint32_t)Cfg::GP * a.plane_stride + 1023u) & ~1023u;
@@ -580,7 +587,7 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
 
 }  // namespace
 
-int tc_box_width(int d) { return kTileM + 2 * d; }
+int tc_box_width(int d) { return (kTileM + 2 * d + 31) / 32 * 32; }
 
 int tc_groups(int C, int prec) { return C / (prec == kBF16 ? 8 : 16); }
 

@@ -4,7 +4,7 @@ Tolerances (derived in the design doc), as normalised max errors max|gpu - ref| / max
 (p compared as logits):
   * FP32 vs the float64 oracle: <= 1e-4;
   * BF16 / FP8 vs the oracle's quantized mode (activations and weights rounded at the same
-    points as the tensor-core path, float64 elsewhere): <= TOL_Q;
+    points as the tensor-core path, float64 elsewhere): max <= TOL_Q and RMS <= TOL_Q_RMS;
   * BF16 / FP8 vs the unquantized float64 oracle (the precision cost, stated per config):
     BF16 <= 3e-2; FP8 <= 0.4 max and <= 0.08 RMS;
   * decode: bit-exact (same bytes) when both sides decode the same float32 maps;
@@ -21,7 +21,8 @@ from paper_2410_02314_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp32": 1e-4, "bf16": 3e-2, "fp8": 0.4}
-TOL_Q = {"bf16": 1e-2, "fp8": 1e-1}
+TOL_Q = {"bf16": 2e-2, "fp8": 1e-1}          # max vs the quantized oracle
+TOL_Q_RMS = {"bf16": 2e-3, "fp8": 2e-2}      # RMS vs the quantized oracle
 FP8_RMS = 0.08
 
 
@@ -79,11 +80,13 @@ def check_quantized(prec, js, blob, frames, cam, maps, logits, scales=None, full
               offset_map=None if cam.offset_map is None else cam.offset_map.astype(np.float64))
     refq = oracle.forward(oracle.quantized(net, prec), frames, quant=prec, scales=scales, **kw)
     eq = map_errors(maps, logits, refq)
+    eq_rms = map_rms(maps, logits, refq)
     ref = full if full is not None else oracle.forward(net, frames, **kw)
     e = map_errors(maps, logits, ref)
-    print(prec, "vs quantized oracle", np.round(eq, 5), "vs float64", np.round(e, 4),
+    print(prec, "vs quantized oracle", np.round(eq, 5), "rms", np.round(eq_rms, 6), "vs float64", np.round(e, 4),
           "rms vs float64", np.round(map_rms(maps, logits, ref), 4))
     assert max(eq) <= TOL_Q[prec]
+    assert max(eq_rms) <= TOL_Q_RMS[prec]
     assert max(e) <= TOL[prec]
     if prec == "fp8":
         assert max(map_rms(maps, logits, ref)) <= FP8_RMS
