@@ -183,6 +183,8 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk-px", type=int, default=0)
+    ap.add_argument("--tc-stages", type=int, default=0)
+    ap.add_argument("--tma-box", default="", choices=["", "row", "wide"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     args = ap.parse_args()
@@ -217,6 +219,10 @@ def main():
         spec = json.loads(w.spec.to_json())
         if args.chunk_px:
             spec["chunk_px"] = args.chunk_px
+        if args.tc_stages:
+            spec["tc_stages"] = args.tc_stages
+        if args.tma_box:
+            spec["tma_box"] = args.tma_box
         js = json.dumps(spec)
         if prec == "fp8":  # per-layer activation scales from a bf16 pass over the first 16 frames
             if d_frames is None:
@@ -361,7 +367,8 @@ def main():
         "dtype": args.precision,
         "data": "synthetic",
         "config": {"workload": f"batched_{T_FRAMES}x{H}x{W}_48ch_8layer", "frames_per_step": T_FRAMES,
-                   "precision": args.precision, "chunk_px": chunk_px, "l2": "flushed between steps (512 MB write)",
+                   "precision": args.precision, "chunk_px": chunk_px, "tc_stages": args.tc_stages or "max",
+                   "tma_box": args.tma_box or "row", "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas{world}"},
         "mpix_per_s": value * H * W / 1e6,
         "records_per_step": n_rec,

@@ -163,7 +163,8 @@ struct Plan {
   unsigned long long* block_offsets = nullptr;
   uint16_t* frames = nullptr;  // staging for host frames
   float* cam_maps = nullptr;   // staging for host camera maps [2][H][W]
-  CUtensorMap tmap[2];  // one per activation buffer
+  CUtensorMap tmap[2][kMaxLayers];  // per buffer and layer: one box per row (box width depends on d)
+  CUtensorMap tmap_wide[2];         // per buffer: 512-byte boxes
 };
 
 struct sml_ctx {
@@ -174,14 +175,19 @@ struct sml_ctx {
   float in_scale = 1e-3f, z_scale = 1000.f, ph_scale = 10000.f;
   float act_scale[kMaxLayers] = {0};
   long long chunk_px = 1 << 20;
+  int tma_wide = 0;   // "tma_box": "row" (default) or "wide"
+  int tc_stages = 0;  // "tc_stages": TMA ring depth, 0 = as deep as shared memory allows
   // device weights
   std::vector<float> w1, b1;  // layer 1 [C][9], [C] (host: passed to the kernel by value)
   float* wf32[kMaxLayers] = {nullptr};  // [9][C][C]
   float* bias[kMaxLayers] = {nullptr};
   void* bimg[kMaxLayers] = {nullptr};
   float* deq[kMaxLayers] = {nullptr};
-  float* head_w = nullptr;
+  float* head_w = nullptr;  // device copies (FP32 SIMT path)
   float* head_b = nullptr;
+  // host copies for the tensor-core path (passed to its kernels by value)
+  std::vector<float> h_bias[kMaxLayers], h_deq[kMaxLayers];
+  std::vector<float> h_head_w, h_head_b;
   // runtime: plans (workspace + TMA maps) for up to kMaxPlans frame sizes, least recently
   // used evicted first; plan points at the one in use
   std::vector<std::unique_ptr<Plan>> plans;
@@ -259,21 +265,32 @@ void free_plan(Plan& p) {
 
 size_t act_elem_bytes(int prec) { return prec == kFP32 ? 4 : (prec == kBF16 ? 2 : 1); }
 
-// Row-planar activations [Tc][H][G][W][16 B] described as 16-bit elements: dim0 runs over
-// the W*8 elements of one (row, group) plane-row, so a box of 256 elements is one contiguous
-// 512-byte run (32 pixels x 16 B).  The conv kernel loads each input row as G x ceil((128+2d)/32)
-// such boxes; elements left of pixel 0 or right of pixel W-1, and rows outside [0,H), are
-// filled with zeros by the TMA unit.
-int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W) {
+// Row-planar activations [Tc][H][G][W][16 B].  Two descriptions for the conv kernel's loads
+// of one input row segment of tc_box_width(d) pixels:
+//  * 5-D (16-byte group, W, G, H, Tc) with box (group, pixels, G, 1, 1): one box per row;
+//  * 4-D (16-bit elements along W*8, G, H, Tc) with box (256 elements, 1, 1, 1): one
+//    contiguous 512-byte run (32 pixels of one group) per box.
+// Pixels left of 0 or right of W-1, and rows outside [0,H), are filled with zeros by TMA.
+int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W, int d) {
   PFN_encodeTiled_t enc = get_encoder();
   if (!enc) return fail(ctx, SML_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const int G = tc_groups(ctx->C, ctx->prec);
-  cuuint64_t dims[4] = {8ull * W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)Tc};
-  cuuint64_t strides[3] = {16ull * W, 16ull * W * G, 16ull * W * G * H};
-  cuuint32_t box[4] = {256u, 1u, 1u, 1u};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r;
+  if (d > 0) {
+    cuuint64_t dims[5] = {8ull, (cuuint64_t)W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)Tc};
+    cuuint64_t strides[4] = {16ull, 16ull * W, 16ull * W * G, 16ull * W * G * H};
+    cuuint32_t box[5] = {8u, (cuuint32_t)tc_box_width(d), (cuuint32_t)G, 1u, 1u};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 5, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t dims[4] = {8ull * W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)Tc};
+    cuuint64_t strides[3] = {16ull * W, 16ull * W * G, 16ull * W * G * H};
+    cuuint32_t box[4] = {256u, 1u, 1u, 1u};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
   if (r != CUDA_SUCCESS) return fail(ctx, SML_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return SML_OK;
 }
@@ -335,11 +352,17 @@ int get_plan(sml_ctx* ctx, int H, int W) {
     return r;
   }
   if (ctx->prec != kFP32) {
-    for (int b = 0; b < 2; ++b)
-      if ((r = encode_act_map(ctx, &p.tmap[b], p.act[b], Tc, H, W))) {
+    for (int b = 0; b < 2; ++b) {
+      if ((r = encode_act_map(ctx, &p.tmap_wide[b], p.act[b], Tc, H, W, 0))) {
         free_plan(p);
         return r;
       }
+      for (int l = 1; l < ctx->L; ++l)
+        if ((r = encode_act_map(ctx, &p.tmap[b][l], p.act[b], Tc, H, W, ctx->dil[l]))) {
+          free_plan(p);
+          return r;
+        }
+    }
   }
   p.H = H;
   p.W = W;
@@ -380,14 +403,17 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, int H, int W, 
                  "fp32 conv");
     } else {
       TcLayerArgs a{};
-      a.tmap = &p.tmap[(l - 1) & 1];
+      a.tmap = &p.tmap[(l - 1) & 1][l];
+      a.tmap_wide = &p.tmap_wide[(l - 1) & 1];
+      a.wide = ctx->tma_wide;
+      a.stages = ctx->tc_stages;
       a.bimg = ctx->bimg[l];
-      a.bias = ctx->bias[l];
-      a.deq = ctx->deq[l];
+      a.bias = ctx->h_bias[l].data();
+      a.deq = ctx->h_deq[l].empty() ? nullptr : ctx->h_deq[l].data();
       a.out_inv_scale = (ctx->prec == kFP8 && !last) ? 1.0f / ctx->act_scale[l + 1] : 1.0f;
       a.out = out;
-      a.head_w = ctx->head_w;
-      a.head_b = ctx->head_b;
+      a.head_w = ctx->h_head_w.data();
+      a.head_b = ctx->h_head_b.data();
       a.maps = maps;
       a.logits = logits;
       a.T = tc;
@@ -495,6 +521,14 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
   ctx->z_scale = (float)num("z_scale", 1000.0);
   ctx->ph_scale = (float)num("ph_scale", 10000.0);
   ctx->chunk_px = (long long)num("chunk_px", (double)(1 << 20));
+  ctx->tc_stages = (int)num("tc_stages", 0);
+  if (ctx->tc_stages < 0 || ctx->tc_stages > 16) return fail(nullptr, SML_ERR_BAD_SPEC, "tc_stages must be 0..16");
+  auto tb = root.obj.find("tma_box");
+  if (tb != root.obj.end()) {
+    if (tb->second.kind != JVal::kStr || (tb->second.str != "row" && tb->second.str != "wide"))
+      return fail(nullptr, SML_ERR_BAD_SPEC, "tma_box must be \"row\" or \"wide\"");
+    ctx->tma_wide = tb->second.str == "wide";
+  }
   if (ctx->in_ch != 1) return fail(nullptr, SML_ERR_BAD_SPEC, "in_ch must be 1");
   if (ctx->C != 16 && ctx->C != 32 && ctx->C != 48 && ctx->C != 64)
     return fail(nullptr, SML_ERR_BAD_SPEC, "channels must be 16, 32, 48 or 64");
@@ -600,15 +634,17 @@ int load_weights(sml_ctx* ctx, const void* blob, size_t bytes) {
       }
       std::vector<uint8_t> img(tc_bimg_bytes(C, ctx->prec));
       tc_pack_bimg(t.data(), C, ctx->prec, wscale.data(), img.data());
-      if ((r = upload(ctx, &ctx->bimg[l], img.data(), img.size())) || (r = upload(ctx, &ctx->bias[l], bias.data(), C * 4)))
-        return r;
-      if (ctx->prec == kFP8 && (r = upload(ctx, &ctx->deq[l], deq.data(), C * 4))) return r;
+      if ((r = upload(ctx, &ctx->bimg[l], img.data(), img.size()))) return r;
+      ctx->h_bias[l] = bias;
+      if (ctx->prec == kFP8) ctx->h_deq[l] = deq;
     }
   }
   std::vector<float> hw = take((size_t)kHeads * C);
   if ((r = upload(ctx, &ctx->head_w, hw.data(), hw.size() * 4))) return r;
+  ctx->h_head_w = hw;
   std::vector<float> hb = take(kHeads);
   if ((r = upload(ctx, &ctx->head_b, hb.data(), hb.size() * 4))) return r;
+  ctx->h_head_b = hb;
   return SML_OK;
 }
 

@@ -7,8 +7,9 @@
 //
 // Activation layout in HBM ("row-planar"): [T][H][G][W][16 bytes], G = C / (channels per
 // 16 bytes) -- 8 channels for BF16, 16 for FP8 e4m3.  An input row segment of 128 + 2d
-// pixels is loaded as G x ceil((128 + 2d) / 32) TMA boxes, each one contiguous 512-byte run
-// (32 pixels of one channel group), and lands in shared memory as G planes of
+// pixels (rounded up to a multiple of 32) is loaded either as one TMA box (16-byte group x
+// pixels x G groups, 5-D map) or as G x ceil((128 + 2d) / 32) boxes that are each one
+// contiguous 512-byte run (4-D map), and lands in shared memory as G planes of
 // [pixel][16 bytes]: exactly the no-swizzle K-major canonical layout of a UMMA operand with
 // 16-byte core-matrix rows, so the operand of tap kx is the same buffer started kx*d rows
 // later (SBO = 128 B between 8-pixel groups, LBO = plane stride between 8/16-channel
@@ -45,6 +46,7 @@ constexpr int kEpiWarps = 4;
 constexpr int kThreads = 192;
 constexpr int kTmemCols = 512;
 constexpr int kMaxSeg = 6;
+constexpr int kMaxStages = 16;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -133,6 +135,15 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint32_t bar) {
   asm volatile(
@@ -155,21 +166,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Kernel arguments; bias, dequantisation factors and head weights travel by value so the
+// epilogue's FMAs read them from the constant bank.
 struct TcKArgs {
   const uint8_t* bimg;
-  const float* bias;
-  const float* deq;
+  float bias[64];
+  float deq[64];
+  float head_w[kHeads * 64];  // [5][C]
+  float head_b[8];
   float out_inv_scale;
   uint8_t* out;
-  const float* head_w;
-  const float* head_b;
   float* maps;
   float* logits;
   int T, H, W, d;
   int NS, NQ;          // column strips, segments per residue class
   long long units;     // T * NS * d * NQ
   uint32_t stage_bytes, plane_stride, tx_bytes;
-  int nbx;  // 512-byte boxes per plane of one input row
+  int nbx;   // 512-byte boxes per plane of one input row ("wide" loads)
+  int wide;  // 1: G x nbx 512-byte boxes per row (4-D map); 0: one box per row (5-D map)
   int nstages;
   int* err;
 };
@@ -213,11 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* s_bimg = smem;
   uint8_t* s_stage = smem + ((Cfg::BIMG + 1023) & ~1023);
-  float* s_bias = reinterpret_cast<float*>(s_stage + (size_t)a.nstages * a.stage_bytes);
-  float* s_deq = s_bias + C;
-  float* s_hw = s_deq + C;
-  float* s_hb = s_hw + kHeads * C;
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uintptr_t>(s_hb + 8 + 1) & ~uintptr_t(7));
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_stage + (size_t)a.nstages * a.stage_bytes);
   // barriers: full[nst], empty[nst], acc_full[SEG], acc_empty[SEG], drain
   constexpr int SEG = Cfg::SEG;
   uint64_t* full_bar = s_bar;
@@ -236,13 +246,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     const uint4* src = reinterpret_cast<const uint4*>(a.bimg);
     uint4* dst = reinterpret_cast<uint4*>(s_bimg);
     for (int k = threadIdx.x; k < Cfg::BIMG / 16; k += kThreads) dst[k] = src[k];
-    for (int k = threadIdx.x; k < C; k += kThreads) {
-      s_bias[k] = a.bias[k];
-      s_deq[k] = a.deq ? a.deq[k] : 1.0f;
-    }
-    if (LAST)
-      for (int k = threadIdx.x; k < kHeads * C + kHeads; k += kThreads)
-        (k < kHeads * C ? s_hw[k] : s_hb[k - kHeads * C]) = (k < kHeads * C ? a.head_w[k] : a.head_b[k - kHeads * C]);
     if (Cfg::GP > Cfg::G) {  // planes beyond the stored groups stay zero (K padding)
       for (int s = 0; s < a.nstages; ++s) {
         uint4* z = reinterpret_cast<uint4*>(s_stage + (size_t)s * a.stage_bytes + (size_t)Cfg::G * a.plane_stride);
@@ -295,10 +298,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           mbar_expect_tx(fb, a.tx_bytes);
           const int row = phi + (q * SEG + kk - 1) * a.d;
           const uint32_t dst = smem_u32(s_stage + (size_t)st * a.stage_bytes);
-          const int x0 = 8 * (j0 - a.d);  // 16-bit elements; 16-byte aligned for any j0, d
-          for (int g = 0; g < Cfg::G; ++g)
-            for (int bx = 0; bx < a.nbx; ++bx)
-              tma_load_4d(dst + (uint32_t)g * a.plane_stride + (uint32_t)bx * 512u, &tmap, x0 + 256 * bx, g, row, t, fb);
+          if (a.wide) {  // G x nbx boxes, each one contiguous 512-byte run
+            const int x0 = 8 * (j0 - a.d);  // 16-bit elements; 16-byte aligned for any j0, d
+            for (int g = 0; g < Cfg::G; ++g)
+              for (int bx = 0; bx < a.nbx; ++bx)
+                tma_load_4d(dst + (uint32_t)g * a.plane_stride + (uint32_t)bx * 512u, &tmap, x0 + 256 * bx, g, row, t, fb);
+          } else {  // one box: (16-byte group) x plane pixels x G groups
+            tma_load_5d(dst, &tmap, 0, j0 - a.d, 0, row, t, fb);
+          }
         }
       }
       // drain: make sure no load of ours is still landing in shared memory
@@ -415,14 +422,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         const int j = j0 + m;
         if (j >= a.W) continue;
 #pragma unroll
-        for (int c = 0; c < C; ++c) v[c] = fmaxf(fmaf(v[c], s_deq[c], s_bias[c]), 0.0f);
+        for (int c = 0; c < C; ++c) v[c] = fmaxf(PREC == kFP8 ? fmaf(v[c], a.deq[c], a.bias[c]) : v[c] + a.bias[c], 0.0f);
         if (LAST) {
           const size_t px = (size_t)i * a.W + j;
 #pragma unroll
           for (int h = 0; h < kHeads; ++h) {
-            float acc = s_hb[h];
+            float acc = a.head_b[h];
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc = fmaf(s_hw[h * C + c], v[c], acc);
+            for (int c = 0; c < C; ++c) acc = fmaf(a.head_w[h * C + c], v[c], acc);
             if (h == 0) {
               if (a.logits) a.logits[(size_t)t * plane + px] = acc;
               acc = 1.0f / (1.0f + expf(-acc));
@@ -539,7 +546,6 @@ size_t tc_smem_bytes(int nstages, uint32_t stage_bytes) {
   size_t b = 1024;                            // alignment slack
   b += (Cfg::BIMG + 1023) & ~1023;            // weights
   b += (size_t)nstages * stage_bytes;         // stages
-  b += sizeof(float) * (2 * C + kHeads * C + 8) + 16;  // bias, deq, heads
   b += 8 * (2 * nstages + 2 * Cfg::SEG + 1) + 16;      // barriers, tmem addr, abort flag
   return b;
 }
@@ -549,12 +555,18 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   using Cfg = TcCfg<C, PREC>;
   TcKArgs a{};
   a.bimg = static_cast<const uint8_t*>(la.bimg);
-  a.bias = la.bias;
-  a.deq = la.deq;
+  for (int c = 0; c < C; ++c) {
+    a.bias[c] = la.bias[c];
+    a.deq[c] = la.deq ? la.deq[c] : 1.0f;
+  }
+  if (LAST) {
+    for (int k = 0; k < kHeads; ++k) {
+      a.head_b[k] = la.head_b[k];
+      for (int c = 0; c < C; ++c) a.head_w[k * C + c] = la.head_w[k * C + c];
+    }
+  }
   a.out_inv_scale = la.out_inv_scale;
   a.out = static_cast<uint8_t*>(la.out);
-  a.head_w = la.head_w;
-  a.head_b = la.head_b;
   a.maps = la.maps;
   a.logits = la.logits;
   a.T = la.T;
@@ -567,13 +579,14 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   a.units = (long long)la.T * a.NS * la.d * a.NQ;
   const int boxw = tc_box_width(la.d);  // pixels per plane, a multiple of 32
   a.nbx = boxw / 32;
+  a.wide = la.wide;
   a.plane_stride = (uint32_t)boxw * 16u;
   a.tx_bytes = (uint32_t)Cfg::G * a.plane_stride;
   a.stage_bytes = ((uint32_t)Cfg::GP * a.plane_stride + 1023u) & ~1023u;
   a.err = la.err;
   if (a.units == 0) return cudaSuccess;
   const size_t budget = 227 * 1024;
-  int nst = 6;
+  int nst = la.stages > 0 ? la.stages : kMaxStages;
   while (nst > 2 && tc_smem_bytes<C, PREC>(nst, a.stage_bytes) > budget) --nst;
   a.nstages = nst;
   size_t smem = tc_smem_bytes<C, PREC>(nst, a.stage_bytes);
@@ -581,7 +594,7 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_dconv_tc<C, PREC, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   long long grid = a.units < (long long)num_sms ? a.units : (long long)num_sms;
-  k_dconv_tc<C, PREC, LAST><<<(unsigned)grid, kThreads, smem, s>>>(*la.tmap, a);
+  k_dconv_tc<C, PREC, LAST><<<(unsigned)grid, kThreads, smem, s>>>(la.wide ? *la.tmap_wide : *la.tmap, a);
   return cudaGetLastError();
 }
 

@@ -63,14 +63,17 @@ cudaError_t launch_dconv_f32_heads(const float* in, const float* w, const float*
 
 // --- tensor-core path (row-planar activations) -------------------------------------
 struct TcLayerArgs {
-  const CUtensorMap* tmap;  // input activations (host copy, passed by value to the kernel)
+  const CUtensorMap* tmap;       // input activations, one box per row (5-D map for this dilation)
+  const CUtensorMap* tmap_wide;  // input activations, 512-byte boxes (4-D map)
+  int wide;                      // use tmap_wide
+  int stages;                    // TMA ring depth (0 = as many as shared memory allows)
   const void* bimg;         // device: packed B operand image for this layer
-  const float* bias;        // device [C] (FP8: already in the output scale domain)
-  const float* deq;         // device [C] per-output-channel dequant factor (FP8) or NULL
+  const float* bias;        // HOST [C] (passed to the kernel by value)
+  const float* deq;         // HOST [C] per-output-channel dequant factor (FP8) or NULL
   float out_inv_scale;      // FP8: 1 / scale of the output activations
   void* out;                // row-planar output activations (middle layers)
-  const float* head_w;      // last layer: device [5][C]
-  const float* head_b;      // last layer: device [5]
+  const float* head_w;      // last layer: HOST [5][C]
+  const float* head_b;      // last layer: HOST [5]
   float* maps;              // last layer: [T][5][H][W]
   float* logits;            // last layer: optional [T][H][W]
   int T, H, W, C, d, prec;

@@ -173,15 +173,20 @@ def test_ragged_frames_multi_chunk_and_scmos(prec):
     assert recs.tobytes() == want.tobytes()
 
 
-def test_dilation_larger_than_tile_margin():
-    """Dilations up to 64 (TMA box 256 pixels) and a frame narrower than the dilation."""
+@pytest.mark.parametrize("tma_box,stages", [("row", 0), ("wide", 0), ("row", 3)])
+def test_dilation_larger_than_tile_margin(tma_box, stages):
+    """Dilations up to 64 (TMA box 256 pixels) and a frame narrower than the dilation, for
+    both TMA load modes and a shallow ring."""
+    import json
+
     rng = np.random.default_rng(8)
     spec = synth.NetSpec(in_ch=1, channels=32, dilations=(1, 64, 3, 17), precision="bf16")
     blob = synth.pack_blob(spec, synth.init_weights(spec, 5))
     frames = rng.integers(100, 600, (2, 90, 40)).astype(np.uint16)
     cam = synth.Camera(1.0, 100.0)
-    loc, maps, logits = gpu_maps(spec.to_json(), blob, frames, cam)
-    check_quantized("bf16", spec.to_json(), blob, frames, cam, maps, logits)
+    js = json.dumps(dict(json.loads(spec.to_json()), tma_box=tma_box, tc_stages=stages))
+    loc, maps, logits = gpu_maps(js, blob, frames, cam)
+    check_quantized("bf16", js, blob, frames, cam, maps, logits)
 
 
 # ----------------------------------------------------------------------------- decode
