@@ -80,7 +80,9 @@ typedef struct {
  *   precision "fp32" (SIMT FP32 FMA), "bf16" (tensor cores, FP32 accumulation) or
  *   "fp8" (e4m3 activations and weights, FP32 accumulation; needs "act_scales": one
  *   positive float per conv layer, the scale of that layer's input activations).
- *   Optional "chunk_px": pixels per device chunk (default 2^20).
+ *   Optional tuning: "chunk_px": pixels per device chunk (default 2^20); "tc_stages": TMA
+ *   ring depth of the tensor-core conv (0 = as deep as shared memory allows, max 16);
+ *   "tma_box": "row" (one TMA box per input row, default) or "wide" (512-byte boxes).
  * weights: an SMLW blob (host memory, read during the call only):
  *   header "<8s7I16i": magic "SMLW0001", version 1, L, C, in_ch, n_heads (5), has_bn,
  *   reserved, dilations[16]; then per layer l: W[C][Cin_l][3][3] f32, b[C] f32 and, if
@@ -156,6 +158,31 @@ int sml_decode_maps(sml_ctx* ctx, const float* d_maps, int T, int H, int W, cons
  */
 int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam,
                         float* amax);
+
+/*
+ * sml_decode_maps_static -- the decode of sml_decode_maps for callers that cannot allocate
+ * device memory.  This entry point has no counterpart in the paper; it exists for callers
+ * that must not call cudaMalloc/cudaFree while they run: an acquisition loop sharing the GPU
+ * with a live camera stream (cudaFree synchronises the whole device), or a plugin whose host
+ * application keeps all device memory in its own pool.  It needs no context and allocates
+ * nothing; the caller passes the maps, the output records and the count.
+ *
+ * d_maps: device float32 [T][5][H][W] in the layout of sml_forward_maps.  z_scale, ph_scale:
+ * the readout scales (z = z_scale*zhat, photons = ph_scale*Nhat).  d_out, capacity, d_n_out
+ * and stream as in sml_decode_maps; *d_n_out is zeroed, then set to the detection count.
+ * Records are identical to those of sml_decode_maps on the same maps.
+ *
+ * Scratch: a fixed array of 192 KiB in device global memory, declared in the library and
+ * kept by every GPU that loads it until the process exits.  It bounds a call to
+ * T*H*W <= 16,777,216 pixels (e.g. 256 frames of 256 x 256); larger calls return
+ * SML_ERR_UNSUPPORTED without touching any buffer.  The first call on a device looks up the
+ * array's device address (with that device current); make that first call before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Errors: SML_ERR_BAD_ARG, SML_ERR_UNSUPPORTED, SML_ERR_CUDA.
+ */
+int sml_decode_maps_static(const float* d_maps, int T, int H, int W, float p_min, float z_scale, float ph_scale,
+                           sml_record* d_out, size_t capacity, unsigned long long* d_n_out, void* stream);
 
 /* Number of kernels the last localize / forward / decode call launched (for profiling). */
 int sml_last_launch_count(const sml_ctx* ctx);

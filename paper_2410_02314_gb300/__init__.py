@@ -39,6 +39,7 @@ EXPORTS = (
     "sml_localize_async",
     "sml_forward_maps",
     "sml_decode_maps",
+    "sml_decode_maps_static",
     "sml_last_launch_count",
     "sml_activation_amax",
     "sml_profile_enable",
@@ -97,6 +98,8 @@ def lib():
         L.sml_forward_maps.restype = I
         L.sml_decode_maps.argtypes = [P, P, I, I, I, ctypes.POINTER(_Thresholds), P, S, P, P]
         L.sml_decode_maps.restype = I
+        L.sml_decode_maps_static.argtypes = [P, I, I, I, F, F, F, P, S, P, P]
+        L.sml_decode_maps_static.restype = I
         L.sml_last_launch_count.argtypes = [P]
         L.sml_last_launch_count.restype = I
         L.sml_activation_amax.argtypes = [P, P, I, I, I, ctypes.POINTER(_Camera), P]
@@ -254,6 +257,16 @@ def sml_profile_read(ctx, kernel_class: int):
     n = ctypes.c_int(0)
     _check(ctx, lib().sml_profile_read(ctx, int(kernel_class), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def sml_decode_maps_static(d_maps, p_min, z_scale, ph_scale, d_out, d_n, stream=None):
+    """Allocation-free decode (see include/sml.h): same records as sml_decode_maps."""
+    T, _, H, W = (int(s) for s in d_maps.shape)
+    cap = int(d_out.numel() * d_out.element_size() // RECORD_DTYPE.itemsize)
+    code = lib().sml_decode_maps_static(_ptr(d_maps), T, H, W, float(p_min), float(z_scale), float(ph_scale),
+                                        _ptr(d_out), cap, _ptr(d_n), _stream(stream))
+    if code != SML_OK:
+        raise SmlError(code, "sml_decode_maps_static failed")
 
 
 def sml_debug_umma(d_a, d_b, d_d, n, k, fp8=False, d_col=0, stream=None):
