@@ -61,11 +61,12 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+        import tempfile
+
+        self.path = os.path.join(tempfile.gettempdir(), f"sml_bench_clocks_gpu{index}_{os.getpid()}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
@@ -143,6 +144,40 @@ def cpu_baseline(w, budget_s=12.0):
                       f"float64 forward + float32 decode, {el:.1f} s"}
 
 
+def serving_run(args, spec_json, blob, dev, capacity_px_per_s, load=0.8, n_requests=24, slots=3):
+    """Mixed stacks 100x512^2, 50x1024^2, 20x2048^2 uint16 (3:2:1), sCMOS astigmatic frames,
+    Poisson arrivals at `load` x the measured pixel capacity; continuous batching over
+    `slots` contexts.  Frames of each size come from a small simulated pool (same content
+    for requests of the same size)."""
+    import numpy as np
+    import torch
+
+    from paper_2410_02314_gb300 import serve, synth
+
+    rng = np.random.default_rng(6)
+    pool = {}
+    for T, S in ((100, 512), (50, 1024), (20, 2048)):
+        w = synth.workload_large_fov(T=1, H=S, W=S, seed=60 + S)
+        pool[S] = (torch.from_numpy(np.repeat(w.frames, T, axis=0)).pin_memory(), w.cam)
+    kinds = rng.choice([512, 1024, 2048], size=n_requests, p=[0.5, 1 / 3, 1 / 6])
+    mean_px = np.mean([pool[k][0].numel() for k in kinds])
+    rate = load * capacity_px_per_s / mean_px
+    arrivals = serve.poisson_arrivals(n_requests, rate, rng)
+    reqs = []
+    for k, (kind, t) in enumerate(zip(kinds, arrivals)):
+        fr, cam = pool[int(kind)]
+        reqs.append(serve.Request(rid=k, frames=fr, arrival=float(t), gain=cam.gain, offset=cam.offset,
+                                  gain_map=torch.from_numpy(cam.gain_map).to(dev),
+                                  offset_map=torch.from_numpy(cam.offset_map).to(dev)))
+    ex = serve.GpuExecutor(spec_json, blob, slots=slots, device=dev.index or 0)
+    ex.warm([(512, 512), (1024, 1024), (2048, 2048)], max_request=(20, 2048, 2048))
+    sch = serve.Scheduler(ex, hbm_budget=48 << 30)
+    rep = serve.report(sch.run(reqs))
+    rep.update({"load": load, "arrival_rate_per_s": rate, "slots": slots, "max_queue": sch.max_queue,
+                "mix": "100x512^2 : 50x1024^2 : 20x2048^2 = 3:2:1, sCMOS astigmatic"})
+    return rep
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle, timed on bounded samples of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -187,6 +222,7 @@ def main():
     ap.add_argument("--tma-box", default="", choices=["", "row", "wide"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -285,7 +321,7 @@ def main():
     l1_ms, l1_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_LAYER1)
     dec_ms, dec_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_DECODE)
     C = w.spec.channels
-    chunk_px = json.loads(spec_json).get("chunk_px", 1 << 20)
+    chunk_px = json.loads(spec_json).get("chunk_px", 1 << 24)
     frames_per_chunk = max(1, chunk_px // (H * W))
     px_per_launch = min(frames_per_chunk, T_FRAMES) * H * W
     pk, pk_kind = peaks()
@@ -346,6 +382,10 @@ def main():
     if "fp32_frames_per_s" in extra:
         extra["speedup_vs_fp32"] = value / extra["fp32_frames_per_s"]
 
+    serving = None
+    if not args.no_serve and world == 1:
+        serving = serving_run(args, spec_json, w.blob, dev, capacity_px_per_s=value * H * W)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -378,6 +418,7 @@ def main():
         "kernel_ms_per_step": breakdown,
         "cpu_baseline": cpu,
         "clocks": clocks,
+        "serving": serving,
         **extra,
     }
     print(json.dumps(line), flush=True)

@@ -80,7 +80,7 @@ typedef struct {
  *   precision "fp32" (SIMT FP32 FMA), "bf16" (tensor cores, FP32 accumulation) or
  *   "fp8" (e4m3 activations and weights, FP32 accumulation; needs "act_scales": one
  *   positive float per conv layer, the scale of that layer's input activations).
- *   Optional tuning: "chunk_px": pixels per device chunk (default 2^20); "tc_stages": TMA
+ *   Optional tuning: "chunk_px": pixels per device chunk (default 2^24); "tc_stages": TMA
  *   ring depth of the tensor-core conv (0 = as deep as shared memory allows, max 16);
  *   "tma_box": "row" (one TMA box per input row, default) or "wide" (512-byte boxes).
  * weights: an SMLW blob (host memory, read during the call only):

@@ -174,7 +174,7 @@ struct sml_ctx {
   int prec = kFP32;
   float in_scale = 1e-3f, z_scale = 1000.f, ph_scale = 10000.f;
   float act_scale[kMaxLayers] = {0};
-  long long chunk_px = 1 << 20;
+  long long chunk_px = 1 << 24;
   int tma_wide = 0;   // "tma_box": "row" (default) or "wide"
   int tc_stages = 0;  // "tc_stages": TMA ring depth, 0 = as deep as shared memory allows
   // device weights
@@ -520,7 +520,7 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
   ctx->in_scale = (float)num("in_scale", 1e-3);
   ctx->z_scale = (float)num("z_scale", 1000.0);
   ctx->ph_scale = (float)num("ph_scale", 10000.0);
-  ctx->chunk_px = (long long)num("chunk_px", (double)(1 << 20));
+  ctx->chunk_px = (long long)num("chunk_px", (double)(1 << 24));
   ctx->tc_stages = (int)num("tc_stages", 0);
   if (ctx->tc_stages < 0 || ctx->tc_stages > 16) return fail(nullptr, SML_ERR_BAD_SPEC, "tc_stages must be 0..16");
   auto tb = root.obj.find("tma_box");

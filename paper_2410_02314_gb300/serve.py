@@ -148,16 +148,32 @@ class GpuExecutor:
         self.locs = [Localizer(spec_json, blob) for _ in range(slots)]
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(slots)]
         self.state = [None] * slots
+        # per-slot buffers, grown on demand and reused (no allocation on the request path
+        # once they are large enough)
+        self.d_out = [None] * slots
+        self.h_out = [None] * slots
+        self.h_n = [torch.empty(1, dtype=torch.int64, pin_memory=True) for _ in range(slots)]
+        self.d_n = [torch.zeros(1, dtype=torch.int64, device=self.dev) for _ in range(slots)]
 
-    def warm(self, shapes):
-        """Create each slot's workspace for the given frame sizes before timing."""
+    def _buffers(self, slot, cap):
         torch = self.torch
-        for loc, st in zip(self.locs, self.streams):
+        if self.d_out[slot] is None or self.d_out[slot].numel() < cap * 24:
+            self.d_out[slot] = torch.empty(cap * 24, dtype=torch.uint8, device=self.dev)
+            self.h_out[slot] = torch.empty(cap * 24, dtype=torch.uint8, pin_memory=True)
+        return self.d_out[slot], self.h_out[slot]
+
+    def warm(self, shapes, max_request=None):
+        """Create each slot's workspace for the given frame sizes (and, if given, record buffers
+        for the largest request shape (T, H, W)) before timing."""
+        torch = self.torch
+        for slot, (loc, st) in enumerate(zip(self.locs, self.streams)):
             for (H, W) in shapes:
                 fr = torch.zeros((1, H, W), dtype=torch.uint16, device=self.dev)
                 out = torch.empty(record_capacity(1, H, W) * 24, dtype=torch.uint8, device=self.dev)
                 n = torch.zeros(1, dtype=torch.int64, device=self.dev)
                 loc.localize_async(fr, 0.5, out, n, stream=st)
+            if max_request is not None:
+                self._buffers(slot, record_capacity(*max_request))
         torch.cuda.synchronize(self.dev)
 
     def start(self, slot, r: Request):
@@ -165,14 +181,13 @@ class GpuExecutor:
         st = self.streams[slot]
         T, H, W = r.shape
         cap = record_capacity(T, H, W)
+        d_out, _ = self._buffers(slot, cap)
+        d_n, h_n = self.d_n[slot], self.h_n[slot]
         with torch.cuda.stream(st):
             d_frames = r.frames.to(self.dev, non_blocking=True)
-            d_out = torch.empty(cap * 24, dtype=torch.uint8, device=self.dev)
-            d_n = torch.zeros(1, dtype=torch.int64, device=self.dev)
-        self.locs[slot].localize_async(d_frames, r.p_min, d_out, d_n, gain=r.gain, offset=r.offset,
+        self.locs[slot].localize_async(d_frames, r.p_min, d_out[: cap * 24], d_n, gain=r.gain, offset=r.offset,
                                        gain_map=r.gain_map, offset_map=r.offset_map, stream=st)
         with torch.cuda.stream(st):
-            h_n = torch.empty(1, dtype=torch.int64, pin_memory=True)
             h_n.copy_(d_n, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
@@ -186,8 +201,8 @@ class GpuExecutor:
         if s["phase"] == 1:  # count known: copy exactly the records back
             n = int(s["h_n"][0])
             st = self.streams[slot]
+            h_out = self.h_out[slot]
             with torch.cuda.stream(st):
-                h_out = torch.empty(max(1, n) * 24, dtype=torch.uint8, pin_memory=True)
                 if n:
                     h_out[: n * 24].copy_(s["d_out"][: n * 24], non_blocking=True)
                 ev = torch.cuda.Event()

@@ -11,7 +11,7 @@ both the CUDA path and the CPU oracle receive what it produces as plain inputs.
   background, Poisson shot noise and the camera's ADU conversion
   ``adu = round(gain * electrons + offset)`` clamped to [0, 65535].  The paper only says
   that its training and test data are simulated (Sec. 3.4, Sec. 4.1); the PSF model,
-  emitter statistics and camera model here are the readings listed in the design doc.
+  emitter statistics and camera model here are this project's reading of those silences.
 """
 from __future__ import annotations
 
@@ -374,14 +374,15 @@ def workload_large_fov(T=2, H=2048, W=2048, precision="bf16", seed=4) -> Workloa
 # --------------------------------------------------------------------------- training data
 
 
-def training_batch(rng, B=256, H=64, W=64, max_emitters=10, astig=True, z_scale=1000.0, ph_scale=10000.0):
+def training_batch(rng, B=256, H=64, W=64, max_emitters=10, astig=True, z_scale=1000.0, ph_scale=10000.0,
+                   min_emitters=0):
     """Simulated training patches and per-pixel targets.
 
     Returns (frames u16 [B,H,W], targets f32 [B,5,H,W], emitters).  Target channel 0 is 1 at
     the pixel containing an emitter (brighter one wins a shared pixel); channels 1-4 hold
     dx, dy (emitter minus pixel centre, px), z / z_scale and photons / ph_scale there.
     """
-    counts = rng.integers(0, max_emitters + 1, B)
+    counts = rng.integers(min_emitters, max_emitters + 1, B)
     n = int(counts.sum())
     x, y = _uniform_positions(rng, n, H, W)
     em = Emitters(

@@ -191,14 +191,14 @@ class DilatedLocNet(torch.nn.Module):
 
 
 def train(net: DilatedLocNet, steps: int, batch: int = 256, patch: int = 64, lr: float = 1e-3, seed: int = 5,
-          pool: int = 16, log_every: int = 50, device="cuda"):
-    """Adam on simulated astigmatic patches (0..10 emitters each).  A pool of simulated
-    batches is generated once and cycled; returns the loss history."""
+          pool: int = 16, log_every: int = 50, device="cuda", max_emitters: int = 10):
+    """Adam on simulated astigmatic patches (0..max_emitters emitters each).  A pool of
+    simulated batches is generated once and cycled; returns the loss history."""
     rng = np.random.default_rng(seed)
     data = []
     for _ in range(pool):
         f, t, _, cam = synth.training_batch(rng, B=batch, H=patch, W=patch, z_scale=net.spec.z_scale,
-                                            ph_scale=net.spec.ph_scale)
+                                            ph_scale=net.spec.ph_scale, max_emitters=max_emitters)
         data.append((torch.from_numpy(f).to(device), torch.from_numpy(t).to(device)))
     opt = torch.optim.Adam(net.parameters(), lr=lr)
     hist = []
