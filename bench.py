@@ -219,7 +219,6 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk-px", type=int, default=0)
     ap.add_argument("--tc-stages", type=int, default=0)
-    ap.add_argument("--tma-box", default="", choices=["", "row", "wide"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -257,8 +256,6 @@ def main():
             spec["chunk_px"] = args.chunk_px
         if args.tc_stages:
             spec["tc_stages"] = args.tc_stages
-        if args.tma_box:
-            spec["tma_box"] = args.tma_box
         js = json.dumps(spec)
         if prec == "fp8":  # per-layer activation scales from a bf16 pass over the first 16 frames
             if d_frames is None:
@@ -408,7 +405,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"batched_{T_FRAMES}x{H}x{W}_48ch_8layer", "frames_per_step": T_FRAMES,
                    "precision": args.precision, "chunk_px": chunk_px, "tc_stages": args.tc_stages or "max",
-                   "tma_box": args.tma_box or "row", "l2": "flushed between steps (512 MB write)",
+                   "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas{world}"},
         "mpix_per_s": value * H * W / 1e6,
         "records_per_step": n_rec,

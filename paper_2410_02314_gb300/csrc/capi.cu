@@ -164,7 +164,6 @@ struct Plan {
   uint16_t* frames = nullptr;  // staging for host frames
   float* cam_maps = nullptr;   // staging for host camera maps [2][H][W]
   CUtensorMap tmap[2][kMaxLayers];  // per buffer and layer: one box per row (box width depends on d)
-  CUtensorMap tmap_wide[2];         // per buffer: 512-byte boxes
 };
 
 struct sml_ctx {
@@ -175,7 +174,6 @@ struct sml_ctx {
   float in_scale = 1e-3f, z_scale = 1000.f, ph_scale = 10000.f;
   float act_scale[kMaxLayers] = {0};
   long long chunk_px = 1 << 24;
-  int tma_wide = 0;   // "tma_box": "row" (default) or "wide"
   int tc_stages = 0;  // "tc_stages": TMA ring depth, 0 = as deep as shared memory allows
   // device weights
   std::vector<float> w1, b1;  // layer 1 [C][9], [C] (host: passed to the kernel by value)
@@ -265,32 +263,24 @@ void free_plan(Plan& p) {
 
 size_t act_elem_bytes(int prec) { return prec == kFP32 ? 4 : (prec == kBF16 ? 2 : 1); }
 
-// Row-planar activations [Tc][H][G][W][16 B].  Two descriptions for the conv kernel's loads
-// of one input row segment of tc_box_width(d) pixels:
-//  * 5-D (16-byte group, W, G, H, Tc) with box (group, pixels, G, 1, 1): one box per row;
-//  * 4-D (16-bit elements along W*8, G, H, Tc) with box (256 elements, 1, 1, 1): one
-//    contiguous 512-byte run (32 pixels of one group) per box.
-// Pixels left of 0 or right of W-1, and rows outside [0,H), are filled with zeros by TMA.
+// Row-planar activations [Tc][H][G][W][row bytes], G = C/16 groups of 16 channels (32-byte
+// rows in BF16, 16-byte rows in FP8).  5-D description (group row, W, G, H, Tc) with box
+// (group row, tc_box_width(d) pixels, G, 1, 1): the conv kernel loads one input row segment
+// per box, BF16 rows with the 32-byte swizzle.  Pixels left of 0 or right of W-1, and rows
+// outside [0,H), are filled with zeros by TMA.
 int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W, int d) {
   PFN_encodeTiled_t enc = get_encoder();
   if (!enc) return fail(ctx, SML_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const int G = tc_groups(ctx->C, ctx->prec);
-  CUresult r;
-  if (d > 0) {
-    cuuint64_t dims[5] = {8ull, (cuuint64_t)W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)Tc};
-    cuuint64_t strides[4] = {16ull, 16ull * W, 16ull * W * G, 16ull * W * G * H};
-    cuuint32_t box[5] = {8u, (cuuint32_t)tc_box_width(d), (cuuint32_t)G, 1u, 1u};
-    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 5, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  } else {
-    cuuint64_t dims[4] = {8ull * W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)Tc};
-    cuuint64_t strides[3] = {16ull * W, 16ull * W * G, 16ull * W * G * H};
-    cuuint32_t box[4] = {256u, 1u, 1u, 1u};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  }
+  const bool bf16 = ctx->prec == kBF16;
+  const cuuint64_t rowb = bf16 ? 32 : 16;
+  cuuint64_t dims[5] = {16ull, (cuuint64_t)W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)Tc};
+  cuuint64_t strides[4] = {rowb, rowb * W, rowb * W * G, rowb * W * G * H};
+  cuuint32_t box[5] = {16u, (cuuint32_t)tc_box_width(d), (cuuint32_t)G, 1u, 1u};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 5, base, dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, bf16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ctx, SML_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return SML_OK;
 }
@@ -353,10 +343,6 @@ int get_plan(sml_ctx* ctx, int H, int W) {
   }
   if (ctx->prec != kFP32) {
     for (int b = 0; b < 2; ++b) {
-      if ((r = encode_act_map(ctx, &p.tmap_wide[b], p.act[b], Tc, H, W, 0))) {
-        free_plan(p);
-        return r;
-      }
       for (int l = 1; l < ctx->L; ++l)
         if ((r = encode_act_map(ctx, &p.tmap[b][l], p.act[b], Tc, H, W, ctx->dil[l]))) {
           free_plan(p);
@@ -404,8 +390,6 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, int H, int W, 
     } else {
       TcLayerArgs a{};
       a.tmap = &p.tmap[(l - 1) & 1][l];
-      a.tmap_wide = &p.tmap_wide[(l - 1) & 1];
-      a.wide = ctx->tma_wide;
       a.stages = ctx->tc_stages;
       a.bimg = ctx->bimg[l];
       a.bias = ctx->h_bias[l].data();
@@ -523,12 +507,7 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
   ctx->chunk_px = (long long)num("chunk_px", (double)(1 << 24));
   ctx->tc_stages = (int)num("tc_stages", 0);
   if (ctx->tc_stages < 0 || ctx->tc_stages > 16) return fail(nullptr, SML_ERR_BAD_SPEC, "tc_stages must be 0..16");
-  auto tb = root.obj.find("tma_box");
-  if (tb != root.obj.end()) {
-    if (tb->second.kind != JVal::kStr || (tb->second.str != "row" && tb->second.str != "wide"))
-      return fail(nullptr, SML_ERR_BAD_SPEC, "tma_box must be \"row\" or \"wide\"");
-    ctx->tma_wide = tb->second.str == "wide";
-  }
+
   if (ctx->in_ch != 1) return fail(nullptr, SML_ERR_BAD_SPEC, "in_ch must be 1");
   if (ctx->C != 16 && ctx->C != 32 && ctx->C != 48 && ctx->C != 64)
     return fail(nullptr, SML_ERR_BAD_SPEC, "channels must be 16, 32, 48 or 64");

@@ -34,7 +34,7 @@ struct L1Params {
 
 constexpr int kL1Tile = 128;  // pixels of one image row per block
 
-// OUT: 0 = float NHWC, 1 = bf16 row-planar (8 ch / 16 B), 2 = e4m3 row-planar (16 ch / 16 B).
+// OUT: 0 = float NHWC, 1 = bf16 row-planar (16 ch / 32 B), 2 = e4m3 row-planar (16 ch / 16 B).
 // One block = 128 consecutive pixels of one row; the three dilated input rows (with a d-pixel
 // margin) are converted to network inputs once, into shared memory.
 template <int C, int OUT>
@@ -71,19 +71,20 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
 #pragma unroll
     for (int c4 = 0; c4 < C / 4; ++c4) dst[c4] = make_float4(a[4 * c4], a[4 * c4 + 1], a[4 * c4 + 2], a[4 * c4 + 3]);
   } else if (OUT == 1) {
-    constexpr int G = C / 8;
+    constexpr int G = C / 16;
     uint8_t* base = static_cast<uint8_t*>(out);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      uint4 v;
-      uint32_t* vw = reinterpret_cast<uint32_t*>(&v);
+      uint4 v[2];
+      uint32_t* vw = reinterpret_cast<uint32_t*>(v);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(a[8 * g + 2 * e], a[8 * g + 2 * e + 1]);
+      for (int e = 0; e < 8; ++e) {
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(a[16 * g + 2 * e], a[16 * g + 2 * e + 1]);
         vw[e] = *reinterpret_cast<uint32_t*>(&h2);
       }
-      size_t off = ((((size_t)t * H + i) * G + g) * W + j) * 16;
-      *reinterpret_cast<uint4*>(base + off) = v;
+      uint4* dst = reinterpret_cast<uint4*>(base + ((((size_t)t * H + i) * G + g) * W + j) * 32);
+      dst[0] = v[0];
+      dst[1] = v[1];
     }
   } else {
     constexpr int G = C / 16;

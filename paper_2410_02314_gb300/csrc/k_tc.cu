@@ -5,15 +5,17 @@
 // GEMM view of one output row segment: D[m, co] = sum_{ky,kx,ci} A[m + kx*d, ci | row ky] W[ky,kx,ci,co]
 // with M = 128 pixels of one image row, N = C output channels, K = 9 taps x C input channels.
 //
-// Activation layout in HBM ("row-planar"): [T][H][G][W][16 bytes], G = C / (channels per
-// 16 bytes) -- 8 channels for BF16, 16 for FP8 e4m3.  An input row segment of 128 + 2d
-// pixels (rounded up to a multiple of 32) is loaded either as one TMA box (16-byte group x
-// pixels x G groups, 5-D map) or as G x ceil((128 + 2d) / 32) boxes that are each one
-// contiguous 512-byte run (4-D map), and lands in shared memory as G planes of
-// [pixel][16 bytes]: exactly the no-swizzle K-major canonical layout of a UMMA operand with
-// 16-byte core-matrix rows, so the operand of tap kx is the same buffer started kx*d rows
-// later (SBO = 128 B between 8-pixel groups, LBO = plane stride between 8/16-channel
-// groups).  The TMA zero fill of out-of-frame pixels and rows is the "same" zero padding.
+// Activation layout in HBM ("row-planar"): [T][H][G][W][row bytes], G = C / 16 groups of
+// 16 channels; a pixel's group row is 32 bytes in BF16 and 16 bytes in FP8 e4m3.  One TMA
+// box per input row (group row x (128 + 2d, rounded up to 32) pixels x G groups) lands in
+// shared memory as G planes of [pixel][row bytes]:
+//   * BF16: 32-byte rows written with the 32-byte swizzle, the canonical SWIZZLE_32B K-major
+//     UMMA operand; one plane = one K=16 step (SBO = 256 B per 8 pixels).  The swizzle is a
+//     function of the absolute shared-memory address, so the operand of tap kx is the same
+//     plane started kx*d rows later, for any d.
+//   * FP8: 16-byte rows, the no-swizzle K-major operand with 16-byte core-matrix rows; a K=32
+//     step spans two planes (LBO = plane stride, SBO = 128 B), and a zero plane pads C=48.
+// The TMA zero fill of out-of-frame pixels and rows is the "same" zero padding.
 //
 // Work decomposition ("row classes"): the three input rows of output row i are i-d, i, i+d,
 // so rows with the same residue mod d form independent chains.  A work unit is
@@ -99,12 +101,13 @@ __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fenc
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: no swizzle, K-major.
-//   bits 0-13 start >> 4, 16-29 LBO >> 4 (K-direction core-matrix stride),
-//   32-45 SBO >> 4 (M/N-direction 8-row-group stride), 46-48 = 0b001, 61-63 swizzle = 0.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor, K-major.
+//   bits 0-13 start >> 4, 16-29 LBO >> 4 (K-direction core-matrix stride, no-swizzle only),
+//   32-45 SBO >> 4 (M/N-direction 8-row-group stride), 46-48 = 0b001, 49-51 base offset = 0,
+//   61-63 layout: 0 = no swizzle, 6 = 32-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout = 0) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
 }
 
 // Instruction descriptor: D = F32, A/B K-major, dense.  kind::f16 with BF16 inputs
@@ -144,15 +147,6 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-      : "memory");
-}
-
 // 32 lanes x 32 bits, 16 consecutive columns per thread.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
@@ -182,19 +176,17 @@ struct TcKArgs {
   int NS, NQ;          // column strips, segments per residue class
   long long units;     // T * NS * d * NQ
   uint32_t stage_bytes, plane_stride, tx_bytes;
-  int nbx;   // 512-byte boxes per plane of one input row ("wide" loads)
-  int wide;  // 1: G x nbx 512-byte boxes per row (4-D map); 0: one box per row (5-D map)
   int nstages;
   int* err;
 };
 
 template <int C, int PREC>
 struct TcCfg {
-  static constexpr int EPG = PREC == kBF16 ? 8 : 16;     // elements per 16-byte group
-  static constexpr int G = C / EPG;                       // groups stored in HBM
+  static constexpr int ROWB = PREC == kBF16 ? 32 : 16;    // bytes of one pixel's group row
+  static constexpr int G = C / 16;                        // 16-channel groups stored in HBM
   static constexpr int KSTEP = PREC == kBF16 ? 16 : 32;   // K per MMA instruction
   static constexpr int NKS = (C + KSTEP - 1) / KSTEP;     // MMAs per tap
-  static constexpr int GP = 2 * NKS;                      // planes in shared memory (FP8: zero pad)
+  static constexpr int GP = PREC == kBF16 ? G : 2 * NKS;  // planes in shared memory (FP8: zero pad)
   static constexpr int BBLK = 3 * (C / 8) * 256;          // bytes of one (kx, k-step) B block: N = 3C
   static constexpr int BIMG = 3 * NKS * BBLK;
   // S = output rows per unit: the window of S+2 input rows needs (S+1)*C + 3C <= 512 columns
@@ -298,14 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           mbar_expect_tx(fb, a.tx_bytes);
           const int row = phi + (q * SEG + kk - 1) * a.d;
           const uint32_t dst = smem_u32(s_stage + (size_t)st * a.stage_bytes);
-          if (a.wide) {  // G x nbx boxes, each one contiguous 512-byte run
-            const int x0 = 8 * (j0 - a.d);  // 16-bit elements; 16-byte aligned for any j0, d
-            for (int g = 0; g < Cfg::G; ++g)
-              for (int bx = 0; bx < a.nbx; ++bx)
-                tma_load_4d(dst + (uint32_t)g * a.plane_stride + (uint32_t)bx * 512u, &tmap, x0 + 256 * bx, g, row, t, fb);
-          } else {  // one box: (16-byte group) x plane pixels x G groups
-            tma_load_5d(dst, &tmap, 0, j0 - a.d, 0, row, t, fb);
-          }
+          tma_load_5d(dst, &tmap, 0, j0 - a.d, 0, row, t, fb);
         }
       }
       // drain: make sure no load of ours is still landing in shared memory
@@ -319,13 +304,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       // Descriptors are computed once: the start-address field (bits 0-13, 16-byte units)
       // is advanced by plain addition, which cannot carry out of the field because every
       // shared-memory address is below 256 KB.
-      const uint64_t a_desc0 = smem_desc(smem_u32(s_stage), a.plane_stride, 128u);
+      // BF16: 32-byte swizzled rows, one plane per K step; FP8: 16-byte rows, two planes per step
+      const uint64_t a_desc0 = PREC == kBF16 ? smem_desc(smem_u32(s_stage), 16u, 256u, 6u)
+                                             : smem_desc(smem_u32(s_stage), a.plane_stride, 128u);
       const uint64_t b_desc0 = smem_desc(smem_u32(s_bimg), 128u, 256u);
-      uint32_t a_off[3 * Cfg::NKS];
+      uint32_t a_off[3 * Cfg::NKS];  // in 16-byte units
 #pragma unroll
       for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
-        for (int ks = 0; ks < Cfg::NKS; ++ks) a_off[kx * Cfg::NKS + ks] = (uint32_t)(kx * a.d) + (uint32_t)ks * (a.plane_stride >> 3);
+        for (int ks = 0; ks < Cfg::NKS; ++ks)
+          a_off[kx * Cfg::NKS + ks] = PREC == kBF16 ? (uint32_t)(2 * kx * a.d) + (uint32_t)ks * (a.plane_stride >> 4)
+                                                    : (uint32_t)(kx * a.d) + (uint32_t)ks * (a.plane_stride >> 3);
       const uint32_t stage16 = a.stage_bytes >> 4;
       uint32_t stc = 0;
       uint32_t uses[SEG];
@@ -439,14 +428,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         } else if (PREC == kBF16) {
 #pragma unroll
           for (int gq = 0; gq < Cfg::G; ++gq) {
-            uint4 o;
-            uint32_t* ow = reinterpret_cast<uint32_t*>(&o);
+            uint4 o[2];
+            uint32_t* ow = reinterpret_cast<uint32_t*>(o);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * gq + 2 * e], v[8 * gq + 2 * e + 1]);
+            for (int e = 0; e < 8; ++e) {
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[16 * gq + 2 * e], v[16 * gq + 2 * e + 1]);
               ow[e] = *reinterpret_cast<uint32_t*>(&h2);
             }
-            *reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 16) = o;
+            uint4* dst = reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 32);
+            dst[0] = o[0];
+            dst[1] = o[1];
           }
         } else {
 #pragma unroll
@@ -578,9 +569,7 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   a.NQ = (rows0 + Cfg::SEG - 1) / Cfg::SEG;
   a.units = (long long)la.T * a.NS * la.d * a.NQ;
   const int boxw = tc_box_width(la.d);  // pixels per plane, a multiple of 32
-  a.nbx = boxw / 32;
-  a.wide = la.wide;
-  a.plane_stride = (uint32_t)boxw * 16u;
+  a.plane_stride = (uint32_t)boxw * Cfg::ROWB;
   a.tx_bytes = (uint32_t)Cfg::G * a.plane_stride;
   a.stage_bytes = ((uint32_t)Cfg::GP * a.plane_stride + 1023u) & ~1023u;
   a.err = la.err;
@@ -594,7 +583,7 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_dconv_tc<C, PREC, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   long long grid = a.units < (long long)num_sms ? a.units : (long long)num_sms;
-  k_dconv_tc<C, PREC, LAST><<<(unsigned)grid, kThreads, smem, s>>>(la.wide ? *la.tmap_wide : *la.tmap, a);
+  k_dconv_tc<C, PREC, LAST><<<(unsigned)grid, kThreads, smem, s>>>(*la.tmap, a);
   return cudaGetLastError();
 }
 
@@ -602,7 +591,10 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
 
 int tc_box_width(int d) { return (kTileM + 2 * d + 31) / 32 * 32; }
 
-int tc_groups(int C, int prec) { return C / (prec == kBF16 ? 8 : 16); }
+int tc_groups(int C, int prec) {
+  (void)prec;
+  return C / 16;
+}
 
 size_t tc_bimg_bytes(int C, int prec) {
   const int kstep = prec == kBF16 ? 16 : 32;

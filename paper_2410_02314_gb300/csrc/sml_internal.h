@@ -45,7 +45,7 @@ struct CamArgs {
 
 // --- layer 1: camera transform + Cin=1 dilated 3x3 conv, bias, ReLU -------------------
 // prec kFP32 writes float NHWC [T][H][W][C]; kBF16 / kFP8 write row-planar activations
-// [T][H][C/g][W][16 bytes] (g = 8 bf16 or 16 e4m3 channels per group).  out_scale
+// [T][H][C/16][W][row bytes] (16 channels per group: 32-byte bf16 rows, 16-byte e4m3 rows).  out_scale
 // multiplies the FP8 output before rounding (1 / activation scale).  w1 [C][9] and b1 [C]
 // are HOST pointers (the weights are passed to the kernel by value).
 cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1,
@@ -63,10 +63,8 @@ cudaError_t launch_dconv_f32_heads(const float* in, const float* w, const float*
 
 // --- tensor-core path (row-planar activations) -------------------------------------
 struct TcLayerArgs {
-  const CUtensorMap* tmap;       // input activations, one box per row (5-D map for this dilation)
-  const CUtensorMap* tmap_wide;  // input activations, 512-byte boxes (4-D map)
-  int wide;                      // use tmap_wide
-  int stages;                    // TMA ring depth (0 = as many as shared memory allows)
+  const CUtensorMap* tmap;  // input activations, one box per row (5-D map for this dilation)
+  int stages;               // TMA ring depth (0 = as many as shared memory allows)
   const void* bimg;         // device: packed B operand image for this layer
   const float* bias;        // HOST [C] (passed to the kernel by value)
   const float* deq;         // HOST [C] per-output-channel dequant factor (FP8) or NULL

@@ -176,10 +176,10 @@ def test_ragged_frames_multi_chunk_and_scmos(prec):
     assert recs.tobytes() == want.tobytes()
 
 
-@pytest.mark.parametrize("tma_box,stages", [("row", 0), ("wide", 0), ("row", 3)])
-def test_dilation_larger_than_tile_margin(tma_box, stages):
-    """Dilations up to 64 (TMA box 256 pixels) and a frame narrower than the dilation, for
-    both TMA load modes and a shallow ring."""
+@pytest.mark.parametrize("stages", [0, 3])
+def test_dilation_larger_than_tile_margin(stages):
+    """Dilations up to 64 (TMA box 256 pixels) and a frame narrower than the dilation, with
+    the deepest and a shallow TMA ring."""
     import json
 
     rng = np.random.default_rng(8)
@@ -187,7 +187,7 @@ def test_dilation_larger_than_tile_margin(tma_box, stages):
     blob = synth.pack_blob(spec, synth.init_weights(spec, 5))
     frames = rng.integers(100, 600, (2, 90, 40)).astype(np.uint16)
     cam = synth.Camera(1.0, 100.0)
-    js = json.dumps(dict(json.loads(spec.to_json()), tma_box=tma_box, tc_stages=stages))
+    js = json.dumps(dict(json.loads(spec.to_json()), tc_stages=stages))
     loc, maps, logits = gpu_maps(js, blob, frames, cam)
     check_quantized("bf16", js, blob, frames, cam, maps, logits)
 
