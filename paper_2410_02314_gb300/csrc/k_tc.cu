@@ -81,8 +81,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
 
 // Bounded wait for the phase with the given parity.  Fails fast once any role of the CTA
 // has given up (abort flag in shared memory).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
-  if (mbar_try_wait(bar, parity)) return true;
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
   unsigned long long t0 = gtimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -95,6 +94,10 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, volatile int*
       }
     }
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
+  return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, err, abort_flag);
 }
 
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -174,7 +177,7 @@ struct TcKArgs {
   float* logits;
   int T, H, W, d;
   int NS, NQ;          // column strips, segments per residue class
-  long long units;     // T * NS * d * NQ
+  uint32_t units;      // T * NS * d * NQ
   uint32_t stage_bytes, plane_stride, tx_bytes;
   int nstages;
   int* err;
@@ -197,17 +200,20 @@ struct TcCfg {
   static constexpr uint32_t IDESC3 = instr_desc(PREC, kTileM, 3 * C);
 };
 
-// Unit -> (t, strip, phi, q); returns the number of valid output rows (<= seg).
-__device__ __forceinline__ int unit_rows(const TcKArgs& a, long long u, int seg, int& t, int& j0, int& phi, int& q) {
-  q = (int)(u % a.NQ);
-  long long r = u / a.NQ;
-  phi = (int)(r % a.d);
-  r /= a.d;
-  int s = (int)(r % a.NS);
-  t = (int)(r / a.NS);
+// Unit -> (t, strip, phi, q); returns the number of valid output rows (<= seg).  32-bit
+// arithmetic (unit counts stay far below 2^31).
+__device__ __forceinline__ int unit_rows(const TcKArgs& a, uint32_t u, int seg, int& t, int& j0, int& phi, int& q) {
+  const uint32_t nq = (uint32_t)a.NQ, d = (uint32_t)a.d, ns = (uint32_t)a.NS;
+  uint32_t r = u / nq;
+  q = (int)(u - r * nq);
+  uint32_t r2 = r / d;
+  phi = (int)(r - r2 * d);
+  uint32_t r3 = r2 / ns;
+  const int s = (int)(r2 - r3 * ns);
+  t = (int)r3;
   j0 = s * kTileM;
-  int n_class = phi < a.H ? (a.H - phi + a.d - 1) / a.d : 0;
-  int n = n_class - q * seg;
+  const int n_class = phi < a.H ? (a.H - phi + a.d - 1) / a.d : 0;
+  const int n = n_class - q * seg;
   return n < 0 ? 0 : (n > seg ? seg : n);
 }
 
@@ -275,28 +281,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
-      uint32_t stc = 0;
+      const uint32_t nst = (uint32_t)a.nstages;
+      uint32_t st = 0, ph = 0, issued = 0;  // stage, phase of its current use, loads issued
       bool ok = true;
-      for (long long u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+      for (uint32_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
         int t, j0, phi, q;
-        int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
-        for (int kk = 0; kk < n_out + 2 && n_out > 0; ++kk, ++stc) {
-          uint32_t st = stc % a.nstages, use = stc / a.nstages;
-          if (use > 0 && !mbar_wait(smem_u32(&empty_bar[st]), (use - 1) & 1, a.err, s_abort)) {
+        const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
+        for (int kk = 0; kk < n_out + 2 && n_out > 0; ++kk) {
+          // the slot was released by the MMA that read its previous load (skip on first use)
+          if (issued >= nst && !mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1u, a.err, s_abort)) {
             ok = false;
             break;
           }
-          uint32_t fb = smem_u32(&full_bar[st]);
+          const uint32_t fb = smem_u32(&full_bar[st]);
           mbar_expect_tx(fb, a.tx_bytes);
           const int row = phi + (q * SEG + kk - 1) * a.d;
-          const uint32_t dst = smem_u32(s_stage + (size_t)st * a.stage_bytes);
-          tma_load_5d(dst, &tmap, 0, j0 - a.d, 0, row, t, fb);
+          tma_load_5d(smem_u32(s_stage + (size_t)st * a.stage_bytes), &tmap, 0, j0 - a.d, 0, row, t, fb);
+          ++issued;
+          if (++st == nst) {
+            st = 0;
+            ph ^= 1u;
+          }
         }
       }
       // drain: make sure no load of ours is still landing in shared memory
-      uint32_t first = stc > (uint32_t)a.nstages ? stc - a.nstages : 0;
-      for (uint32_t k = first; k < stc; ++k)
-        mbar_wait(smem_u32(&full_bar[k % a.nstages]), (k / a.nstages) & 1, a.err, s_abort);
+      const uint32_t n_drain = issued < nst ? issued : nst;
+      for (uint32_t k = 0; k < n_drain; ++k) {
+        // walk back over the last n_drain loads: stage st-1-k with its phase
+        const uint32_t back = k + 1;
+        const uint32_t s2 = (st + nst - (back % nst)) % nst;
+        const uint32_t p2 = (back > st) ? (ph ^ 1u) : ph;
+        mbar_wait(smem_u32(&full_bar[s2]), p2, a.err, s_abort);
+      }
     }
   } else if (warp == 5) {
     // ------------------------------------------------------------ MMA issuer
@@ -316,18 +332,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           a_off[kx * Cfg::NKS + ks] = PREC == kBF16 ? (uint32_t)(2 * kx * a.d) + (uint32_t)ks * (a.plane_stride >> 4)
                                                     : (uint32_t)(kx * a.d) + (uint32_t)ks * (a.plane_stride >> 3);
       const uint32_t stage16 = a.stage_bytes >> 4;
-      uint32_t stc = 0;
-      uint32_t uses[SEG];
-#pragma unroll
-      for (int k = 0; k < SEG; ++k) uses[k] = 0;
+      const uint32_t nst = (uint32_t)a.nstages;
+      uint32_t st = 0, ph = 0;                   // stage and the phase its full barrier is in
+      uint64_t a_st = a_desc0;                   // descriptor of the current stage
+      uint32_t used = 0, par = 0;                // row positions used before / parity of their last use
       bool ok = true, issued = false;
-      for (long long u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+      for (uint32_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
         int t, j0, phi, q;
-        int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
+        const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
         if (n_out == 0) continue;
-        for (int kk = 0; kk < n_out + 2 && ok; ++kk, ++stc) {
-          uint32_t st = stc % a.nstages;
-          if (!mbar_wait(smem_u32(&full_bar[st]), (stc / a.nstages) & 1, a.err, s_abort)) {
+        for (int kk = 0; kk < n_out + 2 && ok; ++kk) {
+          if (!mbar_wait(smem_u32(&full_bar[st]), ph, a.err, s_abort)) {
             ok = false;
             break;
           }
@@ -336,19 +351,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           const int b_lo = kk - n_out + 1 > 0 ? kk - n_out + 1 : 0;
           const int b_hi = kk < 2 ? kk : 2;
           const int nb = b_hi - b_lo + 1;
-          if (b_lo == 0) {  // this input row starts output row kk: its columns must be drained
-            uint32_t use = 0;
-#pragma unroll
-            for (int k = 0; k < SEG; ++k) use = (k == kk) ? uses[k] : use;
-            if (use > 0) {
-              if (!mbar_wait(smem_u32(&acce_bar[kk]), (use - 1) & 1, a.err, s_abort)) {
-                ok = false;
-                break;
-              }
-              fence_after_sync();
+          if (b_lo == 0 && ((used >> kk) & 1u)) {  // row kk's columns must be drained first
+            if (!mbar_wait(smem_u32(&acce_bar[kk]), (par >> kk) & 1u, a.err, s_abort)) {
+              ok = false;
+              break;
             }
+            fence_after_sync();
           }
-          const uint64_t a_st = a_desc0 + (uint64_t)(st * stage16);
           const uint32_t d_col = tmem + Cfg::BASE0 - (uint32_t)(C * kk) + (uint32_t)(C * b_lo);
           const uint32_t b_sub = (uint32_t)(2 * C * b_lo);  // 32*C*b_lo bytes in 16-byte units
           const uint32_t idesc_n = nb == 3 ? Cfg::IDESC3 : (nb == 2 ? Cfg::IDESC2 : Cfg::IDESC1);
@@ -369,9 +378,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           issued = true;
           if (kk >= 2 && kk - 2 < n_out) umma_commit(smem_u32(&accf_bar[kk - 2]));
           umma_commit(smem_u32(&empty_bar[st]));
+          if (++st == nst) {
+            st = 0;
+            ph ^= 1u;
+            a_st = a_desc0;
+          } else {
+            a_st += stage16;
+          }
         }
-#pragma unroll
-        for (int k = 0; k < SEG; ++k) uses[k] += (k < n_out) ? 1u : 0u;
+        // positions 0..n_out-1 were used once more: flip the parity of those used before
+        const uint32_t m = (1u << n_out) - 1u;
+        par ^= m & used;
+        used |= m;
       }
       if (issued) {  // all MMAs of this CTA complete before TMEM is released
         umma_commit(smem_u32(&drain_bar[0]));
@@ -382,20 +400,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     // ------------------------------------------------------------ epilogue (warps 0-3)
     const int m = warp * 32 + lane;  // TMEM lane = pixel within the strip
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    uint32_t uses[SEG];
-#pragma unroll
-    for (int k = 0; k < SEG; ++k) uses[k] = 0;
+    uint32_t fpar = 0;  // per row position: phase of its acc_full barrier for the next use
     bool ok = true;
     const size_t plane = (size_t)a.H * a.W;
-    for (long long u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+    for (uint32_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
       int t, j0, phi, q;
-      int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
+      const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
 #pragma unroll 1
       for (int k = 0; k < n_out; ++k) {
-        uint32_t use = 0;
-#pragma unroll
-        for (int kq = 0; kq < SEG; ++kq) use = (kq == k) ? uses[kq] : use;
-        if (!mbar_wait(smem_u32(&accf_bar[k]), use & 1, a.err, s_abort)) {
+        if (!mbar_wait(smem_u32(&accf_bar[k]), (fpar >> k) & 1u, a.err, s_abort)) {
           ok = false;
           break;
         }
@@ -453,8 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           }
         }
       }
-#pragma unroll
-      for (int k = 0; k < SEG; ++k) uses[k] += (k < n_out) ? 1u : 0u;
+      fpar ^= (1u << n_out) - 1u;
     }
   }
 
@@ -567,7 +579,9 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   a.NS = (la.W + kTileM - 1) / kTileM;
   int rows0 = (la.H + la.d - 1) / la.d;
   a.NQ = (rows0 + Cfg::SEG - 1) / Cfg::SEG;
-  a.units = (long long)la.T * a.NS * la.d * a.NQ;
+  const long long units = (long long)la.T * a.NS * la.d * a.NQ;
+  if (units >= (1LL << 31)) return cudaErrorInvalidValue;
+  a.units = (uint32_t)units;
   const int boxw = tc_box_width(la.d);  // pixels per plane, a multiple of 32
   a.plane_stride = (uint32_t)boxw * Cfg::ROWB;
   a.tx_bytes = (uint32_t)Cfg::G * a.plane_stride;
@@ -582,7 +596,7 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   if (smem > budget) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_dconv_tc<C, PREC, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  long long grid = a.units < (long long)num_sms ? a.units : (long long)num_sms;
+  long long grid = (long long)a.units < (long long)num_sms ? (long long)a.units : (long long)num_sms;
   k_dconv_tc<C, PREC, LAST><<<(unsigned)grid, kThreads, smem, s>>>(*la.tmap, a);
   return cudaGetLastError();
 }
