@@ -31,9 +31,8 @@
 // k-step ascending), so the result does not depend on scheduling, grid size or batch
 // composition.
 //
-// Warp roles (320 threads): warps 0-7 epilogue (TMEM lane quarter = warp % 4; warp / 4 picks
-// half of the channels, or of the heads in the last layer), warp 8 TMA producer, warp 9 TMEM
-// allocator and MMA issuer.  Every mbarrier wait is bounded: on
+// Warp roles (192 threads): warps 0-3 epilogue (TMEM lane quarter = warp index), warp 4 TMA
+// producer, warp 5 TMEM allocator and MMA issuer.  Every mbarrier wait is bounded: on
 // timeout the kernel sets *err, stops issuing, drains its own MMAs and TMA loads (bounded),
 // frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -45,10 +44,8 @@ namespace sml {
 
 namespace {
 
-constexpr int kEpiWarps = 8;   // two warps per TMEM lane quarter, each half of the channels
-constexpr int kProducerWarp = 8;
-constexpr int kMmaWarp = 9;
-constexpr int kThreads = 320;
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = 192;
 constexpr int kTmemCols = 512;
 constexpr int kMaxSeg = 6;
 constexpr int kMaxStages = 16;
@@ -164,15 +161,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
-// 32 lanes x 32 bits, 8 consecutive columns per thread.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-#pragma unroll
-  for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
-}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Kernel arguments; bias, dequantisation factors and head weights travel by value so the
@@ -276,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       *s_abort = 0;
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kMmaWarp) {
+    if (warp == 5) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void*)s_tmem)),
                    "r"(kTmemCols)
                    : "memory");
@@ -289,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
   }
   const uint32_t tmem = *s_tmem;
 
-  if (warp == kProducerWarp) {
+  if (warp == 4) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
@@ -326,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         mbar_wait(smem_u32(&full_bar[s2]), p2, a.err, s_abort);
       }
     }
-  } else if (warp == kMmaWarp) {
+  } else if (warp == 5) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       // Descriptors are computed once: the start-address field (bits 0-13, 16-byte units)
@@ -409,11 +397,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       }
     }
   } else {
-    // ------------------------------------------------------------ epilogue (warps 0-7)
-    const int quarter = warp & 3, half = warp >> 2;
-    constexpr int HC = C / 2;        // channels per half
-    const int m = quarter * 32 + lane;  // TMEM lane = pixel within the strip
-    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    // ------------------------------------------------------------ epilogue (warps 0-3)
+    const int m = warp * 32 + lane;  // TMEM lane = pixel within the strip
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
     uint32_t fpar = 0;  // per row position: phase of its acc_full barrier for the next use
     bool ok = true;
     const size_t plane = (size_t)a.H * a.W;
@@ -427,15 +413,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           break;
         }
         fence_after_sync();
-        // LAST: both halves read every channel (each computes some of the heads);
-        // otherwise each half reads and stores its own channels.
-        constexpr int NV = LAST ? C : HC;
-        const int c0 = LAST ? 0 : half * HC;
-        float v[NV];
-        const uint32_t col = Cfg::BASE0 - (uint32_t)(C * k) + (uint32_t)c0;
+        float v[C];
+        const uint32_t col = Cfg::BASE0 - (uint32_t)(C * k);
 #pragma unroll
-        for (int c = 0; c + 16 <= NV; c += 16) tmem_ld16(lane_addr + col + c, v + c);
-        if (NV % 16) tmem_ld8(lane_addr + col + (NV / 16) * 16, v + (NV / 16) * 16);
+        for (int c = 0; c < C; c += 16) tmem_ld16(lane_addr + col + c, v + c);
         tmem_ld_wait();
         fence_before_sync();
         mbar_arrive(smem_u32(&acce_bar[k]));
@@ -443,15 +424,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         const int j = j0 + m;
         if (j >= a.W) continue;
 #pragma unroll
-        for (int c = 0; c < NV; ++c)
-          v[c] = fmaxf(PREC == kFP8 ? fmaf(v[c], a.deq[c0 + c], a.bias[c0 + c]) : v[c] + a.bias[c0 + c], 0.0f);
+        for (int c = 0; c < C; ++c) v[c] = fmaxf(PREC == kFP8 ? fmaf(v[c], a.deq[c], a.bias[c]) : v[c] + a.bias[c], 0.0f);
         if (LAST) {
           const size_t px = (size_t)i * a.W + j;
-          // half 0: heads 0 (p), 1, 2; half 1: heads 3, 4
 #pragma unroll
-          for (int hh = 0; hh < 3; ++hh) {
-            const int h = half == 0 ? hh : 3 + hh;
-            if (h >= kHeads) break;
+          for (int h = 0; h < kHeads; ++h) {
             float acc = a.head_b[h];
 #pragma unroll
             for (int c = 0; c < C; ++c) acc = fmaf(a.head_w[h * C + c], v[c], acc);
@@ -462,32 +439,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
             a.maps[((size_t)t * kHeads + h) * plane + px] = acc;
           }
         } else if (PREC == kBF16) {
-          // 8-channel pieces (16 bytes) of the 32-byte group rows
 #pragma unroll
-          for (int pc = 0; pc < NV / 8; ++pc) {
-            const int ch = c0 + 8 * pc, gq = ch / 16, off = (ch % 16) * 2;
-            uint4 o;
-            uint32_t* ow = reinterpret_cast<uint32_t*>(&o);
+          for (int gq = 0; gq < Cfg::G; ++gq) {
+            uint4 o[2];
+            uint32_t* ow = reinterpret_cast<uint32_t*>(o);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * pc + 2 * e], v[8 * pc + 2 * e + 1]);
+            for (int e = 0; e < 8; ++e) {
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[16 * gq + 2 * e], v[16 * gq + 2 * e + 1]);
               ow[e] = *reinterpret_cast<uint32_t*>(&h2);
             }
-            *reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 32 + off) = o;
+            uint4* dst = reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 32);
+            dst[0] = o[0];
+            dst[1] = o[1];
           }
         } else {
-          // 8-channel pieces (8 bytes) of the 16-byte e4m3 group rows
 #pragma unroll
-          for (int pc = 0; pc < NV / 8; ++pc) {
-            const int ch = c0 + 8 * pc, gq = ch / 16, off = ch % 16;
-            uint2 o;
+          for (int gq = 0; gq < Cfg::G; ++gq) {
+            uint4 o;
             uint16_t* oh = reinterpret_cast<uint16_t*>(&o);
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
+            for (int e = 0; e < 8; ++e)
               oh[e] = __nv_cvt_float2_to_fp8x2(
-                  make_float2(v[8 * pc + 2 * e] * a.out_inv_scale, v[8 * pc + 2 * e + 1] * a.out_inv_scale),
+                  make_float2(v[16 * gq + 2 * e] * a.out_inv_scale, v[16 * gq + 2 * e + 1] * a.out_inv_scale),
                   __NV_SATFINITE, __NV_E4M3);
-            *reinterpret_cast<uint2*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 16 + off) = o;
+            *reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 16) = o;
           }
         }
       }
@@ -497,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
 
   fence_before_sync();
   __syncthreads();
-  if (warp == kMmaWarp) {
+  if (warp == 5) {
     fence_after_sync();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
