@@ -26,8 +26,9 @@
 // D columns are the three rows' accumulators: output row k of a unit accumulates at TMEM
 // column base0 - C*k, a window that slides down by C columns per input row.  Blocks that
 // would belong to rows outside the unit are not issued (N shrinks to C or 2C at the unit's
-// edges), and the first MMA of a row is split so that its own block starts from zero while
-// the older rows keep accumulating.  Accumulation order inside a row is fixed (ky, kx,
+// edges).  Every MMA accumulates: the epilogue, right after reading a row's accumulator,
+// writes the layer's bias into those columns (FP8: bias / dequantisation factor), so each
+// row starts from its bias.  Accumulation order inside a row is fixed (bias, then ky, kx,
 // k-step ascending), so the result does not depend on scheduling, grid size or batch
 // composition.
 //
@@ -150,6 +151,13 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// max(x, 0) of two floats rounded to bf16 (round to nearest even) and packed, low half = lo.
+__device__ __forceinline__ uint32_t bf16x2_relu(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
 // 32 lanes x 32 bits, 16 consecutive columns per thread.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
@@ -161,6 +169,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
+// 32 lanes x 32 bits, 16 consecutive columns per thread (store).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Kernel arguments; bias, dequantisation factors and head weights travel by value so the
@@ -276,6 +293,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     fence_after_sync();
   }
   const uint32_t tmem = *s_tmem;
+  // accumulator start values: every row position holds the bias (in accumulator units)
+  float acc0[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) acc0[c] = PREC == kFP8 ? a.bias[c] / a.deq[c] : a.bias[c];
+  if (warp < kEpiWarps) {
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int k = 0; k < SEG; ++k)
+#pragma unroll
+      for (int c = 0; c < C; c += 16) tmem_st16(lane_addr + Cfg::BASE0 - (uint32_t)(C * k) + c, acc0 + c);
+    tmem_st_wait();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
 
   if (warp == 4) {
     // ------------------------------------------------------------ TMA producer
@@ -367,13 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
             for (int ks = 0; ks < Cfg::NKS; ++ks) {
               const uint64_t ad = a_st + a_off[kx * Cfg::NKS + ks];
               const uint64_t bd = b_desc0 + (uint64_t)(((kx * Cfg::NKS + ks) * Cfg::BBLK) >> 4) + b_sub;
-              if (kx == 0 && ks == 0 && b_lo == 0) {
-                umma<PREC>(d_col, ad, bd, Cfg::IDESC1, 0u);  // own block starts from zero
-                if (nb > 1)                                  // older rows keep accumulating
-                  umma<PREC>(d_col + C, ad, bd + (uint64_t)(2 * C), nb == 3 ? Cfg::IDESC2 : Cfg::IDESC1, 1u);
-              } else {
-                umma<PREC>(d_col, ad, bd, idesc_n, 1u);
-              }
+              umma<PREC>(d_col, ad, bd, idesc_n, 1u);
             }
           issued = true;
           if (kk >= 2 && kk - 2 < n_out) umma_commit(smem_u32(&accf_bar[kk - 2]));
@@ -418,13 +443,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
 #pragma unroll
         for (int c = 0; c < C; c += 16) tmem_ld16(lane_addr + col + c, v + c);
         tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < C; c += 16) tmem_st16(lane_addr + col + c, acc0 + c);  // next use starts at the bias
+        tmem_st_wait();
         fence_before_sync();
         mbar_arrive(smem_u32(&acce_bar[k]));
         const int i = phi + (q * SEG + k) * a.d;
         const int j = j0 + m;
         if (j >= a.W) continue;
+        // the accumulator already holds the bias; FP8 dequantises, the BF16 path fuses the ReLU
+        // into its conversion
+        if (PREC == kFP8) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) v[c] = fmaxf(PREC == kFP8 ? fmaf(v[c], a.deq[c], a.bias[c]) : v[c] + a.bias[c], 0.0f);
+          for (int c = 0; c < C; ++c) v[c] *= a.deq[c];
+        }
+        if (LAST || PREC == kFP8) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) v[c] = fmaxf(v[c], 0.0f);
+        }
         if (LAST) {
           const size_t px = (size_t)i * a.W + j;
 #pragma unroll
@@ -444,10 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
             uint4 o[2];
             uint32_t* ow = reinterpret_cast<uint32_t*>(o);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[16 * gq + 2 * e], v[16 * gq + 2 * e + 1]);
-              ow[e] = *reinterpret_cast<uint32_t*>(&h2);
-            }
+            for (int e = 0; e < 8; ++e) ow[e] = bf16x2_relu(v[16 * gq + 2 * e], v[16 * gq + 2 * e + 1]);
             uint4* dst = reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 32);
             dst[0] = o[0];
             dst[1] = o[1];
