@@ -373,11 +373,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
         if (n_out == 0) continue;
         for (int kk = 0; kk < n_out + 2 && ok; ++kk) {
+          // TMA data is visible to the MMA once the barrier's transaction count completes
+          // (async proxy on both sides): no tcgen05 fence is needed after this wait
           if (!mbar_wait(smem_u32(&full_bar[st]), ph, a.err, s_abort)) {
             ok = false;
             break;
           }
-          fence_after_sync();
           // blocks b (output rows kk-b) of this input row that belong to the unit
           const int b_lo = kk - n_out + 1 > 0 ? kk - n_out + 1 : 0;
           const int b_hi = kk < 2 ? kk : 2;
