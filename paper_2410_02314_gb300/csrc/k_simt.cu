@@ -26,18 +26,45 @@ __device__ __forceinline__ float cam_input(const uint16_t* __restrict__ f, int H
   return __fmul_rn(__fdiv_rn(__fsub_rn((float)f[px], o), g), cam.in_scale);
 }
 
-// Layer-1 weights (passed by value, staged into shared memory by each block).
+// Layer-1 weights by value: the FMAs read them straight from the constant bank.
 struct L1Params {
   float w[64 * 9];  // [co][ky*3+kx]
   float b[64];
 };
 
-constexpr int kL1Threads = 128;
-constexpr int kL1Px = 2;                        // pixels per thread
-constexpr int kL1Tile = kL1Threads * kL1Px;     // pixels of one image row per block
+constexpr int kL1Tile = 128;  // pixels of one image row per block
 
+// OUT: 0 = float NHWC, 1 = bf16 row-planar (16 ch / 32 B), 2 = e4m3 row-planar (16 ch / 16 B).
+// One block = 128 consecutive pixels of one row; the three dilated input rows (with a d-pixel
+// margin) are converted to network inputs once, into shared memory.
 template <int C, int OUT>
-__device__ __forceinline__ void l1_store(const float* a, void* out, int t, int H, int W, int i, int j, float out_scale) {
+__global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restrict__ frames, int H, int W, int d,
+                                                       int t0, CamArgs cam, const __grid_constant__ L1Params prm,
+                                                       float out_scale, void* __restrict__ out) {
+  __shared__ float xs[3][kL1Tile + 2 * 64];
+  const int j0 = blockIdx.x * kL1Tile, i = blockIdx.y, t = t0 + blockIdx.z;
+  const int span = kL1Tile + 2 * d;
+  const uint16_t* f = frames + (size_t)t * H * W;
+  for (int k = threadIdx.x; k < 3 * span; k += kL1Tile) {
+    int r = k / span, c = k - r * span;
+    xs[r][c] = cam_input(f, H, W, i + (r - 1) * d, j0 - d + c, cam);
+  }
+  __syncthreads();
+  const int j = j0 + threadIdx.x;
+  if (j >= W) return;
+  float x[9];
+#pragma unroll
+  for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xs[ky][threadIdx.x + kx * d];
+  float a[C];
+#pragma unroll
+  for (int co = 0; co < C; ++co) {
+    float s = prm.b[co];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s = fmaf(prm.w[co * 9 + k], x[k], s);
+    a[co] = fmaxf(s, 0.0f);
+  }
   const size_t q = ((size_t)t * H + i) * W + j;
   if (OUT == 0) {
     float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + q * C);
@@ -73,63 +100,6 @@ __device__ __forceinline__ void l1_store(const float* a, void* out, int t, int H
       size_t off = ((((size_t)t * H + i) * G + g) * W + j) * 16;
       *reinterpret_cast<uint4*>(base + off) = v;
     }
-  }
-}
-
-// OUT: 0 = float NHWC, 1 = bf16 row-planar (16 ch / 32 B), 2 = e4m3 row-planar (16 ch / 16 B).
-// One block = 256 consecutive pixels of one row, 2 per thread (j0 + tid and j0 + tid + 128, so
-// each warp's stores stay contiguous); the three dilated input rows (with a d-pixel margin)
-// are converted to network inputs once, into shared memory, and each 4-channel weight read
-// (a broadcast) feeds 8 FMAs.
-template <int C, int OUT>
-__global__ void __launch_bounds__(kL1Threads) k_ingest_l1(const uint16_t* __restrict__ frames, int H, int W, int d,
-                                                          int t0, CamArgs cam, const __grid_constant__ L1Params prm,
-                                                          float out_scale, void* __restrict__ out) {
-  __shared__ float xs[3][kL1Tile + 2 * 64];
-  __shared__ __align__(16) float sw[9][C];  // [tap][co]
-  __shared__ float sb[C];
-  const int j0 = blockIdx.x * kL1Tile, i = blockIdx.y, t = t0 + blockIdx.z;
-  const int span = kL1Tile + 2 * d;
-  const uint16_t* f = frames + (size_t)t * H * W;
-  for (int k = threadIdx.x; k < 3 * span; k += kL1Threads) {
-    int r = k / span, c = k - r * span;
-    xs[r][c] = cam_input(f, H, W, i + (r - 1) * d, j0 - d + c, cam);
-  }
-  for (int k = threadIdx.x; k < 9 * C; k += kL1Threads) sw[k % 9][k / 9] = prm.w[k];
-  for (int k = threadIdx.x; k < C; k += kL1Threads) sb[k] = prm.b[k];
-  __syncthreads();
-  float acc[kL1Px][C];
-#pragma unroll
-  for (int p = 0; p < kL1Px; ++p)
-#pragma unroll
-    for (int co = 0; co < C; ++co) acc[p][co] = sb[co];
-#pragma unroll
-  for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-    for (int kx = 0; kx < 3; ++kx) {
-      float x[kL1Px];
-#pragma unroll
-      for (int p = 0; p < kL1Px; ++p) x[p] = xs[ky][threadIdx.x + p * kL1Threads + kx * d];
-      const float4* w4 = reinterpret_cast<const float4*>(sw[ky * 3 + kx]);
-#pragma unroll
-      for (int c4 = 0; c4 < C / 4; ++c4) {
-        const float4 w = w4[c4];
-#pragma unroll
-        for (int p = 0; p < kL1Px; ++p) {
-          acc[p][4 * c4 + 0] = fmaf(w.x, x[p], acc[p][4 * c4 + 0]);
-          acc[p][4 * c4 + 1] = fmaf(w.y, x[p], acc[p][4 * c4 + 1]);
-          acc[p][4 * c4 + 2] = fmaf(w.z, x[p], acc[p][4 * c4 + 2]);
-          acc[p][4 * c4 + 3] = fmaf(w.w, x[p], acc[p][4 * c4 + 3]);
-        }
-      }
-    }
-#pragma unroll
-  for (int p = 0; p < kL1Px; ++p) {
-    const int j = j0 + threadIdx.x + p * kL1Threads;
-    if (j >= W) continue;
-#pragma unroll
-    for (int co = 0; co < C; ++co) acc[p][co] = fmaxf(acc[p][co], 0.0f);
-    l1_store<C, OUT>(acc[p], out, t, H, W, i, j, out_scale);
   }
 }
 
@@ -233,7 +203,7 @@ cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d,
   memcpy(prm.w, w1, sizeof(float) * C * 9);
   memcpy(prm.b, b1, sizeof(float) * C);
   for (int t0 = 0; t0 < T; t0 += 65535) {
-    dim3 grid((W + kL1Tile - 1) / kL1Tile, H, (unsigned)(T - t0 < 65535 ? T - t0 : 65535)), block(kL1Threads);
+    dim3 grid((W + kL1Tile - 1) / kL1Tile, H, (unsigned)(T - t0 < 65535 ? T - t0 : 65535)), block(kL1Tile);
 #define SML_L1(CC)                                                                                       \
   case CC:                                                                                               \
     if (prec == kFP32)                                                                                   \
