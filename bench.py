@@ -335,10 +335,15 @@ def main():
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         peak_note = "fp32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz (derived, not measured)"
     traffic = profiled_traffic(args.precision)
+    hbm = None
+    if traffic is not None:
+        hbm = {"achieved_gbs": traffic / avg_conv_s / 1e9, "peak_gbs": pk["hbm_gbs"],
+               "frac": traffic / avg_conv_s / 1e9 / pk["hbm_gbs"]}
     roofline = {"bound": "tensor" if args.precision != "fp32" else "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "kernel": "k_dconv_tc (middle layers)"
                 if args.precision != "fp32" else "k_dconv_f32 (middle layers)", "peak_kind": peak_note,
-                "flops_per_launch": flops_launch, "launches": conv_n, "avg_launch_ms": avg_conv_s * 1000}
+                "flops_per_launch": flops_launch, "launches": conv_n, "avg_launch_ms": avg_conv_s * 1000,
+                "hbm": hbm}
     breakdown = {"layer1_ms": l1_ms / args.steps, "conv_ms": conv_ms / args.steps,
                  "conv_heads_ms": heads_ms / args.steps, "decode_ms": dec_ms / args.steps}
 
