@@ -232,11 +232,10 @@ def main():
 
     import __graft_entry__
     import paper_2410_02314_gb300 as sml
-    from paper_2410_02314_gb300 import synth
+    from paper_2410_02314_gb300 import replicas, synth
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ri = replicas.rank_info()
+    rank, world, local = ri.rank, ri.world, ri.local
     if rank == 0:
         __graft_entry__.build()
     dist = None
@@ -250,7 +249,8 @@ def main():
     dev = torch.device("cuda", local)
 
     def workload(prec, d_frames=None):
-        w = synth.workload_batched(T=T_FRAMES, H=H, W=W, precision="bf16" if prec == "fp8" else prec, seed=3 + rank)
+        w = synth.workload_batched(T=T_FRAMES, H=H, W=W, precision="bf16" if prec == "fp8" else prec,
+                                  seed=replicas.frame_seed(3, rank))
         spec = json.loads(w.spec.to_json())
         if args.chunk_px:
             spec["chunk_px"] = args.chunk_px
@@ -297,20 +297,10 @@ def main():
 
     clk = ClockSampler(local)
     clk.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    times = timed(args.steps, profile=True)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    times = replicas.timed_region(lambda: timed(args.steps, profile=True), dist, torch.cuda.synchronize)
     clocks = clk.stop()
-    ms = statistics.mean(times)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * T_FRAMES / (ms / 1000.0)
+    ms = replicas.max_over_ranks(statistics.mean(times), dist, dev)
+    value = replicas.whole_job_rate(T_FRAMES, ms / 1000.0, world)
 
     # dominant kernel: the middle-layer tensor-core (or FP32) conv, timed on its stream
     conv_ms, conv_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_CONV)
@@ -350,17 +340,21 @@ def main():
     # end to end through the synchronous C-ABI call with host buffers
     host_frames = torch.from_numpy(w.frames).pin_memory()
     host_out = torch.empty(cap * 24, dtype=torch.uint8).pin_memory()
-    e2e_times = []
-    for k in range(args.warmup + args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        recs = sml.sml_localize(loc.ctx, host_frames, P_MIN, gain=w.cam.gain, offset=w.cam.offset, out=host_out)
-        el = time.perf_counter() - t0
-        if k >= args.warmup:
-            e2e_times.append(el)
-    e2e_s = statistics.mean(e2e_times)
-    e2e = {"value": world * T_FRAMES / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": int(w.frames.nbytes),
+    def e2e_run():
+        out = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = sml.sml_localize(loc.ctx, host_frames, P_MIN, gain=w.cam.gain, offset=w.cam.offset, out=host_out)
+            el = time.perf_counter() - t0
+            if k >= args.warmup:
+                out.append(el)
+        return out, r
+
+    e2e_times, recs = replicas.timed_region(e2e_run, dist, torch.cuda.synchronize)
+    e2e_s = replicas.max_over_ranks(statistics.mean(e2e_times), dist, dev)
+    e2e = {"value": replicas.whole_job_rate(T_FRAMES, e2e_s, world), "unit": "frames/s", "h2d_bytes_per_step": int(w.frames.nbytes),
            "d2h_bytes_per_step": int(recs.numel() + 8)}
 
     extra = {}
