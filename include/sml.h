@@ -81,7 +81,7 @@ typedef struct {
  *   "fp8" (e4m3 activations and weights, FP32 accumulation; needs "act_scales": one
  *   positive float per conv layer, the scale of that layer's input activations).
  *   Optional tuning: "chunk_px": pixels per device chunk (default 2^24); "tc_stages": TMA
- *   ring depth of the tensor-core conv (0 = as deep as shared memory allows, max 16).
+ *   ring depth of the tensor-core conv (0 = as deep as shared memory allows, else 4..16).
  * weights: an SMLW blob (host memory, read during the call only):
  *   header "<8s7I16i": magic "SMLW0001", version 1, L, C, in_ch, n_heads (5), has_bn,
  *   reserved, dilations[16]; then per layer l: W[C][Cin_l][3][3] f32, b[C] f32 and, if

@@ -506,7 +506,8 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
   ctx->ph_scale = (float)num("ph_scale", 10000.0);
   ctx->chunk_px = (long long)num("chunk_px", (double)(1 << 24));
   ctx->tc_stages = (int)num("tc_stages", 0);
-  if (ctx->tc_stages < 0 || ctx->tc_stages > 16) return fail(nullptr, SML_ERR_BAD_SPEC, "tc_stages must be 0..16");
+  if (ctx->tc_stages < 0 || (ctx->tc_stages > 0 && ctx->tc_stages < 4) || ctx->tc_stages > 16)
+    return fail(nullptr, SML_ERR_BAD_SPEC, "tc_stages must be 0 (as deep as shared memory allows) or 4..16");
 
   if (ctx->in_ch != 1) return fail(nullptr, SML_ERR_BAD_SPEC, "in_ch must be 1");
   if (ctx->C != 16 && ctx->C != 32 && ctx->C != 48 && ctx->C != 64)

@@ -32,10 +32,12 @@
 // k-step ascending), so the result does not depend on scheduling, grid size or batch
 // composition.
 //
-// Warp roles (192 threads): warps 0-3 epilogue (TMEM lane quarter = warp index), warp 4 TMA
-// producer, warp 5 TMEM allocator and MMA issuer.  Every mbarrier wait is bounded: on
-// timeout the kernel sets *err, stops issuing, drains its own MMAs and TMA loads (bounded),
-// frees TMEM and returns.
+// Warp roles (224 threads): warps 0-3 epilogue (TMEM lane quarter = warp index), warp 4 TMA
+// producer, warp 5 TMEM allocator and MMA issuer, warp 6 waiter (the MMA warp's mbarrier
+// waits, handed over through named barriers).  Every mbarrier wait is bounded: on timeout
+// the kernel sets *err, the producer and epilogue stop, the MMA warp finishes its row
+// sequence without waiting, the MMAs and TMA loads in flight are drained (bounded), TMEM is
+// freed and the kernel returns.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -46,7 +48,9 @@ namespace sml {
 namespace {
 
 constexpr int kEpiWarps = 4;
-constexpr int kThreads = 192;
+constexpr int kThreads = 224;
+constexpr int kHandRows = 2;   // input rows per waiter -> MMA handoff
+constexpr int kMinStages = 4;  // the handoff protocol needs a ring of at least 4 stages
 constexpr int kTmemCols = 512;
 constexpr int kMaxSeg = 6;
 constexpr int kMaxStages = 16;
@@ -101,6 +105,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
   return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, err, abort_flag);
 }
 
+// Bounded wait for this thread's own asynchronous work (TMA loads, MMAs) to land before the
+// CTA releases the memory it writes.  Unlike mbar_wait it keeps waiting after another role
+// has aborted: that work completes whatever the other roles did.
+__device__ __noinline__ bool mbar_wait_own(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
+  unsigned long long t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 0 && gtimer() - t0 > kWaitLimitNs) {
+      *abort_flag = 1;
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -137,6 +156,35 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, ui
         : "memory");
   }
 }
+
+// Issued by a whole converged warp; only the lane with leader != 0 issues (no divergence).
+template <int PREC>
+__device__ __forceinline__ void umma_if(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t leader) {
+  if (PREC == kBF16) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %5, 0;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+        "@q tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(leader), "r"(1u)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %5, 0;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+        "@q tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(leader), "r"(1u)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void umma_commit_if(uint32_t bar, uint32_t leader) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t"
+      "@q tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(bar),
+      "r"(leader)
+      : "memory");
+}
+// Named barriers 1 and 2 (0 is __syncthreads) carry the waiter -> MMA handoffs: the waiter
+// warp arrives, the MMA warp syncs (64 threads each time).
+__device__ __forceinline__ void named_arrive(uint32_t id) { asm volatile("bar.arrive %0, 64;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void named_sync(uint32_t id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -342,12 +390,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         const uint32_t back = k + 1;
         const uint32_t s2 = (st + nst - (back % nst)) % nst;
         const uint32_t p2 = (back > st) ? (ph ^ 1u) : ph;
-        mbar_wait(smem_u32(&full_bar[s2]), p2, a.err, s_abort);
+        mbar_wait_own(smem_u32(&full_bar[s2]), p2, a.err, s_abort);
       }
     }
   } else if (warp == 5) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    // The whole warp runs the loop and lane 0 issues (predicated, no divergence).  It never
+    // waits on an mbarrier itself: a shared-memory read whose result this thread consumes
+    // waits behind its in-flight MMAs and empties the MMA queue (measured: about 300 cycles
+    // per input row).  The waiter warp does the waits and hands over through a named barrier
+    // once per kHandRows rows.
+    const uint32_t leader = lane == 0 ? 1u : 0u;
+    {
       // Descriptors are computed once: the start-address field (bits 0-13, 16-byte units)
       // is advanced by plain addition, which cannot carry out of the field because every
       // shared-memory address is below 256 KB.
@@ -364,32 +418,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
                                                     : (uint32_t)(kx * a.d) + (uint32_t)ks * (a.plane_stride >> 3);
       const uint32_t stage16 = a.stage_bytes >> 4;
       const uint32_t nst = (uint32_t)a.nstages;
-      uint32_t st = 0, ph = 0;                   // stage and the phase its full barrier is in
-      uint64_t a_st = a_desc0;                   // descriptor of the current stage
-      uint32_t used = 0, par = 0;                // row positions used before / parity of their last use
-      bool ok = true, issued = false;
-      for (uint32_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+      uint32_t st = 0;             // stage of the current row
+      uint64_t a_st = a_desc0;     // descriptor of the current stage
+      uint32_t hand = 0;           // handoffs taken
+      bool issued = false;
+      for (uint32_t u = blockIdx.x; u < a.units; u += gridDim.x) {
         int t, j0, phi, q;
         const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
         if (n_out == 0) continue;
-        for (int kk = 0; kk < n_out + 2 && ok; ++kk) {
-          // TMA data is visible to the MMA once the barrier's transaction count completes
-          // (async proxy on both sides): no tcgen05 fence is needed after this wait
-          if (!mbar_wait(smem_u32(&full_bar[st]), ph, a.err, s_abort)) {
-            ok = false;
-            break;
+        for (int kk = 0; kk < n_out + 2; ++kk) {
+          if (kk % kHandRows == 0) {
+            // the waiter has seen this group's TMA data and TMEM releases complete
+            named_sync(1u + (hand & 1u));
+            ++hand;
+            fence_after_sync();
           }
           // blocks b (output rows kk-b) of this input row that belong to the unit
           const int b_lo = kk - n_out + 1 > 0 ? kk - n_out + 1 : 0;
           const int b_hi = kk < 2 ? kk : 2;
           const int nb = b_hi - b_lo + 1;
-          if (b_lo == 0 && ((used >> kk) & 1u)) {  // row kk's columns must be drained first
-            if (!mbar_wait(smem_u32(&acce_bar[kk]), (par >> kk) & 1u, a.err, s_abort)) {
-              ok = false;
-              break;
-            }
-            fence_after_sync();
-          }
           const uint32_t d_col = tmem + Cfg::BASE0 - (uint32_t)(C * kk) + (uint32_t)(C * b_lo);
           const uint32_t b_sub = (uint32_t)(2 * C * b_lo);  // 32*C*b_lo bytes in 16-byte units
           const uint32_t idesc_n = nb == 3 ? Cfg::IDESC3 : (nb == 2 ? Cfg::IDESC2 : Cfg::IDESC1);
@@ -399,28 +446,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
             for (int ks = 0; ks < Cfg::NKS; ++ks) {
               const uint64_t ad = a_st + a_off[kx * Cfg::NKS + ks];
               const uint64_t bd = b_desc0 + (uint64_t)(((kx * Cfg::NKS + ks) * Cfg::BBLK) >> 4) + b_sub;
-              umma<PREC>(d_col, ad, bd, idesc_n, 1u);
+              umma_if<PREC>(d_col, ad, bd, idesc_n, leader);
             }
           issued = true;
-          if (kk >= 2 && kk - 2 < n_out) umma_commit(smem_u32(&accf_bar[kk - 2]));
-          umma_commit(smem_u32(&empty_bar[st]));
+          if (kk >= 2 && kk - 2 < n_out) umma_commit_if(smem_u32(&accf_bar[kk - 2]), leader);
+          umma_commit_if(smem_u32(&empty_bar[st]), leader);
           if (++st == nst) {
             st = 0;
-            ph ^= 1u;
             a_st = a_desc0;
           } else {
             a_st += stage16;
           }
         }
-        // positions 0..n_out-1 were used once more: flip the parity of those used before
-        const uint32_t m = (1u << n_out) - 1u;
-        par ^= m & used;
-        used |= m;
       }
-      if (issued) {  // all MMAs of this CTA complete before TMEM is released
+      if (issued && leader) {  // all MMAs of this CTA complete before TMEM is released
         umma_commit(smem_u32(&drain_bar[0]));
-        mbar_wait(smem_u32(&drain_bar[0]), 0, a.err, s_abort);
+        mbar_wait_own(smem_u32(&drain_bar[0]), 0, a.err, s_abort);
       }
+      __syncwarp();
+    }
+  } else if (warp == 6) {
+    // ------------------------------------------------------------ waiter
+    // For each group of kHandRows input rows (groups never span units): wait until their TMA
+    // data has landed and, for rows that open an output row position used before, until the
+    // epilogue has released those TMEM columns; then arrive on the group's named barrier.
+    // It arrives exactly once per group whatever happens (after an abort its waits return at
+    // once), so the MMA warp never blocks for good.  Before arriving for group h it waits for
+    // the MMA's empty-stage commit of group h-2's first row: the MMA warp has then passed
+    // group h-2's sync, so each named barrier has at most one pending arrival.
+    const uint32_t nst = (uint32_t)a.nstages;
+    uint32_t st = 0, ph = 0;             // stage and fill phase of the current row
+    uint32_t used = 0, par = 0;          // row positions used before / parity of their last release
+    uint32_t hand = 0;
+    uint32_t g_st0 = 0, g_ph0 = 0, g_st1 = 0, g_ph1 = 0;  // first row of the last two groups (even, odd)
+    for (uint32_t u = blockIdx.x; u < a.units; u += gridDim.x) {
+      int t, j0, phi, q;
+      const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
+      if (n_out == 0) continue;
+      for (int k0 = 0; k0 < n_out + 2; k0 += kHandRows) {
+        if (lane == 0) {
+          const bool odd = hand & 1u;
+          if (hand >= 2)
+            mbar_wait_own(smem_u32(&empty_bar[odd ? g_st1 : g_st0]), odd ? g_ph1 : g_ph0, a.err, s_abort);
+          if (odd) {
+            g_st1 = st;
+            g_ph1 = ph;
+          } else {
+            g_st0 = st;
+            g_ph0 = ph;
+          }
+          const int k1 = k0 + kHandRows < n_out + 2 ? k0 + kHandRows : n_out + 2;
+          for (int kk = k0; kk < k1; ++kk) {
+            mbar_wait(smem_u32(&full_bar[st]), ph, a.err, s_abort);
+            if (kk < n_out && ((used >> kk) & 1u)) mbar_wait(smem_u32(&acce_bar[kk]), (par >> kk) & 1u, a.err, s_abort);
+            if (++st == nst) {
+              st = 0;
+              ph ^= 1u;
+            }
+          }
+        }
+        __syncwarp();
+        named_arrive(1u + (hand & 1u));
+        ++hand;
+      }
+      // positions 0..n_out-1 were used once more: flip the parity of those used before
+      const uint32_t m = (1u << n_out) - 1u;
+      par ^= m & used;
+      used |= m;
     }
   } else {
     // ------------------------------------------------------------ epilogue (warps 0-3)
@@ -624,7 +716,8 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   if (a.units == 0) return cudaSuccess;
   const size_t budget = 227 * 1024;
   int nst = la.stages > 0 ? la.stages : kMaxStages;
-  while (nst > 2 && tc_smem_bytes<C, PREC>(nst, a.stage_bytes) > budget) --nst;
+  if (nst < kMinStages) return cudaErrorInvalidValue;
+  while (nst > kMinStages && tc_smem_bytes<C, PREC>(nst, a.stage_bytes) > budget) --nst;
   a.nstages = nst;
   size_t smem = tc_smem_bytes<C, PREC>(nst, a.stage_bytes);
   if (smem > budget) return cudaErrorInvalidConfiguration;

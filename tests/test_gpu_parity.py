@@ -176,7 +176,20 @@ def test_ragged_frames_multi_chunk_and_scmos(prec):
     assert recs.tobytes() == want.tobytes()
 
 
-@pytest.mark.parametrize("stages", [0, 3])
+@pytest.mark.parametrize("stages", [1, 3, 17])
+def test_tma_ring_depth_outside_range_is_rejected(stages):
+    """The waiter/MMA handoff needs a ring of at least 4 stages; 1..3 and >16 are spec errors."""
+    import json
+
+    spec = synth.NetSpec(in_ch=1, channels=32, dilations=(1, 2, 1), precision="bf16")
+    blob = synth.pack_blob(spec, synth.init_weights(spec, 5))
+    js = json.dumps(dict(json.loads(spec.to_json()), tc_stages=stages))
+    with pytest.raises(sml.SmlError) as e:
+        sml.Localizer(js, blob)
+    assert e.value.code == sml.SML_ERR_BAD_SPEC
+
+
+@pytest.mark.parametrize("stages", [0, 4])
 def test_dilation_larger_than_tile_margin(stages):
     """Dilations up to 64 (TMA box 256 pixels) and a frame narrower than the dilation, with
     the deepest and a shallow TMA ring."""
