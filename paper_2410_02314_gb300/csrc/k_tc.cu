@@ -19,8 +19,10 @@
 //
 // Work decomposition ("row classes"): the three input rows of output row i are i-d, i, i+d,
 // so rows with the same residue mod d form independent chains.  A work unit is
-// (frame, 128-pixel column strip, residue phi, segment of S consecutive rows of the chain).
-// Its S+2 input rows stream through a ring of TMA stages, each loaded once.  Input row k'
+// (frame, 128-pixel column strip, residue phi, segment of S consecutive rows of the chain);
+// each CTA takes a contiguous range of units in (frame, phi, strip, segment) order, so the
+// rows and columns a unit shares with its successors are still in L2 when they load them.
+// A unit's S+2 input rows stream through a ring of TMA stages, each loaded once.  Input row k'
 // feeds output rows k', k'-1, k'-2 through the vertical taps ky = 0, 1, 2; those three
 // contributions are ONE MMA with N = 3C (B = the three taps' weights side by side) whose
 // D columns are the three rows' accumulators: output row k of a unit accumulates at TMEM
@@ -265,16 +267,18 @@ struct TcCfg {
   static constexpr uint32_t IDESC3 = instr_desc(PREC, kTileM, 3 * C);
 };
 
-// Unit -> (t, strip, phi, q); returns the number of valid output rows (<= seg).  32-bit
-// arithmetic (unit counts stay far below 2^31).
+// Unit -> (t, phi, strip, q), q fastest: consecutive units are the next segment of the same
+// row chain (sharing two input rows) and then the neighbouring strip (sharing halo columns),
+// so with contiguous unit ranges per CTA those re-reads hit L2.  Returns the number of valid
+// output rows (<= seg).  32-bit arithmetic (unit counts stay far below 2^31).
 __device__ __forceinline__ int unit_rows(const TcKArgs& a, uint32_t u, int seg, int& t, int& j0, int& phi, int& q) {
   const uint32_t nq = (uint32_t)a.NQ, d = (uint32_t)a.d, ns = (uint32_t)a.NS;
   uint32_t r = u / nq;
   q = (int)(u - r * nq);
-  uint32_t r2 = r / d;
-  phi = (int)(r - r2 * d);
-  uint32_t r3 = r2 / ns;
-  const int s = (int)(r2 - r3 * ns);
+  uint32_t r2 = r / ns;
+  const int s = (int)(r - r2 * ns);
+  uint32_t r3 = r2 / d;
+  phi = (int)(r2 - r3 * d);
   t = (int)r3;
   j0 = s * kTileM;
   const int n_class = phi < a.H ? (a.H - phi + a.d - 1) / a.d : 0;
@@ -303,6 +307,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // this CTA's contiguous range of units
+  const uint32_t u_begin = (uint32_t)(((unsigned long long)blockIdx.x * a.units) / gridDim.x);
+  const uint32_t u_end = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * a.units) / gridDim.x);
 
   // ---- set-up: weights -> shared, zero pad planes, barriers, TMEM
   {
@@ -363,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       const uint32_t nst = (uint32_t)a.nstages;
       uint32_t st = 0, ph = 0, issued = 0;  // stage, phase of its current use, loads issued
       bool ok = true;
-      for (uint32_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+      for (uint32_t u = u_begin; u < u_end && ok; ++u) {
         int t, j0, phi, q;
         const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
         for (int kk = 0; kk < n_out + 2 && n_out > 0; ++kk) {
@@ -422,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       uint64_t a_st = a_desc0;     // descriptor of the current stage
       uint32_t hand = 0;           // handoffs taken
       bool issued = false;
-      for (uint32_t u = blockIdx.x; u < a.units; u += gridDim.x) {
+      for (uint32_t u = u_begin; u < u_end; ++u) {
         int t, j0, phi, q;
         const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
         if (n_out == 0) continue;
@@ -479,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     uint32_t used = 0, par = 0;          // row positions used before / parity of their last release
     uint32_t hand = 0;
     uint32_t g_st0 = 0, g_ph0 = 0, g_st1 = 0, g_ph1 = 0;  // first row of the last two groups (even, odd)
-    for (uint32_t u = blockIdx.x; u < a.units; u += gridDim.x) {
+    for (uint32_t u = u_begin; u < u_end; ++u) {
       int t, j0, phi, q;
       const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
       if (n_out == 0) continue;
@@ -521,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     uint32_t fpar = 0;  // per row position: phase of its acc_full barrier for the next use
     bool ok = true;
     const size_t plane = (size_t)a.H * a.W;
-    for (uint32_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+    for (uint32_t u = u_begin; u < u_end && ok; ++u) {
       int t, j0, phi, q;
       const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
 #pragma unroll 1
