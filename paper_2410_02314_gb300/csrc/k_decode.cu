@@ -17,42 +17,82 @@ namespace sml {
 
 namespace {
 
-__device__ __forceinline__ bool dec_flag(const float* __restrict__ maps, int H, int W, long long q, float p_min) {
-  long long plane = (long long)H * W;
-  int t = (int)(q / plane);
-  long long px = q - (long long)t * plane;
-  int i = (int)(px / W);
-  int j = (int)(px - (long long)i * W);
-  const float* p = maps + (size_t)t * kHeads * plane;
-  float v = p[px];
-  if (!(v > p_min)) return false;
+constexpr int kPxPerThread = kDecodePxPerBlock / kDecodeThreads;
+
+// Location of a pixel of the chunk: frame t, row i, column j (valid = inside the chunk).
+struct PxLoc {
+  int t, i, j;
+  bool valid;
+};
+
+// Pixels q0 + k*kDecodeThreads + threadIdx.x (k < kPxPerThread) of the block starting at q0:
+// one 64-bit division per thread, then 32-bit arithmetic.
+__device__ __forceinline__ void dec_locate(const DecodeArgs& a, long long q0, PxLoc (&loc)[kPxPerThread]) {
+  const long long npx = (long long)a.T * a.H * a.W;
+  const unsigned plane = (unsigned)a.H * (unsigned)a.W;
+  const long long t0 = q0 / plane;
+  const unsigned r0 = (unsigned)(q0 - t0 * plane);
 #pragma unroll
-  for (int di = -1; di <= 1; ++di) {
-    int ii = i + di;
-    if (ii < 0 || ii >= H) continue;
-#pragma unroll
-    for (int dj = -1; dj <= 1; ++dj) {
-      if (di == 0 && dj == 0) continue;
-      int jj = j + dj;
-      if (jj < 0 || jj >= W) continue;
-      float nb = p[(size_t)ii * W + jj];
-      bool earlier = (di < 0) || (di == 0 && dj < 0);
-      if (earlier ? !(v > nb) : !(v >= nb)) return false;
+  for (int k = 0; k < kPxPerThread; ++k) {
+    const unsigned off = (unsigned)(k * kDecodeThreads) + threadIdx.x;
+    loc[k].valid = q0 + off < npx;
+    unsigned r = r0 + off;
+    int t = (int)t0;
+    if (r >= plane) {  // the block crosses into the next frame(s)
+      const unsigned dt = r / plane;
+      t += (int)dt;
+      r -= dt * plane;
     }
+    const unsigned i = r / (unsigned)a.W;
+    loc[k].t = t;
+    loc[k].i = (int)i;
+    loc[k].j = (int)(r - i * (unsigned)a.W);
   }
-  return true;
+}
+
+// Detection flags of the thread's pixels.  All centre and neighbour loads are issued before
+// any test (out-of-frame neighbours read as -inf, which never blocks a detection), so each
+// thread pays one memory round trip instead of two per pixel.
+__device__ __forceinline__ void dec_flags(const DecodeArgs& a, const PxLoc (&loc)[kPxPerThread],
+                                          bool (&flag)[kPxPerThread]) {
+  const size_t plane = (size_t)a.H * a.W;
+  float v[kPxPerThread][9];
+#pragma unroll
+  for (int k = 0; k < kPxPerThread; ++k) {
+    const float* p = a.maps + (size_t)loc[k].t * kHeads * plane;
+#pragma unroll
+    for (int di = -1; di <= 1; ++di)
+#pragma unroll
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int ii = loc[k].i + di, jj = loc[k].j + dj;
+        const bool in = loc[k].valid && ii >= 0 && ii < a.H && jj >= 0 && jj < a.W;
+        v[k][(di + 1) * 3 + dj + 1] = in ? __ldg(p + (size_t)ii * a.W + jj) : -INFINITY;
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < kPxPerThread; ++k) {
+    const float c = v[k][4];
+    bool f = loc[k].valid && c > a.p_min;
+#pragma unroll
+    for (int n = 0; n < 9; ++n) {
+      if (n == 4) continue;
+      // strict against earlier neighbours (raster order), >= against later ones
+      f = f && (n < 4 ? c > v[k][n] : c >= v[k][n]);
+    }
+    flag[k] = f;
+  }
 }
 
 __global__ void __launch_bounds__(kDecodeThreads) k_decode_count(DecodeArgs a) {
   __shared__ unsigned warp_sum[kDecodeThreads / 32];
-  long long npx = (long long)a.T * a.H * a.W;
-  long long base = (long long)blockIdx.x * kDecodePxPerBlock;
+  const long long q0 = (long long)blockIdx.x * kDecodePxPerBlock;
+  PxLoc loc[kPxPerThread];
+  bool flag[kPxPerThread];
+  dec_locate(a, q0, loc);
+  dec_flags(a, loc, flag);
   unsigned cnt = 0;
-  for (int it = 0; it < kDecodePxPerBlock / kDecodeThreads; ++it) {
-    long long q = base + it * kDecodeThreads + threadIdx.x;
-    bool f = q < npx && dec_flag(a.maps, a.H, a.W, q, a.p_min);
-    cnt += __popc(__ballot_sync(0xffffffffu, f));
-  }
+#pragma unroll
+  for (int k = 0; k < kPxPerThread; ++k) cnt += __popc(__ballot_sync(0xffffffffu, flag[k]));
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) warp_sum[warp] = cnt;
   __syncthreads();
@@ -102,37 +142,42 @@ __global__ void __launch_bounds__(1024) k_decode_scan(DecodeArgs a, long long nb
 }
 
 __global__ void __launch_bounds__(kDecodeThreads) k_decode_write(DecodeArgs a) {
-  __shared__ unsigned warp_cnt[kDecodeThreads / 32];
-  long long npx = (long long)a.T * a.H * a.W;
-  long long plane = (long long)a.H * a.W;
-  long long base = (long long)blockIdx.x * kDecodePxPerBlock;
+  __shared__ unsigned warp_cnt[kPxPerThread][kDecodeThreads / 32];
+  const long long q0 = (long long)blockIdx.x * kDecodePxPerBlock;
+  const size_t plane = (size_t)a.H * a.W;
+  PxLoc loc[kPxPerThread];
+  bool flag[kPxPerThread];
+  dec_locate(a, q0, loc);
+  dec_flags(a, loc, flag);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  unsigned bal[kPxPerThread];
+#pragma unroll
+  for (int k = 0; k < kPxPerThread; ++k) {
+    bal[k] = __ballot_sync(0xffffffffu, flag[k]);
+    if (lane == 0) warp_cnt[k][warp] = __popc(bal[k]);
+  }
+  __syncthreads();
+  // raster order inside the block: pass k, then warp, then lane
   unsigned long long off = a.block_offsets[blockIdx.x];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned lt_mask = (1u << lane) - 1u;
-  for (int it = 0; it < kDecodePxPerBlock / kDecodeThreads; ++it) {
-    long long q = base + it * kDecodeThreads + threadIdx.x;
-    bool f = q < npx && dec_flag(a.maps, a.H, a.W, q, a.p_min);
-    unsigned bal = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) warp_cnt[warp] = __popc(bal);
-    __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kPxPerThread; ++k) {
     unsigned before = 0, total = 0;
+#pragma unroll
     for (int w = 0; w < kDecodeThreads / 32; ++w) {
-      unsigned c = warp_cnt[w];
+      const unsigned c = warp_cnt[k][w];
       before += (w < warp) ? c : 0u;
       total += c;
     }
-    if (f) {
-      unsigned long long idx = off + before + __popc(bal & lt_mask);
+    if (flag[k]) {
+      const unsigned long long idx = off + before + __popc(bal[k] & lt_mask);
       if (idx < a.capacity) {
-        int t = (int)(q / plane);
-        long long px = q - (long long)t * plane;
-        int i = (int)(px / a.W);
-        int j = (int)(px - (long long)i * a.W);
-        const float* m = a.maps + (size_t)t * kHeads * plane;
+        const size_t px = (size_t)loc[k].i * a.W + loc[k].j;
+        const float* m = a.maps + (size_t)loc[k].t * kHeads * plane;
         sml_record r;
-        r.frame = a.frame0 + t;
-        r.x = __fadd_rn((float)j, m[plane + px]);
-        r.y = __fadd_rn((float)i, m[2 * plane + px]);
+        r.frame = a.frame0 + loc[k].t;
+        r.x = __fadd_rn((float)loc[k].j, m[plane + px]);
+        r.y = __fadd_rn((float)loc[k].i, m[2 * plane + px]);
         r.z = __fmul_rn(a.z_scale, m[3 * plane + px]);
         r.photons = __fmul_rn(a.ph_scale, m[4 * plane + px]);
         r.p = m[px];
@@ -140,7 +185,6 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode_write(DecodeArgs a) {
       }
     }
     off += total;
-    __syncthreads();
   }
 }
 
