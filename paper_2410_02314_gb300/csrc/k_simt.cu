@@ -26,79 +26,108 @@ __device__ __forceinline__ float cam_input(const uint16_t* __restrict__ f, int H
   return __fmul_rn(__fdiv_rn(__fsub_rn((float)f[px], o), g), cam.in_scale);
 }
 
-// Layer-1 weights by value: the FMAs read them straight from the constant bank.
+// Layer-1 weights travel by value (kernel parameter); each thread copies the ones it uses
+// into registers once per block.
 struct L1Params {
   float w[64 * 9];  // [co][ky*3+kx]
   float b[64];
 };
 
-constexpr int kL1Tile = 128;  // pixels of one image row per block
+constexpr int kL1Tile = 128;     // pixels of one image row per block (and threads per block)
+constexpr int kL1Rows = 4;       // image rows per block
+constexpr int kL1Px = 8;         // pixels per thread: columns pg + 16*p, p < kL1Px
+constexpr int kL1ChGroups = 8;   // a thread computes C/8 output channels
 
-// OUT: 0 = float NHWC, 1 = bf16 row-planar (16 ch / 32 B), 2 = e4m3 row-planar (16 ch / 16 B).
-// One block = 128 consecutive pixels of one row; the three dilated input rows (with a d-pixel
-// margin) are converted to network inputs once, into shared memory.
+// One block: a 128-pixel strip of kL1Rows rows of one frame.  Thread (pg = lane % 16,
+// cg = 2*warp + lane / 16) computes channels cg*C/8 .. +C/8 for the strip's pixels pg + 16p
+// with its 9*C/8 weights in registers (FMAs with register operands run at full rate; with
+// constant-bank weight operands they ran at half the rate).  The three dilated input rows of
+// every output row of the block go through the camera transform into shared memory first
+// (one global round trip per block); the thread's FMAs follow the order bias, then taps
+// (ky, kx) row-major; outputs are staged in shared memory (rows padded by 16 bytes against
+// bank conflicts) so that the stores to HBM are whole 16-byte chunks, consecutive across
+// threads.
 template <int C, int OUT>
 __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restrict__ frames, int H, int W, int d,
                                                        int t0, CamArgs cam, const __grid_constant__ L1Params prm,
                                                        float out_scale, void* __restrict__ out) {
-  __shared__ float xs[3][kL1Tile + 2 * 64];
-  const int j0 = blockIdx.x * kL1Tile, i = blockIdx.y, t = t0 + blockIdx.z;
+  constexpr int CPT = C / kL1ChGroups;
+  constexpr int OB = OUT == 0 ? 4 : (OUT == 1 ? 2 : 1);  // output bytes per channel
+  constexpr int OS = C * OB + 16;                        // staged bytes per pixel
+  __shared__ float xs[kL1Rows][3][kL1Tile + 2 * 64];
+  __shared__ __align__(16) uint8_t ot[kL1Tile * OS];  // [pixel][channel], padded rows
+  const int j0 = blockIdx.x * kL1Tile, t = t0 + blockIdx.z, i0 = blockIdx.y * kL1Rows;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pg = lane & 15, cg = 2 * warp + (lane >> 4);
   const int span = kL1Tile + 2 * d;
   const uint16_t* f = frames + (size_t)t * H * W;
-  for (int k = threadIdx.x; k < 3 * span; k += kL1Tile) {
-    int r = k / span, c = k - r * span;
-    xs[r][c] = cam_input(f, H, W, i + (r - 1) * d, j0 - d + c, cam);
+  for (int k = threadIdx.x; k < kL1Rows * 3 * span; k += kL1Tile) {
+    const int rr = k / span, c = k - rr * span;  // rr = 3 * (output row) + ky
+    const int r = rr / 3, ky = rr - 3 * r;
+    xs[r][ky][c] = cam_input(f, H, W, i0 + r + (ky - 1) * d, j0 - d + c, cam);
   }
-  __syncthreads();
-  const int j = j0 + threadIdx.x;
-  if (j >= W) return;
-  float x[9];
+  float w[CPT][9], bias[CPT];
 #pragma unroll
-  for (int ky = 0; ky < 3; ++ky)
+  for (int c = 0; c < CPT; ++c) {
+    bias[c] = prm.b[cg * CPT + c];
 #pragma unroll
-    for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xs[ky][threadIdx.x + kx * d];
-  float a[C];
-#pragma unroll
-  for (int co = 0; co < C; ++co) {
-    float s = prm.b[co];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) s = fmaf(prm.w[co * 9 + k], x[k], s);
-    a[co] = fmaxf(s, 0.0f);
+    for (int k = 0; k < 9; ++k) w[c][k] = prm.w[(cg * CPT + c) * 9 + k];
   }
-  const size_t q = ((size_t)t * H + i) * W + j;
-  if (OUT == 0) {
-    float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + q * C);
+  const int npx = W - j0 < kL1Tile ? W - j0 : kL1Tile;  // valid pixels of the strip
+  for (int r = 0; r < kL1Rows; ++r) {
+    const int i = i0 + r;
+    if (i >= H) break;
+    __syncthreads();  // xs is filled; the previous row's ot is written out
 #pragma unroll
-    for (int c4 = 0; c4 < C / 4; ++c4) dst[c4] = make_float4(a[4 * c4], a[4 * c4 + 1], a[4 * c4 + 2], a[4 * c4 + 3]);
-  } else if (OUT == 1) {
-    constexpr int G = C / 16;
-    uint8_t* base = static_cast<uint8_t*>(out);
+    for (int p = 0; p < kL1Px; ++p) {
+      const int px = pg + 16 * p;
+      float x[9];
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      uint4 v[2];
-      uint32_t* vw = reinterpret_cast<uint32_t*>(v);
+      for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(a[16 * g + 2 * e], a[16 * g + 2 * e + 1]);
-        vw[e] = *reinterpret_cast<uint32_t*>(&h2);
+        for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xs[r][ky][px + kx * d];
+      float a[CPT];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        float acc = bias[c];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc = fmaf(w[c][k], x[k], acc);
+        a[c] = fmaxf(acc, 0.0f);
       }
-      uint4* dst = reinterpret_cast<uint4*>(base + ((((size_t)t * H + i) * G + g) * W + j) * 32);
-      dst[0] = v[0];
-      dst[1] = v[1];
+      uint8_t* dst = ot + (size_t)px * OS + cg * CPT * OB;
+      if (OUT == 0) {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) reinterpret_cast<float*>(dst)[c] = a[c];
+      } else if (OUT == 1) {
+#pragma unroll
+        for (int c = 0; c < CPT; c += 2) {
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(a[c], a[c + 1]);
+          *reinterpret_cast<__nv_bfloat162*>(dst + 2 * c) = h2;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < CPT; c += 2)
+          *reinterpret_cast<uint16_t*>(dst + c) = __nv_cvt_float2_to_fp8x2(
+              make_float2(a[c] * out_scale, a[c + 1] * out_scale), __NV_SATFINITE, __NV_E4M3);
+      }
     }
-  } else {
-    constexpr int G = C / 16;
-    uint8_t* base = static_cast<uint8_t*>(out);
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      uint4 v;
-      uint16_t* vh = reinterpret_cast<uint16_t*>(&v);
-#pragma unroll
-      for (int e = 0; e < 8; ++e)
-        vh[e] = __nv_cvt_float2_to_fp8x2(make_float2(a[16 * g + 2 * e] * out_scale, a[16 * g + 2 * e + 1] * out_scale),
-                                         __NV_SATFINITE, __NV_E4M3);
-      size_t off = ((((size_t)t * H + i) * G + g) * W + j) * 16;
-      *reinterpret_cast<uint4*>(base + off) = v;
+    __syncthreads();
+    const size_t row = (size_t)t * H + i;
+    if (OUT == 0) {  // NHWC float: the strip's npx*C floats are contiguous
+      constexpr int CH = C / 4;  // float4 per pixel
+      float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + (row * W + j0) * C);
+      for (int k = threadIdx.x; k < npx * CH; k += kL1Tile) {
+        const int px = k / CH, h = k - px * CH;
+        dst[k] = *reinterpret_cast<const float4*>(ot + (size_t)px * OS + 16 * h);
+      }
+    } else {  // row-planar [T][H][G][W][16 channels]: per group, npx rows of 16*OB bytes
+      constexpr int G = C / 16, CH = OB;  // 16-byte chunks per group row
+      uint8_t* base = static_cast<uint8_t*>(out);
+      for (int k = threadIdx.x; k < G * npx * CH; k += kL1Tile) {
+        const int g = k / (npx * CH), rem = k - g * npx * CH, px = rem / CH, h = rem - px * CH;
+        const uint4 v = *reinterpret_cast<const uint4*>(ot + (size_t)px * OS + 16 * g * OB + 16 * h);
+        *reinterpret_cast<uint4*>(base + (((row * G + g) * W + j0 + px) * 16 * OB) + 16 * h) = v;
+      }
     }
   }
 }
@@ -203,7 +232,8 @@ cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d,
   memcpy(prm.w, w1, sizeof(float) * C * 9);
   memcpy(prm.b, b1, sizeof(float) * C);
   for (int t0 = 0; t0 < T; t0 += 65535) {
-    dim3 grid((W + kL1Tile - 1) / kL1Tile, H, (unsigned)(T - t0 < 65535 ? T - t0 : 65535)), block(kL1Tile);
+    dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + kL1Rows - 1) / kL1Rows, (unsigned)(T - t0 < 65535 ? T - t0 : 65535)),
+        block(kL1Tile);
 #define SML_L1(CC)                                                                                       \
   case CC:                                                                                               \
     if (prec == kFP32)                                                                                   \
