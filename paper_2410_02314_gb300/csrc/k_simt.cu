@@ -61,11 +61,12 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
   const int pg = lane & 15, cg = 2 * warp + (lane >> 4);
   const int span = kL1Tile + 2 * d;
   const uint16_t* f = frames + (size_t)t * H * W;
-  for (int k = threadIdx.x; k < kL1Rows * 3 * span; k += kL1Tile) {
-    const int rr = k / span, c = k - rr * span;  // rr = 3 * (output row) + ky
-    const int r = rr / 3, ky = rr - 3 * r;
-    xs[r][ky][c] = cam_input(f, H, W, i0 + r + (ky - 1) * d, j0 - d + c, cam);
-  }
+#pragma unroll
+  for (int r = 0; r < kL1Rows; ++r)
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+      for (int c = threadIdx.x; c < span; c += kL1Tile)
+        xs[r][ky][c] = cam_input(f, H, W, i0 + r + (ky - 1) * d, j0 - d + c, cam);
   float w[CPT][9], bias[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) {
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
     }
     __syncthreads();
     const size_t row = (size_t)t * H + i;
+    // index arithmetic below divides by compile-time constants only
     if (OUT == 0) {  // NHWC float: the strip's npx*C floats are contiguous
       constexpr int CH = C / 4;  // float4 per pixel
       float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + (row * W + j0) * C);
@@ -123,10 +125,14 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
     } else {  // row-planar [T][H][G][W][16 channels]: per group, npx rows of 16*OB bytes
       constexpr int G = C / 16, CH = OB;  // 16-byte chunks per group row
       uint8_t* base = static_cast<uint8_t*>(out);
-      for (int k = threadIdx.x; k < G * npx * CH; k += kL1Tile) {
-        const int g = k / (npx * CH), rem = k - g * npx * CH, px = rem / CH, h = rem - px * CH;
-        const uint4 v = *reinterpret_cast<const uint4*>(ot + (size_t)px * OS + 16 * g * OB + 16 * h);
-        *reinterpret_cast<uint4*>(base + (((row * G + g) * W + j0 + px) * 16 * OB) + 16 * h) = v;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        uint8_t* grow = base + ((row * G + g) * W + j0) * 16 * OB;
+        for (int k = threadIdx.x; k < npx * CH; k += kL1Tile) {
+          const int px = k / CH, h = k - px * CH;
+          const uint4 v = *reinterpret_cast<const uint4*>(ot + (size_t)px * OS + 16 * g * OB + 16 * h);
+          *reinterpret_cast<uint4*>(grow + 16 * k) = v;
+        }
       }
     }
   }
