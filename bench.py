@@ -178,6 +178,79 @@ def serving_run(args, spec_json, blob, dev, capacity_px_per_s, load=0.8, n_reque
     return rep
 
 
+def large_fov_run(dev, stream, flush, distinct=2, frames=16, reps=5):
+    """Large field of view: 2048x2048 sCMOS frames (per-pixel gain N(2,0.1) and offset
+    N(100,5) maps resident on the device, 2 emitters/um^2, astigmatic), 48-channel 8-layer
+    net, BF16 and FP8.  `distinct` simulated frames are cycled to a resident stack of
+    `frames`; the library runs it as chunks of 2^24 pixels (4 frames)."""
+    import numpy as np
+    import torch
+
+    import paper_2410_02314_gb300 as sml
+    from paper_2410_02314_gb300 import synth
+
+    w = synth.workload_large_fov(T=distinct, precision="bf16", seed=4)
+    H, W = w.frames.shape[1:]
+    d_frames = torch.from_numpy(np.tile(w.frames, (frames // distinct, 1, 1))).to(dev)
+    cam = {"gain": w.cam.gain, "offset": w.cam.offset, "gain_map": torch.from_numpy(w.cam.gain_map).to(dev),
+           "offset_map": torch.from_numpy(w.cam.offset_map).to(dev)}
+    cap = frames * H * W // 4
+    d_out = torch.empty(cap * 24, dtype=torch.uint8, device=dev)
+    d_n = torch.zeros(1, dtype=torch.int64, device=dev)
+    res = {"workload": f"{frames} x {H}x{W} sCMOS frames ({distinct} distinct, cycled), per-pixel gain/offset maps",
+           "l2": "flushed between calls"}
+    for prec in ("bf16", "fp8"):
+        js = w.spec.to_json()
+        if prec == "fp8":
+            js = sml.calibrate_fp8(js, w.blob, d_frames[:1], **cam)
+        loc = sml.Localizer(js, w.blob)
+        for _ in range(2):
+            loc.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream, **cam)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            loc.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream, **cam)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        res[f"{prec}_frames_per_s"] = frames / (ms / 1000)
+        res[f"{prec}_gpx_per_s"] = frames * H * W / (ms / 1000) / 1e9
+        res[f"{prec}_records_per_frame"] = int(d_n.item()) / frames
+        loc.close()
+    return res
+
+
+def small_latency_run(dev, stream, calls=50):
+    """The small configuration (4 frames of 64x64, 32-channel 6-layer FP32 net): device time
+    per call and launches per call (latency-bound: no roofline)."""
+    import torch
+
+    import paper_2410_02314_gb300 as sml
+    from paper_2410_02314_gb300 import synth
+
+    w = synth.workload_small(precision="fp32")
+    loc = sml.Localizer(w.spec.to_json(), w.blob)
+    d_frames = torch.from_numpy(w.frames).to(dev)
+    d_out = torch.empty(4 * 64 * 64 * 24, dtype=torch.uint8, device=dev)
+    d_n = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(5):
+        loc.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream, gain=w.cam.gain, offset=w.cam.offset)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+    for a, b in ev:
+        a.record(stream)
+        loc.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream, gain=w.cam.gain, offset=w.cam.offset)
+        b.record(stream)
+    torch.cuda.synchronize()
+    us = statistics.median(a.elapsed_time(b) for a, b in ev) * 1000
+    res = {"workload": "4 x 64x64 frames, 32-channel 6-layer net, FP32", "us_per_call": us,
+           "launches_per_call": loc.last_launch_count, "records_per_call": int(d_n.item())}
+    loc.close()
+    return res
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle, timed on bounded samples of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -222,6 +295,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the large-FOV and small-config measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -379,8 +453,13 @@ def main():
         extra["speedup_vs_fp32"] = value / extra["fp32_frames_per_s"]
 
     serving = None
-    if not args.no_serve and world == 1:
-        serving = serving_run(args, spec_json, w.blob, dev, capacity_px_per_s=value * H * W)
+    if not args.no_serve and world == 1:  # arrival rates at 0.5, 0.8 and 0.95 of the measured capacity
+        serving = [serving_run(args, spec_json, w.blob, dev, capacity_px_per_s=value * H * W, load=ld)
+                   for ld in (0.5, 0.8, 0.95)]
+    large_fov = small = None
+    if not args.no_extra and world == 1:
+        large_fov = large_fov_run(dev, stream, flush)
+        small = small_latency_run(dev, stream)
 
     if rank != 0:
         if dist:
@@ -415,6 +494,8 @@ def main():
         "cpu_baseline": cpu,
         "clocks": clocks,
         "serving": serving,
+        "large_fov": large_fov,
+        "small_latency": small,
         **extra,
     }
     print(json.dumps(line), flush=True)
