@@ -51,8 +51,7 @@ namespace {
 
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = 224;
-constexpr int kHandRows = 2;   // input rows per waiter -> MMA handoff
-constexpr int kMinStages = 4;  // the handoff protocol needs a ring of at least 4 stages
+constexpr int kMinStages = 4;  // the handoff protocol needs a ring of at least 2 handoff groups
 constexpr int kTmemCols = 512;
 constexpr int kMaxSeg = 6;
 constexpr int kMaxStages = 16;
@@ -307,6 +306,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // input rows per waiter -> MMA handoff: 4, or 2 when the ring is shallower than 8 stages
+  // (the protocol needs a ring of at least two handoff groups)
+  const int hand_rows = a.nstages >= 8 ? 4 : 2;
   // this CTA's contiguous range of units
   const uint32_t u_begin = (uint32_t)(((unsigned long long)blockIdx.x * a.units) / gridDim.x);
   const uint32_t u_end = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * a.units) / gridDim.x);
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     // waits on an mbarrier itself: a shared-memory read whose result this thread consumes
     // waits behind its in-flight MMAs and empties the MMA queue (measured: about 300 cycles
     // per input row).  The waiter warp does the waits and hands over through a named barrier
-    // once per kHandRows rows.
+    // once per hand_rows rows.
     const uint32_t leader = lane == 0 ? 1u : 0u;
     {
       // Descriptors are computed once: the start-address field (bits 0-13, 16-byte units)
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
         if (n_out == 0) continue;
         for (int kk = 0; kk < n_out + 2; ++kk) {
-          if (kk % kHandRows == 0) {
+          if ((kk & (hand_rows - 1)) == 0) {
             // the waiter has seen this group's TMA data and TMEM releases complete
             named_sync(1u + (hand & 1u));
             ++hand;
@@ -474,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     }
   } else if (warp == 6) {
     // ------------------------------------------------------------ waiter
-    // For each group of kHandRows input rows (groups never span units): wait until their TMA
+    // For each group of hand_rows input rows (groups never span units): wait until their TMA
     // data has landed and, for rows that open an output row position used before, until the
     // epilogue has released those TMEM columns; then arrive on the group's named barrier.
     // It arrives exactly once per group whatever happens (after an abort its waits return at
@@ -490,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       int t, j0, phi, q;
       const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
       if (n_out == 0) continue;
-      for (int k0 = 0; k0 < n_out + 2; k0 += kHandRows) {
+      for (int k0 = 0; k0 < n_out + 2; k0 += hand_rows) {
         if (lane == 0) {
           const bool odd = hand & 1u;
           if (hand >= 2)
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
             g_st0 = st;
             g_ph0 = ph;
           }
-          const int k1 = k0 + kHandRows < n_out + 2 ? k0 + kHandRows : n_out + 2;
+          const int k1 = k0 + hand_rows < n_out + 2 ? k0 + hand_rows : n_out + 2;
           for (int kk = k0; kk < k1; ++kk) {
             mbar_wait(smem_u32(&full_bar[st]), ph, a.err, s_abort);
             if (kk < n_out && ((used >> kk) & 1u)) mbar_wait(smem_u32(&acce_bar[kk]), (par >> kk) & 1u, a.err, s_abort);
