@@ -105,3 +105,34 @@ def test_trained_net_vs_mle_baseline():
     assert hist[-1][1] < 0.5 * hist[0][1]
     net_hi, mle_hi = results["high density"][0][1], results["high density"][1][1]
     assert net_hi["jaccard"] > mle_hi["jaccard"], "the trained net should detect overlapping emitters better"
+
+    # single-emitter precision along z against the CRLB (Sec. 4.1.1), net and MLE on the same
+    # frames (3000 photons, background 100, 64x64 frames, 9 axial positions)
+    from oracle import mle
+    from paper_2410_02314_gb300 import evaluate
+
+    p_low = results["low density"][0][0]
+
+    def fit_mle(frames):
+        rows = []
+        for t in range(frames.shape[0]):
+            e = frames[t].astype(np.float64) - 100.0
+            for r in mle.detect_and_fit(e, 100.0, 40.0, win=7):
+                rows.append((t, r[0], r[1], r[2]))
+        out = np.zeros(len(rows), dtype=[("frame", "<i4"), ("x", "<f4"), ("y", "<f4"), ("z", "<f4")])
+        for k, r in enumerate(rows):
+            out[k] = r
+        return out
+
+    zs = np.linspace(-600.0, 600.0, 9)
+    kw = dict(n_per_z=48, photons=3000.0, bg=100.0, size=64, seed=7)
+    net_rows = evaluate.precision_vs_z(lambda f: loc.localize(f, p_low), zs, **kw)
+    mle_rows = evaluate.precision_vs_z(fit_mle, zs, **kw)
+    print("z nm | net: det, rmse x/y/z nm | MLE: det, rmse x/y/z nm | sqrt CRLB x/y/z nm")
+    for a, b in zip(net_rows, mle_rows):
+        print("%5.0f | %.2f %5.1f %5.1f %6.1f | %.2f %5.1f %5.1f %6.1f | %4.1f %4.1f %5.1f" % (
+            a["z_nm"], a["detected"], a["rmse_x_nm"], a["rmse_y_nm"], a["rmse_z_nm"], b["detected"], b["rmse_x_nm"],
+            b["rmse_y_nm"], b["rmse_z_nm"], a["crlb_x_nm"], a["crlb_y_nm"], a["crlb_z_nm"]))
+    assert min(r["detected"] for r in net_rows) > 0.8
+    # the MLE is an efficient estimator: within a factor 2 of sqrt(CRLB) laterally
+    assert all(r["rmse_x_nm"] < 2.0 * r["crlb_x_nm"] for r in mle_rows if r["detected"] > 0.5)
