@@ -7,7 +7,8 @@ its own net-spec and weight-blob parser (below), its own C implementation
 
 What it computes (each function cites the passage it follows):
   * ``forward``        -- float64 forward of the plain dilated 3x3 stack (Sec. 3.2.1) with
-                          DECODE-style per-pixel heads (Sec. 3.2);
+                          DECODE-style per-pixel heads (Sec. 3.2); one input frame, or three
+                          consecutive frames as channels (``context_input``);
   * ``maps_f32``       -- per-pixel maps handed to the decode: p = sigmoid(logit), dx, dy,
                           zhat, Nhat, rounded once to float32;
   * ``decode``         -- float32 decode of maps into (frame, x, y, z, photons, p) records
@@ -153,6 +154,24 @@ def ingest(frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None, in_sc
     return x0
 
 
+def context_input(x, in_ch):
+    """Network input channels from single-frame inputs x [T,H,W]: in_ch = 1 gives x itself;
+    in_ch = 3 gives frames (t-1, t, t+1) as channels 0..2 (three-frame temporal context,
+    Sec. 3.1 on DECODE), zero where t-1 or t+1 falls outside the stack.  Returns
+    [T,in_ch,H,W] float64."""
+    x = np.asarray(x, dtype=np.float64)
+    T = x.shape[0]
+    if in_ch == 1:
+        return x[:, None].copy()
+    if in_ch != 3:
+        raise ValueError("in_ch must be 1 or 3")
+    out = np.zeros((T, 3) + x.shape[1:], dtype=np.float64)
+    out[:, 1] = x
+    out[1:, 0] = x[:-1]
+    out[:-1, 2] = x[1:]
+    return out
+
+
 QUANT = {None: 0, "fp32": 0, "bf16": 1, "fp8": 2}
 
 
@@ -194,7 +213,7 @@ def quantized(net: Net, fmt):
 def act_scales(net: Net, frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None):
     """FP8 activation scales from this oracle's own float64 activations: [1] + [amax_l / 448]
     for the inputs of layers 1..L-1 (amax over the given frames)."""
-    x0 = ingest(frames, gain, offset, gain_map, offset_map, net.in_scale)
+    x0 = context_input(ingest(frames, gain, offset, gain_map, offset_map, net.in_scale), net.in_ch)
     _, a = forward_x(net, x0, acts=True)
     return [1.0] + [float(a[:, l - 1].max()) / 448.0 for l in range(1, net.L)]
 
@@ -222,8 +241,9 @@ def forward_x(net: Net, x0, acts=False, quant=None, scales=None):
 
 
 def forward(net: Net, frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None, quant=None, scales=None):
-    """Raw heads [T,5,H,W] float64 from uint16 frames through the camera transform."""
-    x0 = ingest(frames, gain, offset, gain_map, offset_map, net.in_scale)
+    """Raw heads [T,5,H,W] float64 from uint16 frames through the camera transform (and,
+    for in_ch = 3, the three-frame context of context_input)."""
+    x0 = context_input(ingest(frames, gain, offset, gain_map, offset_map, net.in_scale), net.in_ch)
     return forward_x(net, x0, quant=quant, scales=scales)
 
 

@@ -2,7 +2,7 @@
 and the Cramer-Rao lower bound of the astigmatic PSF model (Sec. 4.1.1).
 
 * ``metrics``: Jaccard index, recall, precision and lateral / axial RMSE over matched pairs,
-  plus the efficiency scores of Sec. 4.1.2.
+  plus the efficiency scores of Sec. 4.1.2-4.1.3.
 * ``efficiency``: the lateral, axial and volume efficiencies, read after Sage et al. 2019.
   The Jaccard index is in percent and the RMSE in nm:
   E = 100 - sqrt((100 - JI)^2 + alpha^2 RMSE^2), with alpha = 1 / nm lateral and
@@ -67,7 +67,7 @@ def match(pred, truth, radius):
 
 
 def efficiency(ji_pct, rmse_lat_nm, rmse_ax_nm=None, alpha_lat=1.0, alpha_ax=0.5):
-    """(E_lateral, E_axial, E_volume) in percent (Sec. 4.1.2); axial terms are None without
+    """(E_lateral, E_axial, E_volume) in percent (Sec. 4.1.3); axial terms are None without
     an axial RMSE."""
     e_lat = 100.0 - math.sqrt((100.0 - ji_pct) ** 2 + (alpha_lat * rmse_lat_nm) ** 2)
     if rmse_ax_nm is None:

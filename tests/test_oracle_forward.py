@@ -269,3 +269,63 @@ def test_quantized_forward_matches_torch_emulation():
             a = torch.relu(F.conv2d(a, wl, torch.from_numpy(w.conv_b[layer]), padding=d, dilation=d))
         ref = F.conv2d(a, torch.from_numpy(w.head_w)[:, :, None, None], torch.from_numpy(w.head_b)).numpy()
         assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max(), fmt
+
+
+# ----------------------------------------------------------------------------- three-frame context
+
+
+def test_context_net_matches_torch_conv2d_with_three_input_channels():
+    """in_ch = 3: the first layer convolves (frame t-1, t, t+1) as three input channels."""
+    _, _, net, w = make_net(3, (1, 2, 4), in_ch=3)
+    rng = np.random.default_rng(21)
+    x0 = rng.normal(0.5, 0.5, (4, 3, 9, 10))
+    got = oracle.forward_x(net, x0)
+    ref = torch_reference(x0, w, (1, 2, 4))
+    assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def _summed_first_layer(spec3, w3, channels):
+    """The in_ch = 1 net whose first-layer weights are w3 summed over the given input channels."""
+    spec1 = synth.NetSpec(in_ch=1, channels=spec3.channels, dilations=spec3.dilations)
+    w1 = synth.init_weights(spec1, 0)
+    w1.conv_w = [w3.conv_w[0][:, channels].sum(axis=1, keepdims=True)] + [a.copy() for a in w3.conv_w[1:]]
+    w1.conv_b = [b.copy() for b in w3.conv_b]
+    w1.head_w, w1.head_b = w3.head_w.copy(), w3.head_b.copy()
+    blob = synth.pack_blob(spec1, w1)
+    return oracle.Net(spec1.to_json(), blob)
+
+
+def test_context_of_a_constant_stack_is_linear_in_the_frame_weights():
+    """On a stack of identical frames the three input channels are equal inside the stack, so
+    the net equals the one-frame net with first-layer weights summed over t-1, t, t+1; at the
+    stack's first and last frame the missing neighbour is zero, which leaves only two of the
+    three weight slices (zero padding in time, not replication)."""
+    spec3 = synth.NetSpec(in_ch=3, channels=4, dilations=(1, 2, 4, 1))
+    w3 = synth.init_weights(spec3, 9)
+    w3.conv_w[0] = np.round(w3.conv_w[0] * 256.0) / 256.0  # sums of these stay exact in float32
+    blob3 = synth.pack_blob(spec3, w3)
+    net3, w3 = oracle.Net(spec3.to_json(), blob3), synth.blob_f32_weights(blob3)
+    rng = np.random.default_rng(5)
+    frame = rng.integers(90, 400, (1, 12, 13)).astype(np.uint16)
+    stack = np.repeat(frame, 4, axis=0)
+    got = oracle.forward(net3, stack, 1.0, 100.0)
+    inner = oracle.forward(_summed_first_layer(spec3, w3, [0, 1, 2]), frame, 1.0, 100.0)[0]
+    first = oracle.forward(_summed_first_layer(spec3, w3, [1, 2]), frame, 1.0, 100.0)[0]
+    last = oracle.forward(_summed_first_layer(spec3, w3, [0, 1]), frame, 1.0, 100.0)[0]
+    tol = 1e-11 * max(1.0, np.abs(inner).max())
+    for t in (1, 2):
+        assert np.max(np.abs(got[t] - inner)) <= tol
+    assert np.max(np.abs(got[0] - first)) <= tol
+    assert np.max(np.abs(got[3] - last)) <= tol
+    assert np.max(np.abs(first - inner)) > 1e3 * tol  # the edge rule is visible in the output
+
+
+def test_context_input_order_and_edges():
+    x = np.arange(3 * 2 * 2, dtype=np.float64).reshape(3, 2, 2)
+    c = oracle.context_input(x, 3)
+    assert c.shape == (3, 3, 2, 2)
+    assert np.array_equal(c[1, 0], x[0]) and np.array_equal(c[1, 1], x[1]) and np.array_equal(c[1, 2], x[2])
+    assert not c[0, 0].any() and not c[2, 2].any()
+    assert np.array_equal(oracle.context_input(x, 1)[:, 0], x)
+    with pytest.raises(ValueError):
+        oracle.context_input(x, 2)
