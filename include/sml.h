@@ -76,7 +76,10 @@ typedef struct {
  * net_spec: NUL-terminated JSON object, e.g.
  *   {"in_ch":1,"channels":48,"dilations":[1,2,4,8,16,8,4,1],"precision":"bf16",
  *    "in_scale":0.001,"z_scale":1000,"ph_scale":10000}
- *   in_ch must be 1; channels in {16,32,48,64}; 2..16 layers with dilations 1..64;
+ *   in_ch 1 (one frame per output frame) or 3 (frames t-1, t, t+1 as the first layer's
+ *   input channels, the three-frame temporal context of Sec. 3.1; zero where t-1 or t+1 lies
+ *   outside the frames of the call; chunk edges inside a call read the neighbouring frames);
+ *   channels in {16,32,48,64}; 2..16 layers with dilations 1..64;
  *   precision "fp32" (SIMT FP32 FMA), "bf16" (tensor cores, FP32 accumulation) or
  *   "fp8" (e4m3 activations and weights, FP32 accumulation; needs "act_scales": one
  *   positive float per conv layer, the scale of that layer's input activations).

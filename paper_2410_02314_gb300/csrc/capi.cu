@@ -176,7 +176,7 @@ struct sml_ctx {
   long long chunk_px = 1 << 24;
   int tc_stages = 0;  // "tc_stages": TMA ring depth, 0 = as deep as shared memory allows
   // device weights
-  std::vector<float> w1, b1;  // layer 1 [C][9], [C] (host: passed to the kernel by value)
+  std::vector<float> w1, b1;  // layer 1 [C][in_ch][9], [C] (host: passed to the kernel by value)
   float* wf32[kMaxLayers] = {nullptr};  // [9][C][C]
   float* bias[kMaxLayers] = {nullptr};
   void* bimg[kMaxLayers] = {nullptr};
@@ -336,7 +336,7 @@ int get_plan(sml_ctx* ctx, int H, int W) {
       (r = dev_alloc(ctx, &p.maps, npx * kHeads * sizeof(float))) ||
       (r = dev_alloc(ctx, &p.block_counts, decode_blocks(npx) * sizeof(unsigned))) ||
       (r = dev_alloc(ctx, &p.block_offsets, decode_blocks(npx) * sizeof(unsigned long long))) ||
-      (r = dev_alloc(ctx, &p.frames, npx * sizeof(uint16_t))) ||
+      (r = dev_alloc(ctx, &p.frames, (size_t)(Tc + 2) * hw * sizeof(uint16_t))) ||  // + context frames
       (r = dev_alloc(ctx, &p.cam_maps, 2 * hw * sizeof(float)))) {
     free_plan(p);
     return r;
@@ -359,15 +359,27 @@ int get_plan(sml_ctx* ctx, int H, int W) {
   return SML_OK;
 }
 
-// One chunk of frames through the network: maps [tc][5][H][W] (+ optional logits).
-int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, int H, int W, const CamArgs& cam, float* maps,
-                  float* logits, cudaStream_t s, unsigned* d_amax = nullptr) {
+// The frames a chunk's first layer may read: with three-frame context (in_ch = 3) the frames
+// just before and after the chunk, where the stack has them.
+struct FrameRange {
+  int first, last;  // relative to the chunk's first frame
+};
+FrameRange chunk_frames(const sml_ctx* ctx, int T, int t0, int tc) {
+  if (ctx->in_ch == 1) return {0, tc - 1};
+  return {t0 > 0 ? -1 : 0, t0 + tc < T ? tc : tc - 1};
+}
+
+// One chunk of frames through the network: maps [tc][5][H][W] (+ optional logits).  d_frames
+// points at the chunk's first frame; frames fr.first .. fr.last around it are readable.
+int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, FrameRange fr, int H, int W, const CamArgs& cam,
+                  float* maps, float* logits, cudaStream_t s, unsigned* d_amax = nullptr) {
   Plan& p = *ctx->plan;
   const int L = ctx->L, C = ctx->C;
   float l1_scale = ctx->prec == kFP8 ? 1.0f / ctx->act_scale[1] : 1.0f;
   {
     ProfScope ps(ctx, SML_KERNEL_LAYER1, s);
-    SML_CUDA(launch_ingest_l1(d_frames, tc, H, W, ctx->dil[0], cam, ctx->w1.data(), ctx->b1.data(), C, ctx->prec, l1_scale, p.act[0], s),
+    SML_CUDA(launch_ingest_l1(d_frames, tc, H, W, ctx->dil[0], cam, ctx->w1.data(), ctx->b1.data(), C, ctx->in_ch, fr.first,
+                              fr.last, ctx->prec, l1_scale, p.act[0], s),
              "layer 1");
   }
   ++ctx->launches;
@@ -466,11 +478,15 @@ int localize_device(sml_ctx* ctx, const uint16_t* d_frames, bool frames_on_host,
   for (int t0 = 0; t0 < T; t0 += p.Tc) {
     int tc = std::min(p.Tc, T - t0);
     const uint16_t* f = d_frames + (size_t)t0 * fpx;
-    if (frames_on_host) {
-      SML_CUDA(cudaMemcpyAsync(p.frames, f, (size_t)tc * fpx * sizeof(uint16_t), cudaMemcpyHostToDevice, s), "H2D frames");
-      f = p.frames;
+    const FrameRange fr = chunk_frames(ctx, T, t0, tc);
+    if (frames_on_host) {  // the chunk and its context frames, staged into the plan's buffer
+      const size_t n = (size_t)(fr.last - fr.first + 1) * fpx;
+      SML_CUDA(cudaMemcpyAsync(p.frames, f + (ptrdiff_t)fr.first * (ptrdiff_t)fpx, n * sizeof(uint16_t),
+                               cudaMemcpyHostToDevice, s),
+               "H2D frames");
+      f = p.frames - (ptrdiff_t)fr.first * (ptrdiff_t)fpx;
     }
-    if ((r = forward_chunk(ctx, f, tc, H, W, cam, p.maps, nullptr, s))) return r;
+    if ((r = forward_chunk(ctx, f, tc, fr, H, W, cam, p.maps, nullptr, s))) return r;
     DecodeArgs da{};
     da.maps = p.maps;
     da.T = tc;
@@ -509,7 +525,8 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
   if (ctx->tc_stages < 0 || (ctx->tc_stages > 0 && ctx->tc_stages < 4) || ctx->tc_stages > 16)
     return fail(nullptr, SML_ERR_BAD_SPEC, "tc_stages must be 0 (as deep as shared memory allows) or 4..16");
 
-  if (ctx->in_ch != 1) return fail(nullptr, SML_ERR_BAD_SPEC, "in_ch must be 1");
+  if (ctx->in_ch != 1 && ctx->in_ch != 3)
+    return fail(nullptr, SML_ERR_BAD_SPEC, "in_ch must be 1 (one frame) or 3 (frames t-1, t, t+1)");
   if (ctx->C != 16 && ctx->C != 32 && ctx->C != 48 && ctx->C != 64)
     return fail(nullptr, SML_ERR_BAD_SPEC, "channels must be 16, 32, 48 or 64");
   if (ctx->chunk_px < 1) return fail(nullptr, SML_ERR_BAD_SPEC, "chunk_px must be >= 1");
@@ -773,8 +790,8 @@ int sml_forward_maps(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W
   const size_t fpx = (size_t)H * W;
   for (int t0 = 0; t0 < T; t0 += ctx->plan->Tc) {
     int tc = std::min(ctx->plan->Tc, T - t0);
-    if ((r = forward_chunk(ctx, d_frames + (size_t)t0 * fpx, tc, H, W, ca, d_maps + (size_t)t0 * kHeads * fpx,
-                           d_logits ? d_logits + (size_t)t0 * fpx : nullptr, s)))
+    if ((r = forward_chunk(ctx, d_frames + (size_t)t0 * fpx, tc, chunk_frames(ctx, T, t0, tc), H, W, ca,
+                           d_maps + (size_t)t0 * kHeads * fpx, d_logits ? d_logits + (size_t)t0 * fpx : nullptr, s)))
       return r;
   }
   return SML_OK;
@@ -864,7 +881,9 @@ int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, in
   const size_t fpx = (size_t)H * W;
   for (int t0 = 0; t0 < T; t0 += ctx->plan->Tc) {
     int tc = std::min(ctx->plan->Tc, T - t0);
-    if ((r = forward_chunk(ctx, d_frames + (size_t)t0 * fpx, tc, H, W, ca, ctx->plan->maps, nullptr, s, d_amax))) return r;
+    if ((r = forward_chunk(ctx, d_frames + (size_t)t0 * fpx, tc, chunk_frames(ctx, T, t0, tc), H, W, ca, ctx->plan->maps,
+                           nullptr, s, d_amax)))
+      return r;
   }
   unsigned h[kMaxLayers];
   SML_CUDA(cudaMemcpyAsync(h, d_amax, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H amax");

@@ -27,9 +27,9 @@ __device__ __forceinline__ float cam_input(const uint16_t* __restrict__ f, int H
 }
 
 // Layer-1 weights travel by value (kernel parameter); each thread copies the ones it uses
-// into registers once per block.
+// into registers.
 struct L1Params {
-  float w[64 * 9];  // [co][ky*3+kx]
+  float w[64 * 3 * 9];  // [co][ci][ky*3+kx]
   float b[64];
 };
 
@@ -37,64 +37,70 @@ constexpr int kL1Tile = 128;     // pixels of one image row per block (and threa
 constexpr int kL1Rows = 4;       // image rows per block
 constexpr int kL1Px = 8;         // pixels per thread: columns pg + 16*p, p < kL1Px
 constexpr int kL1ChGroups = 8;   // a thread computes C/8 output channels
+constexpr int kL1Span = kL1Tile + 2 * 64;  // staged input pixels per row (dilation <= 64)
+
+// Dynamic shared memory of one block: staged inputs [kL1Rows][3][IN_CH][kL1Span] floats,
+// then the padded output tile [kL1Tile][C*OB + 16] bytes.
+template <int C, int OUT, int IN_CH>
+constexpr size_t l1_smem_bytes() {
+  return (size_t)kL1Rows * 3 * IN_CH * kL1Span * 4 + (size_t)kL1Tile * (C * (OUT == 0 ? 4 : (OUT == 1 ? 2 : 1)) + 16);
+}
 
 // One block: a 128-pixel strip of kL1Rows rows of one frame.  Thread (pg = lane % 16,
-// cg = 2*warp + lane / 16) computes channels cg*C/8 .. +C/8 for the strip's pixels pg + 16p
-// with its 9*C/8 weights in registers (FMAs with register operands run at full rate; with
-// constant-bank weight operands they ran at half the rate).  The three dilated input rows of
-// every output row of the block go through the camera transform into shared memory first
-// (one global round trip per block); the thread's FMAs follow the order bias, then taps
-// (ky, kx) row-major; outputs are staged in shared memory (rows padded by 16 bytes against
+// cg = 2*warp + lane / 16) computes channels cg*C/8 .. +C/8 for the strip's pixels pg + 16p.
+// FMAs take their weights from registers (with constant-bank weight operands they ran at half
+// the rate).  The dilated input rows of every output row of the block (IN_CH input channels:
+// the frame itself, or frames t-1, t, t+1) go through the camera transform into shared memory
+// first, one global round trip per block.  FMA order: bias, then input channel, then taps
+// (ky, kx) row-major.  Outputs are staged in shared memory (rows padded by 16 bytes against
 // bank conflicts) so that the stores to HBM are whole 16-byte chunks, consecutive across
 // threads.
-template <int C, int OUT>
+template <int C, int OUT, int IN_CH>
 __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restrict__ frames, int H, int W, int d,
-                                                       int t0, CamArgs cam, const __grid_constant__ L1Params prm,
-                                                       float out_scale, void* __restrict__ out) {
+                                                       int t0, int t_first, int t_last, CamArgs cam,
+                                                       const __grid_constant__ L1Params prm, float out_scale,
+                                                       void* __restrict__ out) {
   constexpr int CPT = C / kL1ChGroups;
   constexpr int OB = OUT == 0 ? 4 : (OUT == 1 ? 2 : 1);  // output bytes per channel
   constexpr int OS = C * OB + 16;                        // staged bytes per pixel
-  __shared__ float xs[kL1Rows][3][kL1Tile + 2 * 64];
-  __shared__ __align__(16) uint8_t ot[kL1Tile * OS];  // [pixel][channel], padded rows
+  extern __shared__ __align__(16) uint8_t l1_smem[];
+  float(*xs)[3][IN_CH][kL1Span] = reinterpret_cast<float(*)[3][IN_CH][kL1Span]>(l1_smem);
+  uint8_t* ot = l1_smem + (size_t)kL1Rows * 3 * IN_CH * kL1Span * 4;
   const int j0 = blockIdx.x * kL1Tile, t = t0 + blockIdx.z, i0 = blockIdx.y * kL1Rows;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int pg = lane & 15, cg = 2 * warp + (lane >> 4);
   const int span = kL1Tile + 2 * d;
-  const uint16_t* f = frames + (size_t)t * H * W;
 #pragma unroll
-  for (int r = 0; r < kL1Rows; ++r)
+  for (int ci = 0; ci < IN_CH; ++ci) {
+    const int tf = IN_CH == 1 ? t : t + ci - 1;  // source frame of input channel ci
+    const bool have = tf >= t_first && tf <= t_last;
+    const uint16_t* f = frames + (ptrdiff_t)tf * H * W;
 #pragma unroll
-    for (int ky = 0; ky < 3; ++ky)
-      for (int c = threadIdx.x; c < span; c += kL1Tile)
-        xs[r][ky][c] = cam_input(f, H, W, i0 + r + (ky - 1) * d, j0 - d + c, cam);
-  float w[CPT][9], bias[CPT];
+    for (int r = 0; r < kL1Rows; ++r)
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky)
+        for (int c = threadIdx.x; c < span; c += kL1Tile)
+          xs[r][ky][ci][c] = have ? cam_input(f, H, W, i0 + r + (ky - 1) * d, j0 - d + c, cam) : 0.0f;
+  }
+  float w[IN_CH == 1 ? CPT : 1][9], bias[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) {
     bias[c] = prm.b[cg * CPT + c];
+    if (IN_CH == 1) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) w[c][k] = prm.w[(cg * CPT + c) * 9 + k];
+      for (int k = 0; k < 9; ++k) w[IN_CH == 1 ? c : 0][k] = prm.w[(cg * CPT + c) * 9 + k];
+    }
   }
   const int npx = W - j0 < kL1Tile ? W - j0 : kL1Tile;  // valid pixels of the strip
   for (int r = 0; r < kL1Rows; ++r) {
     const int i = i0 + r;
     if (i >= H) break;
     __syncthreads();  // xs is filled; the previous row's ot is written out
-#pragma unroll
-    for (int p = 0; p < kL1Px; ++p) {
-      const int px = pg + 16 * p;
-      float x[9];
-#pragma unroll
-      for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-        for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xs[r][ky][px + kx * d];
+    // ReLU, quantise and stage one pixel's CPT outputs
+    auto stage = [&](int px, const float (&acc)[CPT]) {
       float a[CPT];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        float acc = bias[c];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) acc = fmaf(w[c][k], x[k], acc);
-        a[c] = fmaxf(acc, 0.0f);
-      }
+      for (int c = 0; c < CPT; ++c) a[c] = fmaxf(acc[c], 0.0f);
       uint8_t* dst = ot + (size_t)px * OS + cg * CPT * OB;
       if (OUT == 0) {
 #pragma unroll
@@ -111,6 +117,55 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
           *reinterpret_cast<uint16_t*>(dst + c) = __nv_cvt_float2_to_fp8x2(
               make_float2(a[c] * out_scale, a[c + 1] * out_scale), __NV_SATFINITE, __NV_E4M3);
       }
+    };
+    if (IN_CH == 1) {  // one pixel at a time: its outputs are staged right away
+#pragma unroll
+      for (int p = 0; p < kL1Px; ++p) {
+        const int px = pg + 16 * p;
+        float x[9];
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xs[r][ky][0][px + kx * d];
+        float acc[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          float a = bias[c];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) a = fmaf(w[IN_CH == 1 ? c : 0][k], x[k], a);
+          acc[c] = a;
+        }
+        stage(px, acc);
+      }
+    } else {  // input channel outer, so each channel's weights are loaded once per row
+      float acc[kL1Px][CPT];
+#pragma unroll
+      for (int p = 0; p < kL1Px; ++p)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) acc[p][c] = bias[c];
+#pragma unroll
+      for (int ci = 0; ci < IN_CH; ++ci) {
+        float wc[CPT][9];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+#pragma unroll
+          for (int k = 0; k < 9; ++k) wc[c][k] = prm.w[((cg * CPT + c) * IN_CH + ci) * 9 + k];
+#pragma unroll
+        for (int p = 0; p < kL1Px; ++p) {
+          const int px = pg + 16 * p;
+          float x[9];
+#pragma unroll
+          for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xs[r][ky][ci][px + kx * d];
+#pragma unroll
+          for (int c = 0; c < CPT; ++c)
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc[p][c] = fmaf(wc[c][k], x[k], acc[p][c]);
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < kL1Px; ++p) stage(pg + 16 * p, acc[p]);
     }
     __syncthreads();
     const size_t row = (size_t)t * H + i;
@@ -228,38 +283,57 @@ inline unsigned grid_for(long long npx) { return (unsigned)((npx + kSimtThreads 
 
 }  // namespace
 
-cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1,
-                             const float* b1, int C, int prec, float out_scale, void* out, cudaStream_t s) {
-  if ((long long)T * H * W == 0) return cudaSuccess;
-  if (d > 64 || C > 64) return cudaErrorInvalidValue;
-  // w1/b1 are host copies here: they travel as a kernel parameter
-  L1Params prm;
-  memset(&prm, 0, sizeof(prm));
-  memcpy(prm.w, w1, sizeof(float) * C * 9);
-  memcpy(prm.b, b1, sizeof(float) * C);
+template <int C, int OUT, int IN_CH>
+static cudaError_t launch_l1(const uint16_t* frames, int T, int H, int W, int d, int t_first, int t_last,
+                             const CamArgs& cam, const L1Params& prm, float out_scale, void* out, cudaStream_t s) {
+  constexpr size_t smem = l1_smem_bytes<C, OUT, IN_CH>();
+  static bool configured = false;  // opt in to more than 48 KB once per instantiation
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_ingest_l1<C, OUT, IN_CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
   for (int t0 = 0; t0 < T; t0 += 65535) {
     dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + kL1Rows - 1) / kL1Rows, (unsigned)(T - t0 < 65535 ? T - t0 : 65535)),
         block(kL1Tile);
-#define SML_L1(CC)                                                                                       \
-  case CC:                                                                                               \
-    if (prec == kFP32)                                                                                   \
-      k_ingest_l1<CC, 0><<<grid, block, 0, s>>>(frames, H, W, d, t0, cam, prm, out_scale, out);          \
-    else if (prec == kBF16)                                                                              \
-      k_ingest_l1<CC, 1><<<grid, block, 0, s>>>(frames, H, W, d, t0, cam, prm, out_scale, out);          \
-    else                                                                                                 \
-      k_ingest_l1<CC, 2><<<grid, block, 0, s>>>(frames, H, W, d, t0, cam, prm, out_scale, out);          \
-    break;
-    switch (C) {
-      SML_L1(16)
-      SML_L1(32)
-      SML_L1(48)
-      SML_L1(64)
-      default:
-        return cudaErrorInvalidValue;
-    }
-#undef SML_L1
+    k_ingest_l1<C, OUT, IN_CH><<<grid, block, smem, s>>>(frames, H, W, d, t0, t_first, t_last, cam, prm, out_scale, out);
   }
   return cudaGetLastError();
+}
+
+template <int C>
+static cudaError_t launch_l1_prec(const uint16_t* frames, int T, int H, int W, int d, int in_ch, int t_first,
+                                  int t_last, const CamArgs& cam, const L1Params& prm, int prec, float out_scale,
+                                  void* out, cudaStream_t s) {
+  if (in_ch == 1) {
+    if (prec == kFP32) return launch_l1<C, 0, 1>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
+    if (prec == kBF16) return launch_l1<C, 1, 1>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
+    return launch_l1<C, 2, 1>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
+  }
+  if (prec == kFP32) return launch_l1<C, 0, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
+  if (prec == kBF16) return launch_l1<C, 1, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
+  return launch_l1<C, 2, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
+}
+
+cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1,
+                             const float* b1, int C, int in_ch, int t_first, int t_last, int prec, float out_scale,
+                             void* out, cudaStream_t s) {
+  if ((long long)T * H * W == 0) return cudaSuccess;
+  if (d > 64 || C > 64 || (in_ch != 1 && in_ch != 3)) return cudaErrorInvalidValue;
+  if (t_first > 0 || t_last < T - 1) return cudaErrorInvalidValue;
+  // w1/b1 are host copies here: they travel as a kernel parameter
+  L1Params prm;
+  memset(&prm, 0, sizeof(prm));
+  memcpy(prm.w, w1, sizeof(float) * C * in_ch * 9);
+  memcpy(prm.b, b1, sizeof(float) * C);
+  switch (C) {
+    case 16: return launch_l1_prec<16>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, s);
+    case 32: return launch_l1_prec<32>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, s);
+    case 48: return launch_l1_prec<48>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, s);
+    case 64: return launch_l1_prec<64>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_amax(const void* x, size_t n, int prec, unsigned* out, cudaStream_t s) {

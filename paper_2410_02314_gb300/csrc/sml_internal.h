@@ -46,10 +46,13 @@ struct CamArgs {
 // --- layer 1: camera transform + Cin=1 dilated 3x3 conv, bias, ReLU -------------------
 // prec kFP32 writes float NHWC [T][H][W][C]; kBF16 / kFP8 write row-planar activations
 // [T][H][C/16][W][row bytes] (16 channels per group: 32-byte bf16 rows, 16-byte e4m3 rows).  out_scale
-// multiplies the FP8 output before rounding (1 / activation scale).  w1 [C][9] and b1 [C]
-// are HOST pointers (the weights are passed to the kernel by value).
+// multiplies the FP8 output before rounding (1 / activation scale).  w1 [C][in_ch][9] and
+// b1 [C] are HOST pointers (the weights are passed to the kernel by value).  in_ch = 3 takes
+// frames t-1, t, t+1 as the input channels; frames[k] exists for t_first <= k <= t_last
+// (t_first in {-1, 0}, t_last in {T-1, T}) and is zero outside that range.
 cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1,
-                             const float* b1, int C, int prec, float out_scale, void* out, cudaStream_t s);
+                             const float* b1, int C, int in_ch, int t_first, int t_last, int prec, float out_scale,
+                             void* out, cudaStream_t s);
 
 // Max of n post-ReLU activations (fp32 or bf16 buffer) into *out (float bits, atomicMax).
 cudaError_t launch_amax(const void* x, size_t n, int prec, unsigned* out, cudaStream_t s);

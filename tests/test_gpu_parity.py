@@ -400,3 +400,56 @@ def test_large_fov_2048_sampled(prec):
     recs = loc.localize(w.frames, 0.5, gain=w.cam.gain, offset=w.cam.offset, gain_map=w.cam.gain_map,
                         offset_map=w.cam.offset_map, capacity=4_000_000)
     assert recs.tobytes() == oracle.decode(m, 0.5, net.z_scale, net.ph_scale).tobytes()
+
+
+# ----------------------------------------------------------------------------- three-frame context
+
+
+def _context_net(C, dil, prec, seed=31):
+    spec = synth.NetSpec(in_ch=3, channels=C, dilations=tuple(dil), precision=prec)
+    return spec.to_json(), synth.pack_blob(spec, synth.init_weights(spec, seed))
+
+
+@pytest.mark.parametrize("prec,C", [("fp32", 16), ("fp32", 48), ("bf16", 32), ("bf16", 48)])
+def test_three_frame_context_matches_oracle(prec, C):
+    """in_ch = 3 (frames t-1, t, t+1 as the first layer's input channels, zero beyond the
+    stack): parity with the oracle, with per-pixel camera maps and a ragged frame size."""
+    rng = np.random.default_rng(41)
+    js, blob = _context_net(C, (1, 2, 5, 1), prec)
+    T, H, W = 5, 37, 150
+    frames = rng.integers(95, 700, (T, H, W)).astype(np.uint16)
+    cam = synth.Camera(1.0, 100.0, rng.normal(2.0, 0.1, (H, W)).astype(np.float32),
+                       rng.normal(100.0, 5.0, (H, W)).astype(np.float32))
+    _, maps, logits = gpu_maps(js, blob, frames, cam)
+    if prec == "fp32":
+        net = oracle.Net(js, blob)
+        ref = oracle.forward(net, frames, gain=cam.gain, offset=cam.offset, gain_map=cam.gain_map.astype(np.float64),
+                             offset_map=cam.offset_map.astype(np.float64))
+        err = map_errors(maps, logits, ref)
+        print("fp32 context", np.round(err, 7))
+        assert max(err) <= TOL["fp32"]
+    else:
+        check_quantized(prec, js, blob, frames, cam, maps, logits)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_three_frame_context_across_chunk_edges(prec):
+    """Chunks of 2 frames split a 7-frame stack; each chunk's first layer reads the frames
+    just outside it.  Maps and records equal the single-chunk run bit for bit, from device
+    and from host frames."""
+    import json
+
+    rng = np.random.default_rng(43)
+    js, blob = _context_net(32, (1, 4, 2), prec)
+    T, H, W = 7, 40, 64
+    frames = rng.integers(95, 900, (T, H, W)).astype(np.uint16)
+    cam = synth.Camera(2.0, 100.0)
+    small = json.dumps(dict(json.loads(js), chunk_px=2 * H * W))
+    _, maps_one, logits_one = gpu_maps(js, blob, frames, cam)
+    _, maps_two, logits_two = gpu_maps(small, blob, frames, cam)
+    assert torch.equal(maps_one, maps_two) and torch.equal(logits_one, logits_two)
+    one = sml.Localizer(js, blob).localize(frames, 0.5, gain=2.0, offset=100.0)
+    loc2 = sml.Localizer(small, blob)
+    host = loc2.localize(frames, 0.5, gain=2.0, offset=100.0)
+    dev = loc2.localize(torch.from_numpy(frames).cuda(), 0.5, gain=2.0, offset=100.0)
+    assert len(one) > 0 and one.tobytes() == host.tobytes() == dev.tobytes()
