@@ -6,12 +6,13 @@
  * single tcgen05.mma chain through the same shared-memory descriptors, instruction
  * descriptor and TMEM read-out that the dilated-conv kernel uses (the GEMM inside the
  * implicit-GEMM convolution of Sec. 3.2.1).  All pointers are device memory:
- *   d_a: k/e planes of [128 rows][16 bytes] (e = 8 bf16 or 16 e4m3 elements per plane):
- *        element (m, kk) at byte (kk/e)*2048 + m*16 + (kk%e)*size;
- *   d_b: k/s blocks (s = 16 for bf16, 32 for fp8) of (n/8)*256 bytes: element (nn, kk) of
+ *   d_a: k/e planes of [128 rows][16 bytes] (e = 8 bf16, 16 e4m3 or 4 tf32 elements per
+ *        plane): element (m, kk) at byte (kk/e)*2048 + m*16 + (kk%e)*size;
+ *   d_b: k/s blocks (s = 2e elements: one MMA's K) of (n/8)*256 bytes: element (nn, kk) of
  *        block kk/s at byte (nn/8)*256 + ((kk%s)/e)*128 + (nn%8)*16 + (kk%e)*size;
  *   d_d: float32 [128][n] output (row-major).
- * n in 16..256 (multiple of 16); k a positive multiple of 32; fp8 selects e4m3 inputs;
+ * n in 16..256 (multiple of 16); k a positive multiple of 32; kind 0 = bf16 (kind::f16),
+ * 1 = e4m3 (kind::f8f6f4), 2 = tf32 (kind::tf32, fp32 storage of which the MMA uses 19 bits);
  * d_col: first TMEM column of the accumulator (multiple of 16, d_col + n <= 512).
  * Synchronises the stream.  Returns SML_OK, SML_ERR_BAD_ARG or SML_ERR_CUDA (also when the
  * kernel's bounded wait for the MMA gave up).
@@ -23,7 +24,7 @@
 extern "C" {
 #endif
 
-int sml_debug_umma(const void* d_a, const void* d_b, float* d_d, int n, int k, int fp8, int d_col, void* stream);
+int sml_debug_umma(const void* d_a, const void* d_b, float* d_d, int n, int k, int kind, int d_col, void* stream);
 
 #ifdef __cplusplus
 }

@@ -269,9 +269,10 @@ def sml_decode_maps_static(d_maps, p_min, z_scale, ph_scale, d_out, d_n, stream=
         raise SmlError(code, "sml_decode_maps_static failed")
 
 
-def sml_debug_umma(d_a, d_b, d_d, n, k, fp8=False, d_col=0, stream=None):
-    code = lib().sml_debug_umma(_ptr(d_a), _ptr(d_b), _ptr(d_d), int(n), int(k), int(bool(fp8)), int(d_col),
-                                _stream(stream))
+def sml_debug_umma(d_a, d_b, d_d, n, k, kind="bf16", d_col=0, stream=None):
+    """kind: "bf16", "e4m3" or "tf32" (see include/sml_debug.h)."""
+    code = lib().sml_debug_umma(_ptr(d_a), _ptr(d_b), _ptr(d_d), int(n), int(k), {"bf16": 0, "e4m3": 1, "tf32": 2}[kind],
+                                int(d_col), _stream(stream))
     if code != SML_OK:
         raise SmlError(code, "umma self-test failed")
 

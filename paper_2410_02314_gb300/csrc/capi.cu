@@ -932,12 +932,13 @@ int sml_train_heads_loss(const float* a, const float* tgt, int B, int H, int W, 
 }
 
 // Debug entry (include/sml_debug.h): one UMMA tile through the conv kernel's descriptor helpers.
-int sml_debug_umma(const void* d_a, const void* d_b, float* d_d, int n, int k, int fp8, int d_col, void* stream) {
+int sml_debug_umma(const void* d_a, const void* d_b, float* d_d, int n, int k, int kind, int d_col, void* stream) {
   static int* d_err = nullptr;
   if (!d_err && cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) return SML_ERR_OOM;
   cudaMemset(d_err, 0, sizeof(int));
   if (n % 16 || n < 16 || n > 256 || k % 32 || k < 32 || d_col < 0 || d_col % 16 || d_col + n > 512) return SML_ERR_BAD_ARG;
-  cudaError_t e = launch_umma_selftest(d_a, d_b, d_d, n, k, fp8 ? kFP8 : kBF16, d_col, d_err,
+  if (kind < 0 || kind > 2) return SML_ERR_BAD_ARG;
+  cudaError_t e = launch_umma_selftest(d_a, d_b, d_d, n, k, kind == 1 ? kFP8 : (kind == 2 ? kTF32 : kBF16), d_col, d_err,
                                        static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return SML_ERR_CUDA;
   if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return SML_ERR_CUDA;

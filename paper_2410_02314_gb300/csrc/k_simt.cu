@@ -17,14 +17,6 @@ namespace {
 
 constexpr int kSimtThreads = 128;
 
-__device__ __forceinline__ float cam_input(const uint16_t* __restrict__ f, int H, int W, int i, int j,
-                                           const CamArgs& cam) {
-  if (i < 0 || i >= H || j < 0 || j >= W) return 0.0f;
-  size_t px = (size_t)i * W + j;
-  float g = cam.gain_map ? cam.gain_map[px] : cam.gain;
-  float o = cam.offset_map ? cam.offset_map[px] : cam.offset;
-  return __fmul_rn(__fdiv_rn(__fsub_rn((float)f[px], o), g), cam.in_scale);
-}
 
 // Layer-1 weights travel by value (kernel parameter); each thread copies the ones it uses
 // into registers.

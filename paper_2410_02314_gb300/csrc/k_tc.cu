@@ -135,10 +135,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 // Instruction descriptor: D = F32, A/B K-major, dense.  kind::f16 with BF16 inputs
-// (a/b format 1) or kind::f8f6f4 with E4M3 inputs (format 0).
+// (a/b format 1), kind::tf32 (format 2) or kind::f8f6f4 with E4M3 inputs (format 0).
+__host__ __device__ constexpr uint32_t operand_format(int prec) { return prec == kBF16 ? 1u : (prec == kTF32 ? 2u : 0u); }
 __host__ __device__ constexpr uint32_t instr_desc(int prec, int M, int N) {
-  return (1u << 4) | ((prec == kBF16 ? 1u : 0u) << 7) | ((prec == kBF16 ? 1u : 0u) << 10) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+  return (1u << 4) | (operand_format(prec) << 7) | (operand_format(prec) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 template <int PREC>
@@ -147,6 +148,12 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, ui
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else if (PREC == kTF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
   } else {
@@ -615,14 +622,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
 
 // ------------------------------------------------------------------ UMMA self-test
 // One 128 x N x K product: A [128][K] and B [N][K] pre-packed by the host in the same
-// layouts the conv uses (A: planes of [128 rows][16 bytes]; B: the per-block image).
+// layouts the conv and layer 1 use (A: planes of [128 rows][16 bytes]; B: the per-block
+// image).  PREC kBF16, kFP8 or kTF32.
 template <int PREC>
 __global__ void __launch_bounds__(128, 1) k_umma_selftest(const uint8_t* A, const uint8_t* B, float* D, int N, int K,
                                                           int d_col, int* err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  constexpr int ES = PREC == kBF16 ? 2 : 1;
-  constexpr int KSTEP = PREC == kBF16 ? 16 : 32;
+  constexpr int ES = PREC == kBF16 ? 2 : (PREC == kTF32 ? 4 : 1);
+  constexpr int KSTEP = 32 / ES;  // elements per MMA: two 16-byte core-matrix columns
   const int a_bytes = 128 * K * ES, b_bytes = N * K * ES;
   uint8_t* sA = smem;
   uint8_t* sB = smem + a_bytes;
@@ -803,13 +811,17 @@ cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaSt
 
 cudaError_t launch_umma_selftest(const void* A, const void* B, float* D, int N, int K, int prec, int d_col, int* err,
                                  cudaStream_t s) {
-  const int es = prec == kBF16 ? 2 : 1;
+  const int es = prec == kBF16 ? 2 : (prec == kTF32 ? 4 : 1);
   size_t smem = 1024 + (size_t)128 * K * es + (size_t)N * K * es + 64;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   if (prec == kBF16) {
     cudaError_t e = cudaFuncSetAttribute(k_umma_selftest<kBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_umma_selftest<kBF16><<<1, 128, smem, s>>>(static_cast<const uint8_t*>(A), static_cast<const uint8_t*>(B), D, N, K, d_col, err);
+  } else if (prec == kTF32) {
+    cudaError_t e = cudaFuncSetAttribute(k_umma_selftest<kTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_umma_selftest<kTF32><<<1, 128, smem, s>>>(static_cast<const uint8_t*>(A), static_cast<const uint8_t*>(B), D, N, K, d_col, err);
   } else {
     cudaError_t e = cudaFuncSetAttribute(k_umma_selftest<kFP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

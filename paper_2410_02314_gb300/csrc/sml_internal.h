@@ -13,7 +13,7 @@ constexpr int kHeads = 5;
 constexpr int kMaxLayers = 16;
 constexpr int kTileM = 128;  // pixels per MMA tile (one row segment)
 
-enum Precision { kFP32 = 0, kBF16 = 1, kFP8 = 2 };
+enum Precision { kFP32 = 0, kBF16 = 1, kFP8 = 2, kTF32 = 3 /* MMA operand kind of the self-test only */ };
 
 // Decode parameters shared by the fused path and sml_decode_maps.
 struct DecodeArgs {
@@ -42,6 +42,19 @@ struct CamArgs {
   const float* gain_map;
   const float* offset_map;
 };
+
+#ifdef __CUDACC__
+// Network input of pixel (i, j) of one frame: (adu - offset) / gain * in_scale, each step one
+// IEEE rounding; zero outside the frame (the first layer's "same" zero padding).
+__device__ __forceinline__ float cam_input(const uint16_t* __restrict__ f, int H, int W, int i, int j,
+                                           const CamArgs& cam) {
+  if (i < 0 || i >= H || j < 0 || j >= W) return 0.0f;
+  size_t px = (size_t)i * W + j;
+  float g = cam.gain_map ? cam.gain_map[px] : cam.gain;
+  float o = cam.offset_map ? cam.offset_map[px] : cam.offset;
+  return __fmul_rn(__fdiv_rn(__fsub_rn((float)f[px], o), g), cam.in_scale);
+}
+#endif
 
 // --- layer 1: camera transform + Cin=1 dilated 3x3 conv, bias, ReLU -------------------
 // prec kFP32 writes float NHWC [T][H][W][C]; kBF16 / kFP8 write row-planar activations

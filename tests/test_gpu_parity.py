@@ -106,19 +106,28 @@ def _bf16_bits(x):
     return torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16)
 
 
-@pytest.mark.parametrize("fp8,N,d_col", [(False, 48, 0), (True, 48, 0), (False, 144, 48), (False, 48, 336),
-                                          (True, 144, 192), (False, 96, 288)])
-def test_umma_selftest_matches_matmul(fp8, N, d_col):
+def _tf32_values(x):
+    """float32 values with 10 explicit mantissa bits (exactly representable in tf32)."""
+    bits = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32) & np.uint32(0xFFFFE000)
+    return bits.view(np.float32)
+
+
+@pytest.mark.parametrize("kind,N,d_col", [("bf16", 48, 0), ("e4m3", 48, 0), ("bf16", 144, 48), ("bf16", 48, 336),
+                                          ("e4m3", 144, 192), ("bf16", 96, 288), ("tf32", 48, 0), ("tf32", 64, 64)])
+def test_umma_selftest_matches_matmul(kind, N, d_col):
     """One tcgen05 MMA chain: N = 48/96/144 accumulators at offset TMEM columns, as the
-    sliding-window conv uses them."""
+    sliding-window conv uses them; TF32 as the tensor-core layer 1 uses it."""
     rng = np.random.default_rng(0)
     K = 64
     a = rng.normal(0, 1, (128, K)).astype(np.float32)
     b = rng.normal(0, 1, (N, K)).astype(np.float32)
-    if fp8:
+    if kind == "e4m3":
         at = torch.from_numpy(a).to(torch.float8_e4m3fn)
         bt = torch.from_numpy(b).to(torch.float8_e4m3fn)
         e, s = 16, 32
+    elif kind == "tf32":
+        at, bt = torch.from_numpy(_tf32_values(a)), torch.from_numpy(_tf32_values(b))
+        e, s = 4, 8
     else:
         at, bt = _bf16_bits(a), _bf16_bits(b)
         e, s = 8, 16
@@ -127,7 +136,7 @@ def test_umma_selftest_matches_matmul(fp8, N, d_col):
     b_img = bt.reshape(N // 8, 8, K // s, s // e, e).permute(2, 0, 3, 1, 4).contiguous()
     da, db = a_img.view(torch.uint8).cuda(), b_img.view(torch.uint8).cuda()
     dd = torch.zeros((128, N), dtype=torch.float32, device="cuda")
-    sml.sml_debug_umma(da, db, dd, N, K, fp8=fp8, d_col=d_col)
+    sml.sml_debug_umma(da, db, dd, N, K, kind=kind, d_col=d_col)
     ref = af @ bf.T
     got = dd.cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
