@@ -591,8 +591,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
 #pragma unroll
             for (int e = 0; e < 8; ++e) ow[e] = bf16x2_relu(v[16 * gq + 2 * e], v[16 * gq + 2 * e + 1]);
             uint4* dst = reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 32);
-            dst[0] = o[0];
-            dst[1] = o[1];
+            __stcs(dst, o[0]);  // streaming: the next layer reads it from HBM anyway; keep L2 for halos
+            __stcs(dst + 1, o[1]);
           }
         } else {
 #pragma unroll
@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
               oh[e] = __nv_cvt_float2_to_fp8x2(
                   make_float2(v[16 * gq + 2 * e] * a.out_inv_scale, v[16 * gq + 2 * e + 1] * a.out_inv_scale),
                   __NV_SATFINITE, __NV_E4M3);
-            *reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 16) = o;
+            __stcs(reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 16), o);
           }
         }
       }
