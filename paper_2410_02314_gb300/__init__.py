@@ -51,8 +51,24 @@ EXPORTS = (
     "sml_train_conv_bwd",
     "sml_train_heads_work_bytes",
     "sml_train_heads_loss",
+    "sml_reader_open",
+    "sml_reader_next",
+    "sml_reader_release",
+    "sml_reader_stats",
+    "sml_reader_close",
+    "sml_localize_file",
 )
 SML_KERNEL_LAYER1, SML_KERNEL_CONV, SML_KERNEL_CONV_HEADS, SML_KERNEL_DECODE = 0, 1, 2, 3
+
+
+class IoStats(ctypes.Structure):
+    """Mirror of sml_io_stats (include/sml_io.h)."""
+
+    _fields_ = [("bytes_read", ctypes.c_double), ("read_seconds", ctypes.c_double),
+                ("wall_seconds", ctypes.c_double), ("frames", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class SmlError(RuntimeError):
@@ -110,6 +126,20 @@ def lib():
         L.sml_profile_read.restype = I
         L.sml_debug_umma.argtypes = [P, P, P, I, I, I, I, P]
         L.sml_debug_umma.restype = I
+        LL = ctypes.c_longlong
+        L.sml_reader_open.argtypes = [ctypes.c_char_p, LL, I, I, I, I, I, ctypes.POINTER(P)]
+        L.sml_reader_open.restype = I
+        L.sml_reader_next.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(I), ctypes.POINTER(LL), I]
+        L.sml_reader_next.restype = I
+        L.sml_reader_release.argtypes = [P, P]
+        L.sml_reader_release.restype = I
+        L.sml_reader_stats.argtypes = [P, ctypes.POINTER(IoStats)]
+        L.sml_reader_stats.restype = I
+        L.sml_reader_close.argtypes = [P]
+        L.sml_reader_close.restype = None
+        L.sml_localize_file.argtypes = [P, ctypes.c_char_p, LL, I, I, I, ctypes.POINTER(_Camera),
+                                        ctypes.POINTER(_Thresholds), I, P, S, ctypes.POINTER(S), ctypes.POINTER(IoStats)]
+        L.sml_localize_file.restype = I
         _lib = L
     return _lib
 
@@ -192,6 +222,76 @@ def sml_localize(ctx, frames, p_min, gain=1.0, offset=100.0, gain_map=None, offs
     if hasattr(out_arr, "data_ptr"):
         return out_arr[: n.value * RECORD_DTYPE.itemsize]
     return out_arr[: n.value]
+
+
+def sml_localize_file(ctx, path, T, H, W, p_min, batch=64, gain=1.0, offset=100.0, gain_map=None, offset_map=None,
+                      capacity=None, file_offset=0):
+    """Localize a raw uint16 stack file (include/sml_io.h): returns (records, stats dict)."""
+    cap = int(capacity if capacity is not None else max(16, T * ((H + 1) // 2) * ((W + 1) // 2)))
+    out = np.empty(cap, dtype=RECORD_DTYPE)
+    n = ctypes.c_size_t(0)
+    st = IoStats()
+    cam = _camera(gain, offset, gain_map, offset_map)
+    thr = _Thresholds(float(p_min))
+    code = lib().sml_localize_file(ctx, os.fsencode(path), int(file_offset), int(T), int(H), int(W), ctypes.byref(cam),
+                                   ctypes.byref(thr), int(batch), out.ctypes.data, cap, ctypes.byref(n),
+                                   ctypes.byref(st))
+    if code == SML_ERR_CAPACITY:
+        raise SmlError(code, sml_last_error(ctx), needed=int(n.value))
+    _check(ctx, code)
+    return out[: n.value], st.as_dict()
+
+
+class StackReader:
+    """Read-ahead over a raw uint16 stack file (include/sml_io.h).  Iterating yields
+    (first_frame, frames) with frames a numpy uint16 [n, H, W] view of a pinned buffer that
+    stays valid until the next iteration step (the buffer is then given back)."""
+
+    def __init__(self, path, T, H, W, batch=64, n_buffers=3, file_offset=0, timeout_ms=60000):
+        self.H, self.W, self.timeout_ms = int(H), int(W), int(timeout_ms)
+        h = ctypes.c_void_p()
+        code = lib().sml_reader_open(os.fsencode(path), int(file_offset), int(T), int(H), int(W), int(batch),
+                                     int(n_buffers), ctypes.byref(h))
+        if code != SML_OK:
+            raise SmlError(code, f"cannot open stack {path}")
+        self.handle = h.value
+
+    def __iter__(self):
+        held = None
+        try:
+            while True:
+                p, n, first = ctypes.c_void_p(), ctypes.c_int(0), ctypes.c_longlong(0)
+                code = lib().sml_reader_next(self.handle, ctypes.byref(p), ctypes.byref(n), ctypes.byref(first),
+                                             self.timeout_ms)
+                if held is not None:
+                    lib().sml_reader_release(self.handle, held)
+                    held = None
+                if code != SML_OK:
+                    raise SmlError(code, "stack read failed")
+                if n.value == 0:
+                    return
+                held = p.value
+                buf = (ctypes.c_uint16 * (n.value * self.H * self.W)).from_address(p.value)
+                yield int(first.value), np.frombuffer(buf, dtype=np.uint16).reshape(n.value, self.H, self.W)
+        finally:
+            if held is not None and self.handle is not None:
+                lib().sml_reader_release(self.handle, held)
+
+    def stats(self):
+        st = IoStats()
+        lib().sml_reader_stats(self.handle, ctypes.byref(st))
+        return st.as_dict()
+
+    def close(self):
+        if self.handle is not None:
+            lib().sml_reader_close(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sml_localize_async(ctx, d_frames, p_min, d_out, d_n, gain=1.0, offset=100.0, gain_map=None, offset_map=None,
@@ -305,6 +405,9 @@ class Localizer:
 
     def localize(self, frames, p_min, **kw):
         return sml_localize(self.ctx, frames, p_min, **kw)
+
+    def localize_file(self, path, T, H, W, p_min, **kw):
+        return sml_localize_file(self.ctx, path, T, H, W, p_min, **kw)
 
     def forward_maps(self, d_frames, d_maps, d_logits=None, **kw):
         sml_forward_maps(self.ctx, d_frames, d_maps, d_logits, **kw)

@@ -16,6 +16,9 @@
 #include <string>
 #include <vector>
 
+#include <chrono>
+
+#include "../../include/sml_io.h"
 #include "../../include/sml_train.h"
 #include "sml_internal.h"
 
@@ -948,3 +951,146 @@ int sml_debug_umma(const void* d_a, const void* d_b, float* d_d, int n, int k, i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------- stack files
+
+namespace {
+
+// Device-side resources of one sml_localize_file call, released on every exit path.
+struct FilePipe {
+  sml_reader* reader = nullptr;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t h2d[2] = {nullptr, nullptr}, cnt[2] = {nullptr, nullptr}, d2h[2] = {nullptr, nullptr};
+  uint8_t* dev = nullptr;                 // frames[2] | records[2] | counts[2]
+  unsigned long long* h_cnt = nullptr;    // pinned, 2 counts
+  ~FilePipe() {
+    if (copy) cudaStreamSynchronize(copy);
+    for (int k = 0; k < 2; ++k) {
+      if (h2d[k]) cudaEventDestroy(h2d[k]);
+      if (cnt[k]) cudaEventDestroy(cnt[k]);
+      if (d2h[k]) cudaEventDestroy(d2h[k]);
+    }
+    if (copy) cudaStreamDestroy(copy);
+    if (dev) cudaFree(dev);
+    if (h_cnt) cudaFreeHost(h_cnt);
+    if (reader) sml_reader_close(reader);
+  }
+};
+
+}  // namespace
+
+extern "C" int sml_localize_file(sml_ctx* ctx, const char* path, long long offset, int T, int H, int W,
+                                 const sml_camera* cam, const sml_thresholds* thr, int batch, sml_record* out,
+                                 size_t capacity, size_t* n_out, sml_io_stats* stats) {
+  if (!ctx) return SML_ERR_BAD_ARG;
+  ctx->launches = 0;
+  int r;
+  if (!path || !n_out || (capacity > 0 && !out) || batch < 1 || offset < 0) return fail(ctx, SML_ERR_BAD_ARG, "bad argument");
+  if ((r = check_dims(ctx, T, H, W)) || (r = check_thr(ctx, thr))) return r;
+  if (ctx->in_ch != 1) return fail(ctx, SML_ERR_UNSUPPORTED, "stack files need a one-frame input net (in_ch = 1)");
+  CamArgs ca;
+  if ((r = make_cam(ctx, cam, &ca))) return r;
+  *n_out = 0;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (T == 0) return SML_OK;
+  const auto t_start = std::chrono::steady_clock::now();
+  SML_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if ((r = get_plan(ctx, H, W))) return r;
+  cudaStream_t s = ctx->stream;
+  const size_t hw = (size_t)H * W;
+  if (ca.gain_map && !is_device_ptr(ca.gain_map)) {
+    SML_CUDA(cudaMemcpyAsync(ctx->plan->cam_maps, ca.gain_map, hw * 4, cudaMemcpyHostToDevice, s), "H2D gain map");
+    ca.gain_map = ctx->plan->cam_maps;
+  }
+  if (ca.offset_map && !is_device_ptr(ca.offset_map)) {
+    SML_CUDA(cudaMemcpyAsync(ctx->plan->cam_maps + hw, ca.offset_map, hw * 4, cudaMemcpyHostToDevice, s), "H2D offset map");
+    ca.offset_map = ctx->plan->cam_maps + hw;
+  }
+  FilePipe fp;
+  const size_t frame_bytes = (size_t)batch * hw * sizeof(uint16_t);
+  // a detection is a strict local maximum: at most one per 2x2 block of a frame
+  const size_t rec_cap = (size_t)batch * ((H + 1) / 2) * ((W + 1) / 2);
+  const size_t rec_bytes = rec_cap * sizeof(sml_record);
+  if ((r = dev_alloc(ctx, &fp.dev, 2 * frame_bytes + 2 * rec_bytes + 2 * sizeof(unsigned long long)))) return r;
+  uint16_t* d_frames[2] = {reinterpret_cast<uint16_t*>(fp.dev), reinterpret_cast<uint16_t*>(fp.dev + frame_bytes)};
+  sml_record* d_rec[2] = {reinterpret_cast<sml_record*>(fp.dev + 2 * frame_bytes),
+                          reinterpret_cast<sml_record*>(fp.dev + 2 * frame_bytes + rec_bytes)};
+  unsigned long long* d_n = reinterpret_cast<unsigned long long*>(fp.dev + 2 * frame_bytes + 2 * rec_bytes);
+  SML_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&fp.h_cnt), 2 * sizeof(unsigned long long), cudaHostAllocDefault),
+           "pinned counts");
+  SML_CUDA(cudaStreamCreateWithFlags(&fp.copy, cudaStreamNonBlocking), "copy stream");
+  for (int k = 0; k < 2; ++k) {
+    SML_CUDA(cudaEventCreateWithFlags(&fp.h2d[k], cudaEventDisableTiming), "event");
+    SML_CUDA(cudaEventCreateWithFlags(&fp.cnt[k], cudaEventDisableTiming), "event");
+    SML_CUDA(cudaEventCreateWithFlags(&fp.d2h[k], cudaEventDisableTiming), "event");
+  }
+  if ((r = sml_reader_open(path, offset, T, H, W, batch, 3, &fp.reader)))
+    return fail(ctx, r, "cannot read %d frames of %dx%d from %s at offset %lld", T, H, W, path, offset);
+
+  struct Done {
+    long long first;
+    size_t at, n;
+  };
+  std::vector<Done> done;
+  size_t total = 0, written = 0;
+  struct Pending {
+    int slot = -1;
+    long long first = 0;
+    const uint16_t* host = nullptr;
+  } pend;
+  // records of a finished batch: count (host waits for its compute), then an async D2H on
+  // the copy stream, which overlaps the next batch's compute
+  auto finish = [&](const Pending& p) -> int {
+    SML_CUDA(cudaEventSynchronize(fp.cnt[p.slot]), "batch count");
+    int rr = sml_reader_release(fp.reader, p.host);  // its H2D finished before its compute
+    if (rr) return fail(ctx, rr, "reader release");
+    const size_t n = (size_t)fp.h_cnt[p.slot];
+    const size_t m = written < capacity ? std::min(n, capacity - written) : 0;
+    if (m) SML_CUDA(cudaMemcpyAsync(out + written, d_rec[p.slot], m * sizeof(sml_record), cudaMemcpyDeviceToHost, fp.copy),
+                    "D2H records");
+    SML_CUDA(cudaEventRecord(fp.d2h[p.slot], fp.copy), "event");
+    done.push_back({p.first, written, m});
+    written += m;
+    total += n;
+    return SML_OK;
+  };
+  for (long long k = 0;; ++k) {
+    const uint16_t* hp = nullptr;
+    int nf = 0;
+    long long first = 0;
+    if ((r = sml_reader_next(fp.reader, &hp, &nf, &first, 60000)))
+      return fail(ctx, r, "reading %s failed or timed out", path);
+    if (nf == 0) break;
+    const int slot = (int)(k & 1);
+    // the copy stream is in order: this H2D follows the D2H that last read d_rec[slot]
+    SML_CUDA(cudaMemcpyAsync(d_frames[slot], hp, (size_t)nf * hw * sizeof(uint16_t), cudaMemcpyHostToDevice, fp.copy),
+             "H2D frames");
+    SML_CUDA(cudaEventRecord(fp.h2d[slot], fp.copy), "event");
+    SML_CUDA(cudaStreamWaitEvent(s, fp.h2d[slot], 0), "wait H2D");
+    if (k >= 2) SML_CUDA(cudaStreamWaitEvent(s, fp.d2h[slot], 0), "wait D2H");
+    if ((r = localize_device(ctx, d_frames[slot], false, nf, H, W, ca, thr->p_min, d_rec[slot], rec_cap, d_n + slot, s)))
+      return r;
+    SML_CUDA(cudaMemcpyAsync(fp.h_cnt + slot, d_n + slot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
+             "D2H count");
+    SML_CUDA(cudaEventRecord(fp.cnt[slot], s), "event");
+    if (pend.slot >= 0 && (r = finish(pend))) return r;
+    pend.slot = slot;
+    pend.first = first;
+    pend.host = hp;
+  }
+  if (pend.slot >= 0 && (r = finish(pend))) return r;
+  SML_CUDA(cudaStreamSynchronize(fp.copy), "D2H records");
+  SML_CUDA(cudaStreamSynchronize(s), "localize");
+  if ((r = check_device_error(ctx))) return r;
+  for (const Done& d : done)  // frame index within the batch -> index in the stack
+    for (size_t i = d.at; i < d.at + d.n; ++i) out[i].frame += (int32_t)d.first;
+  if (stats) {
+    sml_reader_stats(fp.reader, stats);
+    stats->wall_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    stats->frames = T;
+  }
+  *n_out = total;
+  if (total > capacity) return fail(ctx, SML_ERR_CAPACITY, "%zu detections exceed capacity %zu", total, capacity);
+  return SML_OK;
+}
+
