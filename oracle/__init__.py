@@ -69,6 +69,8 @@ def _load():
             lib.orc_forward_x.restype = None
             lib.orc_forward_xq.argtypes = [P, I, I, I, I, I, I, P, P, P, P, D, P, P, P, P, I, P]
             lib.orc_forward_xq.restype = None
+            lib.orc_conv.argtypes = [P, I, I, I, P, P, I, I, P]
+            lib.orc_conv.restype = None
             lib.orc_round_array.argtypes = [P, ctypes.c_size_t, I]
             lib.orc_round_array.restype = None
             lib.orc_ingest.argtypes = [P, I, I, I, P, P, D, D, D, P]
@@ -91,24 +93,49 @@ def _ptr(a):
 
 
 class Net:
-    """Network description parsed from a JSON net spec and an SMLW weight blob."""
+    """Network description parsed from a JSON net spec and an SMLW weight blob.
+
+    Plain stacks (version-1 blobs): L conv layers of C channels with the spec's dilations.
+    Nets with dense connection dilated blocks (spec key "dcd", version-2 blobs; Sec. 3.2.1):
+    a stem conv (dilations[0], in_ch -> C); per block, dense layers whose input is the block
+    input and every earlier output of the block concatenated (C + j*growth channels, growth
+    outputs, the block's dilations) and a transition conv (d = 1, C + k*growth -> C); then the
+    plain C -> C layers dilations[1:].  ``layers`` lists (cin, cout, dilation, kind)."""
 
     def __init__(self, spec_json: str, blob: bytes):
         s = json.loads(spec_json)
         self.in_ch = int(s.get("in_ch", 1))
         self.C = int(s["channels"])
-        self.dil = [int(d) for d in s["dilations"]]
-        self.L = len(self.dil)
+        self.plain_dil = [int(d) for d in s["dilations"]]
         self.in_scale = float(s.get("in_scale", 1e-3))
         self.z_scale = float(s.get("z_scale", 1000.0))
         self.ph_scale = float(s.get("ph_scale", 10000.0))
-        fmt = "<8s7I16i"
+        C = self.C
+        dcd = s.get("dcd")
+        if dcd:
+            self.growth = int(dcd["growth"])
+            self.layers = [(self.in_ch, C, self.plain_dil[0], "stem")]
+            for block in dcd["blocks"]:
+                for j, d in enumerate(block):
+                    self.layers.append((C + j * self.growth, self.growth, int(d), "dense"))
+                self.layers.append((C + len(block) * self.growth, C, 1, "transition"))
+            self.layers += [(C, C, d, "plain") for d in self.plain_dil[1:]]
+            fmt, version = "<8s7I32i", 2
+        else:
+            self.growth = 0
+            self.layers = [(self.in_ch if l == 0 else C, C, d, "plain") for l, d in enumerate(self.plain_dil)]
+            fmt, version = "<8s7I16i", 1
+        self.dil = [d for _, _, d, _ in self.layers]
+        self.L = len(self.layers)
         hdr = struct.unpack_from(fmt, blob, 0)
         if hdr[0] != b"SMLW0001":
             raise ValueError("weight blob: bad magic")
-        _, _ver, L, C, in_ch, nh, has_bn, _, *dil = hdr
-        if (L, C, in_ch, nh, list(dil[:L])) != (self.L, self.C, self.in_ch, NH, self.dil):
+        _, ver, L, C_, in_ch, nh, has_bn, growth, *dil = hdr
+        if (ver, L, C_, in_ch, nh, list(dil[:L])) != (version, self.L, C, self.in_ch, NH, self.dil) or (
+                version == 2 and growth != self.growth):
             raise ValueError("weight blob does not match net spec")
+        if version == 2 and has_bn:
+            raise ValueError("weight blob: BatchNorm is not supported with dense blocks")
         off = struct.calcsize(fmt)
 
         def take(n):
@@ -119,13 +146,13 @@ class Net:
 
         ws, bs, bns = [], [], []
         self.bn_eps = 0.0
-        for layer in range(L):
-            cin = in_ch if layer == 0 else C
-            ws.append(take(C * cin * 9))
-            bs.append(take(C))
+        for cin, cout, _, _ in self.layers:
+            ws.append(take(cout * cin * 9))
+            bs.append(take(cout))
             if has_bn:
-                bns.append(take(4 * C))
+                bns.append(take(4 * cout))
                 self.bn_eps = float(take(1)[0])
+        self.layer_w, self.layer_b = ws, bs
         self.conv_w = np.ascontiguousarray(np.concatenate(ws))
         self.conv_b = np.ascontiguousarray(np.concatenate(bs))
         self.bn = np.ascontiguousarray(np.concatenate(bns)) if has_bn else None
@@ -193,6 +220,11 @@ def quantized(net: Net, fmt):
     if net.bn is not None:
         raise ValueError("quantized oracle modes need a net without BatchNorm")
     q = copy.copy(net)
+    if net.growth:  # dense blocks: per-layer arrays (layers 1.. run on the tensor cores)
+        if fmt != "bf16":
+            raise ValueError("dense blocks have a bf16 quantized mode only")
+        q.layer_w = [net.layer_w[0]] + [round_to(wl, "bf16") for wl in net.layer_w[1:]]
+        return q
     w = net.conv_w.copy()
     off = net.C * net.in_ch * 9
     n = net.C * net.C * 9
@@ -224,6 +256,8 @@ def forward_x(net: Net, x0, acts=False, quant=None, scales=None):
     quant "bf16" / "fp8" rounds the input activations of layers 1..L-1 to that format
     (fp8: of a / scales[l]) before the layer, as the tensor-core path stores them; pass a
     net from quantized() to round the weights too."""
+    if net.growth:
+        return _forward_dense(net, x0, acts, quant)
     lib = _load()
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     if x0.ndim == 3:
@@ -238,6 +272,49 @@ def forward_x(net: Net, x0, acts=False, quant=None, scales=None):
                        _ptr(net.conv_b), _ptr(net.bn), net.bn_eps, _ptr(net.head_w), _ptr(net.head_b),
                        _ptr(heads), _ptr(a), QUANT[quant], _ptr(sc))
     return (heads, a) if acts else heads
+
+
+def _forward_dense(net: Net, x0, acts=False, quant=None):
+    """Forward of a net with dense connection dilated blocks (Sec. 3.2.1): each layer is the
+    C oracle's conv (float64) on a channel range of a buffer that concatenates the block input
+    and the block's outputs so far.  quant "bf16" rounds every layer's stored output to bf16
+    (what the tensor-core path stores; the stem's input frames stay float).  Returns raw heads
+    [T,5,H,W] (and, with acts, the last layer's activations)."""
+    lib = _load()
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    if x0.ndim == 3:
+        x0 = x0[:, None]
+    T, cin0, H, W = x0.shape
+    assert cin0 == net.in_ch
+    if quant not in (None, "fp32", "bf16"):
+        raise ValueError("dense blocks support the bf16 quantized mode only")
+    rnd = (lambda a: round_to(a, "bf16")) if quant == "bf16" else (lambda a: a)
+    C, g = net.C, net.growth
+    widest = max(cin for cin, _, _, _ in net.layers)
+    heads = np.empty((T, NH, H, W), dtype=np.float64)
+    last = np.empty((T, C, H, W), dtype=np.float64) if acts else None
+    for t in range(T):
+        buf = np.zeros((widest, H, W), dtype=np.float64)  # the current block's concatenation
+        used = 0  # channels of buf filled
+        src = np.ascontiguousarray(x0[t])
+        for li, (cin, cout, d, kind) in enumerate(net.layers):
+            inp = np.ascontiguousarray(src if kind == "stem" else buf[:cin])
+            out = np.empty((cout, H, W), dtype=np.float64)
+            lib.orc_conv(_ptr(inp), cin, H, W, _ptr(np.ascontiguousarray(net.layer_w[li])),
+                         _ptr(np.ascontiguousarray(net.layer_b[li])), cout, d, _ptr(out))
+            if li < net.L - 1:  # stored activations; the last layer's output feeds the heads in FP32
+                out = rnd(out)
+            if kind == "dense":  # appended to the block's concatenation
+                buf[used : used + cout] = out
+                used += cout
+            else:  # stem, transition, plain: a new C-channel block input
+                buf[:cout] = out
+                used = cout
+        a = buf[:C]
+        if acts:
+            last[t] = a
+        heads[t] = net.head_b[:, None, None] + np.einsum("kc,chw->khw", net.head_w.reshape(NH, C), a)
+    return (heads, last) if acts else heads
 
 
 def forward(net: Net, frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None, quant=None, scales=None):

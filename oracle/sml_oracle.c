@@ -142,6 +142,16 @@ static void conv_layer(const double* a, int cin, int H, int W, const double* w, 
 }
 
 /*
+ * One conv layer (Sec. 3.2.1 dilated convolution, "same" zero padding, bias, ReLU) of one
+ * frame: in [cin][H][W] -> out [cout][H][W]; w [cout][cin][3][3], b [cout].  The forward of
+ * nets with dense connection dilated blocks (Sec. 3.2.1) is this layer applied to channel
+ * ranges of concatenated buffers (oracle/__init__.py).
+ */
+void orc_conv(const double* in, int cin, int H, int W, const double* w, const double* b, int cout, int d, double* out) {
+  conv_layer(in, cin, H, W, w, b, NULL, 0.0, cout, d, NULL, out);
+}
+
+/*
  * Forward of the stack on network inputs x0 [T, in_ch, H, W] (float64).
  *   conv_w: concatenated per-layer [Cout][Cin][3][3]; conv_b: [L][C];
  *   bn: NULL or [L][4][C]; head_w [5][C]; head_b [5].

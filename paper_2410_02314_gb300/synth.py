@@ -27,6 +27,10 @@ MAX_LAYERS = 16
 N_HEADS = 5
 HEADER_FMT = "<8s7I16i"  # magic, version, L, C, in_ch, n_heads, has_bn, reserved, dil[16]
 HEADER_BYTES = struct.calcsize(HEADER_FMT)
+# version 2 (nets with dense connection dilated blocks): reserved = growth, dil[32] per layer
+MAX_LAYERS_V2 = 32
+HEADER_FMT_V2 = "<8s7I32i"
+HEADER_BYTES_V2 = struct.calcsize(HEADER_FMT_V2)
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 
@@ -70,6 +74,26 @@ class NetSpec:
     z_scale: float = 1000.0
     ph_scale: float = 10000.0
     act_scales: tuple = ()  # fp8 only: one activation scale per conv layer input
+    # Dense connection dilated blocks, or None for the plain stack: {"growth": g, "blocks":
+    # [[d, ...], ...]}.  The net is then: stem conv (dilations[0], in_ch -> C); per block, one
+    # dense layer per listed dilation (input: the block input and every earlier layer's
+    # output, concatenated; output: g channels) and a transition conv (d = 1, C + k*g -> C);
+    # then the plain C -> C layers dilations[1:], the last of which feeds the heads.
+    dcd: dict | None = None
+
+    def layers(self) -> list:
+        """(cin, cout, dilation) of every conv layer in execution order."""
+        C = self.channels
+        if not self.dcd:
+            return [(self.in_ch if l == 0 else C, C, d) for l, d in enumerate(self.dilations)]
+        g = int(self.dcd["growth"])
+        out = [(self.in_ch, C, self.dilations[0])]
+        for block in self.dcd["blocks"]:
+            for j, d in enumerate(block):
+                out.append((C + j * g, g, int(d)))
+            out.append((C + len(block) * g, C, 1))
+        out += [(C, C, d) for d in self.dilations[1:]]
+        return out
 
     def to_json(self) -> str:
         d = {
@@ -84,16 +108,18 @@ class NetSpec:
         }
         if self.act_scales:
             d["act_scales"] = [float(s) for s in self.act_scales]
+        if self.dcd:
+            d["dcd"] = {"growth": int(self.dcd["growth"]), "blocks": [[int(x) for x in b] for b in self.dcd["blocks"]]}
         return json.dumps(d)
 
     @property
     def L(self) -> int:
-        return len(self.dilations)
+        return len(self.layers())
 
     @property
     def R(self) -> int:
         """Receptive radius of the conv stack in pixels."""
-        return int(sum(self.dilations))
+        return int(sum(d for _, _, d in self.layers()))
 
 
 def spec_small(precision="fp32") -> NetSpec:
@@ -125,15 +151,16 @@ def init_weights(spec: NetSpec, seed: int, bn: bool = False) -> Weights:
     s = _Stream(seed)
     C = spec.channels
     ws, bs, bns = [], [], []
-    for layer in range(spec.L):
-        cin = spec.in_ch if layer == 0 else C
+    for cin, cout, _ in spec.layers():
         fan_in = cin * 9
         bound = math.sqrt(6.0 / fan_in)
-        w = s.uniform(C * cin * 9, -bound, bound).reshape(C, cin, 3, 3)
-        b = s.uniform(C, -1.0 / math.sqrt(fan_in), 1.0 / math.sqrt(fan_in))
+        w = s.uniform(cout * cin * 9, -bound, bound).reshape(cout, cin, 3, 3)
+        b = s.uniform(cout, -1.0 / math.sqrt(fan_in), 1.0 / math.sqrt(fan_in))
         ws.append(w)
         bs.append(b)
         if bn:
+            if spec.dcd:
+                raise ValueError("BatchNorm is not supported with dense blocks")
             gamma = s.uniform(C, 0.5, 1.5)
             beta = s.uniform(C, -0.1, 0.1)
             mean = s.uniform(C, -0.1, 0.1)
@@ -146,11 +173,17 @@ def init_weights(spec: NetSpec, seed: int, bn: bool = False) -> Weights:
 
 
 def pack_blob(spec: NetSpec, w: Weights) -> bytes:
-    """Serialise weights into an SMLW blob (little endian, float32 payload)."""
+    """Serialise weights into an SMLW blob (little endian, float32 payload).  Plain stacks use
+    version 1 (dil[16]); nets with dense blocks version 2 (reserved = growth, dil[32] = every
+    layer's dilation in execution order)."""
     L, C = spec.L, spec.channels
-    dil = list(spec.dilations) + [0] * (MAX_LAYERS - L)
     has_bn = 1 if w.bn is not None else 0
-    parts = [struct.pack(HEADER_FMT, MAGIC, 1, L, C, spec.in_ch, N_HEADS, has_bn, 0, *dil)]
+    if spec.dcd:
+        dil = [d for _, _, d in spec.layers()] + [0] * (MAX_LAYERS_V2 - L)
+        parts = [struct.pack(HEADER_FMT_V2, MAGIC, 2, L, C, spec.in_ch, N_HEADS, has_bn, int(spec.dcd["growth"]), *dil)]
+    else:
+        dil = list(spec.dilations) + [0] * (MAX_LAYERS - L)
+        parts = [struct.pack(HEADER_FMT, MAGIC, 1, L, C, spec.in_ch, N_HEADS, has_bn, 0, *dil)]
     for layer in range(L):
         parts.append(np.ascontiguousarray(w.conv_w[layer], dtype="<f4").tobytes())
         parts.append(np.ascontiguousarray(w.conv_b[layer], dtype="<f4").tobytes())
@@ -162,13 +195,23 @@ def pack_blob(spec: NetSpec, w: Weights) -> bytes:
     return b"".join(parts)
 
 
-def unpack_blob(blob: bytes) -> tuple[dict, Weights]:
-    """Parse an SMLW blob back into float64 arrays (header dict, Weights)."""
+def unpack_blob(blob: bytes, spec: NetSpec | None = None) -> tuple[dict, Weights]:
+    """Parse an SMLW blob back into float64 arrays (header dict, Weights).  A version-2 blob
+    (dense blocks) needs its spec for the layers' channel counts."""
     head = struct.unpack_from(HEADER_FMT, blob, 0)
     if head[0] != MAGIC:
         raise ValueError("bad magic")
+    version = head[1]
+    if version == 2:
+        head = struct.unpack_from(HEADER_FMT_V2, blob, 0)
     _, version, L, C, in_ch, n_heads, has_bn, _, *dil = head
-    off = HEADER_BYTES
+    off = HEADER_BYTES_V2 if version == 2 else HEADER_BYTES
+    if version == 2:
+        if spec is None:
+            raise ValueError("a version-2 blob needs its net spec")
+        shapes = [(cout, cin) for cin, cout, _ in spec.layers()]
+    else:
+        shapes = [(C, in_ch if layer == 0 else C) for layer in range(L)]
 
     def take(n):
         nonlocal off
@@ -177,10 +220,9 @@ def unpack_blob(blob: bytes) -> tuple[dict, Weights]:
         return a
 
     ws, bs, bns, eps = [], [], [], 1e-5
-    for layer in range(L):
-        cin = in_ch if layer == 0 else C
-        ws.append(take(C * cin * 9).reshape(C, cin, 3, 3))
-        bs.append(take(C))
+    for cout, cin in shapes:
+        ws.append(take(cout * cin * 9).reshape(cout, cin, 3, 3))
+        bs.append(take(cout))
         if has_bn:
             bns.append(take(4 * C).reshape(4, C))
             eps = float(take(1)[0])
@@ -192,9 +234,9 @@ def unpack_blob(blob: bytes) -> tuple[dict, Weights]:
     return hdr, Weights(ws, bs, bns if has_bn else None, eps, hw, hb)
 
 
-def blob_f32_weights(blob: bytes) -> Weights:
+def blob_f32_weights(blob: bytes, spec: NetSpec | None = None) -> Weights:
     """The weights exactly as stored (float32-rounded), as float64 arrays."""
-    return unpack_blob(blob)[1]
+    return unpack_blob(blob, spec)[1]
 
 
 # --------------------------------------------------------------------------- camera + frames

@@ -329,3 +329,79 @@ def test_context_input_order_and_edges():
     assert np.array_equal(oracle.context_input(x, 1)[:, 0], x)
     with pytest.raises(ValueError):
         oracle.context_input(x, 2)
+
+
+# ----------------------------------------------------------------------------- dense blocks
+
+
+def _dcd_net(C=8, g=16, blocks=((2, 4), (3,)), plain=(1, 1), seed=13, zero_dense=False):
+    spec = synth.NetSpec(in_ch=1, channels=C, dilations=tuple(plain), dcd={"growth": g, "blocks": [list(b) for b in blocks]})
+    w = synth.init_weights(spec, seed)
+    if zero_dense:
+        k = 0
+        for b in blocks:
+            k += 1  # skip the stem / previous transition
+            for _ in b:
+                w.conv_w[k] = np.zeros_like(w.conv_w[k])
+                w.conv_b[k] = np.zeros_like(w.conv_b[k])
+                k += 1
+    blob = synth.pack_blob(spec, w)
+    return spec, oracle.Net(spec.to_json(), blob), synth.blob_f32_weights(blob, spec)
+
+
+def test_dense_blocks_match_torch_concatenation():
+    """Dense connection dilated blocks: every dense layer convolves the concatenation of the
+    block input and the block's earlier outputs; a transition conv maps back to C channels."""
+    spec, net, w = _dcd_net()
+    rng = np.random.default_rng(17)
+    x0 = rng.normal(0.5, 0.5, (2, 1, 11, 13))
+    got = oracle.forward_x(net, x0)
+    a = torch.from_numpy(x0)
+    li = 0
+
+    def conv(t, d):
+        nonlocal li
+        out = torch.relu(F.conv2d(t, torch.from_numpy(w.conv_w[li]), torch.from_numpy(w.conv_b[li]), padding=d, dilation=d))
+        li += 1
+        return out
+
+    a = conv(a, spec.dilations[0])
+    for block in spec.dcd["blocks"]:
+        feats = [a]
+        for d in block:
+            feats.append(conv(torch.cat(feats, 1), d))
+        a = conv(torch.cat(feats, 1), 1)
+    for d in spec.dilations[1:]:
+        a = conv(a, d)
+    ref = F.conv2d(a, torch.from_numpy(w.head_w)[:, :, None, None], torch.from_numpy(w.head_b)).numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_dense_blocks_with_silent_dense_layers_reduce_to_the_plain_stack():
+    """With all dense layers zero (weights and biases), their outputs are ReLU(0) = 0, so each
+    transition sees the block input padded with zeros: the net equals the plain stack whose
+    transition weights are their first C input channels (computed by the plain forward)."""
+    C = 8
+    spec, net, w = _dcd_net(C=C, zero_dense=True)
+    plain_spec = synth.NetSpec(in_ch=1, channels=C, dilations=(1, 1, 1, 1))  # stem, 2 transitions, last
+    pw = synth.init_weights(plain_spec, 0)
+    keep = [0, 3, 5, 6]  # stem, transition 1, transition 2, last plain layer
+    pw.conv_w = [w.conv_w[k][:, :C] if k in (3, 5) else w.conv_w[k] for k in keep]
+    pw.conv_b = [w.conv_b[k] for k in keep]
+    pw.head_w, pw.head_b = w.head_w, w.head_b
+    plain = oracle.Net(plain_spec.to_json(), synth.pack_blob(plain_spec, pw))
+    rng = np.random.default_rng(3)
+    frames = rng.integers(90, 500, (2, 14, 15)).astype(np.uint16)
+    got = oracle.forward(net, frames, 1.0, 100.0)
+    want = oracle.forward(plain, frames, 1.0, 100.0)
+    assert np.max(np.abs(got - want)) <= 1e-12 * max(1.0, np.abs(want).max())
+
+
+def test_dense_blocks_window_equals_whole_frame():
+    spec, net, _ = _dcd_net()
+    assert net.R == sum(d for _, _, d in spec.layers())
+    rng = np.random.default_rng(9)
+    frames = rng.integers(90, 500, (1, 40, 44)).astype(np.uint16)
+    whole = oracle.forward(net, frames, 1.0, 100.0)
+    win = oracle.forward_window(net, frames, 18, 24, 20, 27, 1.0, 100.0)
+    assert np.array_equal(win, whole[:, :, 18:24, 20:27])
