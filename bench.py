@@ -251,6 +251,56 @@ def small_latency_run(dev, stream, calls=50):
     return res
 
 
+def dcd_run(dev, stream, flush, reps=5):
+    """Dense connection dilated blocks (Sec. 3.2.1): the 256 frames of 256x256 of the main
+    workload through the 22-layer dense-block net (32 channels, growth 16, four blocks of
+    dilations 2, 4, 8, 16 with transitions), BF16 and FP32.  The conv-class kernels (dense
+    layers, transitions, plain middle layers) are timed with the library's event pairs; their
+    algorithmic HBM bytes are one read of every input channel and one write of every output
+    channel per pixel and layer (BF16: 2 bytes each)."""
+    import torch
+
+    import paper_2410_02314_gb300 as sml
+    from paper_2410_02314_gb300 import synth
+
+    res = {"workload": f"dcd_{T_FRAMES}x{H}x{W}_32ch_g16_4x4dense_22layer", "l2": "flushed between calls"}
+    pk, pk_kind = peaks()
+    for prec in ("bf16", "fp32"):
+        w = synth.workload_dcd(T=T_FRAMES, H=H, W=W, precision=prec)
+        loc = sml.Localizer(w.spec.to_json(), w.blob)
+        d_frames = torch.from_numpy(w.frames).to(dev)
+        d_out = torch.empty(T_FRAMES * H * W // 4 * 24, dtype=torch.uint8, device=dev)
+        d_n = torch.zeros(1, dtype=torch.int64, device=dev)
+        for _ in range(3):
+            loc.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        sml.sml_profile_enable(loc.ctx, True)
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            loc.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        sml.sml_profile_enable(loc.ctx, False)
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        conv_ms, conv_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_CONV)
+        res[f"{prec}_frames_per_s"] = T_FRAMES / (ms / 1000)
+        res[f"{prec}_launches_per_call"] = loc.last_launch_count
+        if prec == "bf16":
+            mid = w.spec.layers()[1:-1]  # the conv-class launches of one chunk
+            px = T_FRAMES * H * W
+            nbytes = sum(2 * (ci + co) for ci, co, _ in mid) * px
+            flops = sum(18 * ci * co for ci, co, _ in mid) * px
+            conv_s = conv_ms / reps / 1000.0
+            res.update({"bf16_conv_ms_per_call": conv_ms / reps, "bf16_records_per_call": int(d_n.item()),
+                        "conv_algorithmic_bytes_per_call": nbytes, "conv_hbm_gbs": nbytes / conv_s / 1e9,
+                        "conv_hbm_frac": nbytes / conv_s / 1e9 / pk["hbm_gbs"],
+                        "conv_tflops": flops / conv_s / 1e12, "peak_kind": pk_kind})
+        loc.close()
+    return res
+
+
 def file_pipeline_run(spec_json, blob, frames, cam, batch=256, repeat=4):
     """Stack-file pipeline (reader thread -> pinned buffers -> H2D -> localize -> D2H records,
     overlapped): the batch's frames written `repeat` times to one raw file in a temporary
@@ -481,11 +531,12 @@ def main():
     if not args.no_serve and world == 1:  # arrival rates at 0.5, 0.8 and 0.95 of the measured capacity
         serving = [serving_run(args, spec_json, w.blob, dev, capacity_px_per_s=value * H * W, load=ld)
                    for ld in (0.5, 0.8, 0.95)]
-    large_fov = small = file_pipe = None
+    large_fov = small = file_pipe = dcd = None
     if not args.no_extra and world == 1:
         large_fov = large_fov_run(dev, stream, flush)
         small = small_latency_run(dev, stream)
         file_pipe = file_pipeline_run(spec_json, w.blob, w.frames, w.cam)
+        dcd = dcd_run(dev, stream, flush)
 
     if rank != 0:
         if dist:
@@ -523,6 +574,7 @@ def main():
         "large_fov": large_fov,
         "small_latency": small,
         "file_pipeline": file_pipe,
+        "dcd": dcd,
         **extra,
     }
     print(json.dumps(line), flush=True)

@@ -166,13 +166,28 @@ struct Plan {
   unsigned long long* block_offsets = nullptr;
   uint16_t* frames = nullptr;  // staging for host frames
   float* cam_maps = nullptr;   // staging for host camera maps [2][H][W]
-  CUtensorMap tmap[2][kMaxLayers];  // per buffer and layer: one box per row (box width depends on d)
+  CUtensorMap tmap[kMaxLayers];  // per layer, over its input buffer: one box per row (width depends on d)
+};
+
+// One conv layer of the net in execution order: cin -> cout channels at dilation d.  Layer 0
+// reads the frames; layer l >= 1 reads channels [0, cin) of activation buffer in_buf and
+// (unless it is the last layer, whose output feeds the heads) writes channels
+// [out_off, out_off + cout) of buffer out_buf.  Plain stacks alternate between the two buffers.
+// A dense block (Sec. 3.2.1) keeps its concatenation in one buffer: the block input in
+// channels [0, C), dense layer j reads [0, C + j g) and appends its g outputs at C + j g; the
+// transition reads the whole concatenation and writes the next block input into [0, C) of
+// the other buffer.
+struct LayerDesc {
+  int cin = 0, cout = 0, d = 1, in_buf = -1, out_buf = 0, out_off = 0;
 };
 
 struct sml_ctx {
   int device = 0, num_sms = 0;
   // spec
-  int in_ch = 1, C = 0, L = 0, dil[kMaxLayers] = {0};
+  int in_ch = 1, C = 0, L = 0;
+  LayerDesc lay[kMaxLayers];
+  int growth = 0;  // dense blocks: channels each dense layer adds (0: plain stack)
+  int ct = 0;      // channels per pixel of the activation buffers (C, or C + the longest block's k g)
   int prec = kFP32;
   float in_scale = 1e-3f, z_scale = 1000.f, ph_scale = 10000.f;
   float act_scale[kMaxLayers] = {0};
@@ -180,7 +195,7 @@ struct sml_ctx {
   int tc_stages = 0;  // "tc_stages": TMA ring depth, 0 = as deep as shared memory allows
   // device weights
   std::vector<float> w1, b1;  // layer 1 [C][in_ch][9], [C] (host: passed to the kernel by value)
-  float* wf32[kMaxLayers] = {nullptr};  // [9][C][C]
+  float* wf32[kMaxLayers] = {nullptr};  // [9][cin][cout]
   float* bias[kMaxLayers] = {nullptr};
   void* bimg[kMaxLayers] = {nullptr};
   float* deq[kMaxLayers] = {nullptr};
@@ -266,20 +281,21 @@ void free_plan(Plan& p) {
 
 size_t act_elem_bytes(int prec) { return prec == kFP32 ? 4 : (prec == kBF16 ? 2 : 1); }
 
-// Row-planar activations [Tc][H][G][W][row bytes], G = C/16 groups of 16 channels (32-byte
-// rows in BF16, 16-byte rows in FP8).  5-D description (group row, W, G, H, Tc) with box
-// (group row, tc_box_width(d) pixels, G, 1, 1): the conv kernel loads one input row segment
-// per box, BF16 rows with the 32-byte swizzle.  Pixels left of 0 or right of W-1, and rows
-// outside [0,H), are filled with zeros by TMA.
-int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W, int d) {
+// Row-planar activations [Tc][H][Gt][W][row bytes], Gt = ct/16 groups of 16 channels (32-byte
+// rows in BF16, 16-byte rows in FP8).  A layer reading its first g_in groups sees the 5-D
+// tensor (group row, W, g_in, H, Tc) with the buffer's strides and loads boxes (group row,
+// tc_box_width(d) pixels, g_in, 1, 1): one input row segment per box, BF16 rows with the
+// 32-byte swizzle.  Pixels left of 0 or right of W-1, and rows outside [0,H), are filled with
+// zeros by TMA.
+int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W, int d, int g_in) {
   PFN_encodeTiled_t enc = get_encoder();
   if (!enc) return fail(ctx, SML_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  const int G = tc_groups(ctx->C, ctx->prec);
+  const int gt = ctx->ct / 16;
   const bool bf16 = ctx->prec == kBF16;
   const cuuint64_t rowb = bf16 ? 32 : 16;
-  cuuint64_t dims[5] = {16ull, (cuuint64_t)W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)Tc};
-  cuuint64_t strides[4] = {rowb, rowb * W, rowb * W * G, rowb * W * G * H};
-  cuuint32_t box[5] = {16u, (cuuint32_t)tc_box_width(d), (cuuint32_t)G, 1u, 1u};
+  cuuint64_t dims[5] = {16ull, (cuuint64_t)W, (cuuint64_t)g_in, (cuuint64_t)H, (cuuint64_t)Tc};
+  cuuint64_t strides[4] = {rowb, rowb * W, rowb * W * gt, rowb * W * gt * H};
+  cuuint32_t box[5] = {16u, (cuuint32_t)tc_box_width(d), (cuuint32_t)g_in, 1u, 1u};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 5, base, dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, bf16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -333,7 +349,7 @@ int get_plan(sml_ctx* ctx, int H, int W) {
   long long hw = (long long)H * W;
   int Tc = (int)std::max(1LL, ctx->chunk_px / hw);
   size_t npx = (size_t)Tc * hw;
-  size_t ab = npx * ctx->C * act_elem_bytes(ctx->prec);
+  size_t ab = npx * ctx->ct * act_elem_bytes(ctx->prec);
   int r;
   if ((r = dev_alloc(ctx, &p.act[0], ab)) || (r = dev_alloc(ctx, &p.act[1], ab)) ||
       (r = dev_alloc(ctx, &p.maps, npx * kHeads * sizeof(float))) ||
@@ -345,12 +361,12 @@ int get_plan(sml_ctx* ctx, int H, int W) {
     return r;
   }
   if (ctx->prec != kFP32) {
-    for (int b = 0; b < 2; ++b) {
-      for (int l = 1; l < ctx->L; ++l)
-        if ((r = encode_act_map(ctx, &p.tmap[b][l], p.act[b], Tc, H, W, ctx->dil[l]))) {
-          free_plan(p);
-          return r;
-        }
+    for (int l = 1; l < ctx->L; ++l) {
+      const LayerDesc& y = ctx->lay[l];
+      if ((r = encode_act_map(ctx, &p.tmap[l], p.act[y.in_buf], Tc, H, W, y.d, y.cin / 16))) {
+        free_plan(p);
+        return r;
+      }
     }
   }
   p.H = H;
@@ -381,36 +397,49 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, FrameRange fr,
   float l1_scale = ctx->prec == kFP8 ? 1.0f / ctx->act_scale[1] : 1.0f;
   {
     ProfScope ps(ctx, SML_KERNEL_LAYER1, s);
-    SML_CUDA(launch_ingest_l1(d_frames, tc, H, W, ctx->dil[0], cam, ctx->w1.data(), ctx->b1.data(), C, ctx->in_ch, fr.first,
-                              fr.last, ctx->prec, l1_scale, p.act[0], s),
+    SML_CUDA(launch_ingest_l1(d_frames, tc, H, W, ctx->lay[0].d, cam, ctx->w1.data(), ctx->b1.data(), C, ctx->in_ch,
+                              fr.first, fr.last, ctx->prec, l1_scale, p.act[ctx->lay[0].out_buf], ctx->ct, s),
              "layer 1");
   }
   ++ctx->launches;
-  const size_t n_act = (size_t)tc * H * W * C;
+  const size_t n_act = (size_t)tc * H * W * C;  // whole buffers of a plain stack (ct == C)
   if (d_amax) SML_CUDA(launch_amax(p.act[0], n_act, ctx->prec, d_amax + 1, s), "amax");
   for (int l = 1; l < L; ++l) {
     const bool last = (l == L - 1);
-    void* in = p.act[(l - 1) & 1];
-    void* out = p.act[l & 1];
+    const LayerDesc& y = ctx->lay[l];
+    void* in = p.act[y.in_buf];
+    void* out = last ? nullptr : p.act[y.out_buf];
     ProfScope ps(ctx, last ? SML_KERNEL_CONV_HEADS : SML_KERNEL_CONV, s);
     if (ctx->prec == kFP32) {
+      F32LayerArgs fa{};
+      fa.in = static_cast<const float*>(in);
+      fa.out = static_cast<float*>(out);
+      fa.w = ctx->wf32[l];
+      fa.b = ctx->bias[l];
+      fa.T = tc;
+      fa.H = H;
+      fa.W = W;
+      fa.d = y.d;
+      fa.ci = y.cin;
+      fa.co = y.cout;
+      fa.in_ct = ctx->ct;
+      fa.out_ct = ctx->ct;
+      fa.out_off = y.out_off;
       if (last)
-        SML_CUDA(launch_dconv_f32_heads(static_cast<float*>(in), ctx->wf32[l], ctx->bias[l], ctx->head_w, ctx->head_b, tc,
-                                        H, W, C, ctx->dil[l], maps, logits, s),
-                 "fp32 conv+heads");
+        SML_CUDA(launch_dconv_f32_heads(fa, ctx->head_w, ctx->head_b, maps, logits, s), "fp32 conv+heads");
       else
-        SML_CUDA(launch_dconv_f32(static_cast<float*>(in), static_cast<float*>(out), ctx->wf32[l], ctx->bias[l], tc, H, W,
-                                  C, ctx->dil[l], s),
-                 "fp32 conv");
+        SML_CUDA(launch_dconv_f32(fa, s), "fp32 conv");
     } else {
       TcLayerArgs a{};
-      a.tmap = &p.tmap[(l - 1) & 1][l];
+      a.tmap = &p.tmap[l];
       a.stages = ctx->tc_stages;
       a.bimg = ctx->bimg[l];
       a.bias = ctx->h_bias[l].data();
       a.deq = ctx->h_deq[l].empty() ? nullptr : ctx->h_deq[l].data();
       a.out_inv_scale = (ctx->prec == kFP8 && !last) ? 1.0f / ctx->act_scale[l + 1] : 1.0f;
       a.out = out;
+      a.out_g0 = y.out_off / 16;
+      a.out_gt = ctx->ct / 16;
       a.head_w = ctx->h_head_w.data();
       a.head_b = ctx->h_head_b.data();
       a.maps = maps;
@@ -418,8 +447,9 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, FrameRange fr,
       a.T = tc;
       a.H = H;
       a.W = W;
-      a.C = C;
-      a.d = ctx->dil[l];
+      a.d = y.d;
+      a.ci = y.cin;
+      a.co = y.cout;
       a.prec = ctx->prec;
       a.err = ctx->d_err;
       SML_CUDA(launch_dconv_tc(a, last, ctx->num_sms, s), "tensor-core conv");
@@ -535,13 +565,80 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
   if (ctx->chunk_px < 1) return fail(nullptr, SML_ERR_BAD_SPEC, "chunk_px must be >= 1");
   auto it = root.obj.find("dilations");
   if (it == root.obj.end() || it->second.kind != JVal::kArr) return fail(nullptr, SML_ERR_BAD_SPEC, "dilations missing");
-  ctx->L = (int)it->second.arr.size();
-  if (ctx->L < 2 || ctx->L > kMaxLayers) return fail(nullptr, SML_ERR_BAD_SPEC, "need 2..16 layers");
-  for (int l = 0; l < ctx->L; ++l) {
-    const JVal& v = it->second.arr[l];
-    if (v.kind != JVal::kNum || v.num < 1 || v.num > 64 || v.num != floor(v.num))
-      return fail(nullptr, SML_ERR_BAD_SPEC, "dilation %d must be an integer in 1..64", l);
-    ctx->dil[l] = (int)v.num;
+  auto dil_of = [](const JVal& v, int* out) {
+    if (v.kind != JVal::kNum || v.num < 1 || v.num > 64 || v.num != floor(v.num)) return false;
+    *out = (int)v.num;
+    return true;
+  };
+  std::vector<int> dil(it->second.arr.size());
+  for (size_t l = 0; l < dil.size(); ++l)
+    if (!dil_of(it->second.arr[l], &dil[l]))
+      return fail(nullptr, SML_ERR_BAD_SPEC, "dilation %d must be an integer in 1..64", (int)l);
+  const int C = ctx->C;
+  auto dc = root.obj.find("dcd");
+  if (dc == root.obj.end() || dc->second.kind == JVal::kNull) {
+    // plain stack: layer l reads buffer (l-1) & 1 and writes buffer l & 1
+    ctx->L = (int)dil.size();
+    if (ctx->L < 2 || ctx->L > 16) return fail(nullptr, SML_ERR_BAD_SPEC, "need 2..16 layers");
+    ctx->ct = C;
+    for (int l = 0; l < ctx->L; ++l) {
+      LayerDesc& y = ctx->lay[l];
+      y.cin = l ? C : ctx->in_ch;
+      y.cout = C;
+      y.d = dil[l];
+      y.in_buf = l ? (l - 1) & 1 : -1;
+      y.out_buf = l & 1;
+      y.out_off = 0;
+    }
+  } else {
+    // dense blocks (Sec. 3.2.1): stem (dilations[0]); per block, dense layers and a transition
+    // back to C channels (d = 1); then the plain layers dilations[1:] (the last feeds the heads)
+    const JVal& o = dc->second;
+    auto gi = o.obj.find("growth");
+    auto bi = o.obj.find("blocks");
+    if (o.kind != JVal::kObj || gi == o.obj.end() || gi->second.kind != JVal::kNum || bi == o.obj.end() ||
+        bi->second.kind != JVal::kArr || bi->second.arr.empty())
+      return fail(nullptr, SML_ERR_BAD_SPEC, "dcd needs growth and a non-empty list of blocks");
+    const int g = (int)gi->second.num;
+    if (gi->second.num != g || (g != 16 && g != 32 && g != 48 && g != 64))
+      return fail(nullptr, SML_ERR_BAD_SPEC, "dcd growth must be 16, 32, 48 or 64");
+    if (dil.size() < 2) return fail(nullptr, SML_ERR_BAD_SPEC, "dcd nets need a stem and at least one plain layer");
+    ctx->growth = g;
+    int L = 0, cur = 0, widest = C;
+    auto add = [&](int cin, int cout, int d, int in_buf, int out_buf, int out_off) {
+      if (L < kMaxLayers) {
+        LayerDesc& y = ctx->lay[L];
+        y.cin = cin;
+        y.cout = cout;
+        y.d = d;
+        y.in_buf = in_buf;
+        y.out_buf = out_buf;
+        y.out_off = out_off;
+      }
+      ++L;
+    };
+    add(ctx->in_ch, C, dil[0], -1, 0, 0);
+    for (const JVal& blk : bi->second.arr) {
+      if (blk.kind != JVal::kArr || blk.arr.empty()) return fail(nullptr, SML_ERR_BAD_SPEC, "dcd blocks must be non-empty lists");
+      const int k = (int)blk.arr.size();
+      for (int j = 0; j < k; ++j) {
+        int d = 0;
+        if (!dil_of(blk.arr[j], &d)) return fail(nullptr, SML_ERR_BAD_SPEC, "dcd dilations must be integers in 1..64");
+        add(C + j * g, g, d, cur, cur, C + j * g);
+      }
+      add(C + k * g, C, 1, cur, 1 - cur, 0);
+      cur = 1 - cur;
+      widest = std::max(widest, C + k * g);
+    }
+    for (size_t l = 1; l < dil.size(); ++l) {
+      add(C, C, dil[l], cur, 1 - cur, 0);
+      cur = 1 - cur;
+    }
+    if (L > kMaxLayers) return fail(nullptr, SML_ERR_BAD_SPEC, "dcd net has %d conv layers (at most %d)", L, kMaxLayers);
+    if (widest > kTcMaxCin)
+      return fail(nullptr, SML_ERR_BAD_SPEC, "dcd block concatenation has %d channels (at most %d)", widest, kTcMaxCin);
+    ctx->L = L;
+    ctx->ct = widest;
   }
   auto pr = root.obj.find("precision");
   std::string prec = (pr != root.obj.end() && pr->second.kind == JVal::kStr) ? pr->second.str : "fp32";
@@ -559,30 +656,61 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
       ctx->act_scale[l] = (float)v.num;
     }
   }
+  if (ctx->growth && ctx->prec == kFP8)
+    return fail(nullptr, SML_ERR_UNSUPPORTED, "dcd nets run in fp32 or bf16 (fp8 activation scales are per layer)");
+  for (int l = 1; l < ctx->L; ++l) {  // every layer must fit its kernel's shared memory
+    const LayerDesc& y = ctx->lay[l];
+    const bool fits = ctx->prec == kFP32 ? y.cin * y.cout <= kF32MaxWeights : tc_layer_fits(y.cin, y.cout, y.d, ctx->prec);
+    if (!fits)
+      return fail(nullptr, SML_ERR_UNSUPPORTED, "conv layer %d (%d -> %d channels, d = %d) does not fit shared memory", l,
+                  y.cin, y.cout, y.d);
+  }
   auto hd = root.obj.find("heads");
   if (hd != root.obj.end() && (hd->second.kind != JVal::kArr || hd->second.arr.size() != kHeads))
     return fail(nullptr, SML_ERR_BAD_SPEC, "heads must list 5 outputs");
   return SML_OK;
 }
 
-int load_weights(sml_ctx* ctx, const void* blob, size_t bytes) {
+// Weight blob: header "<8s7I16i" (version 1, plain stacks) or "<8s7I32i" (version 2, nets
+// with dense blocks: reserved = growth, dil[32] = every layer's dilation in execution order);
+// then per layer W[cout][cin][3][3], b[cout] (+ BatchNorm, version 1 only) and the heads.
+// Checks the header against the spec and the size; host only (runs before any device call).
+int check_blob(const sml_ctx* ctx, const void* blob, size_t bytes, size_t* hdr_out, int* has_bn_out) {
   const uint8_t* b = static_cast<const uint8_t*>(blob);
-  const size_t hdr_bytes = 8 + 7 * 4 + 16 * 4;
+  const bool v2 = ctx->growth > 0;
+  const int ndil = v2 ? 32 : 16;
+  const size_t hdr_bytes = 8 + 7 * 4 + (size_t)ndil * 4;
   if (!blob || bytes < hdr_bytes || memcmp(b, "SMLW0001", 8) != 0)
     return fail(nullptr, SML_ERR_BAD_WEIGHTS, "weight blob: bad magic or too short");
   uint32_t h[7];
-  int32_t dil[16];
+  int32_t dil[32];
   memcpy(h, b + 8, sizeof(h));
-  memcpy(dil, b + 8 + sizeof(h), sizeof(dil));
+  memcpy(dil, b + 8 + sizeof(h), (size_t)ndil * 4);
   const int L = (int)h[1], C = (int)h[2], in_ch = (int)h[3], nh = (int)h[4], has_bn = (int)h[5];
-  if (h[0] != 1 || L != ctx->L || C != ctx->C || in_ch != ctx->in_ch || nh != kHeads)
+  if (h[0] != (v2 ? 2u : 1u) || L != ctx->L || C != ctx->C || in_ch != ctx->in_ch || nh != kHeads ||
+      (v2 && ((int)h[6] != ctx->growth || has_bn)))
     return fail(nullptr, SML_ERR_BAD_WEIGHTS, "weight blob header does not match the net spec");
   for (int l = 0; l < L; ++l)
-    if (dil[l] != ctx->dil[l]) return fail(nullptr, SML_ERR_BAD_WEIGHTS, "weight blob dilations do not match the net spec");
+    if (dil[l] != ctx->lay[l].d) return fail(nullptr, SML_ERR_BAD_WEIGHTS, "weight blob dilations do not match the net spec");
   size_t need = hdr_bytes;
-  for (int l = 0; l < L; ++l) need += 4 * ((size_t)C * (l ? C : in_ch) * 9 + C + (has_bn ? 4 * C + 1 : 0));
+  for (int l = 0; l < L; ++l) {
+    const LayerDesc& y = ctx->lay[l];
+    need += 4 * ((size_t)y.cout * y.cin * 9 + y.cout + (has_bn ? 4 * (size_t)y.cout + 1 : 0));
+  }
   need += 4 * ((size_t)kHeads * C + kHeads);
   if (bytes != need) return fail(nullptr, SML_ERR_BAD_WEIGHTS, "weight blob has %zu bytes, expected %zu", bytes, need);
+  if (hdr_out) *hdr_out = hdr_bytes;
+  if (has_bn_out) *has_bn_out = has_bn;
+  return SML_OK;
+}
+
+int load_weights(sml_ctx* ctx, const void* blob, size_t bytes) {
+  size_t hdr_bytes = 0;
+  int has_bn = 0;
+  int r = check_blob(ctx, blob, bytes, &hdr_bytes, &has_bn);
+  if (r) return r;
+  const uint8_t* b = static_cast<const uint8_t*>(blob);
+  const int L = ctx->L, C = ctx->C;
   const float* f = reinterpret_cast<const float*>(b + hdr_bytes);  // blob offsets are 4-byte aligned
   std::vector<float> tmp;
   size_t off = 0;
@@ -592,18 +720,17 @@ int load_weights(sml_ctx* ctx, const void* blob, size_t bytes) {
     off += n;
     return tmp;
   };
-  int r;
   for (int l = 0; l < L; ++l) {
-    const int cin = l ? C : in_ch;
-    std::vector<float> w = take((size_t)C * cin * 9);
-    std::vector<float> bias = take(C);
+    const int cin = ctx->lay[l].cin, cout = ctx->lay[l].cout;
+    std::vector<float> w = take((size_t)cout * cin * 9);
+    std::vector<float> bias = take(cout);
     if (has_bn) {
-      std::vector<float> bn = take(4 * (size_t)C);
+      std::vector<float> bn = take(4 * (size_t)cout);
       float eps = take(1)[0];
-      for (int co = 0; co < C; ++co) {  // fold: W' = W g/sqrt(v+e); b' = (b-m) g/sqrt(v+e) + beta
-        double sc = (double)bn[co] / sqrt((double)bn[3 * C + co] + (double)eps);
+      for (int co = 0; co < cout; ++co) {  // fold: W' = W g/sqrt(v+e); b' = (b-m) g/sqrt(v+e) + beta
+        double sc = (double)bn[co] / sqrt((double)bn[3 * cout + co] + (double)eps);
         for (int k = 0; k < cin * 9; ++k) w[(size_t)co * cin * 9 + k] = (float)(w[(size_t)co * cin * 9 + k] * sc);
-        bias[co] = (float)(((double)bias[co] - bn[2 * C + co]) * sc + bn[C + co]);
+        bias[co] = (float)(((double)bias[co] - bn[2 * cout + co]) * sc + bn[cout + co]);
       }
     }
     if (!std::all_of(w.begin(), w.end(), [](float x) { return std::isfinite(x); }) ||
@@ -615,25 +742,25 @@ int load_weights(sml_ctx* ctx, const void* blob, size_t bytes) {
       continue;
     }
     // [co][ci][ky][kx] -> [tap][ci][co]
-    std::vector<float> t((size_t)9 * C * C);
-    for (int co = 0; co < C; ++co)
-      for (int ci = 0; ci < C; ++ci)
-        for (int tap = 0; tap < 9; ++tap) t[((size_t)tap * C + ci) * C + co] = w[((size_t)co * C + ci) * 9 + tap];
+    std::vector<float> t((size_t)9 * cin * cout);
+    for (int co = 0; co < cout; ++co)
+      for (int ci = 0; ci < cin; ++ci)
+        for (int tap = 0; tap < 9; ++tap) t[((size_t)tap * cin + ci) * cout + co] = w[((size_t)co * cin + ci) * 9 + tap];
     if (ctx->prec == kFP32) {
-      if ((r = upload(ctx, &ctx->wf32[l], t.data(), t.size() * 4)) || (r = upload(ctx, &ctx->bias[l], bias.data(), C * 4)))
+      if ((r = upload(ctx, &ctx->wf32[l], t.data(), t.size() * 4)) || (r = upload(ctx, &ctx->bias[l], bias.data(), cout * 4)))
         return r;
     } else {
-      std::vector<float> wscale(C, 1.0f), deq(C, 1.0f);
+      std::vector<float> wscale(cout, 1.0f), deq(cout, 1.0f);
       if (ctx->prec == kFP8) {
-        for (int co = 0; co < C; ++co) {
+        for (int co = 0; co < cout; ++co) {
           float amax = 0.f;
-          for (int k = 0; k < 9 * C; ++k) amax = std::max(amax, fabsf(t[(size_t)k * C + co]));
+          for (int k = 0; k < 9 * cin; ++k) amax = std::max(amax, fabsf(t[(size_t)k * cout + co]));
           wscale[co] = amax > 0.f ? amax / 448.0f : 1.0f;
           deq[co] = ctx->act_scale[l] * wscale[co];
         }
       }
-      std::vector<uint8_t> img(tc_bimg_bytes(C, ctx->prec));
-      tc_pack_bimg(t.data(), C, ctx->prec, wscale.data(), img.data());
+      std::vector<uint8_t> img(tc_bimg_bytes(cin, cout, ctx->prec));
+      tc_pack_bimg(t.data(), cin, cout, ctx->prec, wscale.data(), img.data());
       if ((r = upload(ctx, &ctx->bimg[l], img.data(), img.size()))) return r;
       ctx->h_bias[l] = bias;
       if (ctx->prec == kFP8) ctx->h_deq[l] = deq;
@@ -660,6 +787,7 @@ int sml_create(const char* net_spec, const void* weights, size_t weights_bytes, 
   std::unique_ptr<sml_ctx> ctx(new sml_ctx());
   int r = parse_spec(ctx.get(), net_spec);
   if (r) return r;
+  if ((r = check_blob(ctx.get(), weights, weights_bytes, nullptr, nullptr))) return r;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(nullptr, SML_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
@@ -870,6 +998,7 @@ int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, in
   int r;
   if (!amax || (T > 0 && !d_frames)) return fail(ctx, SML_ERR_BAD_ARG, "NULL argument");
   if (ctx->prec == kFP8) return fail(ctx, SML_ERR_UNSUPPORTED, "activation maxima need an fp32 or bf16 context");
+  if (ctx->growth) return fail(ctx, SML_ERR_UNSUPPORTED, "activation maxima are for plain stacks (fp8 calibration)");
   if ((r = check_dims(ctx, T, H, W))) return r;
   CamArgs ca;
   if ((r = make_cam(ctx, cam, &ca))) return r;

@@ -51,7 +51,7 @@ template <int C, int OUT, int IN_CH>
 __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restrict__ frames, int H, int W, int d,
                                                        int t0, int t_first, int t_last, CamArgs cam,
                                                        const __grid_constant__ L1Params prm, float out_scale,
-                                                       void* __restrict__ out) {
+                                                       void* __restrict__ out, int out_ct) {
   constexpr int CPT = C / kL1ChGroups;
   constexpr int OB = OUT == 0 ? 4 : (OUT == 1 ? 2 : 1);  // output bytes per channel
   constexpr int OS = C * OB + 16;                        // staged bytes per pixel
@@ -162,19 +162,21 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
     __syncthreads();
     const size_t row = (size_t)t * H + i;
     // index arithmetic below divides by compile-time constants only
-    if (OUT == 0) {  // NHWC float: the strip's npx*C floats are contiguous
+    if (OUT == 0) {  // NHWC float: pixels out_ct floats apart, channels 0..C-1 of each
       constexpr int CH = C / 4;  // float4 per pixel
-      float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + (row * W + j0) * C);
+      const int pst = out_ct / 4;
+      float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + (row * W + j0) * out_ct);
       for (int k = threadIdx.x; k < npx * CH; k += kL1Tile) {
         const int px = k / CH, h = k - px * CH;
-        dst[k] = *reinterpret_cast<const float4*>(ot + (size_t)px * OS + 16 * h);
+        dst[(size_t)px * pst + h] = *reinterpret_cast<const float4*>(ot + (size_t)px * OS + 16 * h);
       }
-    } else {  // row-planar [T][H][G][W][16 channels]: per group, npx rows of 16*OB bytes
+    } else {  // row-planar [T][H][out_ct/16][W][16 channels]: per group, npx rows of 16*OB bytes
       constexpr int G = C / 16, CH = OB;  // 16-byte chunks per group row
+      const int gt = out_ct / 16;         // groups per pixel row of the buffer
       uint8_t* base = static_cast<uint8_t*>(out);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        uint8_t* grow = base + ((row * G + g) * W + j0) * 16 * OB;
+        uint8_t* grow = base + ((row * gt + g) * W + j0) * 16 * OB;
         for (int k = threadIdx.x; k < npx * CH; k += kL1Tile) {
           const int px = k / CH, h = k - px * CH;
           const uint4 v = *reinterpret_cast<const uint4*>(ot + (size_t)px * OS + 16 * g * OB + 16 * h);
@@ -185,44 +187,45 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
   }
 }
 
-// FP32 dilated conv: one thread per pixel, all C output channels in registers.
+// FP32 dilated conv: one thread per pixel, all CO output channels in registers.  Input
+// channels 0..ci-1 of pixels in_ct floats apart; outputs at channel out_off of pixels out_ct
+// floats apart (a channel range of a dense block's concatenation, or the whole pixel).
 // Weights in shared memory as [tap][ci][co]; each float4 read is a warp-wide broadcast.
-template <int C, bool HEADS>
-__global__ void __launch_bounds__(kSimtThreads) k_dconv_f32(const float* __restrict__ in, float* __restrict__ out,
-                                                            const float* __restrict__ w, const float* __restrict__ b,
-                                                            const float* __restrict__ hw, const float* __restrict__ hb,
-                                                            int T, int H, int W, int d, float* __restrict__ maps,
+template <int CO, bool HEADS>
+__global__ void __launch_bounds__(kSimtThreads) k_dconv_f32(const F32LayerArgs a, const float* __restrict__ hw,
+                                                            const float* __restrict__ hb, float* __restrict__ maps,
                                                             float* __restrict__ logits) {
   extern __shared__ float4 smem4[];
   float* sw = reinterpret_cast<float*>(smem4);
-  for (int k = threadIdx.x; k < 9 * C * C / 4; k += blockDim.x) smem4[k] = reinterpret_cast<const float4*>(w)[k];
+  const int ci_n = a.ci, H = a.H, W = a.W, d = a.d;
+  for (int k = threadIdx.x; k < 9 * ci_n * CO / 4; k += blockDim.x) smem4[k] = reinterpret_cast<const float4*>(a.w)[k];
   __syncthreads();
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long npx = (long long)T * H * W;
+  long long npx = (long long)a.T * H * W;
   if (q >= npx) return;
   int j = (int)(q % W);
   int i = (int)((q / W) % H);
   int t = (int)(q / ((long long)H * W));
-  float acc[C];
+  float acc[CO];
 #pragma unroll
-  for (int co = 0; co < C; ++co) acc[co] = b[co];
+  for (int co = 0; co < CO; ++co) acc[co] = a.b[co];
   for (int ky = 0; ky < 3; ++ky) {
     int ii = i + (ky - 1) * d;
     if (ii < 0 || ii >= H) continue;
     for (int kx = 0; kx < 3; ++kx) {
       int jj = j + (kx - 1) * d;
       if (jj < 0 || jj >= W) continue;
-      const float4* src = reinterpret_cast<const float4*>(in + (((size_t)t * H + ii) * W + jj) * C);
-      const float* wt = sw + (ky * 3 + kx) * C * C;
+      const float4* src = reinterpret_cast<const float4*>(a.in + (((size_t)t * H + ii) * W + jj) * a.in_ct);
+      const float* wt = sw + (ky * 3 + kx) * ci_n * CO;
 #pragma unroll 2
-      for (int c4 = 0; c4 < C / 4; ++c4) {
+      for (int c4 = 0; c4 < ci_n / 4; ++c4) {
         float4 v = __ldg(src + c4);
         float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float4* wr = reinterpret_cast<const float4*>(wt + (4 * c4 + e) * C);
+          const float4* wr = reinterpret_cast<const float4*>(wt + (4 * c4 + e) * CO);
 #pragma unroll
-          for (int o4 = 0; o4 < C / 4; ++o4) {
+          for (int o4 = 0; o4 < CO / 4; ++o4) {
             float4 ww = wr[o4];
             acc[4 * o4 + 0] = fmaf(vv[e], ww.x, acc[4 * o4 + 0]);
             acc[4 * o4 + 1] = fmaf(vv[e], ww.y, acc[4 * o4 + 1]);
@@ -234,11 +237,11 @@ __global__ void __launch_bounds__(kSimtThreads) k_dconv_f32(const float* __restr
     }
   }
 #pragma unroll
-  for (int co = 0; co < C; ++co) acc[co] = fmaxf(acc[co], 0.0f);
+  for (int co = 0; co < CO; ++co) acc[co] = fmaxf(acc[co], 0.0f);
   if (!HEADS) {
-    float4* dst = reinterpret_cast<float4*>(out + (size_t)q * C);
+    float4* dst = reinterpret_cast<float4*>(a.out + (size_t)q * a.out_ct + a.out_off);
 #pragma unroll
-    for (int c4 = 0; c4 < C / 4; ++c4)
+    for (int c4 = 0; c4 < CO / 4; ++c4)
       dst[c4] = make_float4(acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]);
   } else {
     // 1x1 heads (Sec. 3.2): h_k = hb[k] + sum_c hw[k,c] a[c]; p = sigmoid(h_0)
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(kSimtThreads) k_dconv_f32(const float* __restr
     for (int k = 0; k < kHeads; ++k) {
       float h = hb[k];
 #pragma unroll
-      for (int c = 0; c < C; ++c) h = fmaf(hw[k * C + c], acc[c], h);
+      for (int c = 0; c < CO; ++c) h = fmaf(hw[k * CO + c], acc[c], h);
       if (k == 0) {
         if (logits) logits[(size_t)t * plane + px] = h;
         h = 1.0f / (1.0f + expf(-h));
@@ -277,7 +280,8 @@ inline unsigned grid_for(long long npx) { return (unsigned)((npx + kSimtThreads 
 
 template <int C, int OUT, int IN_CH>
 static cudaError_t launch_l1(const uint16_t* frames, int T, int H, int W, int d, int t_first, int t_last,
-                             const CamArgs& cam, const L1Params& prm, float out_scale, void* out, cudaStream_t s) {
+                             const CamArgs& cam, const L1Params& prm, float out_scale, void* out, int out_ct,
+                             cudaStream_t s) {
   constexpr size_t smem = l1_smem_bytes<C, OUT, IN_CH>();
   static bool configured = false;  // opt in to more than 48 KB once per instantiation
   if (!configured) {
@@ -289,7 +293,8 @@ static cudaError_t launch_l1(const uint16_t* frames, int T, int H, int W, int d,
   for (int t0 = 0; t0 < T; t0 += 65535) {
     dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + kL1Rows - 1) / kL1Rows, (unsigned)(T - t0 < 65535 ? T - t0 : 65535)),
         block(kL1Tile);
-    k_ingest_l1<C, OUT, IN_CH><<<grid, block, smem, s>>>(frames, H, W, d, t0, t_first, t_last, cam, prm, out_scale, out);
+    k_ingest_l1<C, OUT, IN_CH><<<grid, block, smem, s>>>(frames, H, W, d, t0, t_first, t_last, cam, prm, out_scale, out,
+                                                         out_ct);
   }
   return cudaGetLastError();
 }
@@ -297,33 +302,34 @@ static cudaError_t launch_l1(const uint16_t* frames, int T, int H, int W, int d,
 template <int C>
 static cudaError_t launch_l1_prec(const uint16_t* frames, int T, int H, int W, int d, int in_ch, int t_first,
                                   int t_last, const CamArgs& cam, const L1Params& prm, int prec, float out_scale,
-                                  void* out, cudaStream_t s) {
+                                  void* out, int out_ct, cudaStream_t s) {
   if (in_ch == 1) {
-    if (prec == kFP32) return launch_l1<C, 0, 1>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
-    if (prec == kBF16) return launch_l1<C, 1, 1>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
-    return launch_l1<C, 2, 1>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
+    if (prec == kFP32) return launch_l1<C, 0, 1>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, out_ct, s);
+    if (prec == kBF16) return launch_l1<C, 1, 1>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, out_ct, s);
+    return launch_l1<C, 2, 1>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, out_ct, s);
   }
-  if (prec == kFP32) return launch_l1<C, 0, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
-  if (prec == kBF16) return launch_l1<C, 1, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
-  return launch_l1<C, 2, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, s);
+  if (prec == kFP32) return launch_l1<C, 0, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, out_ct, s);
+  if (prec == kBF16) return launch_l1<C, 1, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, out_ct, s);
+  return launch_l1<C, 2, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, out_ct, s);
 }
 
 cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1,
                              const float* b1, int C, int in_ch, int t_first, int t_last, int prec, float out_scale,
-                             void* out, cudaStream_t s) {
+                             void* out, int out_ct, cudaStream_t s) {
   if ((long long)T * H * W == 0) return cudaSuccess;
   if (d > 64 || C > 64 || (in_ch != 1 && in_ch != 3)) return cudaErrorInvalidValue;
   if (t_first > 0 || t_last < T - 1) return cudaErrorInvalidValue;
+  if (out_ct < C || out_ct % 16) return cudaErrorInvalidValue;
   // w1/b1 are host copies here: they travel as a kernel parameter
   L1Params prm;
   memset(&prm, 0, sizeof(prm));
   memcpy(prm.w, w1, sizeof(float) * C * in_ch * 9);
   memcpy(prm.b, b1, sizeof(float) * C);
   switch (C) {
-    case 16: return launch_l1_prec<16>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, s);
-    case 32: return launch_l1_prec<32>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, s);
-    case 48: return launch_l1_prec<48>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, s);
-    case 64: return launch_l1_prec<64>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, s);
+    case 16: return launch_l1_prec<16>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, out_ct, s);
+    case 32: return launch_l1_prec<32>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, out_ct, s);
+    case 48: return launch_l1_prec<48>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, out_ct, s);
+    case 64: return launch_l1_prec<64>(frames, T, H, W, d, in_ch, t_first, t_last, cam, prm, prec, out_scale, out, out_ct, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -336,42 +342,43 @@ cudaError_t launch_amax(const void* x, size_t n, int prec, unsigned* out, cudaSt
   return cudaGetLastError();
 }
 
-template <int C, bool HEADS>
-static cudaError_t launch_f32_impl(const float* in, float* out, const float* w, const float* b, const float* hw,
-                                   const float* hb, int T, int H, int W, int d, float* maps, float* logits,
-                                   cudaStream_t s) {
-  size_t smem = sizeof(float) * 9 * C * C;
-  static bool configured = false;
+template <int CO, bool HEADS>
+static cudaError_t launch_f32_impl(const F32LayerArgs& a, const float* hw, const float* hb, float* maps,
+                                   float* logits, cudaStream_t s) {
+  if (a.ci < 4 || a.ci % 4 || a.ci * CO > kF32MaxWeights || a.in_ct < a.ci || a.in_ct % 4) return cudaErrorInvalidValue;
+  if (!HEADS && (a.out_off < 0 || a.out_off % 4 || a.out_off + CO > a.out_ct || a.out_ct % 4)) return cudaErrorInvalidValue;
+  size_t smem = sizeof(float) * 9 * a.ci * CO;
+  static bool configured = false;  // opt in to the largest weight image once per instantiation
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_dconv_f32<C, HEADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_dconv_f32<CO, HEADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(float) * 9 * kF32MaxWeights);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  long long npx = (long long)T * H * W;
+  long long npx = (long long)a.T * a.H * a.W;
   if (npx == 0) return cudaSuccess;
-  k_dconv_f32<C, HEADS><<<grid_for(npx), kSimtThreads, smem, s>>>(in, out, w, b, hw, hb, T, H, W, d, maps, logits);
+  k_dconv_f32<CO, HEADS><<<grid_for(npx), kSimtThreads, smem, s>>>(a, hw, hb, maps, logits);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dconv_f32(const float* in, float* out, const float* w, const float* b, int T, int H, int W,
-                             int C, int d, cudaStream_t s) {
-  switch (C) {
-    case 16: return launch_f32_impl<16, false>(in, out, w, b, nullptr, nullptr, T, H, W, d, nullptr, nullptr, s);
-    case 32: return launch_f32_impl<32, false>(in, out, w, b, nullptr, nullptr, T, H, W, d, nullptr, nullptr, s);
-    case 48: return launch_f32_impl<48, false>(in, out, w, b, nullptr, nullptr, T, H, W, d, nullptr, nullptr, s);
-    case 64: return launch_f32_impl<64, false>(in, out, w, b, nullptr, nullptr, T, H, W, d, nullptr, nullptr, s);
+cudaError_t launch_dconv_f32(const F32LayerArgs& a, cudaStream_t s) {
+  switch (a.co) {
+    case 16: return launch_f32_impl<16, false>(a, nullptr, nullptr, nullptr, nullptr, s);
+    case 32: return launch_f32_impl<32, false>(a, nullptr, nullptr, nullptr, nullptr, s);
+    case 48: return launch_f32_impl<48, false>(a, nullptr, nullptr, nullptr, nullptr, s);
+    case 64: return launch_f32_impl<64, false>(a, nullptr, nullptr, nullptr, nullptr, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_dconv_f32_heads(const float* in, const float* w, const float* b, const float* hw,
-                                   const float* hb, int T, int H, int W, int C, int d, float* maps, float* logits,
-                                   cudaStream_t s) {
-  switch (C) {
-    case 16: return launch_f32_impl<16, true>(in, nullptr, w, b, hw, hb, T, H, W, d, maps, logits, s);
-    case 32: return launch_f32_impl<32, true>(in, nullptr, w, b, hw, hb, T, H, W, d, maps, logits, s);
-    case 48: return launch_f32_impl<48, true>(in, nullptr, w, b, hw, hb, T, H, W, d, maps, logits, s);
-    case 64: return launch_f32_impl<64, true>(in, nullptr, w, b, hw, hb, T, H, W, d, maps, logits, s);
+cudaError_t launch_dconv_f32_heads(const F32LayerArgs& a, const float* hw, const float* hb, float* maps,
+                                   float* logits, cudaStream_t s) {
+  if (a.ci != a.co) return cudaErrorInvalidValue;
+  switch (a.co) {
+    case 16: return launch_f32_impl<16, true>(a, hw, hb, maps, logits, s);
+    case 32: return launch_f32_impl<32, true>(a, hw, hb, maps, logits, s);
+    case 48: return launch_f32_impl<48, true>(a, hw, hb, maps, logits, s);
+    case 64: return launch_f32_impl<64, true>(a, hw, hb, maps, logits, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -253,24 +253,32 @@ struct TcKArgs {
   uint32_t units;      // T * NS * d * NQ
   uint32_t stage_bytes, plane_stride, tx_bytes;
   int nstages;
+  // runtime-K instances (CI = 0): K steps per tap, input groups loaded per row, planes per
+  // stage, bytes of the B image; output: first group and groups per pixel row of the buffer
+  int nks, g_in, g_planes;
+  uint32_t bimg_bytes;
+  int out_g0, out_gt;
   int* err;
 };
 
-template <int C, int PREC>
+// Compile-time shape of one layer: CI input channels (K = 9 taps x CI), CO output channels
+// (N = 3 CO per MMA).  CI = 0 is the runtime-K instance: the K-dependent sizes come from the
+// kernel arguments instead (dense-block layers, whose CI grows along the block).
+template <int CI, int CO, int PREC>
 struct TcCfg {
-  static constexpr int ROWB = PREC == kBF16 ? 32 : 16;    // bytes of one pixel's group row
-  static constexpr int G = C / 16;                        // 16-channel groups stored in HBM
+  static constexpr int G = CI / 16;                       // 16-channel input groups stored in HBM
+  static constexpr int GO = CO / 16;                      // output groups
   static constexpr int KSTEP = PREC == kBF16 ? 16 : 32;   // K per MMA instruction
-  static constexpr int NKS = (C + KSTEP - 1) / KSTEP;     // MMAs per tap
+  static constexpr int NKS = (CI + KSTEP - 1) / KSTEP;    // MMAs per tap
   static constexpr int GP = PREC == kBF16 ? G : 2 * NKS;  // planes in shared memory (FP8: zero pad)
-  static constexpr int BBLK = 3 * (C / 8) * 256;          // bytes of one (kx, k-step) B block: N = 3C
+  static constexpr int BBLK = 3 * (CO / 8) * 256;         // bytes of one (kx, k-step) B block: N = 3 CO
   static constexpr int BIMG = 3 * NKS * BBLK;
-  // S = output rows per unit: the window of S+2 input rows needs (S+1)*C + 3C <= 512 columns
-  static constexpr int SEG = (512 / C - 4) < kMaxSeg ? (512 / C - 4) : kMaxSeg;
-  static constexpr uint32_t BASE0 = (uint32_t)(SEG + 1) * C;  // TMEM column of output row 0
-  static constexpr uint32_t IDESC1 = instr_desc(PREC, kTileM, C);
-  static constexpr uint32_t IDESC2 = instr_desc(PREC, kTileM, 2 * C);
-  static constexpr uint32_t IDESC3 = instr_desc(PREC, kTileM, 3 * C);
+  // S = output rows per unit: the window of S+2 input rows needs (S+1)*CO + 3CO <= 512 columns
+  static constexpr int SEG = (512 / CO - 4) < kMaxSeg ? (512 / CO - 4) : kMaxSeg;
+  static constexpr uint32_t BASE0 = (uint32_t)(SEG + 1) * CO;  // TMEM column of output row 0
+  static constexpr uint32_t IDESC1 = instr_desc(PREC, kTileM, CO);
+  static constexpr uint32_t IDESC2 = instr_desc(PREC, kTileM, 2 * CO);
+  static constexpr uint32_t IDESC3 = instr_desc(PREC, kTileM, 3 * CO);
 };
 
 // Unit -> (t, phi, strip, q), q fastest: consecutive units are the next segment of the same
@@ -292,14 +300,19 @@ __device__ __forceinline__ int unit_rows(const TcKArgs& a, uint32_t u, int seg, 
   return n < 0 ? 0 : (n > seg ? seg : n);
 }
 
-template <int C, int PREC, bool LAST>
+template <int CI, int CO, int PREC, bool LAST>
 __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant__ CUtensorMap tmap, const TcKArgs a) {
-  using Cfg = TcCfg<C, PREC>;
+  using Cfg = TcCfg<CI, CO, PREC>;
+  // K-dependent sizes: compile-time constants, or the arguments' values for CI = 0
+  const int nks = CI > 0 ? Cfg::NKS : a.nks;
+  const int g_in = CI > 0 ? Cfg::G : a.g_in;
+  const int g_planes = CI > 0 ? Cfg::GP : a.g_planes;
+  const uint32_t bimg_bytes = CI > 0 ? (uint32_t)Cfg::BIMG : a.bimg_bytes;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // carve shared memory (1024-aligned base)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* s_bimg = smem;
-  uint8_t* s_stage = smem + ((Cfg::BIMG + 1023) & ~1023);
+  uint8_t* s_stage = smem + ((bimg_bytes + 1023u) & ~1023u);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_stage + (size_t)a.nstages * a.stage_bytes);
   // barriers: full[nst], empty[nst], acc_full[SEG], acc_empty[SEG], drain
   constexpr int SEG = Cfg::SEG;
@@ -324,11 +337,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.bimg);
     uint4* dst = reinterpret_cast<uint4*>(s_bimg);
-    for (int k = threadIdx.x; k < Cfg::BIMG / 16; k += kThreads) dst[k] = src[k];
-    if (Cfg::GP > Cfg::G) {  // planes beyond the stored groups stay zero (K padding)
+    for (int k = threadIdx.x; k < (int)(bimg_bytes / 16); k += kThreads) dst[k] = src[k];
+    if (g_planes > g_in) {  // planes beyond the stored groups stay zero (K padding)
       for (int s = 0; s < a.nstages; ++s) {
-        uint4* z = reinterpret_cast<uint4*>(s_stage + (size_t)s * a.stage_bytes + (size_t)Cfg::G * a.plane_stride);
-        int n16 = (Cfg::GP - Cfg::G) * a.plane_stride / 16;
+        uint4* z = reinterpret_cast<uint4*>(s_stage + (size_t)s * a.stage_bytes + (size_t)g_in * a.plane_stride);
+        int n16 = (g_planes - g_in) * a.plane_stride / 16;
         for (int k = threadIdx.x; k < n16; k += kThreads) z[k] = make_uint4(0, 0, 0, 0);
       }
     }
@@ -358,14 +371,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
   }
   const uint32_t tmem = *s_tmem;
   // accumulator start values: every row position holds the bias (in accumulator units)
-  float acc0[C];
+  float acc0[CO];
 #pragma unroll
-  for (int c = 0; c < C; ++c) acc0[c] = PREC == kFP8 ? a.bias[c] / a.deq[c] : a.bias[c];
+  for (int c = 0; c < CO; ++c) acc0[c] = PREC == kFP8 ? a.bias[c] / a.deq[c] : a.bias[c];
   if (warp < kEpiWarps) {
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
     for (int k = 0; k < SEG; ++k)
 #pragma unroll
-      for (int c = 0; c < C; c += 16) tmem_st16(lane_addr + Cfg::BASE0 - (uint32_t)(C * k) + c, acc0 + c);
+      for (int c = 0; c < CO; c += 16) tmem_st16(lane_addr + Cfg::BASE0 - (uint32_t)(CO * k) + c, acc0 + c);
     tmem_st_wait();
   }
   fence_before_sync();
@@ -425,13 +438,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       const uint64_t a_desc0 = PREC == kBF16 ? smem_desc(smem_u32(s_stage), 16u, 256u, 6u)
                                              : smem_desc(smem_u32(s_stage), a.plane_stride, 128u);
       const uint64_t b_desc0 = smem_desc(smem_u32(s_bimg), 128u, 256u);
-      uint32_t a_off[3 * Cfg::NKS];  // in 16-byte units
-#pragma unroll
-      for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-        for (int ks = 0; ks < Cfg::NKS; ++ks)
-          a_off[kx * Cfg::NKS + ks] = PREC == kBF16 ? (uint32_t)(2 * kx * a.d) + (uint32_t)ks * (a.plane_stride >> 4)
-                                                    : (uint32_t)(kx * a.d) + (uint32_t)ks * (a.plane_stride >> 3);
+      // A offsets in 16-byte units: tap kx starts kx*d pixel rows later, K step ks one plane
+      // (BF16) or two planes (FP8) further
+      const uint32_t a_kx = PREC == kBF16 ? (uint32_t)(2 * a.d) : (uint32_t)a.d;
+      const uint32_t a_ks = PREC == kBF16 ? (a.plane_stride >> 4) : (a.plane_stride >> 3);
       const uint32_t stage16 = a.stage_bytes >> 4;
       const uint32_t nst = (uint32_t)a.nstages;
       uint32_t st = 0;             // stage of the current row
@@ -453,15 +463,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           const int b_lo = kk - n_out + 1 > 0 ? kk - n_out + 1 : 0;
           const int b_hi = kk < 2 ? kk : 2;
           const int nb = b_hi - b_lo + 1;
-          const uint32_t d_col = tmem + Cfg::BASE0 - (uint32_t)(C * kk) + (uint32_t)(C * b_lo);
-          const uint32_t b_sub = (uint32_t)(2 * C * b_lo);  // 32*C*b_lo bytes in 16-byte units
+          const uint32_t d_col = tmem + Cfg::BASE0 - (uint32_t)(CO * kk) + (uint32_t)(CO * b_lo);
+          const uint32_t b_sub = (uint32_t)(2 * CO * b_lo);  // 32*CO*b_lo bytes in 16-byte units
           const uint32_t idesc_n = nb == 3 ? Cfg::IDESC3 : (nb == 2 ? Cfg::IDESC2 : Cfg::IDESC1);
 #pragma unroll
           for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
-            for (int ks = 0; ks < Cfg::NKS; ++ks) {
-              const uint64_t ad = a_st + a_off[kx * Cfg::NKS + ks];
-              const uint64_t bd = b_desc0 + (uint64_t)(((kx * Cfg::NKS + ks) * Cfg::BBLK) >> 4) + b_sub;
+            for (int ks = 0; ks < nks; ++ks) {
+              const uint64_t ad = a_st + (uint32_t)kx * a_kx + (uint32_t)ks * a_ks;
+              const uint64_t bd = b_desc0 + (uint64_t)((uint32_t)(kx * nks + ks) * (uint32_t)(Cfg::BBLK >> 4)) + b_sub;
               umma_if<PREC>(d_col, ad, bd, idesc_n, leader);
             }
           issued = true;
@@ -536,6 +546,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
     uint32_t fpar = 0;  // per row position: phase of its acc_full barrier for the next use
     bool ok = true;
+    // output buffer: groups per pixel row and the first group this layer writes
+    const int out_gt = CI > 0 ? Cfg::GO : a.out_gt;
+    const int out_g0 = CI > 0 ? 0 : a.out_g0;
     const size_t plane = (size_t)a.H * a.W;
     for (uint32_t u = u_begin; u < u_end && ok; ++u) {
       int t, j0, phi, q;
@@ -547,13 +560,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           break;
         }
         fence_after_sync();
-        float v[C];
-        const uint32_t col = Cfg::BASE0 - (uint32_t)(C * k);
+        float v[CO];
+        const uint32_t col = Cfg::BASE0 - (uint32_t)(CO * k);
 #pragma unroll
-        for (int c = 0; c < C; c += 16) tmem_ld16(lane_addr + col + c, v + c);
+        for (int c = 0; c < CO; c += 16) tmem_ld16(lane_addr + col + c, v + c);
         tmem_ld_wait();
 #pragma unroll
-        for (int c = 0; c < C; c += 16) tmem_st16(lane_addr + col + c, acc0 + c);  // next use starts at the bias
+        for (int c = 0; c < CO; c += 16) tmem_st16(lane_addr + col + c, acc0 + c);  // next use starts at the bias
         tmem_st_wait();
         fence_before_sync();
         mbar_arrive(smem_u32(&acce_bar[k]));
@@ -564,11 +577,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         // into its conversion
         if (PREC == kFP8) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) v[c] *= a.deq[c];
+          for (int c = 0; c < CO; ++c) v[c] *= a.deq[c];
         }
         if (LAST || PREC == kFP8) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) v[c] = fmaxf(v[c], 0.0f);
+          for (int c = 0; c < CO; ++c) v[c] = fmaxf(v[c], 0.0f);
         }
         if (LAST) {
           const size_t px = (size_t)i * a.W + j;
@@ -576,7 +589,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           for (int h = 0; h < kHeads; ++h) {
             float acc = a.head_b[h];
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc = fmaf(a.head_w[h * C + c], v[c], acc);
+            for (int c = 0; c < CO; ++c) acc = fmaf(a.head_w[h * CO + c], v[c], acc);
             if (h == 0) {
               if (a.logits) a.logits[(size_t)t * plane + px] = acc;
               acc = 1.0f / (1.0f + expf(-acc));
@@ -585,18 +598,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           }
         } else if (PREC == kBF16) {
 #pragma unroll
-          for (int gq = 0; gq < Cfg::G; ++gq) {
+          for (int gq = 0; gq < Cfg::GO; ++gq) {
             uint4 o[2];
             uint32_t* ow = reinterpret_cast<uint32_t*>(o);
 #pragma unroll
             for (int e = 0; e < 8; ++e) ow[e] = bf16x2_relu(v[16 * gq + 2 * e], v[16 * gq + 2 * e + 1]);
-            uint4* dst = reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 32);
+            uint4* dst = reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * out_gt + out_g0 + gq) * a.W + j) * 32);
             __stcs(dst, o[0]);  // streaming: the next layer reads it from HBM anyway; keep L2 for halos
             __stcs(dst + 1, o[1]);
           }
         } else {
 #pragma unroll
-          for (int gq = 0; gq < Cfg::G; ++gq) {
+          for (int gq = 0; gq < Cfg::GO; ++gq) {
             uint4 o;
             uint16_t* oh = reinterpret_cast<uint16_t*>(&o);
 #pragma unroll
@@ -604,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
               oh[e] = __nv_cvt_float2_to_fp8x2(
                   make_float2(v[16 * gq + 2 * e] * a.out_inv_scale, v[16 * gq + 2 * e + 1] * a.out_inv_scale),
                   __NV_SATFINITE, __NV_E4M3);
-            __stcs(reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * Cfg::G + gq) * a.W + j) * 16), o);
+            __stcs(reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.H + i) * out_gt + out_g0 + gq) * a.W + j) * 16), o);
           }
         }
       }
@@ -686,29 +699,51 @@ __global__ void __launch_bounds__(128, 1) k_umma_selftest(const uint8_t* A, cons
   }
 }
 
-template <int C, int PREC>
-size_t tc_smem_bytes(int nstages, uint32_t stage_bytes) {
-  using Cfg = TcCfg<C, PREC>;
-  size_t b = 1024;                            // alignment slack
-  b += (Cfg::BIMG + 1023) & ~1023;            // weights
-  b += (size_t)nstages * stage_bytes;         // stages
-  b += 8 * (2 * nstages + 2 * Cfg::SEG + 1) + 16;      // barriers, tmem addr, abort flag
+size_t tc_smem_bytes(uint32_t bimg_bytes, int seg, int nstages, uint32_t stage_bytes) {
+  size_t b = 1024;                                 // alignment slack
+  b += (bimg_bytes + 1023u) & ~1023u;              // weights
+  b += (size_t)nstages * stage_bytes;              // stages
+  b += 8 * (2 * nstages + 2 * seg + 1) + 16;       // barriers, tmem addr, abort flag
   return b;
 }
 
-template <int C, int PREC, bool LAST>
+constexpr size_t kSmemBudget = 227 * 1024;
+
+// Row sizes of a layer with ci input channels at dilation d.
+struct TcSizes {
+  int nks, g_in, g_planes;
+  uint32_t bimg_bytes, plane_stride, tx_bytes, stage_bytes;
+};
+TcSizes tc_sizes(int ci, int co, int d, int prec) {
+  TcSizes z;
+  const int kstep = prec == kBF16 ? 16 : 32;
+  z.nks = (ci + kstep - 1) / kstep;
+  z.g_in = ci / 16;
+  z.g_planes = prec == kBF16 ? z.g_in : 2 * z.nks;
+  z.bimg_bytes = (uint32_t)(3 * z.nks * 3 * (co / 8) * 256);
+  z.plane_stride = (uint32_t)tc_box_width(d) * (prec == kBF16 ? 32u : 16u);  // box width: a multiple of 32
+  z.tx_bytes = (uint32_t)z.g_in * z.plane_stride;
+  z.stage_bytes = ((uint32_t)z.g_planes * z.plane_stride + 1023u) & ~1023u;
+  return z;
+}
+
+int tc_seg(int co) { return (512 / co - 4) < kMaxSeg ? (512 / co - 4) : kMaxSeg; }
+
+template <int CI, int CO, int PREC, bool LAST>
 cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
-  using Cfg = TcCfg<C, PREC>;
+  using Cfg = TcCfg<CI, CO, PREC>;
+  const int ci = CI > 0 ? CI : la.ci;
+  if (la.co != CO || ci != la.ci || ci < 16 || ci > kTcMaxCin || ci % 16) return cudaErrorInvalidValue;
   TcKArgs a{};
   a.bimg = static_cast<const uint8_t*>(la.bimg);
-  for (int c = 0; c < C; ++c) {
+  for (int c = 0; c < CO; ++c) {
     a.bias[c] = la.bias[c];
     a.deq[c] = la.deq ? la.deq[c] : 1.0f;
   }
   if (LAST) {
     for (int k = 0; k < kHeads; ++k) {
       a.head_b[k] = la.head_b[k];
-      for (int c = 0; c < C; ++c) a.head_w[k * C + c] = la.head_w[k * C + c];
+      for (int c = 0; c < CO; ++c) a.head_w[k * CO + c] = la.head_w[k * CO + c];
     }
   }
   a.out_inv_scale = la.out_inv_scale;
@@ -725,23 +760,31 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   const long long units = (long long)la.T * a.NS * la.d * a.NQ;
   if (units >= (1LL << 31)) return cudaErrorInvalidValue;
   a.units = (uint32_t)units;
-  const int boxw = tc_box_width(la.d);  // pixels per plane, a multiple of 32
-  a.plane_stride = (uint32_t)boxw * Cfg::ROWB;
-  a.tx_bytes = (uint32_t)Cfg::G * a.plane_stride;
-  a.stage_bytes = ((uint32_t)Cfg::GP * a.plane_stride + 1023u) & ~1023u;
+  const TcSizes z = tc_sizes(ci, CO, la.d, PREC);
+  a.nks = z.nks;
+  a.g_in = z.g_in;
+  a.g_planes = z.g_planes;
+  a.bimg_bytes = z.bimg_bytes;
+  a.plane_stride = z.plane_stride;
+  a.tx_bytes = z.tx_bytes;
+  a.stage_bytes = z.stage_bytes;
+  a.out_g0 = la.out_g0;
+  a.out_gt = la.out_gt;
+  if (CI > 0 && !LAST && (la.out_g0 != 0 || la.out_gt != Cfg::GO)) return cudaErrorInvalidValue;
+  if (!LAST && (la.out_g0 < 0 || la.out_g0 + Cfg::GO > la.out_gt)) return cudaErrorInvalidValue;
   a.err = la.err;
   if (a.units == 0) return cudaSuccess;
-  const size_t budget = 227 * 1024;
   int nst = la.stages > 0 ? la.stages : kMaxStages;
   if (nst < kMinStages) return cudaErrorInvalidValue;
-  while (nst > kMinStages && tc_smem_bytes<C, PREC>(nst, a.stage_bytes) > budget) --nst;
+  while (nst > kMinStages && tc_smem_bytes(z.bimg_bytes, Cfg::SEG, nst, z.stage_bytes) > kSmemBudget) --nst;
   a.nstages = nst;
-  size_t smem = tc_smem_bytes<C, PREC>(nst, a.stage_bytes);
-  if (smem > budget) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_dconv_tc<C, PREC, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  size_t smem = tc_smem_bytes(z.bimg_bytes, Cfg::SEG, nst, z.stage_bytes);
+  if (smem > kSmemBudget) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_dconv_tc<CI, CO, PREC, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   long long grid = (long long)a.units < (long long)num_sms ? (long long)a.units : (long long)num_sms;
-  k_dconv_tc<C, PREC, LAST><<<(unsigned)grid, kThreads, smem, s>>>(*la.tmap, a);
+  k_dconv_tc<CI, CO, PREC, LAST><<<(unsigned)grid, kThreads, smem, s>>>(*la.tmap, a);
   return cudaGetLastError();
 }
 
@@ -749,36 +792,34 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
 
 int tc_box_width(int d) { return (kTileM + 2 * d + 31) / 32 * 32; }
 
-int tc_groups(int C, int prec) {
-  (void)prec;
-  return C / 16;
+size_t tc_bimg_bytes(int ci, int co, int prec) { return tc_sizes(ci, co, 1, prec).bimg_bytes; }
+
+bool tc_layer_fits(int ci, int co, int d, int prec) {
+  if (ci < 16 || ci > kTcMaxCin || ci % 16 || co < 16 || co > 64 || co % 16) return false;
+  const TcSizes z = tc_sizes(ci, co, d, prec);
+  return tc_smem_bytes(z.bimg_bytes, tc_seg(co), kMinStages, z.stage_bytes) <= kSmemBudget;
 }
 
-size_t tc_bimg_bytes(int C, int prec) {
-  const int kstep = prec == kBF16 ? 16 : 32;
-  const int nks = (C + kstep - 1) / kstep;
-  return (size_t)3 * nks * 3 * (C / 8) * 256;
-}
-
-// B image: for horizontal tap kx and k-step ks, one [N = 3C][K = kstep] block whose rows are
-// n = ky*C + co (the three vertical taps side by side), in no-swizzle K-major core-matrix
-// order: byte (n/8)*256 + (k/EPG)*128 + (n%8)*16 + (k%EPG)*esize.  Input channels beyond C
+// B image: for horizontal tap kx and k-step ks, one [N = 3 CO][K = kstep] block whose rows are
+// n = ky*CO + co (the three vertical taps side by side), in no-swizzle K-major core-matrix
+// order: byte (n/8)*256 + (k/EPG)*128 + (n%8)*16 + (k%EPG)*esize.  Input channels beyond CI
 // (FP8 padding) are zero.  FP8 weights are divided by w_scale[co].
-void tc_pack_bimg(const float* w /*[9][C][C] tap, ci, co*/, int C, int prec, const float* w_scale, void* dst) {
+void tc_pack_bimg(const float* w /*[9][CI][CO] tap, ci, co*/, int CI, int CO, int prec, const float* w_scale,
+                  void* dst) {
   const int kstep = prec == kBF16 ? 16 : 32;
   const int epg = prec == kBF16 ? 8 : 16;
   const int es = prec == kBF16 ? 2 : 1;
-  const int nks = (C + kstep - 1) / kstep;
-  const size_t bblk = (size_t)3 * (C / 8) * 256;
+  const int nks = (CI + kstep - 1) / kstep;
+  const size_t bblk = (size_t)3 * (CO / 8) * 256;
   uint8_t* out = static_cast<uint8_t*>(dst);
   for (int kx = 0; kx < 3; ++kx)
     for (int ks = 0; ks < nks; ++ks) {
       uint8_t* blk = out + ((size_t)kx * nks + ks) * bblk;
-      for (int n = 0; n < 3 * C; ++n) {
-        const int ky = n / C, co = n % C, tap = ky * 3 + kx;
+      for (int n = 0; n < 3 * CO; ++n) {
+        const int ky = n / CO, co = n % CO, tap = ky * 3 + kx;
         for (int k = 0; k < kstep; ++k) {
           int ci = ks * kstep + k;
-          float v = ci < C ? w[((size_t)tap * C + ci) * C + co] : 0.0f;
+          float v = ci < CI ? w[((size_t)tap * CI + ci) * CO + co] : 0.0f;
           size_t off = (size_t)(n / 8) * 256 + (size_t)(k / epg) * 128 + (size_t)(n % 8) * 16 + (size_t)(k % epg) * es;
           if (prec == kBF16) {
             __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -792,20 +833,35 @@ void tc_pack_bimg(const float* w /*[9][C][C] tap, ci, co*/, int C, int prec, con
     }
 }
 
+// Plain layers (ci == co, output filling whole pixel rows of its buffer) and every last layer
+// run the compile-time instances; layers of dense blocks (ci != co, or an output that is a
+// channel range of a wider buffer) run the runtime-K instances (BF16 only).
 cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaStream_t s) {
-#define SML_TC(CC)                                                                               \
-  case CC:                                                                                       \
-    if (a.prec == kBF16)                                                                         \
-      return last ? launch_tc_impl<CC, kBF16, true>(a, num_sms, s) : launch_tc_impl<CC, kBF16, false>(a, num_sms, s); \
-    else                                                                                         \
-      return last ? launch_tc_impl<CC, kFP8, true>(a, num_sms, s) : launch_tc_impl<CC, kFP8, false>(a, num_sms, s);
-  switch (a.C) {
-    SML_TC(16)
-    SML_TC(32)
-    SML_TC(48)
-    SML_TC(64)
-  }
+  const bool plain = a.ci == a.co && a.out_g0 == 0 && a.out_gt == a.co / 16;
+  if (last || plain) {
+#define SML_TC(CC)                                                                                          \
+  case CC:                                                                                                  \
+    if (a.prec == kBF16)                                                                                    \
+      return last ? launch_tc_impl<CC, CC, kBF16, true>(a, num_sms, s) : launch_tc_impl<CC, CC, kBF16, false>(a, num_sms, s); \
+    else                                                                                                    \
+      return last ? launch_tc_impl<CC, CC, kFP8, true>(a, num_sms, s) : launch_tc_impl<CC, CC, kFP8, false>(a, num_sms, s);
+    if (a.ci != a.co) return cudaErrorInvalidValue;
+    switch (a.co) {
+      SML_TC(16)
+      SML_TC(32)
+      SML_TC(48)
+      SML_TC(64)
+    }
 #undef SML_TC
+    return cudaErrorInvalidValue;
+  }
+  if (a.prec != kBF16) return cudaErrorInvalidValue;
+  switch (a.co) {
+    case 16: return launch_tc_impl<0, 16, kBF16, false>(a, num_sms, s);
+    case 32: return launch_tc_impl<0, 32, kBF16, false>(a, num_sms, s);
+    case 48: return launch_tc_impl<0, 48, kBF16, false>(a, num_sms, s);
+    case 64: return launch_tc_impl<0, 64, kBF16, false>(a, num_sms, s);
+  }
   return cudaErrorInvalidValue;
 }
 

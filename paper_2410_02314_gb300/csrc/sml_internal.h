@@ -10,7 +10,8 @@
 namespace sml {
 
 constexpr int kHeads = 5;
-constexpr int kMaxLayers = 16;
+constexpr int kMaxLayers = 32;  // conv layers of a net (plain stacks: 16)
+constexpr int kTcMaxCin = 128;   // widest tensor-core conv input (8 groups of 16 channels)
 constexpr int kTileM = 128;  // pixels per MMA tile (one row segment)
 
 enum Precision { kFP32 = 0, kBF16 = 1, kFP8 = 2, kTF32 = 3 /* MMA operand kind of the self-test only */ };
@@ -57,47 +58,63 @@ __device__ __forceinline__ float cam_input(const uint16_t* __restrict__ f, int H
 #endif
 
 // --- layer 1: camera transform + Cin=1 dilated 3x3 conv, bias, ReLU -------------------
-// prec kFP32 writes float NHWC [T][H][W][C]; kBF16 / kFP8 write row-planar activations
-// [T][H][C/16][W][row bytes] (16 channels per group: 32-byte bf16 rows, 16-byte e4m3 rows).  out_scale
+// prec kFP32 writes float NHWC [T][H][W][out_ct] channels 0..C-1; kBF16 / kFP8 write row-planar
+// activations [T][H][out_ct/16][W][row bytes] groups 0..C/16-1 (16 channels per group:
+// 32-byte bf16 rows, 16-byte e4m3 rows).  out_ct = C except for nets with dense blocks, whose
+// buffers hold the block's concatenation (out_ct > C, a multiple of 16).  out_scale
 // multiplies the FP8 output before rounding (1 / activation scale).  w1 [C][in_ch][9] and
 // b1 [C] are HOST pointers (the weights are passed to the kernel by value).  in_ch = 3 takes
 // frames t-1, t, t+1 as the input channels; frames[k] exists for t_first <= k <= t_last
 // (t_first in {-1, 0}, t_last in {T-1, T}) and is zero outside that range.
 cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1,
                              const float* b1, int C, int in_ch, int t_first, int t_last, int prec, float out_scale,
-                             void* out, cudaStream_t s);
+                             void* out, int out_ct, cudaStream_t s);
 
 // Max of n post-ReLU activations (fp32 or bf16 buffer) into *out (float bits, atomicMax).
 cudaError_t launch_amax(const void* x, size_t n, int prec, unsigned* out, cudaStream_t s);
 
 // --- SIMT FP32 path (NHWC float activations) ------------------------------------------
-cudaError_t launch_dconv_f32(const float* in, float* out, const float* w, const float* b, int T, int H, int W,
-                             int C, int d, cudaStream_t s);
-cudaError_t launch_dconv_f32_heads(const float* in, const float* w, const float* b, const float* hw,
-                                   const float* hb, int T, int H, int W, int C, int d, float* maps, float* logits,
-                                   cudaStream_t s);
+// Reads channels 0..ci-1 of pixels in_ct floats apart; writes channels out_off..out_off+co-1
+// of pixels out_ct floats apart.  w [9][ci][co] (tap, ci, co), b [co] (device).
+struct F32LayerArgs {
+  const float* in;
+  float* out;
+  const float* w;
+  const float* b;
+  int T, H, W, d;
+  int ci, co, in_ct, out_ct, out_off;
+};
+cudaError_t launch_dconv_f32(const F32LayerArgs& a, cudaStream_t s);
+// Last layer (ci == co == C) with the fused heads.
+cudaError_t launch_dconv_f32_heads(const F32LayerArgs& a, const float* hw, const float* hb, float* maps,
+                                   float* logits, cudaStream_t s);
+// Largest ci * co whose FP32 weights fit in shared memory.
+constexpr int kF32MaxWeights = 227 * 1024 / (9 * 4);
 
 // --- tensor-core path (row-planar activations) -------------------------------------
 struct TcLayerArgs {
   const CUtensorMap* tmap;  // input activations, one box per row (5-D map for this dilation)
   int stages;               // TMA ring depth (0 = as many as shared memory allows)
   const void* bimg;         // device: packed B operand image for this layer
-  const float* bias;        // HOST [C] (passed to the kernel by value)
-  const float* deq;         // HOST [C] per-output-channel dequant factor (FP8) or NULL
+  const float* bias;        // HOST [co] (passed to the kernel by value)
+  const float* deq;         // HOST [co] per-output-channel dequant factor (FP8) or NULL
   float out_inv_scale;      // FP8: 1 / scale of the output activations
   void* out;                // row-planar output activations (middle layers)
+  int out_g0, out_gt;       // output: first group written, groups per pixel row of the buffer
   const float* head_w;      // last layer: HOST [5][C]
   const float* head_b;      // last layer: HOST [5]
   float* maps;              // last layer: [T][5][H][W]
   float* logits;            // last layer: optional [T][H][W]
-  int T, H, W, C, d, prec;
+  int T, H, W, d, prec;
+  int ci, co;               // input channels read (groups 0..ci/16-1 of the input buffer), outputs
   int* err;                 // device error word (wait timeouts)
 };
 cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaStream_t s);
-size_t tc_bimg_bytes(int C, int prec);
-void tc_pack_bimg(const float* w_tap_ci_co /*[9][C][C]*/, int C, int prec, const float* w_scale, void* dst);
+size_t tc_bimg_bytes(int ci, int co, int prec);
+void tc_pack_bimg(const float* w_tap_ci_co /*[9][ci][co]*/, int ci, int co, int prec, const float* w_scale, void* dst);
 int tc_box_width(int d);
-int tc_groups(int C, int prec);
+// Whether a ci -> co layer at dilation d fits the tensor-core conv's shared memory.
+bool tc_layer_fits(int ci, int co, int d, int prec);
 
 // --- training (k_train.cu) -------------------------------------------------------------
 size_t train_conv_work_bytes(int B, int H, int W, int cin, int cout);

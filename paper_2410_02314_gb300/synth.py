@@ -132,6 +132,15 @@ def spec_48(precision="bf16") -> NetSpec:
     return NetSpec(in_ch=1, channels=48, dilations=(1, 2, 4, 8, 16, 8, 4, 1), precision=precision)
 
 
+def spec_dcd(precision="bf16") -> NetSpec:
+    """32-channel net with dense connection dilated blocks: stem (d = 1); one coarse block and
+    three context blocks, each of four dense layers (growth 16, dilations 2, 4, 8, 16) and a
+    transition back to 32 channels; then a last 32-channel layer (d = 1) feeding the heads.
+    22 conv layers, receptive radius 126 px."""
+    return NetSpec(in_ch=1, channels=32, dilations=(1, 1), precision=precision,
+                   dcd={"growth": 16, "blocks": [[2, 4, 8, 16] for _ in range(4)]})
+
+
 # --------------------------------------------------------------------------- weights
 
 
@@ -399,6 +408,17 @@ def workload_batched(T=256, H=256, W=256, precision="bf16", seed=3) -> Workload:
     spec = spec_48(precision)
     blob = pack_blob(spec, init_weights(spec, seed + 1000))
     return Workload("batched_256", frames, cam, em, spec, blob, False)
+
+
+def workload_dcd(T=256, H=256, W=256, precision="bf16", seed=3) -> Workload:
+    """The frames of workload_batched (same seed) through the dense-block net of spec_dcd."""
+    rng = np.random.default_rng(seed)
+    em = emitters_density(rng, T, H, W, 1.0)
+    cam = Camera(1.0, 100.0)
+    frames = simulate(em, T, H, W, cam, False, rng)
+    spec = spec_dcd(precision)
+    blob = pack_blob(spec, init_weights(spec, seed + 2000))
+    return Workload("dcd_256", frames, cam, em, spec, blob, False)
 
 
 def workload_large_fov(T=2, H=2048, W=2048, precision="bf16", seed=4) -> Workload:

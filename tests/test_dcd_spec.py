@@ -1,0 +1,99 @@
+"""Host logic of nets with dense connection dilated blocks (Sec. 3.2.1): the library parses the
+"dcd" spec key and checks version-2 weight blobs before it touches a device, so a malformed
+or unsupported request is refused the same way with or without a GPU."""
+import json
+
+import pytest
+import torch
+
+import paper_2410_02314_gb300 as sml
+from paper_2410_02314_gb300 import synth
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2410_02314_gb300 import _build
+
+    _build.build()
+
+
+def _net(C=32, g=16, blocks=((2, 4), (1, 8, 3)), dil=(1, 2, 1), prec="bf16", in_ch=1, seed=3):
+    spec = synth.NetSpec(in_ch=in_ch, channels=C, dilations=tuple(dil), precision=prec,
+                         dcd={"growth": g, "blocks": [list(b) for b in blocks]})
+    return spec, spec.to_json(), synth.pack_blob(spec, synth.init_weights(spec, seed))
+
+
+def _code(js, blob):
+    with pytest.raises(sml.SmlError) as e:
+        sml.sml_create(js, blob)
+    return e.value.code
+
+
+def _edit(js, **kw):
+    d = json.loads(js)
+    d["dcd"].update(kw.pop("dcd", {}))
+    d.update(kw)
+    return json.dumps(d)
+
+
+def test_layer_plan_of_the_dcd_spec():
+    """Execution order and channel counts: stem, dense layers with inputs C + j g, transition
+    C + k g -> C at d = 1, then the plain layers."""
+    spec, _, _ = _net()
+    assert spec.layers() == [(1, 32, 1), (32, 16, 2), (48, 16, 4), (64, 32, 1), (32, 16, 1), (48, 16, 8),
+                             (64, 16, 3), (80, 32, 1), (32, 32, 2), (32, 32, 1)]
+    assert spec.R == 1 + 2 + 4 + 1 + 1 + 8 + 3 + 1 + 2 + 1
+    big = synth.spec_dcd()
+    assert big.L == 22 and big.R == 126 and max(c for c, _, _ in big.layers()) == 96
+
+
+@pytest.mark.parametrize("edit,code", [
+    (dict(dcd={"growth": 8}), sml.SML_ERR_BAD_SPEC),                       # growth not a multiple of 16
+    (dict(dcd={"blocks": []}), sml.SML_ERR_BAD_SPEC),                      # no block
+    (dict(dcd={"blocks": [[2, 4], []]}), sml.SML_ERR_BAD_SPEC),            # empty block
+    (dict(dcd={"blocks": [[2, 0]]}), sml.SML_ERR_BAD_SPEC),                # dilation 0
+    (dict(dcd={"blocks": [[2, 65]]}), sml.SML_ERR_BAD_SPEC),               # dilation beyond 64
+    (dict(dilations=[1]), sml.SML_ERR_BAD_SPEC),                            # no plain layer for the heads
+    (dict(dcd={"growth": 32, "blocks": [[1, 2, 4, 8]]}), sml.SML_ERR_BAD_SPEC),  # 160-channel concatenation
+    (dict(dcd={"blocks": [[1]] * 16}), sml.SML_ERR_BAD_SPEC),              # 35 conv layers (at most 32)
+    (dict(precision="fp8", act_scales=[1.0] * 10), sml.SML_ERR_UNSUPPORTED),  # fp8 with dense blocks
+])
+def test_bad_dcd_specs_are_refused(edit, code):
+    _, js, blob = _net()
+    assert _code(_edit(js, **edit), blob) == code
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_layers_beyond_shared_memory_are_unsupported(prec):
+    """C = 64 with four dense layers of growth 16: the 128 -> 64 transition's weights do not fit
+    one CTA's shared memory next to a four-stage ring (BF16) or as FP32 (128 x 64 x 9 floats)."""
+    _, js, blob = _net(C=64, g=16, blocks=((1, 2, 4, 8),), dil=(1, 1), prec=prec)
+    assert _code(js, blob) == sml.SML_ERR_UNSUPPORTED
+
+
+def test_blob_must_match_the_dense_spec():
+    spec, js, blob = _net()
+    # a version-1 blob of a plain net of the same C and layer count
+    plain = synth.NetSpec(in_ch=1, channels=32, dilations=(1,) * spec.L, precision="bf16")
+    assert _code(js, synth.pack_blob(plain, synth.init_weights(plain, 1))) == sml.SML_ERR_BAD_WEIGHTS
+    # another growth in the header
+    _, _, blob32 = _net(g=32)
+    assert _code(js, blob32) == sml.SML_ERR_BAD_WEIGHTS
+    # another dilation of one dense layer
+    _, _, other = _net(blocks=((2, 4), (1, 8, 5)))
+    assert _code(js, other) == sml.SML_ERR_BAD_WEIGHTS
+    # truncated payload
+    assert _code(js, blob[:-4]) == sml.SML_ERR_BAD_WEIGHTS
+    # a plain spec refuses the version-2 blob
+    assert _code(plain.to_json(), blob) == sml.SML_ERR_BAD_WEIGHTS
+
+
+def test_valid_dcd_net_reaches_the_device_check():
+    """Spec and blob pass the host checks; without a GPU the call then fails loudly."""
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    for prec in ("bf16", "fp32"):
+        _, js, blob = _net(prec=prec)
+        assert _code(js, blob) == sml.SML_ERR_CUDA
+    spec = synth.spec_dcd()
+    assert _code(spec.to_json(), synth.pack_blob(spec, synth.init_weights(spec, 1))) == sml.SML_ERR_CUDA
