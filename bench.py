@@ -46,6 +46,11 @@ def conv_flops_per_px(C):
     return 2 * 9 * C * C
 
 
+def middle_layers(spec):
+    """(cin, cout, d) of the conv-class launches: every layer but the first and the last."""
+    return spec.layers()[1:-1]
+
+
 def algorithmic_flops_per_px(spec):
     C, L = spec.channels, spec.L
     return 2 * (9 * C + (L - 1) * 9 * C * C + 5 * C)
@@ -110,10 +115,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(precision):
+def profiled_traffic(precision, workload="batched256"):
     """DRAM bytes per launch of the middle-layer conv kernel from the committed ncu summary,
     valid only if the kernel source hash recorded there matches the current source."""
-    p = os.path.join(ROOT, "profiles", f"dconv_tc_{precision}_batched256.md")
+    p = os.path.join(ROOT, "profiles", f"dconv_tc_{precision}_{workload}.md")
     if not os.path.exists(p):
         return None
     text = open(p).read()
@@ -359,11 +364,16 @@ def run_reference(args):
 
 
 def main():
+    global T_FRAMES
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
+    ap.add_argument("--frames", type=int, default=T_FRAMES,
+                    help="frames per step (default 256; smaller stacks for profiler captures)")
+    ap.add_argument("--workload", default="batched", choices=["batched", "dcd"],
+                    help="batched: the 48-channel 8-layer net; dcd: the 22-layer dense-block net (fp32/bf16)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk-px", type=int, default=0)
     ap.add_argument("--tc-stages", type=int, default=0)
@@ -372,6 +382,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the large-FOV and small-config measurements")
     args = ap.parse_args()
+    T_FRAMES = args.frames
     if args.impl == "reference":
         run_reference(args)
         return
@@ -397,9 +408,12 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
+    if args.workload == "dcd" and args.precision == "fp8":
+        raise SystemExit("the dense-block net runs in fp32 or bf16")
+
     def workload(prec, d_frames=None):
-        w = synth.workload_batched(T=T_FRAMES, H=H, W=W, precision="bf16" if prec == "fp8" else prec,
-                                  seed=replicas.frame_seed(3, rank))
+        make = synth.workload_dcd if args.workload == "dcd" else synth.workload_batched
+        w = make(T=T_FRAMES, H=H, W=W, precision="bf16" if prec == "fp8" else prec, seed=replicas.frame_seed(3, rank))
         spec = json.loads(w.spec.to_json())
         if args.chunk_px:
             spec["chunk_px"] = args.chunk_px
@@ -461,7 +475,11 @@ def main():
     frames_per_chunk = max(1, chunk_px // (H * W))
     px_per_launch = min(frames_per_chunk, T_FRAMES) * H * W
     pk, pk_kind = peaks()
-    flops_launch = conv_flops_per_px(C) * px_per_launch
+    mid = middle_layers(w.spec)
+    # per launch: the conv-class FLOPs of one step spread over its launches (all equal for a plain stack)
+    flops_launch = sum(conv_flops_per_px(1) * ci * co for ci, co, _ in mid) / len(mid) * px_per_launch
+    bytes_launch = sum(ci + co for ci, co, _ in mid) / len(mid) * px_per_launch * (2 if args.precision == "bf16" else (
+        1 if args.precision == "fp8" else 4))
     avg_conv_s = conv_ms / max(conv_n, 1) / 1000.0
     achieved = flops_launch / avg_conv_s / 1e12
     if args.precision == "bf16":
@@ -473,11 +491,11 @@ def main():
     else:
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         peak_note = "fp32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz (derived, not measured)"
-    traffic = profiled_traffic(args.precision)
-    hbm = None
+    traffic = profiled_traffic(args.precision, "batched256" if args.workload == "batched" else "dcd256")
+    hbm = {"algorithmic_bytes_per_launch": bytes_launch, "algorithmic_gbs": bytes_launch / avg_conv_s / 1e9,
+           "peak_gbs": pk["hbm_gbs"], "algorithmic_frac": bytes_launch / avg_conv_s / 1e9 / pk["hbm_gbs"]}
     if traffic is not None:
-        hbm = {"achieved_gbs": traffic / avg_conv_s / 1e9, "peak_gbs": pk["hbm_gbs"],
-               "frac": traffic / avg_conv_s / 1e9 / pk["hbm_gbs"]}
+        hbm.update({"achieved_gbs": traffic / avg_conv_s / 1e9, "frac": traffic / avg_conv_s / 1e9 / pk["hbm_gbs"]})
     roofline = {"bound": "tensor" if args.precision != "fp32" else "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "kernel": "k_dconv_tc (middle layers)"
                 if args.precision != "fp32" else "k_dconv_f32 (middle layers)", "peak_kind": peak_note,
@@ -507,7 +525,8 @@ def main():
            "d2h_bytes_per_step": int(recs.numel() + 8)}
 
     extra = {}
-    others = [] if args.no_fp32 else [p for p in ("fp32", "bf16", "fp8") if p != args.precision]
+    others = [] if args.no_fp32 else [p for p in ("fp32", "bf16", "fp8")
+                                      if p != args.precision and not (args.workload == "dcd" and p == "fp8")]
     for prec in others:  # the same batch at the other precisions, same timing method
         wo, jso = workload(prec, d_frames)
         loco = sml.Localizer(jso, wo.blob)
@@ -536,7 +555,7 @@ def main():
         large_fov = large_fov_run(dev, stream, flush)
         small = small_latency_run(dev, stream)
         file_pipe = file_pipeline_run(spec_json, w.blob, w.frames, w.cam)
-        dcd = dcd_run(dev, stream, flush)
+        dcd = dcd_run(dev, stream, flush) if args.workload == "batched" else None
 
     if rank != 0:
         if dist:
@@ -558,7 +577,8 @@ def main():
         "vs_baseline": None,
         "dtype": args.precision,
         "data": "synthetic",
-        "config": {"workload": f"batched_{T_FRAMES}x{H}x{W}_48ch_8layer", "frames_per_step": T_FRAMES,
+        "config": {"workload": f"batched_{T_FRAMES}x{H}x{W}_48ch_8layer" if args.workload == "batched"
+                   else f"dcd_{T_FRAMES}x{H}x{W}_32ch_g16_4x4dense_22layer", "frames_per_step": T_FRAMES,
                    "precision": args.precision, "chunk_px": chunk_px, "tc_stages": args.tc_stages or "max",
                    "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas{world}"},
