@@ -56,6 +56,16 @@ typedef struct {
   float p;       /* detection probability at the peak pixel */
 } sml_record;
 
+/* Uncertainties of one detection (nets with the four uncertainty heads, Sec. 3.2): the
+ * predicted standard deviations of x and y (pixels), z (nm) and photons (e-), read at the
+ * detection's pixel: sigma_x = sx, sigma_y = sy, sigma_z = z_scale * sz,
+ * sigma_photons = ph_scale * sN, each one float32 rounding. */
+typedef struct {
+  float sigma_x, sigma_y; /* pixels */
+  float sigma_z;          /* nm */
+  float sigma_photons;    /* photo-electrons */
+} sml_sigma;
+
 /* Camera model.  If gain_map / offset_map are non-NULL they hold per-pixel values [H][W]
  * (float32) and override the scalars.  Their memory space must match the call: host or
  * device for sml_localize, device for the *_async entry points. */
@@ -80,19 +90,33 @@ typedef struct {
  *   input channels, the three-frame temporal context of Sec. 3.1; zero where t-1 or t+1 lies
  *   outside the frames of the call; chunk edges inside a call read the neighbouring frames);
  *   channels in {16,32,48,64}; 2..16 layers with dilations 1..64;
+ *   "heads": 5 names (p, dx, dy, z, N: probability logit, sub-pixel offsets, zhat, Nhat) or
+ *   9 (those and the uncertainty heads sx, sy, sz, sN, Sec. 3.2; each sigma map is
+ *   softplus(h) = log(1 + exp(h)) of its raw head); default 5;
+ *   "dcd": dense connection dilated blocks (Sec. 3.2.1), {"growth": g, "blocks": [[d, ...],
+ *   ...]} with g in {16,32,48,64}: a stem conv (dilations[0], in_ch -> C), per block one
+ *   dense layer per listed dilation (input: the block input and every earlier output of the
+ *   block, concatenated; g outputs) and a transition (d = 1, C + k g -> C), then the plain
+ *   layers dilations[1:] (at least one); concatenations up to 128 channels, at most 32 conv
+ *   layers, fp32 or bf16 (fp8: SML_ERR_UNSUPPORTED; so is a layer whose weights do not fit
+ *   one CTA's shared memory);
  *   precision "fp32" (SIMT FP32 FMA), "bf16" (tensor cores, FP32 accumulation) or
  *   "fp8" (e4m3 activations and weights, FP32 accumulation; needs "act_scales": one
  *   positive float per conv layer, the scale of that layer's input activations).
  *   Optional tuning: "chunk_px": pixels per device chunk (default 2^24); "tc_stages": TMA
  *   ring depth of the tensor-core conv (0 = as deep as shared memory allows, else 4..16).
  * weights: an SMLW blob (host memory, read during the call only):
- *   header "<8s7I16i": magic "SMLW0001", version 1, L, C, in_ch, n_heads (5), has_bn,
+ *   header "<8s7I16i": magic "SMLW0001", version 1, L, C, in_ch, n_heads (5 or 9), has_bn,
  *   reserved, dilations[16]; then per layer l: W[C][Cin_l][3][3] f32, b[C] f32 and, if
  *   has_bn, gamma[C], beta[C], mean[C], var[C] f32 and eps f32; then the heads
- *   Wh[5][C] f32 and bh[5] f32 (head order: p logit, dx, dy, zhat, Nhat).
- *   BatchNorm is folded into the conv weights here.
+ *   Wh[n_heads][C] f32 and bh[n_heads] f32 (head order: p logit, dx, dy, zhat, Nhat, then
+ *   sx, sy, sz, sN).  BatchNorm is folded into the conv weights here.
+ *   Nets with dense blocks use version 2: header "<8s7I32i" with reserved = growth and the
+ *   32 dilations of every conv layer in execution order; layer l's W is [Cout_l][Cin_l][3][3]
+ *   with the channel counts of the dcd plan; no BatchNorm.
  * out: receives the context (owned by the caller, freed with sml_destroy).
- * Errors: SML_ERR_BAD_SPEC, SML_ERR_BAD_WEIGHTS, SML_ERR_OOM, SML_ERR_CUDA.
+ * Errors: SML_ERR_BAD_SPEC, SML_ERR_BAD_WEIGHTS, SML_ERR_UNSUPPORTED, SML_ERR_OOM, SML_ERR_CUDA.
+ * The spec and the blob are checked on the host before any device call.
  */
 int sml_create(const char* net_spec, const void* weights, size_t weights_bytes, sml_ctx** out);
 
@@ -117,6 +141,19 @@ const char* sml_last_error(const sml_ctx* ctx);
 int sml_localize(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, const sml_camera* cam,
                  const sml_thresholds* thr, sml_record* out, size_t capacity, size_t* n_out);
 
+/* Number of output heads of the context's net: 5, or 9 with the uncertainty heads. */
+int sml_num_heads(const sml_ctx* ctx);
+
+/*
+ * sml_localize_sigma -- sml_localize plus the uncertainties of every detection, for nets
+ * with 9 heads: out_sigma[k] belongs to out[k].  out_sigma is host or device memory
+ * (detected) of capacity entries.  Capacity and errors as in sml_localize; a 5-head net
+ * returns SML_ERR_UNSUPPORTED.
+ */
+int sml_localize_sigma(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, const sml_camera* cam,
+                       const sml_thresholds* thr, sml_record* out, sml_sigma* out_sigma, size_t capacity,
+                       size_t* n_out);
+
 /*
  * sml_localize_async -- device-resident variant, stream ordered, no host synchronisation.
  *
@@ -134,16 +171,18 @@ int sml_localize_async(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int
 /*
  * sml_forward_maps -- the network alone (no decode), device-resident, stream ordered.
  *
- * d_maps: device float32 [T][5][H][W]: channel 0 = p = sigmoid(logit), channels 1..4 =
- * dx, dy, zhat, Nhat (raw head outputs).  d_logits: device float32 [T][H][W] or NULL.
+ * d_maps: device float32 [T][n_heads][H][W] (n_heads = sml_num_heads): channel 0 = p =
+ * sigmoid(logit), channels 1..4 = dx, dy, zhat, Nhat (raw head outputs), channels 5..8 (9-head
+ * nets) = softplus of the uncertainty heads sx, sy, sz, sN.  d_logits: device float32
+ * [T][H][W] or NULL.
  * These are exactly the maps that sml_localize decodes.
  */
 int sml_forward_maps(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam,
                      float* d_maps, float* d_logits, void* stream);
 
 /*
- * sml_decode_maps -- decode caller-supplied maps [T][5][H][W] (device float32, layout of
- * sml_forward_maps) into records, stream ordered; the decode half of sml_localize.
+ * sml_decode_maps -- decode caller-supplied maps [T][n_heads][H][W] (device float32, layout
+ * of sml_forward_maps) into records, stream ordered; the decode half of sml_localize.
  * z_scale and ph_scale come from the context's net spec.  d_out / d_n_out as in
  * sml_localize_async.
  */

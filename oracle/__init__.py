@@ -37,10 +37,12 @@ _SRC = os.path.join(_HERE, "sml_oracle.c")
 _lock = threading.Lock()
 _lib = None
 
-NH = 5
+NH = 5  # position heads: logit p, dx, dy, zhat, Nhat
+NH_SIGMA = 9  # with the uncertainty heads sx, sy, sz, sN (Sec. 3.2)
 RECORD_DTYPE = np.dtype(
     [("frame", "<i4"), ("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("photons", "<f4"), ("p", "<f4")]
 )
+SIGMA_DTYPE = np.dtype([("sigma_x", "<f4"), ("sigma_y", "<f4"), ("sigma_z", "<f4"), ("sigma_photons", "<f4")])
 
 
 def build(force: bool = False) -> str:
@@ -69,6 +71,12 @@ def _load():
             lib.orc_forward_x.restype = None
             lib.orc_forward_xq.argtypes = [P, I, I, I, I, I, I, P, P, P, P, D, P, P, P, P, I, P]
             lib.orc_forward_xq.restype = None
+            lib.orc_forward_xqh.argtypes = [P, I, I, I, I, I, I, P, P, P, P, D, I, P, P, P, P, I, P]
+            lib.orc_forward_xqh.restype = None
+            lib.orc_decode_h.argtypes = [P, I, I, I, I, F, F, F, P, P, ctypes.c_long]
+            lib.orc_decode_h.restype = ctypes.c_long
+            lib.orc_softplus.argtypes = [P, ctypes.c_size_t, P]
+            lib.orc_softplus.restype = None
             lib.orc_conv.argtypes = [P, I, I, I, P, P, I, I, P]
             lib.orc_conv.restype = None
             lib.orc_round_array.argtypes = [P, ctypes.c_size_t, I]
@@ -110,6 +118,10 @@ class Net:
         self.in_scale = float(s.get("in_scale", 1e-3))
         self.z_scale = float(s.get("z_scale", 1000.0))
         self.ph_scale = float(s.get("ph_scale", 10000.0))
+        # heads: the 5 position heads, or those and the 4 uncertainty heads (Sec. 3.2)
+        self.nh = len(s.get("heads", ["p", "dx", "dy", "z", "N"]))
+        if self.nh not in (NH, NH_SIGMA):
+            raise ValueError("heads must list 5 or 9 outputs")
         C = self.C
         dcd = s.get("dcd")
         if dcd:
@@ -131,7 +143,7 @@ class Net:
         if hdr[0] != b"SMLW0001":
             raise ValueError("weight blob: bad magic")
         _, ver, L, C_, in_ch, nh, has_bn, growth, *dil = hdr
-        if (ver, L, C_, in_ch, nh, list(dil[:L])) != (version, self.L, C, self.in_ch, NH, self.dil) or (
+        if (ver, L, C_, in_ch, nh, list(dil[:L])) != (version, self.L, C, self.in_ch, self.nh, self.dil) or (
                 version == 2 and growth != self.growth):
             raise ValueError("weight blob does not match net spec")
         if version == 2 and has_bn:
@@ -156,8 +168,8 @@ class Net:
         self.conv_w = np.ascontiguousarray(np.concatenate(ws))
         self.conv_b = np.ascontiguousarray(np.concatenate(bs))
         self.bn = np.ascontiguousarray(np.concatenate(bns)) if has_bn else None
-        self.head_w = np.ascontiguousarray(take(NH * C))
-        self.head_b = np.ascontiguousarray(take(NH))
+        self.head_w = np.ascontiguousarray(take(self.nh * C))
+        self.head_b = np.ascontiguousarray(take(self.nh))
         if off != len(blob):
             raise ValueError("weight blob: trailing bytes")
 
@@ -251,7 +263,7 @@ def act_scales(net: Net, frames, gain=1.0, offset=100.0, gain_map=None, offset_m
 
 
 def forward_x(net: Net, x0, acts=False, quant=None, scales=None):
-    """Raw heads [T,5,H,W] (float64) of the dilated stack on inputs x0 [T,in_ch,H,W]
+    """Raw heads [T,nh,H,W] (float64) of the dilated stack on inputs x0 [T,in_ch,H,W]
     (Sec. 3.2.1 dilated convolution, zero padding at every layer; Sec. 3.2 heads).
     quant "bf16" / "fp8" rounds the input activations of layers 1..L-1 to that format
     (fp8: of a / scales[l]) before the layer, as the tensor-core path stores them; pass a
@@ -264,13 +276,13 @@ def forward_x(net: Net, x0, acts=False, quant=None, scales=None):
         x0 = x0[:, None]
     T, cin, H, W = x0.shape
     assert cin == net.in_ch
-    heads = np.empty((T, NH, H, W), dtype=np.float64)
+    heads = np.empty((T, net.nh, H, W), dtype=np.float64)
     a = np.empty((T, net.L, net.C, H, W), dtype=np.float64) if acts else None
     dil = np.asarray(net.dil, dtype=np.int32)
     sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float64)
-    lib.orc_forward_xq(_ptr(x0), T, H, W, net.L, net.C, net.in_ch, _ptr(dil), _ptr(net.conv_w),
-                       _ptr(net.conv_b), _ptr(net.bn), net.bn_eps, _ptr(net.head_w), _ptr(net.head_b),
-                       _ptr(heads), _ptr(a), QUANT[quant], _ptr(sc))
+    lib.orc_forward_xqh(_ptr(x0), T, H, W, net.L, net.C, net.in_ch, _ptr(dil), _ptr(net.conv_w),
+                        _ptr(net.conv_b), _ptr(net.bn), net.bn_eps, net.nh, _ptr(net.head_w), _ptr(net.head_b),
+                        _ptr(heads), _ptr(a), QUANT[quant], _ptr(sc))
     return (heads, a) if acts else heads
 
 
@@ -279,7 +291,7 @@ def _forward_dense(net: Net, x0, acts=False, quant=None):
     C oracle's conv (float64) on a channel range of a buffer that concatenates the block input
     and the block's outputs so far.  quant "bf16" rounds every layer's stored output to bf16
     (what the tensor-core path stores; the stem's input frames stay float).  Returns raw heads
-    [T,5,H,W] (and, with acts, the last layer's activations)."""
+    [T,nh,H,W] (and, with acts, the last layer's activations)."""
     lib = _load()
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     if x0.ndim == 3:
@@ -291,7 +303,7 @@ def _forward_dense(net: Net, x0, acts=False, quant=None):
     rnd = (lambda a: round_to(a, "bf16")) if quant == "bf16" else (lambda a: a)
     C, g = net.C, net.growth
     widest = max(cin for cin, _, _, _ in net.layers)
-    heads = np.empty((T, NH, H, W), dtype=np.float64)
+    heads = np.empty((T, net.nh, H, W), dtype=np.float64)
     last = np.empty((T, C, H, W), dtype=np.float64) if acts else None
     for t in range(T):
         buf = np.zeros((widest, H, W), dtype=np.float64)  # the current block's concatenation
@@ -313,7 +325,7 @@ def _forward_dense(net: Net, x0, acts=False, quant=None):
         a = buf[:C]
         if acts:
             last[t] = a
-        heads[t] = net.head_b[:, None, None] + np.einsum("kc,chw->khw", net.head_w.reshape(NH, C), a)
+        heads[t] = net.head_b[:, None, None] + np.einsum("kc,chw->khw", net.head_w.reshape(net.nh, C), a)
     return (heads, last) if acts else heads
 
 
@@ -329,23 +341,39 @@ def sigmoid(h):
     return 1.0 / (1.0 + np.exp(-np.asarray(h, dtype=np.float64)))
 
 
+def softplus(h):
+    """Uncertainty-head activation softplus(h) = log(1 + exp(h)) in float64 (the C oracle's
+    overflow-free form of that definition)."""
+    lib = _load()
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    out = np.empty_like(h)
+    lib.orc_softplus(_ptr(h), h.size, _ptr(out))
+    return out
+
+
 def maps_f32(heads):
-    """Decode input [T,5,H,W] float32: channel 0 = sigmoid(logit), channels 1-4 unchanged."""
+    """Decode input [T,nh,H,W] float32: channel 0 = sigmoid(logit), channels 1-4 unchanged,
+    channels 5-8 (uncertainty heads, nh = 9) = softplus of the raw heads."""
     m = np.array(heads, dtype=np.float64, copy=True)
     m[:, 0] = sigmoid(m[:, 0])
+    if m.shape[1] > NH:
+        m[:, NH:] = softplus(m[:, NH:])
     return m.astype(np.float32)
 
 
-def decode(maps, p_min, z_scale, ph_scale, cap=None):
-    """Float32 decode (Sec. 2.2 post-processing): records ordered by (frame, row, col)."""
+def decode(maps, p_min, z_scale, ph_scale, cap=None, with_sigma=False):
+    """Float32 decode (Sec. 2.2 post-processing): records ordered by (frame, row, col).
+    maps [T,nh,H,W] with nh 5 or 9; with_sigma (nh = 9) also returns the uncertainties of
+    each record (sigma_x, sigma_y px, sigma_z = z_scale*sz nm, sigma_photons = ph_scale*sN)."""
     lib = _load()
     m = np.ascontiguousarray(maps, dtype=np.float32)
     T, nh, H, W = m.shape
-    assert nh == NH
-    n = lib.orc_decode(_ptr(m), T, H, W, p_min, z_scale, ph_scale, None, 0)
+    assert nh in (NH, NH_SIGMA) and (nh == NH_SIGMA or not with_sigma)
+    n = lib.orc_decode_h(_ptr(m), T, nh, H, W, p_min, z_scale, ph_scale, None, None, 0)
     out = np.zeros(n if cap is None else min(n, cap), dtype=RECORD_DTYPE)
-    lib.orc_decode(_ptr(m), T, H, W, p_min, z_scale, ph_scale, _ptr(out), out.size)
-    return out
+    sig = np.zeros(out.size, dtype=SIGMA_DTYPE) if with_sigma else None
+    lib.orc_decode_h(_ptr(m), T, nh, H, W, p_min, z_scale, ph_scale, _ptr(out), _ptr(sig), out.size)
+    return (out, sig) if with_sigma else out
 
 
 def localize(net: Net, frames, p_min, gain=1.0, offset=100.0, gain_map=None, offset_map=None):
@@ -356,7 +384,7 @@ def localize(net: Net, frames, p_min, gain=1.0, offset=100.0, gain_map=None, off
 
 def forward_window(net: Net, frames, i0, i1, j0, j1, gain=1.0, offset=100.0, gain_map=None,
                    offset_map=None, quant=None, scales=None):
-    """Exact heads [T,5,i1-i0,j1-j0] of the block [i0,i1) x [j0,j1) of full frames.
+    """Exact heads [T,nh,i1-i0,j1-j0] of the block [i0,i1) x [j0,j1) of full frames.
 
     The crop extends the block by the receptive radius R = sum of dilations (clipped at the
     frame border).  Every output inside the block depends only on inputs within R of it,

@@ -8,8 +8,8 @@
  * It is the plain definition of what the path computes, written slowly and directly:
  *   - forward of the plain dilated 3x3 stack (dilated convolution, Sec. 3.2.1) with
  *     "same" zero padding at every layer, optional BatchNorm applied unfolded, ReLU,
- *     then 1x1 heads (per-pixel probability and offsets, DECODE-style outputs, Sec. 3.2),
- *     all in float64;
+ *     then 1x1 heads (per-pixel probability and offsets, DECODE-style outputs, Sec. 3.2;
+ *     optionally the four uncertainty heads, activated by softplus), all in float64;
  *   - the decode of per-pixel maps into a localization list (post-processing of
  *     Sec. 2.2 / Sec. 4.2.1), in float32 with every operation rounded once
  *     (compiled with -ffp-contract=off);
@@ -30,6 +30,10 @@ typedef struct {
   int32_t frame;
   float x, y, z, photons, p;
 } orc_record; /* 24 bytes */
+
+typedef struct {
+  float sx, sy, sz, sN; /* uncertainties of x, y (px), z (nm), photons */
+} orc_sigma;
 
 /* ------------------------------------------------------------------ rounding to narrow formats */
 
@@ -154,14 +158,15 @@ void orc_conv(const double* in, int cin, int H, int W, const double* w, const do
 /*
  * Forward of the stack on network inputs x0 [T, in_ch, H, W] (float64).
  *   conv_w: concatenated per-layer [Cout][Cin][3][3]; conv_b: [L][C];
- *   bn: NULL or [L][4][C]; head_w [5][C]; head_b [5].
- *   heads out: [T,5,H,W] raw head values (logit of p, dx, dy, z/z_scale, N/ph_scale).
+ *   bn: NULL or [L][4][C]; head_w [nh][C]; head_b [nh].
+ *   heads out: [T,nh,H,W] raw head values (logit of p, dx, dy, z/z_scale, N/ph_scale, and with
+ *   nh = 9 the four uncertainty heads).
  *   acts (optional): [T][L][C][H][W] post-ReLU activations of every layer.
  */
-void orc_forward_xq(const double* x0, int T, int H, int W, int L, int C, int in_ch, const int* dil,
-                    const double* conv_w, const double* conv_b, const double* bn, double bn_eps,
-                    const double* head_w, const double* head_b, double* heads, double* acts, int quant,
-                    const double* act_scales) {
+void orc_forward_xqh(const double* x0, int T, int H, int W, int L, int C, int in_ch, const int* dil,
+                     const double* conv_w, const double* conv_b, const double* bn, double bn_eps, int nh,
+                     const double* head_w, const double* head_b, double* heads, double* acts, int quant,
+                     const double* act_scales) {
   size_t plane = (size_t)H * W;
   double* bufA = (double*)malloc(sizeof(double) * C * plane);
   double* bufB = (double*)malloc(sizeof(double) * C * plane);
@@ -180,15 +185,23 @@ void orc_forward_xq(const double* x0, int T, int H, int W, int L, int C, int in_
       cur = (cur == bufA) ? bufB : bufA;
     }
     /* 1x1 heads: h[k] = head_b[k] + sum_c head_w[k,c] * a_L[c] */
-    for (int k = 0; k < NH; ++k)
+    for (int k = 0; k < nh; ++k)
       for (size_t px = 0; px < plane; ++px) {
         double s = head_b[k];
         for (int c = 0; c < C; ++c) s += head_w[(size_t)k * C + c] * in[(size_t)c * plane + px];
-        heads[((size_t)t * NH + k) * plane + px] = s;
+        heads[((size_t)t * nh + k) * plane + px] = s;
       }
   }
   free(bufA);
   free(bufB);
+}
+
+void orc_forward_xq(const double* x0, int T, int H, int W, int L, int C, int in_ch, const int* dil,
+                    const double* conv_w, const double* conv_b, const double* bn, double bn_eps,
+                    const double* head_w, const double* head_b, double* heads, double* acts, int quant,
+                    const double* act_scales) {
+  orc_forward_xqh(x0, T, H, W, L, C, in_ch, dil, conv_w, conv_b, bn, bn_eps, NH, head_w, head_b, heads, acts, quant,
+                  act_scales);
 }
 
 void orc_forward_x(const double* x0, int T, int H, int W, int L, int C, int in_ch, const int* dil,
@@ -216,21 +229,23 @@ void orc_sigmoid(const double* h, size_t n, double* p) {
 /* ------------------------------------------------------------------ decode (float32) */
 
 /*
- * Decode per-pixel maps [T,5,H,W] float32 (channel 0 = p, then dx, dy, zhat, Nhat) into
- * records ordered by (frame, row, column).  Pixel (t,i,j) is kept iff
+ * Decode per-pixel maps [T,nh,H,W] float32 (channel 0 = p, then dx, dy, zhat, Nhat; with
+ * nh = 9 then the uncertainty maps sx, sy, sz, sN) into records ordered by (frame, row,
+ * column).  Pixel (t,i,j) is kept iff
  *   p > p_min, and
  *   p > p[n] for each in-frame 8-neighbour n earlier in raster order, and
  *   p >= p[n] for each in-frame 8-neighbour n later in raster order.
  * Readout: x = j + dx, y = i + dy (pixels, centre of pixel = its index), z = z_scale*zhat,
- * photons = ph_scale*Nhat, p.  Each value is one float32 operation.
- * Returns the number of detections; writes at most cap records.
+ * photons = ph_scale*Nhat, p.  With sig (nh = 9): sigma_x = sx, sigma_y = sy,
+ * sigma_z = z_scale*sz, sigma_photons = ph_scale*sN at the same pixel.  Each value is one
+ * float32 operation.  Returns the number of detections; writes at most cap records.
  */
-long orc_decode(const float* maps, int T, int H, int W, float p_min, float z_scale, float ph_scale,
-                orc_record* out, long cap) {
+long orc_decode_h(const float* maps, int T, int nh, int H, int W, float p_min, float z_scale, float ph_scale,
+                  orc_record* out, orc_sigma* sig, long cap) {
   long n = 0;
   size_t plane = (size_t)H * W;
   for (int t = 0; t < T; ++t) {
-    const float* p = maps + (size_t)t * NH * plane;
+    const float* p = maps + (size_t)t * nh * plane;
     for (int i = 0; i < H; ++i)
       for (int j = 0; j < W; ++j) {
         float v = p[(size_t)i * W + j];
@@ -253,17 +268,39 @@ long orc_decode(const float* maps, int T, int H, int W, float p_min, float z_sca
           size_t px = (size_t)i * W + j;
           orc_record r;
           r.frame = t;
-          r.x = (float)j + maps[((size_t)t * NH + 1) * plane + px];
-          r.y = (float)i + maps[((size_t)t * NH + 2) * plane + px];
-          r.z = z_scale * maps[((size_t)t * NH + 3) * plane + px];
-          r.photons = ph_scale * maps[((size_t)t * NH + 4) * plane + px];
+          r.x = (float)j + maps[((size_t)t * nh + 1) * plane + px];
+          r.y = (float)i + maps[((size_t)t * nh + 2) * plane + px];
+          r.z = z_scale * maps[((size_t)t * nh + 3) * plane + px];
+          r.photons = ph_scale * maps[((size_t)t * nh + 4) * plane + px];
           r.p = v;
           out[n] = r;
+          if (sig && nh >= 9) {
+            orc_sigma u;
+            u.sx = maps[((size_t)t * nh + 5) * plane + px];
+            u.sy = maps[((size_t)t * nh + 6) * plane + px];
+            u.sz = z_scale * maps[((size_t)t * nh + 7) * plane + px];
+            u.sN = ph_scale * maps[((size_t)t * nh + 8) * plane + px];
+            sig[n] = u;
+          }
         }
         ++n;
       }
   }
   return n;
+}
+
+long orc_decode(const float* maps, int T, int H, int W, float p_min, float z_scale, float ph_scale,
+                orc_record* out, long cap) {
+  return orc_decode_h(maps, T, NH, H, W, p_min, z_scale, ph_scale, out, NULL, cap);
+}
+
+/* Uncertainty-head activation: softplus(h) = log(1 + exp(h)), float64, in the form
+ * max(h, 0) + log1p(exp(-|h|)) (the same value, without overflow of exp for large h). */
+void orc_softplus(const double* h, size_t n, double* out) {
+  for (size_t k = 0; k < n; ++k) {
+    double a = fabs(h[k]);
+    out[k] = (h[k] > 0 ? h[k] : 0.0) + log1p(exp(-a));
+  }
 }
 
 /* ------------------------------------------------------------------ training loss + gradient */

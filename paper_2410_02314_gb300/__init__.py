@@ -29,6 +29,8 @@ SML_ERR_UNSUPPORTED = -7
 RECORD_DTYPE = np.dtype(
     [("frame", "<i4"), ("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("photons", "<f4"), ("p", "<f4")]
 )
+# sml_sigma: uncertainties of one record (nets with 9 heads)
+SIGMA_DTYPE = np.dtype([("sigma_x", "<f4"), ("sigma_y", "<f4"), ("sigma_z", "<f4"), ("sigma_photons", "<f4")])
 
 # every symbol the headers in include/ declare
 EXPORTS = (
@@ -36,6 +38,8 @@ EXPORTS = (
     "sml_destroy",
     "sml_last_error",
     "sml_localize",
+    "sml_num_heads",
+    "sml_localize_sigma",
     "sml_localize_async",
     "sml_forward_maps",
     "sml_decode_maps",
@@ -107,6 +111,11 @@ def lib():
         L.sml_localize.argtypes = [P, P, I, I, I, ctypes.POINTER(_Camera), ctypes.POINTER(_Thresholds), P, S,
                                    ctypes.POINTER(S)]
         L.sml_localize.restype = I
+        L.sml_num_heads.argtypes = [P]
+        L.sml_num_heads.restype = I
+        L.sml_localize_sigma.argtypes = [P, P, I, I, I, ctypes.POINTER(_Camera), ctypes.POINTER(_Thresholds), P, P, S,
+                                         ctypes.POINTER(S)]
+        L.sml_localize_sigma.restype = I
         L.sml_localize_async.argtypes = [P, P, I, I, I, ctypes.POINTER(_Camera), ctypes.POINTER(_Thresholds), P, S,
                                          P, P]
         L.sml_localize_async.restype = I
@@ -222,6 +231,30 @@ def sml_localize(ctx, frames, p_min, gain=1.0, offset=100.0, gain_map=None, offs
     if hasattr(out_arr, "data_ptr"):
         return out_arr[: n.value * RECORD_DTYPE.itemsize]
     return out_arr[: n.value]
+
+
+def sml_num_heads(ctx) -> int:
+    return lib().sml_num_heads(ctx)
+
+
+def sml_localize_sigma(ctx, frames, p_min, gain=1.0, offset=100.0, gain_map=None, offset_map=None, capacity=None):
+    """sml_localize plus the uncertainties of each record (9-head nets): returns (records,
+    sigmas) as numpy arrays of RECORD_DTYPE and SIGMA_DTYPE, sigmas[k] belonging to records[k]."""
+    T, H, W = (int(s) for s in frames.shape)
+    if isinstance(frames, np.ndarray):
+        frames = np.ascontiguousarray(frames, dtype=np.uint16)
+    cap = int(capacity if capacity is not None else max(16, T * H * W // 9 + 16))
+    out = np.empty(cap, dtype=RECORD_DTYPE)
+    sig = np.empty(cap, dtype=SIGMA_DTYPE)
+    n = ctypes.c_size_t(0)
+    cam = _camera(gain, offset, gain_map, offset_map)
+    thr = _Thresholds(float(p_min))
+    code = lib().sml_localize_sigma(ctx, _ptr(frames), T, H, W, ctypes.byref(cam), ctypes.byref(thr), out.ctypes.data,
+                                    sig.ctypes.data, cap, ctypes.byref(n))
+    if code == SML_ERR_CAPACITY:
+        raise SmlError(code, sml_last_error(ctx), needed=int(n.value))
+    _check(ctx, code)
+    return out[: n.value], sig[: n.value]
 
 
 def sml_localize_file(ctx, path, T, H, W, p_min, batch=64, gain=1.0, offset=100.0, gain_map=None, offset_map=None,
@@ -405,6 +438,13 @@ class Localizer:
 
     def localize(self, frames, p_min, **kw):
         return sml_localize(self.ctx, frames, p_min, **kw)
+
+    def localize_sigma(self, frames, p_min, **kw):
+        return sml_localize_sigma(self.ctx, frames, p_min, **kw)
+
+    @property
+    def num_heads(self):
+        return sml_num_heads(self.ctx)
 
     def localize_file(self, path, T, H, W, p_min, **kw):
         return sml_localize_file(self.ctx, path, T, H, W, p_min, **kw)

@@ -187,6 +187,7 @@ struct sml_ctx {
   int in_ch = 1, C = 0, L = 0;
   LayerDesc lay[kMaxLayers];
   int growth = 0;  // dense blocks: channels each dense layer adds (0: plain stack)
+  int nh = kHeads; // output heads: 5, or 9 with the uncertainty heads
   int ct = 0;      // channels per pixel of the activation buffers (C, or C + the longest block's k g)
   int prec = kFP32;
   float in_scale = 1e-3f, z_scale = 1000.f, ph_scale = 10000.f;
@@ -214,6 +215,8 @@ struct sml_ctx {
   int* d_err = nullptr;
   sml_record* d_rec = nullptr;
   size_t d_rec_cap = 0;
+  sml_sigma* d_sig = nullptr;  // staging of uncertainty records for host outputs
+  size_t d_sig_cap = 0;
   std::vector<void*> owned;
   std::string err;
   int launches = 0;
@@ -352,7 +355,7 @@ int get_plan(sml_ctx* ctx, int H, int W) {
   size_t ab = npx * ctx->ct * act_elem_bytes(ctx->prec);
   int r;
   if ((r = dev_alloc(ctx, &p.act[0], ab)) || (r = dev_alloc(ctx, &p.act[1], ab)) ||
-      (r = dev_alloc(ctx, &p.maps, npx * kHeads * sizeof(float))) ||
+      (r = dev_alloc(ctx, &p.maps, npx * ctx->nh * sizeof(float))) ||
       (r = dev_alloc(ctx, &p.block_counts, decode_blocks(npx) * sizeof(unsigned))) ||
       (r = dev_alloc(ctx, &p.block_offsets, decode_blocks(npx) * sizeof(unsigned long long))) ||
       (r = dev_alloc(ctx, &p.frames, (size_t)(Tc + 2) * hw * sizeof(uint16_t))) ||  // + context frames
@@ -426,7 +429,7 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, FrameRange fr,
       fa.out_ct = ctx->ct;
       fa.out_off = y.out_off;
       if (last)
-        SML_CUDA(launch_dconv_f32_heads(fa, ctx->head_w, ctx->head_b, maps, logits, s), "fp32 conv+heads");
+        SML_CUDA(launch_dconv_f32_heads(fa, ctx->head_w, ctx->head_b, ctx->nh, maps, logits, s), "fp32 conv+heads");
       else
         SML_CUDA(launch_dconv_f32(fa, s), "fp32 conv");
     } else {
@@ -442,6 +445,7 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, FrameRange fr,
       a.out_gt = ctx->ct / 16;
       a.head_w = ctx->h_head_w.data();
       a.head_b = ctx->h_head_b.data();
+      a.nh = ctx->nh;
       a.maps = maps;
       a.logits = logits;
       a.T = tc;
@@ -502,7 +506,8 @@ int make_cam(sml_ctx* ctx, const sml_camera* cam, CamArgs* out) {
 
 // Whole call on device-resident frames: chunks of whole frames, one running record count.
 int localize_device(sml_ctx* ctx, const uint16_t* d_frames, bool frames_on_host, int T, int H, int W, const CamArgs& cam,
-                    float p_min, sml_record* d_out, size_t capacity, unsigned long long* d_n, cudaStream_t s) {
+                    float p_min, sml_record* d_out, size_t capacity, unsigned long long* d_n, cudaStream_t s,
+                    sml_sigma* d_sigma = nullptr) {
   int r = get_plan(ctx, H, W);
   if (r) return r;
   Plan& p = *ctx->plan;
@@ -530,6 +535,8 @@ int localize_device(sml_ctx* ctx, const uint16_t* d_frames, bool frames_on_host,
     da.z_scale = ctx->z_scale;
     da.ph_scale = ctx->ph_scale;
     da.out = d_out;
+    da.out_sigma = d_sigma;
+    da.nh = ctx->nh;
     da.capacity = capacity;
     da.total = d_n;
     da.block_counts = p.block_counts;
@@ -666,8 +673,17 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
                   y.cin, y.cout, y.d);
   }
   auto hd = root.obj.find("heads");
-  if (hd != root.obj.end() && (hd->second.kind != JVal::kArr || hd->second.arr.size() != kHeads))
-    return fail(nullptr, SML_ERR_BAD_SPEC, "heads must list 5 outputs");
+  if (hd != root.obj.end()) {
+    // 5 position heads, or those and the 4 uncertainty heads, in this order
+    static const char* kNames[kMaxHeads] = {"p", "dx", "dy", "z", "N", "sx", "sy", "sz", "sN"};
+    const JVal& h = hd->second;
+    if (h.kind != JVal::kArr || (h.arr.size() != kHeads && h.arr.size() != kMaxHeads))
+      return fail(nullptr, SML_ERR_BAD_SPEC, "heads must list 5 outputs (p, dx, dy, z, N) or 9 (and sx, sy, sz, sN)");
+    for (size_t k = 0; k < h.arr.size(); ++k)
+      if (h.arr[k].kind != JVal::kStr || h.arr[k].str != kNames[k])
+        return fail(nullptr, SML_ERR_BAD_SPEC, "head %d must be \"%s\"", (int)k, kNames[k]);
+    ctx->nh = (int)h.arr.size();
+  }
   return SML_OK;
 }
 
@@ -687,7 +703,7 @@ int check_blob(const sml_ctx* ctx, const void* blob, size_t bytes, size_t* hdr_o
   memcpy(h, b + 8, sizeof(h));
   memcpy(dil, b + 8 + sizeof(h), (size_t)ndil * 4);
   const int L = (int)h[1], C = (int)h[2], in_ch = (int)h[3], nh = (int)h[4], has_bn = (int)h[5];
-  if (h[0] != (v2 ? 2u : 1u) || L != ctx->L || C != ctx->C || in_ch != ctx->in_ch || nh != kHeads ||
+  if (h[0] != (v2 ? 2u : 1u) || L != ctx->L || C != ctx->C || in_ch != ctx->in_ch || nh != ctx->nh ||
       (v2 && ((int)h[6] != ctx->growth || has_bn)))
     return fail(nullptr, SML_ERR_BAD_WEIGHTS, "weight blob header does not match the net spec");
   for (int l = 0; l < L; ++l)
@@ -697,7 +713,7 @@ int check_blob(const sml_ctx* ctx, const void* blob, size_t bytes, size_t* hdr_o
     const LayerDesc& y = ctx->lay[l];
     need += 4 * ((size_t)y.cout * y.cin * 9 + y.cout + (has_bn ? 4 * (size_t)y.cout + 1 : 0));
   }
-  need += 4 * ((size_t)kHeads * C + kHeads);
+  need += 4 * ((size_t)ctx->nh * C + ctx->nh);
   if (bytes != need) return fail(nullptr, SML_ERR_BAD_WEIGHTS, "weight blob has %zu bytes, expected %zu", bytes, need);
   if (hdr_out) *hdr_out = hdr_bytes;
   if (has_bn_out) *has_bn_out = has_bn;
@@ -766,10 +782,10 @@ int load_weights(sml_ctx* ctx, const void* blob, size_t bytes) {
       if (ctx->prec == kFP8) ctx->h_deq[l] = deq;
     }
   }
-  std::vector<float> hw = take((size_t)kHeads * C);
+  std::vector<float> hw = take((size_t)ctx->nh * C);
   if ((r = upload(ctx, &ctx->head_w, hw.data(), hw.size() * 4))) return r;
   ctx->h_head_w = hw;
-  std::vector<float> hb = take(kHeads);
+  std::vector<float> hb = take(ctx->nh);
   if ((r = upload(ctx, &ctx->head_b, hb.data(), hb.size() * 4))) return r;
   ctx->h_head_b = hb;
   return SML_OK;
@@ -825,6 +841,7 @@ void sml_destroy(sml_ctx* ctx) {
   cudaFree(ctx->d_total);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_rec);
+  cudaFree(ctx->d_sig);
   for (auto& e : ctx->prof_events) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -837,9 +854,26 @@ const char* sml_last_error(const sml_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 int sml_last_launch_count(const sml_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
-int sml_localize(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, const sml_camera* cam,
-                 const sml_thresholds* thr, sml_record* out, size_t capacity, size_t* n_out) {
-  if (!ctx) return SML_ERR_BAD_ARG;
+}  // extern "C"
+
+namespace {
+
+// Device staging buffer of at least n elements (grown on demand, kept by the context).
+template <typename T>
+int staging(sml_ctx* ctx, T** buf, size_t* cap, size_t n) {
+  if (*buf && *cap >= n) return SML_OK;
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  int r = dev_alloc(ctx, buf, std::max<size_t>(n, 1) * sizeof(T));
+  if (r) return r;
+  *cap = std::max<size_t>(n, 1);
+  return SML_OK;
+}
+
+// sml_localize and sml_localize_sigma: out_sigma NULL for records only.
+int localize_sync(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, const sml_camera* cam,
+                  const sml_thresholds* thr, sml_record* out, sml_sigma* out_sigma, size_t capacity, size_t* n_out) {
   ctx->launches = 0;
   int r;
   if (!n_out || (T > 0 && !frames) || (capacity > 0 && !out)) return fail(ctx, SML_ERR_BAD_ARG, "NULL argument");
@@ -864,28 +898,52 @@ int sml_localize(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, cons
   const bool out_dev = capacity > 0 && is_device_ptr(out);
   sml_record* d_out = out;
   if (!out_dev) {
-    if (ctx->d_rec_cap < capacity || !ctx->d_rec) {
-      cudaFree(ctx->d_rec);
-      ctx->d_rec = nullptr;
-      ctx->d_rec_cap = 0;
-      if ((r = dev_alloc(ctx, &ctx->d_rec, std::max<size_t>(capacity, 1) * sizeof(sml_record)))) return r;
-      ctx->d_rec_cap = std::max<size_t>(capacity, 1);
-    }
+    if ((r = staging(ctx, &ctx->d_rec, &ctx->d_rec_cap, capacity))) return r;
     d_out = ctx->d_rec;
   }
+  const bool sig_dev = out_sigma && capacity > 0 && is_device_ptr(out_sigma);
+  sml_sigma* d_sig = out_sigma;
+  if (out_sigma && !sig_dev) {
+    if ((r = staging(ctx, &ctx->d_sig, &ctx->d_sig_cap, capacity))) return r;
+    d_sig = ctx->d_sig;
+  }
   const bool host_frames = !is_device_ptr(frames);
-  if ((r = localize_device(ctx, frames, host_frames, T, H, W, ca, thr->p_min, d_out, capacity, ctx->d_total, s))) return r;
+  if ((r = localize_device(ctx, frames, host_frames, T, H, W, ca, thr->p_min, d_out, capacity, ctx->d_total, s, d_sig)))
+    return r;
   unsigned long long total = 0;
   SML_CUDA(cudaMemcpyAsync(&total, ctx->d_total, sizeof(total), cudaMemcpyDeviceToHost, s), "D2H count");
   SML_CUDA(cudaStreamSynchronize(s), "localize");
   if ((r = check_device_error(ctx))) return r;
   *n_out = (size_t)total;
   if (total > capacity) return fail(ctx, SML_ERR_CAPACITY, "%llu detections exceed capacity %zu", total, capacity);
-  if (!out_dev && total > 0) {
+  if (!out_dev && total > 0)
     SML_CUDA(cudaMemcpyAsync(out, d_out, (size_t)total * sizeof(sml_record), cudaMemcpyDeviceToHost, s), "D2H records");
-    SML_CUDA(cudaStreamSynchronize(s), "D2H records");
-  }
+  if (out_sigma && !sig_dev && total > 0)
+    SML_CUDA(cudaMemcpyAsync(out_sigma, d_sig, (size_t)total * sizeof(sml_sigma), cudaMemcpyDeviceToHost, s),
+             "D2H uncertainties");
+  SML_CUDA(cudaStreamSynchronize(s), "D2H records");
   return SML_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sml_localize(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, const sml_camera* cam,
+                 const sml_thresholds* thr, sml_record* out, size_t capacity, size_t* n_out) {
+  if (!ctx) return SML_ERR_BAD_ARG;
+  return localize_sync(ctx, frames, T, H, W, cam, thr, out, nullptr, capacity, n_out);
+}
+
+int sml_num_heads(const sml_ctx* ctx) { return ctx ? ctx->nh : 0; }
+
+int sml_localize_sigma(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, const sml_camera* cam,
+                       const sml_thresholds* thr, sml_record* out, sml_sigma* out_sigma, size_t capacity,
+                       size_t* n_out) {
+  if (!ctx) return SML_ERR_BAD_ARG;
+  if (ctx->nh != kMaxHeads) return fail(ctx, SML_ERR_UNSUPPORTED, "the net has no uncertainty heads");
+  if (capacity > 0 && !out_sigma) return fail(ctx, SML_ERR_BAD_ARG, "NULL argument");
+  return localize_sync(ctx, frames, T, H, W, cam, thr, out, out_sigma, capacity, n_out);
 }
 
 int sml_localize_async(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam,
@@ -922,7 +980,7 @@ int sml_forward_maps(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W
   for (int t0 = 0; t0 < T; t0 += ctx->plan->Tc) {
     int tc = std::min(ctx->plan->Tc, T - t0);
     if ((r = forward_chunk(ctx, d_frames + (size_t)t0 * fpx, tc, chunk_frames(ctx, T, t0, tc), H, W, ca,
-                           d_maps + (size_t)t0 * kHeads * fpx, d_logits ? d_logits + (size_t)t0 * fpx : nullptr, s)))
+                           d_maps + (size_t)t0 * ctx->nh * fpx, d_logits ? d_logits + (size_t)t0 * fpx : nullptr, s)))
       return r;
   }
   return SML_OK;
@@ -944,7 +1002,8 @@ int sml_decode_maps(sml_ctx* ctx, const float* d_maps, int T, int H, int W, cons
   for (int t0 = 0; t0 < T; t0 += p.Tc) {
     int tc = std::min(p.Tc, T - t0);
     DecodeArgs da{};
-    da.maps = d_maps + (size_t)t0 * kHeads * fpx;
+    da.maps = d_maps + (size_t)t0 * ctx->nh * fpx;
+    da.nh = ctx->nh;
     da.T = tc;
     da.H = H;
     da.W = W;

@@ -59,7 +59,7 @@ __device__ __forceinline__ void dec_flags(const DecodeArgs& a, const PxLoc (&loc
   float v[kPxPerThread][9];
 #pragma unroll
   for (int k = 0; k < kPxPerThread; ++k) {
-    const float* p = a.maps + (size_t)loc[k].t * kHeads * plane;
+    const float* p = a.maps + (size_t)loc[k].t * a.nh * plane;
 #pragma unroll
     for (int di = -1; di <= 1; ++di)
 #pragma unroll
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode_write(DecodeArgs a) {
       const unsigned long long idx = off + before + __popc(bal[k] & lt_mask);
       if (idx < a.capacity) {
         const size_t px = (size_t)loc[k].i * a.W + loc[k].j;
-        const float* m = a.maps + (size_t)loc[k].t * kHeads * plane;
+        const float* m = a.maps + (size_t)loc[k].t * a.nh * plane;
         sml_record r;
         r.frame = a.frame0 + loc[k].t;
         r.x = __fadd_rn((float)loc[k].j, m[plane + px]);
@@ -182,6 +182,14 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode_write(DecodeArgs a) {
         r.photons = __fmul_rn(a.ph_scale, m[4 * plane + px]);
         r.p = m[px];
         a.out[idx] = r;
+        if (a.out_sigma) {  // uncertainty maps 5..8 at the same pixel
+          sml_sigma u;
+          u.sigma_x = m[5 * plane + px];
+          u.sigma_y = m[6 * plane + px];
+          u.sigma_z = __fmul_rn(a.z_scale, m[7 * plane + px]);
+          u.sigma_photons = __fmul_rn(a.ph_scale, m[8 * plane + px]);
+          a.out_sigma[idx] = u;
+        }
       }
     }
     off += total;

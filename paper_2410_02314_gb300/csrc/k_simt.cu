@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
 // Weights in shared memory as [tap][ci][co]; each float4 read is a warp-wide broadcast.
 template <int CO, bool HEADS>
 __global__ void __launch_bounds__(kSimtThreads) k_dconv_f32(const F32LayerArgs a, const float* __restrict__ hw,
-                                                            const float* __restrict__ hb, float* __restrict__ maps,
-                                                            float* __restrict__ logits) {
+                                                            const float* __restrict__ hb, int nh,
+                                                            float* __restrict__ maps, float* __restrict__ logits) {
   extern __shared__ float4 smem4[];
   float* sw = reinterpret_cast<float*>(smem4);
   const int ci_n = a.ci, H = a.H, W = a.W, d = a.d;
@@ -244,19 +244,23 @@ __global__ void __launch_bounds__(kSimtThreads) k_dconv_f32(const F32LayerArgs a
     for (int c4 = 0; c4 < CO / 4; ++c4)
       dst[c4] = make_float4(acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]);
   } else {
-    // 1x1 heads (Sec. 3.2): h_k = hb[k] + sum_c hw[k,c] a[c]; p = sigmoid(h_0)
+    // 1x1 heads (Sec. 3.2): h_k = hb[k] + sum_c hw[k,c] a[c]; p = sigmoid(h_0); the
+    // uncertainty heads (k >= 5) are softplus(h_k)
     size_t plane = (size_t)H * W;
     size_t px = (size_t)i * W + j;
 #pragma unroll
-    for (int k = 0; k < kHeads; ++k) {
+    for (int k = 0; k < kMaxHeads; ++k) {
+      if (k >= nh) break;
       float h = hb[k];
 #pragma unroll
       for (int c = 0; c < CO; ++c) h = fmaf(hw[k * CO + c], acc[c], h);
       if (k == 0) {
         if (logits) logits[(size_t)t * plane + px] = h;
         h = 1.0f / (1.0f + expf(-h));
+      } else if (k >= kHeads) {
+        h = softplus_f(h);
       }
-      maps[((size_t)t * kHeads + k) * plane + px] = h;
+      maps[((size_t)t * nh + k) * plane + px] = h;
     }
   }
 }
@@ -343,8 +347,9 @@ cudaError_t launch_amax(const void* x, size_t n, int prec, unsigned* out, cudaSt
 }
 
 template <int CO, bool HEADS>
-static cudaError_t launch_f32_impl(const F32LayerArgs& a, const float* hw, const float* hb, float* maps,
+static cudaError_t launch_f32_impl(const F32LayerArgs& a, const float* hw, const float* hb, int nh, float* maps,
                                    float* logits, cudaStream_t s) {
+  if (HEADS && nh != kHeads && nh != kMaxHeads) return cudaErrorInvalidValue;
   if (a.ci < 4 || a.ci % 4 || a.ci * CO > kF32MaxWeights || a.in_ct < a.ci || a.in_ct % 4) return cudaErrorInvalidValue;
   if (!HEADS && (a.out_off < 0 || a.out_off % 4 || a.out_off + CO > a.out_ct || a.out_ct % 4)) return cudaErrorInvalidValue;
   size_t smem = sizeof(float) * 9 * a.ci * CO;
@@ -357,28 +362,28 @@ static cudaError_t launch_f32_impl(const F32LayerArgs& a, const float* hw, const
   }
   long long npx = (long long)a.T * a.H * a.W;
   if (npx == 0) return cudaSuccess;
-  k_dconv_f32<CO, HEADS><<<grid_for(npx), kSimtThreads, smem, s>>>(a, hw, hb, maps, logits);
+  k_dconv_f32<CO, HEADS><<<grid_for(npx), kSimtThreads, smem, s>>>(a, hw, hb, nh, maps, logits);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dconv_f32(const F32LayerArgs& a, cudaStream_t s) {
   switch (a.co) {
-    case 16: return launch_f32_impl<16, false>(a, nullptr, nullptr, nullptr, nullptr, s);
-    case 32: return launch_f32_impl<32, false>(a, nullptr, nullptr, nullptr, nullptr, s);
-    case 48: return launch_f32_impl<48, false>(a, nullptr, nullptr, nullptr, nullptr, s);
-    case 64: return launch_f32_impl<64, false>(a, nullptr, nullptr, nullptr, nullptr, s);
+    case 16: return launch_f32_impl<16, false>(a, nullptr, nullptr, 0, nullptr, nullptr, s);
+    case 32: return launch_f32_impl<32, false>(a, nullptr, nullptr, 0, nullptr, nullptr, s);
+    case 48: return launch_f32_impl<48, false>(a, nullptr, nullptr, 0, nullptr, nullptr, s);
+    case 64: return launch_f32_impl<64, false>(a, nullptr, nullptr, 0, nullptr, nullptr, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_dconv_f32_heads(const F32LayerArgs& a, const float* hw, const float* hb, float* maps,
+cudaError_t launch_dconv_f32_heads(const F32LayerArgs& a, const float* hw, const float* hb, int nh, float* maps,
                                    float* logits, cudaStream_t s) {
   if (a.ci != a.co) return cudaErrorInvalidValue;
   switch (a.co) {
-    case 16: return launch_f32_impl<16, true>(a, hw, hb, maps, logits, s);
-    case 32: return launch_f32_impl<32, true>(a, hw, hb, maps, logits, s);
-    case 48: return launch_f32_impl<48, true>(a, hw, hb, maps, logits, s);
-    case 64: return launch_f32_impl<64, true>(a, hw, hb, maps, logits, s);
+    case 16: return launch_f32_impl<16, true>(a, hw, hb, nh, maps, logits, s);
+    case 32: return launch_f32_impl<32, true>(a, hw, hb, nh, maps, logits, s);
+    case 48: return launch_f32_impl<48, true>(a, hw, hb, nh, maps, logits, s);
+    case 64: return launch_f32_impl<64, true>(a, hw, hb, nh, maps, logits, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -242,8 +242,9 @@ struct TcKArgs {
   const uint8_t* bimg;
   float bias[64];
   float deq[64];
-  float head_w[kHeads * 64];  // [5][C]
-  float head_b[8];
+  float head_w[kMaxHeads * 64];  // [nh][C]
+  float head_b[12];
+  int nh;                        // heads: 5, or 9 with the uncertainty heads
   float out_inv_scale;
   uint8_t* out;
   float* maps;
@@ -586,15 +587,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         if (LAST) {
           const size_t px = (size_t)i * a.W + j;
 #pragma unroll
-          for (int h = 0; h < kHeads; ++h) {
+          for (int h = 0; h < kMaxHeads; ++h) {
+            if (h >= a.nh) break;
             float acc = a.head_b[h];
 #pragma unroll
             for (int c = 0; c < CO; ++c) acc = fmaf(a.head_w[h * CO + c], v[c], acc);
             if (h == 0) {
               if (a.logits) a.logits[(size_t)t * plane + px] = acc;
               acc = 1.0f / (1.0f + expf(-acc));
+            } else if (h >= kHeads) {
+              acc = softplus_f(acc);  // uncertainty heads
             }
-            a.maps[((size_t)t * kHeads + h) * plane + px] = acc;
+            a.maps[((size_t)t * a.nh + h) * plane + px] = acc;
           }
         } else if (PREC == kBF16) {
 #pragma unroll
@@ -741,7 +745,9 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
     a.deq[c] = la.deq ? la.deq[c] : 1.0f;
   }
   if (LAST) {
-    for (int k = 0; k < kHeads; ++k) {
+    if (la.nh != kHeads && la.nh != kMaxHeads) return cudaErrorInvalidValue;
+    a.nh = la.nh;
+    for (int k = 0; k < la.nh; ++k) {
       a.head_b[k] = la.head_b[k];
       for (int c = 0; c < CO; ++c) a.head_w[k * CO + c] = la.head_w[k * CO + c];
     }

@@ -9,7 +9,8 @@
 
 namespace sml {
 
-constexpr int kHeads = 5;
+constexpr int kHeads = 5;     // position heads: p logit, dx, dy, zhat, Nhat (the training heads)
+constexpr int kMaxHeads = 9;  // + the uncertainty heads sx, sy, sz, sN (Sec. 3.2)
 constexpr int kMaxLayers = 32;  // conv layers of a net (plain stacks: 16)
 constexpr int kTcMaxCin = 128;   // widest tensor-core conv input (8 groups of 16 channels)
 constexpr int kTileM = 128;  // pixels per MMA tile (one row segment)
@@ -23,6 +24,8 @@ struct DecodeArgs {
   int frame0;  // frame index of the chunk's first frame
   float p_min, z_scale, ph_scale;
   sml_record* out;
+  sml_sigma* out_sigma = nullptr;  // uncertainties of each record (9-head maps) or NULL
+  int nh = kHeads;                 // channels of the maps: 5, or 9 with the uncertainty maps
   unsigned long long capacity;
   unsigned long long* total;  // running count (device); updated by the scan kernel
   unsigned int* block_counts;  // [nblocks]
@@ -45,6 +48,10 @@ struct CamArgs {
 };
 
 #ifdef __CUDACC__
+// Uncertainty-head activation: softplus(h) = log(1 + exp(h)), by its defining formula below
+// h = 20 (where exp(h) is still far from overflow) and h itself above (the rest is < 2e-9 h).
+__device__ __forceinline__ float softplus_f(float h) { return h > 20.0f ? h : log1pf(expf(h)); }
+
 // Network input of pixel (i, j) of one frame: (adu - offset) / gain * in_scale, each step one
 // IEEE rounding; zero outside the frame (the first layer's "same" zero padding).
 __device__ __forceinline__ float cam_input(const uint16_t* __restrict__ f, int H, int W, int i, int j,
@@ -86,7 +93,7 @@ struct F32LayerArgs {
 };
 cudaError_t launch_dconv_f32(const F32LayerArgs& a, cudaStream_t s);
 // Last layer (ci == co == C) with the fused heads.
-cudaError_t launch_dconv_f32_heads(const F32LayerArgs& a, const float* hw, const float* hb, float* maps,
+cudaError_t launch_dconv_f32_heads(const F32LayerArgs& a, const float* hw, const float* hb, int nh, float* maps,
                                    float* logits, cudaStream_t s);
 // Largest ci * co whose FP32 weights fit in shared memory.
 constexpr int kF32MaxWeights = 227 * 1024 / (9 * 4);
@@ -101,9 +108,10 @@ struct TcLayerArgs {
   float out_inv_scale;      // FP8: 1 / scale of the output activations
   void* out;                // row-planar output activations (middle layers)
   int out_g0, out_gt;       // output: first group written, groups per pixel row of the buffer
-  const float* head_w;      // last layer: HOST [5][C]
-  const float* head_b;      // last layer: HOST [5]
-  float* maps;              // last layer: [T][5][H][W]
+  const float* head_w;      // last layer: HOST [nh][C]
+  const float* head_b;      // last layer: HOST [nh]
+  int nh;                   // last layer: heads (5, or 9 with the uncertainty heads)
+  float* maps;              // last layer: [T][nh][H][W]
   float* logits;            // last layer: optional [T][H][W]
   int T, H, W, d, prec;
   int ci, co;               // input channels read (groups 0..ci/16-1 of the input buffer), outputs

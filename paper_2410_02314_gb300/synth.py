@@ -24,7 +24,9 @@ import numpy as np
 
 MAGIC = b"SMLW0001"
 MAX_LAYERS = 16
-N_HEADS = 5
+N_HEADS = 5  # position heads: p logit, dx, dy, zhat, Nhat
+# head names of the net spec: the position heads, then the uncertainty heads (Sec. 3.2)
+HEAD_NAMES = ("p", "dx", "dy", "z", "N", "sx", "sy", "sz", "sN")
 HEADER_FMT = "<8s7I16i"  # magic, version, L, C, in_ch, n_heads, has_bn, reserved, dil[16]
 HEADER_BYTES = struct.calcsize(HEADER_FMT)
 # version 2 (nets with dense connection dilated blocks): reserved = growth, dil[32] per layer
@@ -80,6 +82,8 @@ class NetSpec:
     # output, concatenated; output: g channels) and a transition conv (d = 1, C + k*g -> C);
     # then the plain C -> C layers dilations[1:], the last of which feeds the heads.
     dcd: dict | None = None
+    # 5 (position heads) or 9 (and the uncertainty heads sx, sy, sz, sN)
+    n_heads: int = N_HEADS
 
     def layers(self) -> list:
         """(cin, cout, dilation) of every conv layer in execution order."""
@@ -100,7 +104,7 @@ class NetSpec:
             "in_ch": self.in_ch,
             "channels": self.channels,
             "dilations": list(self.dilations),
-            "heads": ["p", "dx", "dy", "z", "N"],
+            "heads": list(HEAD_NAMES[: self.n_heads]),
             "precision": self.precision,
             "in_scale": self.in_scale,
             "z_scale": self.z_scale,
@@ -176,8 +180,9 @@ def init_weights(spec: NetSpec, seed: int, bn: bool = False) -> Weights:
             var = s.uniform(C, 0.5, 1.5)
             bns.append(np.stack([gamma, beta, mean, var]))
     bound = math.sqrt(6.0 / C)
-    hw = s.uniform(N_HEADS * C, -bound, bound).reshape(N_HEADS, C)
-    hb = s.uniform(N_HEADS, -1.0 / math.sqrt(C), 1.0 / math.sqrt(C))
+    nh = spec.n_heads
+    hw = s.uniform(nh * C, -bound, bound).reshape(nh, C)
+    hb = s.uniform(nh, -1.0 / math.sqrt(C), 1.0 / math.sqrt(C))
     return Weights(ws, bs, bns if bn else None, 1e-5, hw, hb)
 
 
@@ -187,12 +192,13 @@ def pack_blob(spec: NetSpec, w: Weights) -> bytes:
     layer's dilation in execution order)."""
     L, C = spec.L, spec.channels
     has_bn = 1 if w.bn is not None else 0
+    nh = int(np.asarray(w.head_b).size)
     if spec.dcd:
         dil = [d for _, _, d in spec.layers()] + [0] * (MAX_LAYERS_V2 - L)
-        parts = [struct.pack(HEADER_FMT_V2, MAGIC, 2, L, C, spec.in_ch, N_HEADS, has_bn, int(spec.dcd["growth"]), *dil)]
+        parts = [struct.pack(HEADER_FMT_V2, MAGIC, 2, L, C, spec.in_ch, nh, has_bn, int(spec.dcd["growth"]), *dil)]
     else:
         dil = list(spec.dilations) + [0] * (MAX_LAYERS - L)
-        parts = [struct.pack(HEADER_FMT, MAGIC, 1, L, C, spec.in_ch, N_HEADS, has_bn, 0, *dil)]
+        parts = [struct.pack(HEADER_FMT, MAGIC, 1, L, C, spec.in_ch, nh, has_bn, 0, *dil)]
     for layer in range(L):
         parts.append(np.ascontiguousarray(w.conv_w[layer], dtype="<f4").tobytes())
         parts.append(np.ascontiguousarray(w.conv_b[layer], dtype="<f4").tobytes())

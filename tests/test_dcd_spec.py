@@ -1,6 +1,7 @@
-"""Host logic of nets with dense connection dilated blocks (Sec. 3.2.1): the library parses the
-"dcd" spec key and checks version-2 weight blobs before it touches a device, so a malformed
-or unsupported request is refused the same way with or without a GPU."""
+"""Host logic of the net spec's extensions: dense connection dilated blocks (Sec. 3.2.1, the
+"dcd" key and version-2 weight blobs) and the uncertainty heads (Sec. 3.2, the "heads" list).
+The library checks spec and blob before it touches a device, so a malformed or unsupported
+request is refused the same way with or without a GPU."""
 import json
 
 import pytest
@@ -97,3 +98,39 @@ def test_valid_dcd_net_reaches_the_device_check():
         assert _code(js, blob) == sml.SML_ERR_CUDA
     spec = synth.spec_dcd()
     assert _code(spec.to_json(), synth.pack_blob(spec, synth.init_weights(spec, 1))) == sml.SML_ERR_CUDA
+
+
+# ----------------------------------------------------------------------------- heads
+
+
+def _plain(n_heads=5, prec="bf16"):
+    spec = synth.NetSpec(in_ch=1, channels=32, dilations=(1, 2, 1), precision=prec, n_heads=n_heads)
+    return spec, spec.to_json(), synth.pack_blob(spec, synth.init_weights(spec, 5))
+
+
+def test_heads_spec_lists_five_or_nine_named_outputs():
+    _, js, blob = _plain(9)
+    d = json.loads(js)
+    assert d["heads"] == ["p", "dx", "dy", "z", "N", "sx", "sy", "sz", "sN"]
+    for heads in (d["heads"][:7], d["heads"][:4], ["p", "dx", "dy", "z", "N", "sy", "sx", "sz", "sN"], "p"):
+        assert _code(json.dumps(dict(d, heads=heads)), blob) == sml.SML_ERR_BAD_SPEC
+
+
+def test_blob_head_count_must_match_the_spec():
+    _, js9, blob9 = _plain(9)
+    _, js5, blob5 = _plain(5)
+    assert _code(js9, blob5) == sml.SML_ERR_BAD_WEIGHTS
+    assert _code(js5, blob9) == sml.SML_ERR_BAD_WEIGHTS
+
+
+def test_valid_nine_head_nets_reach_the_device_check():
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    for prec in ("fp32", "bf16", "fp8"):
+        spec, js, blob = _plain(9, prec)
+        if prec == "fp8":
+            js = json.dumps(dict(json.loads(js), act_scales=[1.0] * spec.L))
+        assert _code(js, blob) == sml.SML_ERR_CUDA
+    spec = synth.NetSpec(in_ch=1, channels=32, dilations=(1, 1), n_heads=9, precision="bf16",
+                         dcd={"growth": 16, "blocks": [[2, 4]]})
+    assert _code(spec.to_json(), synth.pack_blob(spec, synth.init_weights(spec, 2))) == sml.SML_ERR_CUDA
