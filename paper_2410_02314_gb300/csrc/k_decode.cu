@@ -53,13 +53,14 @@ __device__ __forceinline__ void dec_locate(const DecodeArgs& a, long long q0, Px
 // Detection flags of the thread's pixels.  All centre and neighbour loads are issued before
 // any test (out-of-frame neighbours read as -inf, which never blocks a detection), so each
 // thread pays one memory round trip instead of two per pixel.
+template <int NH>
 __device__ __forceinline__ void dec_flags(const DecodeArgs& a, const PxLoc (&loc)[kPxPerThread],
                                           bool (&flag)[kPxPerThread]) {
   const size_t plane = (size_t)a.H * a.W;
   float v[kPxPerThread][9];
 #pragma unroll
   for (int k = 0; k < kPxPerThread; ++k) {
-    const float* p = a.maps + (size_t)loc[k].t * a.nh * plane;
+    const float* p = a.maps + (size_t)loc[k].t * NH * plane;
 #pragma unroll
     for (int di = -1; di <= 1; ++di)
 #pragma unroll
@@ -83,13 +84,15 @@ __device__ __forceinline__ void dec_flags(const DecodeArgs& a, const PxLoc (&loc
   }
 }
 
+// NH: channels of the maps (5, or 9 with the uncertainty maps).
+template <int NH>
 __global__ void __launch_bounds__(kDecodeThreads) k_decode_count(DecodeArgs a) {
   __shared__ unsigned warp_sum[kDecodeThreads / 32];
   const long long q0 = (long long)blockIdx.x * kDecodePxPerBlock;
   PxLoc loc[kPxPerThread];
   bool flag[kPxPerThread];
   dec_locate(a, q0, loc);
-  dec_flags(a, loc, flag);
+  dec_flags<NH>(a, loc, flag);
   unsigned cnt = 0;
 #pragma unroll
   for (int k = 0; k < kPxPerThread; ++k) cnt += __popc(__ballot_sync(0xffffffffu, flag[k]));
@@ -141,6 +144,8 @@ __global__ void __launch_bounds__(1024) k_decode_scan(DecodeArgs a, long long nb
   if (threadIdx.x == 0) *a.total = carry;
 }
 
+// SIGMA: also write the uncertainties of each record (9-head maps).
+template <int NH, bool SIGMA>
 __global__ void __launch_bounds__(kDecodeThreads) k_decode_write(DecodeArgs a) {
   __shared__ unsigned warp_cnt[kPxPerThread][kDecodeThreads / 32];
   const long long q0 = (long long)blockIdx.x * kDecodePxPerBlock;
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode_write(DecodeArgs a) {
   PxLoc loc[kPxPerThread];
   bool flag[kPxPerThread];
   dec_locate(a, q0, loc);
-  dec_flags(a, loc, flag);
+  dec_flags<NH>(a, loc, flag);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   unsigned bal[kPxPerThread];
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode_write(DecodeArgs a) {
       const unsigned long long idx = off + before + __popc(bal[k] & lt_mask);
       if (idx < a.capacity) {
         const size_t px = (size_t)loc[k].i * a.W + loc[k].j;
-        const float* m = a.maps + (size_t)loc[k].t * a.nh * plane;
+        const float* m = a.maps + (size_t)loc[k].t * NH * plane;
         sml_record r;
         r.frame = a.frame0 + loc[k].t;
         r.x = __fadd_rn((float)loc[k].j, m[plane + px]);
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode_write(DecodeArgs a) {
         r.photons = __fmul_rn(a.ph_scale, m[4 * plane + px]);
         r.p = m[px];
         a.out[idx] = r;
-        if (a.out_sigma) {  // uncertainty maps 5..8 at the same pixel
+        if (SIGMA) {  // uncertainty maps 5..8 at the same pixel
           sml_sigma u;
           u.sigma_x = m[5 * plane + px];
           u.sigma_y = m[6 * plane + px];
@@ -199,12 +204,21 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode_write(DecodeArgs a) {
 }  // namespace
 
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int* launches) {
+  if (a.nh != kHeads && a.nh != kMaxHeads) return cudaErrorInvalidValue;
   long long npx = (long long)a.T * a.H * a.W;
   long long nb = decode_blocks(npx);
   if (nb == 0) return cudaSuccess;
-  k_decode_count<<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+  if (a.nh == kMaxHeads)
+    k_decode_count<kMaxHeads><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+  else
+    k_decode_count<kHeads><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
   k_decode_scan<<<1, 1024, 0, s>>>(a, nb);
-  k_decode_write<<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+  if (a.nh == kMaxHeads && a.out_sigma)
+    k_decode_write<kMaxHeads, true><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+  else if (a.nh == kMaxHeads)
+    k_decode_write<kMaxHeads, false><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+  else
+    k_decode_write<kHeads, false><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
   if (launches) *launches += 3;
   return cudaGetLastError();
 }

@@ -187,6 +187,26 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
   }
 }
 
+// Heads of one pixel from its CO final activations (one fully unrolled loop per head count).
+template <int CO, int NH>
+__device__ __forceinline__ void f32_heads_out(const float (&acc)[CO], const float* __restrict__ hw,
+                                              const float* __restrict__ hb, int t, size_t px, size_t plane,
+                                              float* __restrict__ maps, float* __restrict__ logits) {
+#pragma unroll
+  for (int k = 0; k < NH; ++k) {
+    float h = hb[k];
+#pragma unroll
+    for (int c = 0; c < CO; ++c) h = fmaf(hw[k * CO + c], acc[c], h);
+    if (k == 0) {
+      if (logits) logits[(size_t)t * plane + px] = h;
+      h = 1.0f / (1.0f + expf(-h));
+    } else if (k >= kHeads) {
+      h = softplus_f(h);
+    }
+    maps[((size_t)t * NH + k) * plane + px] = h;
+  }
+}
+
 // FP32 dilated conv: one thread per pixel, all CO output channels in registers.  Input
 // channels 0..ci-1 of pixels in_ct floats apart; outputs at channel out_off of pixels out_ct
 // floats apart (a channel range of a dense block's concatenation, or the whole pixel).
@@ -248,20 +268,10 @@ __global__ void __launch_bounds__(kSimtThreads) k_dconv_f32(const F32LayerArgs a
     // uncertainty heads (k >= 5) are softplus(h_k)
     size_t plane = (size_t)H * W;
     size_t px = (size_t)i * W + j;
-#pragma unroll
-    for (int k = 0; k < kMaxHeads; ++k) {
-      if (k >= nh) break;
-      float h = hb[k];
-#pragma unroll
-      for (int c = 0; c < CO; ++c) h = fmaf(hw[k * CO + c], acc[c], h);
-      if (k == 0) {
-        if (logits) logits[(size_t)t * plane + px] = h;
-        h = 1.0f / (1.0f + expf(-h));
-      } else if (k >= kHeads) {
-        h = softplus_f(h);
-      }
-      maps[((size_t)t * nh + k) * plane + px] = h;
-    }
+    if (nh == kHeads)
+      f32_heads_out<CO, kHeads>(acc, hw, hb, t, px, plane, maps, logits);
+    else
+      f32_heads_out<CO, kMaxHeads>(acc, hw, hb, t, px, plane, maps, logits);
   }
 }
 

@@ -301,6 +301,26 @@ __device__ __forceinline__ int unit_rows(const TcKArgs& a, uint32_t u, int seg, 
   return n < 0 ? 0 : (n > seg ? seg : n);
 }
 
+// Fused 1x1 heads of the last layer for one pixel (Sec. 3.2): h_k = b_k + sum_c w_kc v_c with
+// p = sigmoid(h_0) (the logit is also stored when requested), h_1..h_4 as they are, and the
+// uncertainty heads h_5..h_8 (NH = 9) through softplus.  Maps are [T][NH][H][W].
+template <int CO, int NH>
+__device__ __forceinline__ void heads_out(const TcKArgs& a, const float (&v)[CO], int t, size_t px, size_t plane) {
+#pragma unroll
+  for (int h = 0; h < NH; ++h) {
+    float acc = a.head_b[h];
+#pragma unroll
+    for (int c = 0; c < CO; ++c) acc = fmaf(a.head_w[h * CO + c], v[c], acc);
+    if (h == 0) {
+      if (a.logits) a.logits[(size_t)t * plane + px] = acc;
+      acc = 1.0f / (1.0f + expf(-acc));
+    } else if (h >= kHeads) {
+      acc = softplus_f(acc);
+    }
+    a.maps[((size_t)t * NH + h) * plane + px] = acc;
+  }
+}
+
 template <int CI, int CO, int PREC, bool LAST>
 __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant__ CUtensorMap tmap, const TcKArgs a) {
   using Cfg = TcCfg<CI, CO, PREC>;
@@ -586,20 +606,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         }
         if (LAST) {
           const size_t px = (size_t)i * a.W + j;
-#pragma unroll
-          for (int h = 0; h < kMaxHeads; ++h) {
-            if (h >= a.nh) break;
-            float acc = a.head_b[h];
-#pragma unroll
-            for (int c = 0; c < CO; ++c) acc = fmaf(a.head_w[h * CO + c], v[c], acc);
-            if (h == 0) {
-              if (a.logits) a.logits[(size_t)t * plane + px] = acc;
-              acc = 1.0f / (1.0f + expf(-acc));
-            } else if (h >= kHeads) {
-              acc = softplus_f(acc);  // uncertainty heads
-            }
-            a.maps[((size_t)t * a.nh + h) * plane + px] = acc;
-          }
+          // the head count is uniform across the grid: one fully unrolled loop per count
+          if (a.nh == kHeads)
+            heads_out<CO, kHeads>(a, v, t, px, plane);
+          else
+            heads_out<CO, kMaxHeads>(a, v, t, px, plane);
         } else if (PREC == kBF16) {
 #pragma unroll
           for (int gq = 0; gq < Cfg::GO; ++gq) {
