@@ -108,7 +108,12 @@ class Net:
     a stem conv (dilations[0], in_ch -> C); per block, dense layers whose input is the block
     input and every earlier output of the block concatenated (C + j*growth channels, growth
     outputs, the block's dilations) and a transition conv (d = 1, C + k*growth -> C); then the
-    plain C -> C layers dilations[1:].  ``layers`` lists (cin, cout, dilation, kind)."""
+    plain C -> C layers dilations[1:].
+    A U-Net fine stage (spec key "unet": {"levels": L}, L in 1..2; Sec. 3.2, version-2 blobs)
+    sits right before the last conv layer: per level down a 2x2 max pool (ceil) and a 3x3
+    conv C -> C ("down"), per level up a nearest 2x upsample concatenated after that level's
+    skip features and a 3x3 conv 2C -> C ("up").  ``layers`` lists (cin, cout, dilation,
+    kind) of every conv layer in execution order."""
 
     def __init__(self, spec_json: str, blob: bytes):
         s = json.loads(spec_json)
@@ -137,6 +142,15 @@ class Net:
             self.growth = 0
             self.layers = [(self.in_ch if l == 0 else C, C, d, "plain") for l, d in enumerate(self.plain_dil)]
             fmt, version = "<8s7I16i", 1
+        unet = s.get("unet")
+        self.unet = int(unet["levels"]) if unet else 0
+        if self.unet:
+            if self.unet not in (1, 2) or len(self.layers) < 2:
+                raise ValueError("unet needs 1 or 2 levels and a conv layer before the last one")
+            last = self.layers[-1]
+            self.layers = (self.layers[:-1] + [(C, C, 1, "down")] * self.unet + [(2 * C, C, 1, "up")] * self.unet
+                           + [last])
+            fmt, version = "<8s7I32i", 2
         self.dil = [d for _, _, d, _ in self.layers]
         self.L = len(self.layers)
         hdr = struct.unpack_from(fmt, blob, 0)
@@ -175,7 +189,10 @@ class Net:
 
     @property
     def R(self) -> int:
-        return sum(self.dil)
+        """Receptive radius (px): the sum of the dilations outside the U-Net, plus for a U-Net of
+        L levels the bound 3 * 2^(L+1) on its reach (pooling and upsampling included)."""
+        plain = sum(d for _, _, d, kind in self.layers if kind not in ("down", "up"))
+        return plain + (3 * 2 ** (self.unet + 1) if self.unet else 0)
 
 
 # ----------------------------------------------------------------------------- forward
@@ -232,9 +249,9 @@ def quantized(net: Net, fmt):
     if net.bn is not None:
         raise ValueError("quantized oracle modes need a net without BatchNorm")
     q = copy.copy(net)
-    if net.growth:  # dense blocks: per-layer arrays (layers 1.. run on the tensor cores)
+    if net.growth or net.unet:  # per-layer arrays (layers 1.. run on the tensor cores)
         if fmt != "bf16":
-            raise ValueError("dense blocks have a bf16 quantized mode only")
+            raise ValueError("dense blocks and the U-Net have a bf16 quantized mode only")
         q.layer_w = [net.layer_w[0]] + [round_to(wl, "bf16") for wl in net.layer_w[1:]]
         return q
     w = net.conv_w.copy()
@@ -268,7 +285,7 @@ def forward_x(net: Net, x0, acts=False, quant=None, scales=None):
     quant "bf16" / "fp8" rounds the input activations of layers 1..L-1 to that format
     (fp8: of a / scales[l]) before the layer, as the tensor-core path stores them; pass a
     net from quantized() to round the weights too."""
-    if net.growth:
+    if net.growth or net.unet:
         return _forward_dense(net, x0, acts, quant)
     lib = _load()
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
@@ -286,11 +303,27 @@ def forward_x(net: Net, x0, acts=False, quant=None, scales=None):
     return (heads, a) if acts else heads
 
 
+def pool2(a):
+    """2x2 max pooling with stride 2 of [C,H,W] to [C,ceil(H/2),ceil(W/2)]; a window that
+    overhangs the frame's last row or column takes the max of its in-frame pixels."""
+    C, H, W = a.shape
+    p = np.full((C, H + H % 2, W + W % 2), -np.inf)
+    p[:, :H, :W] = a
+    return p.reshape(C, p.shape[1] // 2, 2, p.shape[2] // 2, 2).max(axis=(2, 4))
+
+
+def upsample2(a, H, W):
+    """Nearest-neighbour 2x upsampling of [C,h,w] cropped to [C,H,W]: out[c,i,j] = a[c,i//2,j//2]."""
+    return a.repeat(2, axis=1).repeat(2, axis=2)[:, :H, :W]
+
+
 def _forward_dense(net: Net, x0, acts=False, quant=None):
-    """Forward of a net with dense connection dilated blocks (Sec. 3.2.1): each layer is the
-    C oracle's conv (float64) on a channel range of a buffer that concatenates the block input
-    and the block's outputs so far.  quant "bf16" rounds every layer's stored output to bf16
-    (what the tensor-core path stores; the stem's input frames stay float).  Returns raw heads
+    """Forward of a net with dense connection dilated blocks (Sec. 3.2.1) and/or a U-Net fine
+    stage (Sec. 3.2): each conv is the C oracle's conv (float64) on a channel range of a
+    buffer that concatenates the block input and the block's outputs so far; the U-Net
+    pools, convolves, upsamples and concatenates with numpy.  quant "bf16" rounds every conv
+    layer's stored output to bf16 (what the tensor-core path stores; pooling and upsampling
+    move stored values unchanged; the stem's input frames stay float).  Returns raw heads
     [T,nh,H,W] (and, with acts, the last layer's activations)."""
     lib = _load()
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
@@ -299,29 +332,50 @@ def _forward_dense(net: Net, x0, acts=False, quant=None):
     T, cin0, H, W = x0.shape
     assert cin0 == net.in_ch
     if quant not in (None, "fp32", "bf16"):
-        raise ValueError("dense blocks support the bf16 quantized mode only")
+        raise ValueError("dense blocks and the U-Net support the bf16 quantized mode only")
     rnd = (lambda a: round_to(a, "bf16")) if quant == "bf16" else (lambda a: a)
     C, g = net.C, net.growth
     widest = max(cin for cin, _, _, _ in net.layers)
+
+    def conv(li, inp):
+        cin, cout, d, _ = net.layers[li]
+        inp = np.ascontiguousarray(inp)
+        h, w = inp.shape[1:]
+        out = np.empty((cout, h, w), dtype=np.float64)
+        lib.orc_conv(_ptr(inp), cin, h, w, _ptr(np.ascontiguousarray(net.layer_w[li])),
+                     _ptr(np.ascontiguousarray(net.layer_b[li])), cout, d, _ptr(out))
+        return out if li == net.L - 1 else rnd(out)  # the last layer's output feeds the heads in FP32
+
     heads = np.empty((T, net.nh, H, W), dtype=np.float64)
     last = np.empty((T, C, H, W), dtype=np.float64) if acts else None
     for t in range(T):
         buf = np.zeros((widest, H, W), dtype=np.float64)  # the current block's concatenation
         used = 0  # channels of buf filled
         src = np.ascontiguousarray(x0[t])
-        for li, (cin, cout, d, kind) in enumerate(net.layers):
-            inp = np.ascontiguousarray(src if kind == "stem" else buf[:cin])
-            out = np.empty((cout, H, W), dtype=np.float64)
-            lib.orc_conv(_ptr(inp), cin, H, W, _ptr(np.ascontiguousarray(net.layer_w[li])),
-                         _ptr(np.ascontiguousarray(net.layer_b[li])), cout, d, _ptr(out))
-            if li < net.L - 1:  # stored activations; the last layer's output feeds the heads in FP32
-                out = rnd(out)
+        li = 0
+        while li < net.L:
+            cin, cout, d, kind = net.layers[li]
+            if kind == "down":  # the U-Net: levels down, then up (2 * levels conv layers)
+                skips = [buf[:C].copy()]
+                for _ in range(net.unet):
+                    skips.append(conv(li, pool2(skips[-1])))
+                    li += 1
+                up = skips.pop()
+                while skips:
+                    skip = skips.pop()
+                    up = conv(li, np.concatenate([skip, upsample2(up, *skip.shape[1:])]))
+                    li += 1
+                buf[:C] = up
+                used = C
+                continue
+            out = conv(li, src if li == 0 else buf[:cin])  # the first layer reads the network input
             if kind == "dense":  # appended to the block's concatenation
                 buf[used : used + cout] = out
                 used += cout
             else:  # stem, transition, plain: a new C-channel block input
                 buf[:cout] = out
                 used = cout
+            li += 1
         a = buf[:C]
         if acts:
             last[t] = a
@@ -386,15 +440,17 @@ def forward_window(net: Net, frames, i0, i1, j0, j1, gain=1.0, offset=100.0, gai
                    offset_map=None, quant=None, scales=None):
     """Exact heads [T,nh,i1-i0,j1-j0] of the block [i0,i1) x [j0,j1) of full frames.
 
-    The crop extends the block by the receptive radius R = sum of dilations (clipped at the
-    frame border).  Every output inside the block depends only on inputs within R of it,
-    and layer l's outputs are wrong only within sum_{k<=l} d_k of a crop edge that is not
-    a frame edge, so the block's values equal those of the whole-frame forward.
+    The crop extends the block by the receptive radius R (clipped at the frame border).
+    Every output inside the block depends only on inputs within R of it, and layer l's
+    outputs are wrong only within its reach of a crop edge that is not a frame edge, so the
+    block's values equal those of the whole-frame forward.  With a U-Net of L levels the
+    crop starts on a multiple of 2^L, so that its pooling windows are the whole frame's.
     """
     T, H, W = frames.shape
     R = net.R
-    ci0, ci1 = max(0, i0 - R), min(H, i1 + R)
-    cj0, cj1 = max(0, j0 - R), min(W, j1 + R)
+    a = 2 ** net.unet
+    ci0, ci1 = max(0, i0 - R) // a * a, min(H, i1 + R)
+    cj0, cj1 = max(0, j0 - R) // a * a, min(W, j1 + R)
     crop = np.ascontiguousarray(frames[:, ci0:ci1, cj0:cj1])
     gm = None if gain_map is None else gain_map[ci0:ci1, cj0:cj1]
     om = None if offset_map is None else offset_map[ci0:ci1, cj0:cj1]

@@ -84,19 +84,26 @@ class NetSpec:
     dcd: dict | None = None
     # 5 (position heads) or 9 (and the uncertainty heads sx, sy, sz, sN)
     n_heads: int = N_HEADS
+    # U-Net fine stage: number of levels (0 = none, 1 or 2), inserted before the last layer.
+    # Per level down: 2x2 max pool, then a 3x3 conv C -> C; per level up: nearest 2x
+    # upsample concatenated after the level's skip features, then a 3x3 conv 2C -> C.
+    unet: int = 0
 
     def layers(self) -> list:
         """(cin, cout, dilation) of every conv layer in execution order."""
         C = self.channels
         if not self.dcd:
-            return [(self.in_ch if l == 0 else C, C, d) for l, d in enumerate(self.dilations)]
-        g = int(self.dcd["growth"])
-        out = [(self.in_ch, C, self.dilations[0])]
-        for block in self.dcd["blocks"]:
-            for j, d in enumerate(block):
-                out.append((C + j * g, g, int(d)))
-            out.append((C + len(block) * g, C, 1))
-        out += [(C, C, d) for d in self.dilations[1:]]
+            out = [(self.in_ch if l == 0 else C, C, d) for l, d in enumerate(self.dilations)]
+        else:
+            g = int(self.dcd["growth"])
+            out = [(self.in_ch, C, self.dilations[0])]
+            for block in self.dcd["blocks"]:
+                for j, d in enumerate(block):
+                    out.append((C + j * g, g, int(d)))
+                out.append((C + len(block) * g, C, 1))
+            out += [(C, C, d) for d in self.dilations[1:]]
+        if self.unet:
+            out = out[:-1] + [(C, C, 1)] * self.unet + [(2 * C, C, 1)] * self.unet + out[-1:]
         return out
 
     def to_json(self) -> str:
@@ -114,6 +121,8 @@ class NetSpec:
             d["act_scales"] = [float(s) for s in self.act_scales]
         if self.dcd:
             d["dcd"] = {"growth": int(self.dcd["growth"]), "blocks": [[int(x) for x in b] for b in self.dcd["blocks"]]}
+        if self.unet:
+            d["unet"] = {"levels": int(self.unet)}
         return json.dumps(d)
 
     @property
@@ -122,8 +131,12 @@ class NetSpec:
 
     @property
     def R(self) -> int:
-        """Receptive radius of the conv stack in pixels."""
-        return int(sum(d for _, _, d in self.layers()))
+        """Receptive radius of the net in pixels: the sum of the dilations outside the U-Net,
+        plus 3 * 2^(levels+1) for a U-Net (a bound on its reach, pooling included)."""
+        n = 2 * self.unet
+        lay = self.layers()
+        plain = lay[: len(lay) - 1 - n] + lay[-1:] if n else lay
+        return int(sum(d for _, _, d in plain) + (3 * 2 ** (self.unet + 1) if self.unet else 0))
 
 
 def spec_small(precision="fp32") -> NetSpec:
@@ -172,8 +185,8 @@ def init_weights(spec: NetSpec, seed: int, bn: bool = False) -> Weights:
         ws.append(w)
         bs.append(b)
         if bn:
-            if spec.dcd:
-                raise ValueError("BatchNorm is not supported with dense blocks")
+            if spec.dcd or spec.unet:
+                raise ValueError("BatchNorm is not supported with dense blocks or a U-Net")
             gamma = s.uniform(C, 0.5, 1.5)
             beta = s.uniform(C, -0.1, 0.1)
             mean = s.uniform(C, -0.1, 0.1)
@@ -188,14 +201,15 @@ def init_weights(spec: NetSpec, seed: int, bn: bool = False) -> Weights:
 
 def pack_blob(spec: NetSpec, w: Weights) -> bytes:
     """Serialise weights into an SMLW blob (little endian, float32 payload).  Plain stacks use
-    version 1 (dil[16]); nets with dense blocks version 2 (reserved = growth, dil[32] = every
+    version 1 (dil[16]); nets with dense blocks or a U-Net version 2 (reserved = growth, dil[32] = every
     layer's dilation in execution order)."""
     L, C = spec.L, spec.channels
     has_bn = 1 if w.bn is not None else 0
     nh = int(np.asarray(w.head_b).size)
-    if spec.dcd:
+    if spec.dcd or spec.unet:
         dil = [d for _, _, d in spec.layers()] + [0] * (MAX_LAYERS_V2 - L)
-        parts = [struct.pack(HEADER_FMT_V2, MAGIC, 2, L, C, spec.in_ch, nh, has_bn, int(spec.dcd["growth"]), *dil)]
+        growth = int(spec.dcd["growth"]) if spec.dcd else 0
+        parts = [struct.pack(HEADER_FMT_V2, MAGIC, 2, L, C, spec.in_ch, nh, has_bn, growth, *dil)]
     else:
         dil = list(spec.dilations) + [0] * (MAX_LAYERS - L)
         parts = [struct.pack(HEADER_FMT, MAGIC, 1, L, C, spec.in_ch, nh, has_bn, 0, *dil)]
