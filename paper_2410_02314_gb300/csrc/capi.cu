@@ -157,10 +157,13 @@ std::string g_create_error;
 }  // namespace
 
 // ------------------------------------------------------------------ context
+constexpr int kMaxBufs = 6;    // activation buffers: 2 at full resolution, 2 per U-Net level
+constexpr int kMaxLevels = 2;  // U-Net levels
+
 struct Plan {
   int H = 0, W = 0, Tc = 0;
   unsigned long long last_use = 0;
-  void* act[2] = {nullptr, nullptr};
+  void* act[kMaxBufs] = {nullptr};
   float* maps = nullptr;
   unsigned* block_counts = nullptr;
   unsigned long long* block_offsets = nullptr;
@@ -179,6 +182,23 @@ struct Plan {
 // the other buffer.
 struct LayerDesc {
   int cin = 0, cout = 0, d = 1, in_buf = -1, out_buf = 0, out_off = 0;
+  int level = 0;  // resolution: H and W halved (rounded up) level times (U-Net layers)
+};
+
+// An activation buffer: its resolution level and channels per pixel.  Buffers 0 and 1 are the
+// full-resolution ping-pong pair; a U-Net of L levels adds per level l a skip buffer A_l
+// (2C channels: the level's features, then the upsampled ones) and a work buffer B_l (C).
+struct BufDesc {
+  int level = 0, ct = 0;
+};
+
+// One launch of the forward after layer 1, in order: a conv layer (LayerDesc index `layer`),
+// or a 2x2 max pool / nearest 2x upsample of channels [0, C) of in_buf into channels
+// [out_off, out_off + C) of out_buf.
+enum StepKind { kStepConv = 0, kStepPool = 1, kStepUp = 2 };
+struct Step {
+  int kind = kStepConv, layer = 0;
+  int in_buf = 0, out_buf = 0, out_off = 0, C = 0;
 };
 
 struct sml_ctx {
@@ -188,6 +208,10 @@ struct sml_ctx {
   LayerDesc lay[kMaxLayers];
   int growth = 0;  // dense blocks: channels each dense layer adds (0: plain stack)
   int nh = kHeads; // output heads: 5, or 9 with the uncertainty heads
+  int unet = 0;    // U-Net fine stage levels before the last layer (0: none)
+  BufDesc buf[kMaxBufs];
+  int nbuf = 2;
+  std::vector<Step> steps;
   int ct = 0;      // channels per pixel of the activation buffers (C, or C + the longest block's k g)
   int prec = kFP32;
   float in_scale = 1e-3f, z_scale = 1000.f, ph_scale = 10000.f;
@@ -272,8 +296,7 @@ int upload(sml_ctx* ctx, T** dst, const void* src, size_t bytes) {
 }
 
 void free_plan(Plan& p) {
-  cudaFree(p.act[0]);
-  cudaFree(p.act[1]);
+  for (void* a : p.act) cudaFree(a);
   cudaFree(p.maps);
   cudaFree(p.block_counts);
   cudaFree(p.block_offsets);
@@ -284,16 +307,21 @@ void free_plan(Plan& p) {
 
 size_t act_elem_bytes(int prec) { return prec == kFP32 ? 4 : (prec == kBF16 ? 2 : 1); }
 
+// Size of a frame dimension at a U-Net level: halved, rounded up, `level` times.
+int level_dim(int n, int level) {
+  for (int k = 0; k < level; ++k) n = (n + 1) / 2;
+  return n;
+}
+
 // Row-planar activations [Tc][H][Gt][W][row bytes], Gt = ct/16 groups of 16 channels (32-byte
 // rows in BF16, 16-byte rows in FP8).  A layer reading its first g_in groups sees the 5-D
 // tensor (group row, W, g_in, H, Tc) with the buffer's strides and loads boxes (group row,
 // tc_box_width(d) pixels, g_in, 1, 1): one input row segment per box, BF16 rows with the
 // 32-byte swizzle.  Pixels left of 0 or right of W-1, and rows outside [0,H), are filled with
 // zeros by TMA.
-int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W, int d, int g_in) {
+int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W, int d, int g_in, int gt) {
   PFN_encodeTiled_t enc = get_encoder();
   if (!enc) return fail(ctx, SML_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  const int gt = ctx->ct / 16;
   const bool bf16 = ctx->prec == kBF16;
   const cuuint64_t rowb = bf16 ? 32 : 16;
   cuuint64_t dims[5] = {16ull, (cuuint64_t)W, (cuuint64_t)g_in, (cuuint64_t)H, (cuuint64_t)Tc};
@@ -352,10 +380,15 @@ int get_plan(sml_ctx* ctx, int H, int W) {
   long long hw = (long long)H * W;
   int Tc = (int)std::max(1LL, ctx->chunk_px / hw);
   size_t npx = (size_t)Tc * hw;
-  size_t ab = npx * ctx->ct * act_elem_bytes(ctx->prec);
   int r;
-  if ((r = dev_alloc(ctx, &p.act[0], ab)) || (r = dev_alloc(ctx, &p.act[1], ab)) ||
-      (r = dev_alloc(ctx, &p.maps, npx * ctx->nh * sizeof(float))) ||
+  for (int b = 0; b < ctx->nbuf; ++b) {
+    const size_t px = (size_t)Tc * level_dim(H, ctx->buf[b].level) * level_dim(W, ctx->buf[b].level);
+    if ((r = dev_alloc(ctx, &p.act[b], px * ctx->buf[b].ct * act_elem_bytes(ctx->prec)))) {
+      free_plan(p);
+      return r;
+    }
+  }
+  if ((r = dev_alloc(ctx, &p.maps, npx * ctx->nh * sizeof(float))) ||
       (r = dev_alloc(ctx, &p.block_counts, decode_blocks(npx) * sizeof(unsigned))) ||
       (r = dev_alloc(ctx, &p.block_offsets, decode_blocks(npx) * sizeof(unsigned long long))) ||
       (r = dev_alloc(ctx, &p.frames, (size_t)(Tc + 2) * hw * sizeof(uint16_t))) ||  // + context frames
@@ -366,7 +399,8 @@ int get_plan(sml_ctx* ctx, int H, int W) {
   if (ctx->prec != kFP32) {
     for (int l = 1; l < ctx->L; ++l) {
       const LayerDesc& y = ctx->lay[l];
-      if ((r = encode_act_map(ctx, &p.tmap[l], p.act[y.in_buf], Tc, H, W, y.d, y.cin / 16))) {
+      if ((r = encode_act_map(ctx, &p.tmap[l], p.act[y.in_buf], Tc, level_dim(H, y.level), level_dim(W, y.level), y.d,
+                              y.cin / 16, ctx->buf[y.in_buf].ct / 16))) {
         free_plan(p);
         return r;
       }
@@ -400,18 +434,38 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, FrameRange fr,
   float l1_scale = ctx->prec == kFP8 ? 1.0f / ctx->act_scale[1] : 1.0f;
   {
     ProfScope ps(ctx, SML_KERNEL_LAYER1, s);
+    const int b0 = ctx->lay[0].out_buf;
     SML_CUDA(launch_ingest_l1(d_frames, tc, H, W, ctx->lay[0].d, cam, ctx->w1.data(), ctx->b1.data(), C, ctx->in_ch,
-                              fr.first, fr.last, ctx->prec, l1_scale, p.act[ctx->lay[0].out_buf], ctx->ct, s),
+                              fr.first, fr.last, ctx->prec, l1_scale, p.act[b0], ctx->buf[b0].ct, s),
              "layer 1");
   }
   ++ctx->launches;
   const size_t n_act = (size_t)tc * H * W * C;  // whole buffers of a plain stack (ct == C)
   if (d_amax) SML_CUDA(launch_amax(p.act[0], n_act, ctx->prec, d_amax + 1, s), "amax");
-  for (int l = 1; l < L; ++l) {
+  for (const Step& st : ctx->steps) {
+    if (st.kind != kStepConv) {  // U-Net resolution change
+      const BufDesc& bi = ctx->buf[st.in_buf];
+      const BufDesc& bo = ctx->buf[st.out_buf];
+      ProfScope ps(ctx, SML_KERNEL_CONV, s);
+      if (st.kind == kStepPool)
+        SML_CUDA(launch_pool2(p.act[st.in_buf], bi.ct, p.act[st.out_buf], bo.ct, st.out_off, st.C, tc,
+                              level_dim(H, bi.level), level_dim(W, bi.level), ctx->prec, s),
+                 "pool");
+      else
+        SML_CUDA(launch_upsample2(p.act[st.in_buf], bi.ct, level_dim(H, bi.level), level_dim(W, bi.level),
+                                  p.act[st.out_buf], bo.ct, st.out_off, st.C, tc, level_dim(H, bo.level),
+                                  level_dim(W, bo.level), ctx->prec, s),
+                 "upsample");
+      ++ctx->launches;
+      continue;
+    }
+    const int l = st.layer;
     const bool last = (l == L - 1);
     const LayerDesc& y = ctx->lay[l];
+    const int Hl = level_dim(H, y.level), Wl = level_dim(W, y.level);
     void* in = p.act[y.in_buf];
     void* out = last ? nullptr : p.act[y.out_buf];
+    const int out_ct = last ? C : ctx->buf[y.out_buf].ct;
     ProfScope ps(ctx, last ? SML_KERNEL_CONV_HEADS : SML_KERNEL_CONV, s);
     if (ctx->prec == kFP32) {
       F32LayerArgs fa{};
@@ -420,13 +474,13 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, FrameRange fr,
       fa.w = ctx->wf32[l];
       fa.b = ctx->bias[l];
       fa.T = tc;
-      fa.H = H;
-      fa.W = W;
+      fa.H = Hl;
+      fa.W = Wl;
       fa.d = y.d;
       fa.ci = y.cin;
       fa.co = y.cout;
-      fa.in_ct = ctx->ct;
-      fa.out_ct = ctx->ct;
+      fa.in_ct = ctx->buf[y.in_buf].ct;
+      fa.out_ct = out_ct;
       fa.out_off = y.out_off;
       if (last)
         SML_CUDA(launch_dconv_f32_heads(fa, ctx->head_w, ctx->head_b, ctx->nh, maps, logits, s), "fp32 conv+heads");
@@ -442,15 +496,15 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, FrameRange fr,
       a.out_inv_scale = (ctx->prec == kFP8 && !last) ? 1.0f / ctx->act_scale[l + 1] : 1.0f;
       a.out = out;
       a.out_g0 = y.out_off / 16;
-      a.out_gt = ctx->ct / 16;
+      a.out_gt = out_ct / 16;
       a.head_w = ctx->h_head_w.data();
       a.head_b = ctx->h_head_b.data();
       a.nh = ctx->nh;
       a.maps = maps;
       a.logits = logits;
       a.T = tc;
-      a.H = H;
-      a.W = W;
+      a.H = Hl;
+      a.W = Wl;
       a.d = y.d;
       a.ci = y.cin;
       a.co = y.cout;
@@ -647,6 +701,71 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
     ctx->L = L;
     ctx->ct = widest;
   }
+  // launches after layer 1: one per conv layer, on the full-resolution ping-pong buffers
+  ctx->nbuf = 2;
+  ctx->buf[0] = ctx->buf[1] = BufDesc{0, ctx->ct};
+  ctx->steps.clear();
+  for (int l = 1; l < ctx->L; ++l) ctx->steps.push_back(Step{kStepConv, l, 0, 0, 0, 0});
+  auto un = root.obj.find("unet");
+  if (un != root.obj.end() && un->second.kind != JVal::kNull) {
+    // U-Net fine stage (Sec. 3.2) before the last layer: per level down a 2x2 max pool and a
+    // 3x3 conv C -> C; per level up a nearest 2x upsample concatenated after the level's skip
+    // features and a 3x3 conv 2C -> C
+    const JVal& o = un->second;
+    auto li = o.obj.find("levels");
+    if (o.kind != JVal::kObj || li == o.obj.end() || li->second.kind != JVal::kNum || li->second.num < 1 ||
+        li->second.num > kMaxLevels || li->second.num != floor(li->second.num))
+      return fail(nullptr, SML_ERR_BAD_SPEC, "unet needs \"levels\": 1..%d", kMaxLevels);
+    const int lv = (int)li->second.num;
+    if (ctx->L < 2) return fail(nullptr, SML_ERR_BAD_SPEC, "unet needs a conv layer before the last one");
+    if (ctx->L - 1 + 2 * lv + 1 > kMaxLayers)
+      return fail(nullptr, SML_ERR_BAD_SPEC, "the net has more than %d conv layers", kMaxLayers);
+    ctx->unet = lv;
+    LayerDesc last = ctx->lay[ctx->L - 1];
+    const int cur = last.in_buf;  // holds the features [0, C) the U-Net starts from
+    ctx->steps.pop_back();
+    int L = ctx->L - 1;
+    ctx->ct = std::max(ctx->ct, 2 * C);  // room for the upsampled features after the skip
+    ctx->buf[0] = ctx->buf[1] = BufDesc{0, ctx->ct};
+    auto A = [](int l) { return 2 + 2 * (l - 1); };  // skip buffer of level l (2C)
+    auto B = [](int l) { return 3 + 2 * (l - 1); };  // work buffer of level l (C)
+    for (int l = 1; l <= lv; ++l) {
+      ctx->buf[A(l)] = BufDesc{l, 2 * C};
+      ctx->buf[B(l)] = BufDesc{l, C};
+    }
+    ctx->nbuf = 2 + 2 * lv;
+    auto conv = [&](int cin, int in_buf, int out_buf, int level) {
+      LayerDesc& y = ctx->lay[L];
+      y = LayerDesc{};
+      y.cin = cin;
+      y.cout = C;
+      y.d = 1;
+      y.in_buf = in_buf;
+      y.out_buf = out_buf;
+      y.out_off = 0;
+      y.level = level;
+      ctx->steps.push_back(Step{kStepConv, L, 0, 0, 0, 0});
+      ++L;
+    };
+    int src = cur;
+    for (int l = 1; l <= lv; ++l) {  // down: pool, then conv into the level's skip buffer
+      ctx->steps.push_back(Step{kStepPool, -1, src, B(l), 0, C});
+      conv(C, B(l), A(l), l);
+      src = A(l);
+    }
+    int g = A(lv);  // the deepest level's features
+    for (int l = lv; l >= 1; --l) {  // up: upsample after the skip of level l-1, then conv
+      const int cat = l - 1 == 0 ? cur : A(l - 1);
+      ctx->steps.push_back(Step{kStepUp, -1, g, cat, C, C});
+      const int out = l - 1 == 0 ? 1 - cur : B(l - 1);
+      conv(2 * C, cat, out, l - 1);
+      g = out;
+    }
+    last.in_buf = g;
+    ctx->lay[L] = last;
+    ctx->steps.push_back(Step{kStepConv, L, 0, 0, 0, 0});
+    ctx->L = L + 1;
+  }
   auto pr = root.obj.find("precision");
   std::string prec = (pr != root.obj.end() && pr->second.kind == JVal::kStr) ? pr->second.str : "fp32";
   if (prec == "fp32") ctx->prec = kFP32;
@@ -663,8 +782,9 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
       ctx->act_scale[l] = (float)v.num;
     }
   }
-  if (ctx->growth && ctx->prec == kFP8)
-    return fail(nullptr, SML_ERR_UNSUPPORTED, "dcd nets run in fp32 or bf16 (fp8 activation scales are per layer)");
+  if ((ctx->growth || ctx->unet) && ctx->prec == kFP8)
+    return fail(nullptr, SML_ERR_UNSUPPORTED,
+                "dcd and unet nets run in fp32 or bf16 (fp8 activation scales are per layer, not per concatenation)");
   for (int l = 1; l < ctx->L; ++l) {  // every layer must fit its kernel's shared memory
     const LayerDesc& y = ctx->lay[l];
     const bool fits = ctx->prec == kFP32 ? y.cin * y.cout <= kF32MaxWeights : tc_layer_fits(y.cin, y.cout, y.d, ctx->prec);
@@ -693,7 +813,7 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
 // Checks the header against the spec and the size; host only (runs before any device call).
 int check_blob(const sml_ctx* ctx, const void* blob, size_t bytes, size_t* hdr_out, int* has_bn_out) {
   const uint8_t* b = static_cast<const uint8_t*>(blob);
-  const bool v2 = ctx->growth > 0;
+  const bool v2 = ctx->growth > 0 || ctx->unet > 0;
   const int ndil = v2 ? 32 : 16;
   const size_t hdr_bytes = 8 + 7 * 4 + (size_t)ndil * 4;
   if (!blob || bytes < hdr_bytes || memcmp(b, "SMLW0001", 8) != 0)
@@ -1057,7 +1177,8 @@ int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, in
   int r;
   if (!amax || (T > 0 && !d_frames)) return fail(ctx, SML_ERR_BAD_ARG, "NULL argument");
   if (ctx->prec == kFP8) return fail(ctx, SML_ERR_UNSUPPORTED, "activation maxima need an fp32 or bf16 context");
-  if (ctx->growth) return fail(ctx, SML_ERR_UNSUPPORTED, "activation maxima are for plain stacks (fp8 calibration)");
+  if (ctx->growth || ctx->unet)
+    return fail(ctx, SML_ERR_UNSUPPORTED, "activation maxima are for plain stacks (fp8 calibration)");
   if ((r = check_dims(ctx, T, H, W))) return r;
   CamArgs ca;
   if ((r = make_cam(ctx, cam, &ca))) return r;

@@ -98,6 +98,18 @@ cudaError_t launch_dconv_f32_heads(const F32LayerArgs& a, const float* hw, const
 // Largest ci * co whose FP32 weights fit in shared memory.
 constexpr int kF32MaxWeights = 227 * 1024 / (9 * 4);
 
+// --- U-Net resolution changes (k_resample.cu) ------------------------------------------
+// 2x2 max pool (stride 2, ceil: output ceil(H/2) x ceil(W/2)) of channels [0, C) of `in`
+// ([T][H][W] pixels, in_ct channels each) into channels [out_off, out_off + C) of `out`
+// (out_ct channels per pixel).  prec kFP32 (NHWC float, C, cts, offset multiples of 4) or
+// kBF16 (row-planar, multiples of 16).
+cudaError_t launch_pool2(const void* in, int in_ct, void* out, int out_ct, int out_off, int C, int T, int H, int W,
+                         int prec, cudaStream_t s);
+// Nearest 2x upsample of channels [0, C) of `in` (h x w, h = ceil(H/2), w = ceil(W/2)) into
+// channels [out_off, out_off + C) of `out` (H x W): out(i, j) = in(i/2, j/2).
+cudaError_t launch_upsample2(const void* in, int in_ct, int h, int w, void* out, int out_ct, int out_off, int C, int T,
+                             int H, int W, int prec, cudaStream_t s);
+
 // --- tensor-core path (row-planar activations) -------------------------------------
 struct TcLayerArgs {
   const CUtensorMap* tmap;  // input activations, one box per row (5-D map for this dilation)

@@ -158,6 +158,14 @@ def spec_dcd(precision="bf16") -> NetSpec:
                    dcd={"growth": 16, "blocks": [[2, 4, 8, 16] for _ in range(4)]})
 
 
+def spec_dilatedloc(precision="bf16") -> NetSpec:
+    """The paper's full topology with our widths (Sec. 3.2): the dense-block feature extractor of
+    spec_dcd (one coarse and three context blocks), a two-level U-Net fine stage and the nine
+    heads (positions and their uncertainties).  26 conv layers."""
+    return NetSpec(in_ch=1, channels=32, dilations=(1, 1), precision=precision, n_heads=9, unet=2,
+                   dcd={"growth": 16, "blocks": [[2, 4, 8, 16] for _ in range(4)]})
+
+
 # --------------------------------------------------------------------------- weights
 
 
@@ -439,6 +447,17 @@ def workload_dcd(T=256, H=256, W=256, precision="bf16", seed=3) -> Workload:
     spec = spec_dcd(precision)
     blob = pack_blob(spec, init_weights(spec, seed + 2000))
     return Workload("dcd_256", frames, cam, em, spec, blob, False)
+
+
+def workload_dilatedloc(T=256, H=256, W=256, precision="bf16", seed=3) -> Workload:
+    """The frames of workload_batched (same seed) through the full-topology net of spec_dilatedloc."""
+    rng = np.random.default_rng(seed)
+    em = emitters_density(rng, T, H, W, 1.0)
+    cam = Camera(1.0, 100.0)
+    frames = simulate(em, T, H, W, cam, False, rng)
+    spec = spec_dilatedloc(precision)
+    blob = pack_blob(spec, init_weights(spec, seed + 3000))
+    return Workload("dilatedloc_256", frames, cam, em, spec, blob, False)
 
 
 def workload_large_fov(T=2, H=2048, W=2048, precision="bf16", seed=4) -> Workload:

@@ -134,3 +134,57 @@ def test_valid_nine_head_nets_reach_the_device_check():
     spec = synth.NetSpec(in_ch=1, channels=32, dilations=(1, 1), n_heads=9, precision="bf16",
                          dcd={"growth": 16, "blocks": [[2, 4]]})
     assert _code(spec.to_json(), synth.pack_blob(spec, synth.init_weights(spec, 2))) == sml.SML_ERR_CUDA
+
+
+# ----------------------------------------------------------------------------- U-Net
+
+
+def _unet(levels=2, C=32, prec="bf16", dcd=None, dil=(1, 2, 1), n_heads=5):
+    spec = synth.NetSpec(in_ch=1, channels=C, dilations=tuple(dil), precision=prec, unet=levels, dcd=dcd,
+                         n_heads=n_heads)
+    return spec, spec.to_json(), synth.pack_blob(spec, synth.init_weights(spec, 8))
+
+
+def test_unet_layer_plan():
+    """The U-Net sits before the last layer: levels down convs C -> C, then levels up convs
+    2C -> C, all d = 1; version-2 blob with growth 0."""
+    spec, js, blob = _unet(2)
+    assert spec.layers() == [(1, 32, 1), (32, 32, 2), (32, 32, 1), (32, 32, 1), (64, 32, 1), (64, 32, 1), (32, 32, 1)]
+    assert json.loads(js)["unet"] == {"levels": 2} and blob[8:12] == (2).to_bytes(4, "little")
+    assert spec.R == 1 + 2 + 1 + 24
+
+
+@pytest.mark.parametrize("edit,code", [
+    (dict(unet={"levels": 3}), sml.SML_ERR_BAD_SPEC),
+    (dict(unet={"levels": 0}), sml.SML_ERR_BAD_SPEC),
+    (dict(unet={}), sml.SML_ERR_BAD_SPEC),
+    (dict(unet=2), sml.SML_ERR_BAD_SPEC),
+    (dict(precision="fp8", act_scales=[1.0] * 7), sml.SML_ERR_UNSUPPORTED),
+])
+def test_bad_unet_specs_are_refused(edit, code):
+    _, js, blob = _unet(2)
+    assert _code(json.dumps(dict(json.loads(js), **edit)), blob) == code
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_unet_up_conv_beyond_shared_memory_is_unsupported(prec):
+    """C = 64: the 128 -> 64 up convs do not fit (as for the dense-block transition)."""
+    _, js, blob = _unet(1, C=64, prec=prec)
+    assert _code(js, blob) == sml.SML_ERR_UNSUPPORTED
+
+
+def test_unet_blob_must_match():
+    _, js, blob = _unet(2)
+    _, _, blob1 = _unet(1)
+    assert _code(js, blob1) == sml.SML_ERR_BAD_WEIGHTS
+    plain = synth.NetSpec(in_ch=1, channels=32, dilations=(1, 2, 1), precision="bf16")
+    assert _code(js, synth.pack_blob(plain, synth.init_weights(plain, 1))) == sml.SML_ERR_BAD_WEIGHTS
+
+
+def test_valid_unet_nets_reach_the_device_check():
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    for kw in (dict(levels=1), dict(levels=2, prec="fp32"), dict(levels=2, dcd={"growth": 16, "blocks": [[2, 4]]}, n_heads=9),
+               dict(levels=2, C=48)):
+        _, js, blob = _unet(**kw)
+        assert _code(js, blob) == sml.SML_ERR_CUDA, kw
