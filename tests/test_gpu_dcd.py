@@ -4,7 +4,9 @@ Dense layers read a channel range of the block's concatenation buffer and append
 outputs to it; transitions write the next block input into the other buffer.  The FP32 path
 (SIMT) is compared with the float64 oracle (<= 1e-4, normalised max error per map); BF16
 (tensor cores) with the oracle's bf16 mode, which rounds weights and every stored activation
-where the library does (max <= 2e-2, RMS <= 2e-3), and with float64 (<= 3e-2)."""
+where the library does (max <= 2e-2, RMS <= 2e-3), and with float64 (<= 3e-2), each scaled by
+sqrt(n / 7) for n > 7 tensor-core layers (one-ulp rounding flips accumulate with depth; the
+base gates are those of the 8-layer net's 7)."""
 import json
 
 import numpy as np
@@ -48,6 +50,11 @@ def _maps(js, blob, frames, cam):
     got = maps.cpu().numpy().astype(np.float64)
     got[:, 0] = logits.cpu().numpy()
     return loc, maps, got
+
+
+def depth_scale(net):
+    """sqrt(n / 7) for n > 7 tensor-core layers (all conv layers after the first)."""
+    return float(np.sqrt(max(1.0, (net.L - 1) / 7.0)))
 
 
 def _err(got, ref):
@@ -100,7 +107,8 @@ def test_dcd_maps_match_oracle(prec, C, g, blocks, dil, in_ch):
     refq = oracle.forward(oracle.quantized(net, "bf16"), frames, quant="bf16", **_cam_kw(cam))
     eq, rq = _err(got, refq), _rms(got, refq)
     print(prec, C, g, "vs quantized", np.round(eq, 5), "rms", np.round(rq, 6), "vs float64", np.round(e, 4))
-    assert max(eq) <= TOL_Q and max(rq) <= TOL_Q_RMS and max(e) <= TOL["bf16"]
+    k = depth_scale(net)
+    assert max(eq) <= TOL_Q * k and max(rq) <= TOL_Q_RMS * k and max(e) <= TOL["bf16"] * k
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -143,8 +151,9 @@ def test_dcd_full_size_sampled():
         refq = oracle.forward_window(qnet, w.frames[t : t + 1], i0, i0 + 24, j0, j0 + 24, quant="bf16")
         worst = max(worst, max(_err(blk, ref)))
         worst_q = max(worst_q, max(_err(blk, refq)))
-    print("dcd full-size sampled worst", worst, "vs quantized", worst_q)
-    assert worst <= TOL["bf16"] and worst_q <= TOL_Q
+    k = depth_scale(net)
+    print("dcd full-size sampled worst", worst, "vs quantized", worst_q, "depth scale", k)
+    assert worst <= TOL["bf16"] * k and worst_q <= TOL_Q * k
     recs = loc.localize(w.frames, 0.5, capacity=4_000_000)
     want = oracle.decode(maps.cpu().numpy(), 0.5, net.z_scale, net.ph_scale)
     assert recs.tobytes() == want.tobytes()

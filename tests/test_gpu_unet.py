@@ -2,8 +2,10 @@
 through the C ABI: 2x2 max pooling and nearest upsampling kernels between resolution
 levels, convs on the half- and quarter-resolution buffers, the skip concatenation as an
 offset store.  FP32 against float64 (<= 1e-4); BF16 against the oracle's bf16 mode (max
-<= 2e-2, RMS <= 2e-3) and float64 (<= 3e-2); records bit-exact against the oracle's decode
-of the GPU maps."""
+<= 2e-2, RMS <= 2e-3) and float64 (<= 3e-2), each scaled by sqrt(n / 7) for n > 7
+tensor-core layers (independent one-ulp rounding flips accumulate with depth; the base gates
+are those of the 8-layer net's 7); records bit-exact against the oracle's decode of the GPU
+maps."""
 import json
 
 import numpy as np
@@ -38,6 +40,11 @@ def _maps(loc, frames, cam, nh):
     got = m.astype(np.float64)
     got[:, 0] = logits.cpu().numpy()
     return m, got
+
+
+def depth_scale(net):
+    """sqrt(n / 7) for n > 7 tensor-core layers (all conv layers after the first)."""
+    return float(np.sqrt(max(1.0, (net.L - 1) / 7.0)))
 
 
 def _err(got, ref, ks):
@@ -89,7 +96,8 @@ def test_unet_maps_and_records_match_oracle(prec, C, levels, dcd, dil, nh, size)
         eq, rq = _err(got, refq, range(5)), _rms(got, refq, range(5))
         print(prec, C, levels, dcd is not None, "vs quantized", np.round(eq, 5), "rms", np.round(rq, 6), "vs float64",
               np.round(e, 4))
-        assert max(eq) <= 2e-2 and max(rq) <= 2e-3 and max(e) <= 3e-2
+        k = depth_scale(net)
+        assert max(eq) <= 2e-2 * k and max(rq) <= 2e-3 * k and max(e) <= 3e-2 * k
     if nh == 9:
         want, want_sig = oracle.decode(maps, 0.5, net.z_scale, net.ph_scale, with_sigma=True)
         recs, sig = loc.localize_sigma(frames, 0.5, gain=cam.gain, offset=cam.offset, gain_map=cam.gain_map,
@@ -132,8 +140,9 @@ def test_full_topology_full_size_sampled():
         refq = oracle.forward_window(qnet, w.frames[t : t + 1], i0, i0 + 24, j0, j0 + 24, quant="bf16")
         worst = max(worst, max(_err(blk, ref, range(5))))
         worst_q = max(worst_q, max(_err(blk, refq, range(5))))
-    print("full topology sampled worst", worst, "vs quantized", worst_q)
-    assert worst <= 3e-2 and worst_q <= 2e-2
+    k = depth_scale(net)
+    print("full topology sampled worst", worst, "vs quantized", worst_q, "depth scale", k)
+    assert worst <= 3e-2 * k and worst_q <= 2e-2 * k
     want, want_sig = oracle.decode(maps, 0.5, net.z_scale, net.ph_scale, with_sigma=True)
     recs, sig = loc.localize_sigma(w.frames, 0.5, capacity=4_000_000)
     assert recs.tobytes() == want.tobytes() and sig.tobytes() == want_sig.tobytes()
