@@ -46,9 +46,24 @@ def conv_flops_per_px(C):
     return 2 * 9 * C * C
 
 
-def middle_layers(spec):
-    """(cin, cout, d) of the conv-class launches: every layer but the first and the last."""
-    return spec.layers()[1:-1]
+def conv_class_work(spec, px, elem_bytes):
+    """Algorithmic FLOPs and HBM bytes of one chunk's conv-class launches (every conv layer but
+    the first and the last, and the U-Net's pool and upsample launches) over px full-resolution
+    pixels, and the number of those launches.  A conv reads its ci input channels and writes
+    its co outputs once per pixel of its level (px / 4^level); a pool or upsample reads and
+    writes C channels at the two levels it joins."""
+    lay = spec.layers()
+    C, U = spec.channels, spec.unet
+    feat = lay[1 : len(lay) - 1 - 2 * U]
+    flops = sum(18 * ci * co for ci, co, _ in feat) * px
+    nbytes = sum(ci + co for ci, co, _ in feat) * px * elem_bytes
+    launches = len(feat)
+    for lv in range(1, U + 1):
+        lo, hi = px / 4 ** lv, px / 4 ** (lv - 1)
+        flops += 18 * C * C * lo + 18 * 2 * C * C * hi  # down conv at lv, up conv at lv - 1
+        nbytes += ((C + C) * lo + (2 * C + C) * hi + 2 * C * (lo + hi)) * elem_bytes  # convs, pool, upsample
+        launches += 4
+    return flops, nbytes, launches
 
 
 def algorithmic_flops_per_px(spec):
@@ -256,22 +271,30 @@ def small_latency_run(dev, stream, calls=50):
     return res
 
 
-def dcd_run(dev, stream, flush, reps=5):
-    """Dense connection dilated blocks (Sec. 3.2.1): the 256 frames of 256x256 of the main
-    workload through the 22-layer dense-block net (32 channels, growth 16, four blocks of
-    dilations 2, 4, 8, 16 with transitions), BF16 and FP32.  The conv-class kernels (dense
-    layers, transitions, plain middle layers) are timed with the library's event pairs; their
-    algorithmic HBM bytes are one read of every input channel and one write of every output
-    channel per pixel and layer (BF16: 2 bytes each)."""
+TOPOLOGIES = {
+    "dcd": ("dcd_{T}x{H}x{W}_32ch_g16_4x4dense_22layer", "workload_dcd"),
+    "dilatedloc": ("dilatedloc_{T}x{H}x{W}_32ch_g16_4x4dense_unet2_9heads_26layer", "workload_dilatedloc"),
+}
+
+
+def topology_run(dev, stream, flush, which, reps=5):
+    """The paper's topology beyond the plain stack: the 256 frames of 256x256 of the main
+    workload through the 22-layer dense-block net ("dcd": 32 channels, growth 16, four blocks
+    of dilations 2, 4, 8, 16 with transitions; Sec. 3.2.1) or the full topology ("dilatedloc":
+    those blocks, a two-level U-Net and the nine heads with uncertainties; Sec. 3.2), BF16 and
+    FP32.  The conv-class kernels (dense layers, transitions, U-Net convs, pools and upsamples)
+    are timed with the library's event pairs; their algorithmic HBM bytes are one read of
+    every input channel and one write of every output channel per pixel of their level."""
     import torch
 
     import paper_2410_02314_gb300 as sml
     from paper_2410_02314_gb300 import synth
 
-    res = {"workload": f"dcd_{T_FRAMES}x{H}x{W}_32ch_g16_4x4dense_22layer", "l2": "flushed between calls"}
+    name, maker = TOPOLOGIES[which]
+    res = {"workload": name.format(T=T_FRAMES, H=H, W=W), "l2": "flushed between calls"}
     pk, pk_kind = peaks()
     for prec in ("bf16", "fp32"):
-        w = synth.workload_dcd(T=T_FRAMES, H=H, W=W, precision=prec)
+        w = getattr(synth, maker)(T=T_FRAMES, H=H, W=W, precision=prec)
         loc = sml.Localizer(w.spec.to_json(), w.blob)
         d_frames = torch.from_numpy(w.frames).to(dev)
         d_out = torch.empty(T_FRAMES * H * W // 4 * 24, dtype=torch.uint8, device=dev)
@@ -293,10 +316,7 @@ def dcd_run(dev, stream, flush, reps=5):
         res[f"{prec}_frames_per_s"] = T_FRAMES / (ms / 1000)
         res[f"{prec}_launches_per_call"] = loc.last_launch_count
         if prec == "bf16":
-            mid = w.spec.layers()[1:-1]  # the conv-class launches of one chunk
-            px = T_FRAMES * H * W
-            nbytes = sum(2 * (ci + co) for ci, co, _ in mid) * px
-            flops = sum(18 * ci * co for ci, co, _ in mid) * px
+            flops, nbytes, _ = conv_class_work(w.spec, T_FRAMES * H * W, 2)
             conv_s = conv_ms / reps / 1000.0
             res.update({"bf16_conv_ms_per_call": conv_ms / reps, "bf16_records_per_call": int(d_n.item()),
                         "conv_algorithmic_bytes_per_call": nbytes, "conv_hbm_gbs": nbytes / conv_s / 1e9,
@@ -372,8 +392,9 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
     ap.add_argument("--frames", type=int, default=T_FRAMES,
                     help="frames per step (default 256; smaller stacks for profiler captures)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "dcd"],
-                    help="batched: the 48-channel 8-layer net; dcd: the 22-layer dense-block net (fp32/bf16)")
+    ap.add_argument("--workload", default="batched", choices=["batched", "dcd", "dilatedloc"],
+                    help="batched: the 48-channel 8-layer net; dcd: the 22-layer dense-block net; dilatedloc: the "
+                         "full topology (dense blocks, U-Net, uncertainty heads); dcd and dilatedloc run fp32/bf16")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk-px", type=int, default=0)
     ap.add_argument("--tc-stages", type=int, default=0)
@@ -408,11 +429,12 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    if args.workload == "dcd" and args.precision == "fp8":
-        raise SystemExit("the dense-block net runs in fp32 or bf16")
+    if args.workload != "batched" and args.precision == "fp8":
+        raise SystemExit("the dense-block and full-topology nets run in fp32 or bf16")
 
     def workload(prec, d_frames=None):
-        make = synth.workload_dcd if args.workload == "dcd" else synth.workload_batched
+        make = {"batched": synth.workload_batched, "dcd": synth.workload_dcd,
+                "dilatedloc": synth.workload_dilatedloc}[args.workload]
         w = make(T=T_FRAMES, H=H, W=W, precision="bf16" if prec == "fp8" else prec, seed=replicas.frame_seed(3, rank))
         spec = json.loads(w.spec.to_json())
         if args.chunk_px:
@@ -475,11 +497,10 @@ def main():
     frames_per_chunk = max(1, chunk_px // (H * W))
     px_per_launch = min(frames_per_chunk, T_FRAMES) * H * W
     pk, pk_kind = peaks()
-    mid = middle_layers(w.spec)
-    # per launch: the conv-class FLOPs of one step spread over its launches (all equal for a plain stack)
-    flops_launch = sum(conv_flops_per_px(1) * ci * co for ci, co, _ in mid) / len(mid) * px_per_launch
-    bytes_launch = sum(ci + co for ci, co, _ in mid) / len(mid) * px_per_launch * (2 if args.precision == "bf16" else (
-        1 if args.precision == "fp8" else 4))
+    # per launch: the conv-class FLOPs and bytes of one chunk spread over its launches (all
+    # equal for a plain stack)
+    fl, nb, n_launch = conv_class_work(w.spec, px_per_launch, {"bf16": 2, "fp8": 1, "fp32": 4}[args.precision])
+    flops_launch, bytes_launch = fl / n_launch, nb / n_launch
     avg_conv_s = conv_ms / max(conv_n, 1) / 1000.0
     achieved = flops_launch / avg_conv_s / 1e12
     if args.precision == "bf16":
@@ -491,7 +512,7 @@ def main():
     else:
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         peak_note = "fp32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz (derived, not measured)"
-    traffic = profiled_traffic(args.precision, "batched256" if args.workload == "batched" else "dcd256")
+    traffic = profiled_traffic(args.precision, {"batched": "batched256", "dcd": "dcd256"}.get(args.workload, ""))
     hbm = {"algorithmic_bytes_per_launch": bytes_launch, "algorithmic_gbs": bytes_launch / avg_conv_s / 1e9,
            "peak_gbs": pk["hbm_gbs"], "algorithmic_frac": bytes_launch / avg_conv_s / 1e9 / pk["hbm_gbs"]}
     if traffic is not None:
@@ -526,7 +547,7 @@ def main():
 
     extra = {}
     others = [] if args.no_fp32 else [p for p in ("fp32", "bf16", "fp8")
-                                      if p != args.precision and not (args.workload == "dcd" and p == "fp8")]
+                                      if p != args.precision and not (args.workload != "batched" and p == "fp8")]
     for prec in others:  # the same batch at the other precisions, same timing method
         wo, jso = workload(prec, d_frames)
         loco = sml.Localizer(jso, wo.blob)
@@ -555,7 +576,7 @@ def main():
         large_fov = large_fov_run(dev, stream, flush)
         small = small_latency_run(dev, stream)
         file_pipe = file_pipeline_run(spec_json, w.blob, w.frames, w.cam)
-        dcd = dcd_run(dev, stream, flush) if args.workload == "batched" else None
+        dcd = ({k: topology_run(dev, stream, flush, k) for k in TOPOLOGIES} if args.workload == "batched" else None)
 
     if rank != 0:
         if dist:
@@ -578,7 +599,7 @@ def main():
         "dtype": args.precision,
         "data": "synthetic",
         "config": {"workload": f"batched_{T_FRAMES}x{H}x{W}_48ch_8layer" if args.workload == "batched"
-                   else f"dcd_{T_FRAMES}x{H}x{W}_32ch_g16_4x4dense_22layer", "frames_per_step": T_FRAMES,
+                   else TOPOLOGIES[args.workload][0].format(T=T_FRAMES, H=H, W=W), "frames_per_step": T_FRAMES,
                    "precision": args.precision, "chunk_px": chunk_px, "tc_stages": args.tc_stages or "max",
                    "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas{world}"},
@@ -594,7 +615,7 @@ def main():
         "large_fov": large_fov,
         "small_latency": small,
         "file_pipeline": file_pipe,
-        "dcd": dcd,
+        "topologies": dcd,
         **extra,
     }
     print(json.dumps(line), flush=True)
