@@ -43,6 +43,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <type_traits>
+
 #include "sml_internal.h"
 
 namespace sml {
@@ -301,6 +303,21 @@ __device__ __forceinline__ int unit_rows(const TcKArgs& a, uint32_t u, int seg, 
   return n < 0 ? 0 : (n > seg ? seg : n);
 }
 
+// The MMAs of one input row: for each horizontal tap kx and K step ks one M=128 MMA, fully
+// unrolled for a compile-time count of K steps.  The issuing warp then runs no per-MMA loop
+// arithmetic between the MMAs (measured: such arithmetic slows the issue of small-N MMAs by
+// about a third).  A offsets: kx*a_kx + ks*a_ks (16-byte units); B blocks BBLK16 apart.
+template <int PREC, int NKS, int BBLK16, int MAXK>
+__device__ __forceinline__ void issue_row(uint32_t d_col, uint64_t a_st, uint64_t b_row, uint32_t idesc,
+                                          const uint32_t (&a_off)[3][MAXK], uint32_t leader) {
+  static_assert(NKS <= MAXK, "K steps beyond the precomputed offsets");
+#pragma unroll
+  for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+    for (int ks = 0; ks < NKS; ++ks)
+      umma_if<PREC>(d_col, a_st + a_off[kx][ks], b_row + (uint64_t)((kx * NKS + ks) * BBLK16), idesc, leader);
+}
+
 // Fused 1x1 heads of the last layer for one pixel (Sec. 3.2): h_k = b_k + sum_c w_kc v_c with
 // p = sigmoid(h_0) (the logit is also stored when requested), h_1..h_4 as they are, and the
 // uncertainty heads h_5..h_8 (NH = 9) through softplus.  Maps are [T][NH][H][W].
@@ -465,50 +482,69 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       const uint32_t a_ks = PREC == kBF16 ? (a.plane_stride >> 4) : (a.plane_stride >> 3);
       const uint32_t stage16 = a.stage_bytes >> 4;
       const uint32_t nst = (uint32_t)a.nstages;
-      uint32_t st = 0;             // stage of the current row
-      uint64_t a_st = a_desc0;     // descriptor of the current stage
-      uint32_t hand = 0;           // handoffs taken
-      bool issued = false;
-      for (uint32_t u = u_begin; u < u_end; ++u) {
-        int t, j0, phi, q;
-        const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
-        if (n_out == 0) continue;
-        for (int kk = 0; kk < n_out + 2; ++kk) {
-          if ((kk & (hand_rows - 1)) == 0) {
-            // the waiter has seen this group's TMA data and TMEM releases complete
-            named_sync(1u + (hand & 1u));
-            ++hand;
-            fence_after_sync();
-          }
-          // blocks b (output rows kk-b) of this input row that belong to the unit
-          const int b_lo = kk - n_out + 1 > 0 ? kk - n_out + 1 : 0;
-          const int b_hi = kk < 2 ? kk : 2;
-          const int nb = b_hi - b_lo + 1;
-          const uint32_t d_col = tmem + Cfg::BASE0 - (uint32_t)(CO * kk) + (uint32_t)(CO * b_lo);
-          const uint32_t b_sub = (uint32_t)(2 * CO * b_lo);  // 32*CO*b_lo bytes in 16-byte units
-          const uint32_t idesc_n = nb == 3 ? Cfg::IDESC3 : (nb == 2 ? Cfg::IDESC2 : Cfg::IDESC1);
+      // The whole row loop is instantiated per count of K steps and selected once per CTA:
+      // a per-row branch on it cost about 200 cycles per row (its jump-table load waits
+      // behind the MMAs in flight, like any load this thread consumes).
+      auto mma_loop = [&](auto nk_c) {
+        constexpr int NK = decltype(nk_c)::value;
+        // every (kx, ks) offset once per CTA, kept in registers (the row loop only adds them)
+        uint32_t a_off[3][NK];
 #pragma unroll
-          for (int kx = 0; kx < 3; ++kx)
+        for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
-            for (int ks = 0; ks < nks; ++ks) {
-              const uint64_t ad = a_st + (uint32_t)kx * a_kx + (uint32_t)ks * a_ks;
-              const uint64_t bd = b_desc0 + (uint64_t)((uint32_t)(kx * nks + ks) * (uint32_t)(Cfg::BBLK >> 4)) + b_sub;
-              umma_if<PREC>(d_col, ad, bd, idesc_n, leader);
+          for (int ks = 0; ks < NK; ++ks) a_off[kx][ks] = (uint32_t)kx * a_kx + (uint32_t)ks * a_ks;
+        uint32_t st = 0;             // stage of the current row
+        uint64_t a_st = a_desc0;     // descriptor of the current stage
+        uint32_t hand = 0;           // handoffs taken
+        bool issued = false;
+        for (uint32_t u = u_begin; u < u_end; ++u) {
+          int t, j0, phi, q;
+          const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
+          if (n_out == 0) continue;
+          for (int kk = 0; kk < n_out + 2; ++kk) {
+            if ((kk & (hand_rows - 1)) == 0) {
+              // the waiter has seen this group's TMA data and TMEM releases complete
+              named_sync(1u + (hand & 1u));
+              ++hand;
+              fence_after_sync();
             }
-          issued = true;
-          if (kk >= 2 && kk - 2 < n_out) umma_commit_if(smem_u32(&accf_bar[kk - 2]), leader);
-          umma_commit_if(smem_u32(&empty_bar[st]), leader);
-          if (++st == nst) {
-            st = 0;
-            a_st = a_desc0;
-          } else {
-            a_st += stage16;
+            // blocks b (output rows kk-b) of this input row that belong to the unit
+            const int b_lo = kk - n_out + 1 > 0 ? kk - n_out + 1 : 0;
+            const int b_hi = kk < 2 ? kk : 2;
+            const int nb = b_hi - b_lo + 1;
+            const uint32_t d_col = tmem + Cfg::BASE0 - (uint32_t)(CO * kk) + (uint32_t)(CO * b_lo);
+            const uint32_t b_sub = (uint32_t)(2 * CO * b_lo);  // 32*CO*b_lo bytes in 16-byte units
+            const uint32_t idesc_n = nb == 3 ? Cfg::IDESC3 : (nb == 2 ? Cfg::IDESC2 : Cfg::IDESC1);
+            issue_row<PREC, NK, (Cfg::BBLK >> 4)>(d_col, a_st, b_desc0 + b_sub, idesc_n, a_off, leader);
+            issued = true;
+            if (kk >= 2 && kk - 2 < n_out) umma_commit_if(smem_u32(&accf_bar[kk - 2]), leader);
+            umma_commit_if(smem_u32(&empty_bar[st]), leader);
+            if (++st == nst) {
+              st = 0;
+              a_st = a_desc0;
+            } else {
+              a_st += stage16;
+            }
           }
         }
-      }
-      if (issued && leader) {  // all MMAs of this CTA complete before TMEM is released
-        umma_commit(smem_u32(&drain_bar[0]));
-        mbar_wait_own(smem_u32(&drain_bar[0]), 0, a.err, s_abort);
+        if (issued && leader) {  // all MMAs of this CTA complete before TMEM is released
+          umma_commit(smem_u32(&drain_bar[0]));
+          mbar_wait_own(smem_u32(&drain_bar[0]), 0, a.err, s_abort);
+        }
+      };
+      if constexpr (CI > 0) {
+        mma_loop(std::integral_constant<int, Cfg::NKS>{});
+      } else {
+        switch (nks) {
+          case 1: mma_loop(std::integral_constant<int, 1>{}); break;
+          case 2: mma_loop(std::integral_constant<int, 2>{}); break;
+          case 3: mma_loop(std::integral_constant<int, 3>{}); break;
+          case 4: mma_loop(std::integral_constant<int, 4>{}); break;
+          case 5: mma_loop(std::integral_constant<int, 5>{}); break;
+          case 6: mma_loop(std::integral_constant<int, 6>{}); break;
+          case 7: mma_loop(std::integral_constant<int, 7>{}); break;
+          default: mma_loop(std::integral_constant<int, 8>{}); break;
+        }
       }
       __syncwarp();
     }
