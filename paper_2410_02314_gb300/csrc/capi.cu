@@ -167,6 +167,7 @@ struct Plan {
   float* maps = nullptr;
   unsigned* block_counts = nullptr;
   unsigned long long* block_offsets = nullptr;
+  unsigned* flag_words = nullptr;  // decode: the count pass's detection ballots
   uint16_t* frames = nullptr;  // staging for host frames
   float* cam_maps = nullptr;   // staging for host camera maps [2][H][W]
   CUtensorMap tmap[kMaxLayers];  // per layer, over its input buffer: one box per row (width depends on d)
@@ -300,6 +301,7 @@ void free_plan(Plan& p) {
   cudaFree(p.maps);
   cudaFree(p.block_counts);
   cudaFree(p.block_offsets);
+  cudaFree(p.flag_words);
   cudaFree(p.frames);
   cudaFree(p.cam_maps);
   p = Plan();
@@ -391,6 +393,7 @@ int get_plan(sml_ctx* ctx, int H, int W) {
   if ((r = dev_alloc(ctx, &p.maps, npx * ctx->nh * sizeof(float))) ||
       (r = dev_alloc(ctx, &p.block_counts, decode_blocks(npx) * sizeof(unsigned))) ||
       (r = dev_alloc(ctx, &p.block_offsets, decode_blocks(npx) * sizeof(unsigned long long))) ||
+      (r = dev_alloc(ctx, &p.flag_words, decode_blocks(npx) * (kDecodePxPerBlock / 32) * sizeof(unsigned))) ||
       (r = dev_alloc(ctx, &p.frames, (size_t)(Tc + 2) * hw * sizeof(uint16_t))) ||  // + context frames
       (r = dev_alloc(ctx, &p.cam_maps, 2 * hw * sizeof(float)))) {
     free_plan(p);
@@ -595,6 +598,7 @@ int localize_device(sml_ctx* ctx, const uint16_t* d_frames, bool frames_on_host,
     da.total = d_n;
     da.block_counts = p.block_counts;
     da.block_offsets = p.block_offsets;
+    da.flag_words = p.flag_words;
     ProfScope ps(ctx, SML_KERNEL_DECODE, s);
     SML_CUDA(launch_decode(da, s, &ctx->launches), "decode");
   }
@@ -1136,6 +1140,7 @@ int sml_decode_maps(sml_ctx* ctx, const float* d_maps, int T, int H, int W, cons
     da.total = d_n_out;
     da.block_counts = p.block_counts;
     da.block_offsets = p.block_offsets;
+    da.flag_words = p.flag_words;
     ProfScope ps(ctx, SML_KERNEL_DECODE, s);
     SML_CUDA(launch_decode(da, s, &ctx->launches), "decode");
   }

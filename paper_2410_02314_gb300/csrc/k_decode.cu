@@ -10,7 +10,9 @@
 // Order: three kernels give (frame, row, column) order without atomics.  Each block owns
 // 1024 consecutive pixels (4 passes of 256 threads); count -> exclusive scan of the block
 // counts (plus a running total that carries over chunks) -> write at block offset + rank,
-// where the rank inside a block comes from warp ballots.
+// where the rank inside a block comes from warp ballots.  The count pass stores its ballots
+// (one bit per pixel) when given room for them, and the write pass then reads them instead of
+// evaluating the 3x3 neighbourhoods again.
 #include "sml_internal.h"
 
 namespace sml {
@@ -93,10 +95,15 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode_count(DecodeArgs a) {
   bool flag[kPxPerThread];
   dec_locate(a, q0, loc);
   dec_flags<NH>(a, loc, flag);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned cnt = 0;
 #pragma unroll
-  for (int k = 0; k < kPxPerThread; ++k) cnt += __popc(__ballot_sync(0xffffffffu, flag[k]));
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < kPxPerThread; ++k) {
+    const unsigned b = __ballot_sync(0xffffffffu, flag[k]);
+    cnt += __popc(b);
+    if (a.flag_words && lane == 0)
+      a.flag_words[((size_t)blockIdx.x * kPxPerThread + k) * (kDecodeThreads / 32) + warp] = b;
+  }
   if (lane == 0) warp_sum[warp] = cnt;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -144,8 +151,9 @@ __global__ void __launch_bounds__(1024) k_decode_scan(DecodeArgs a, long long nb
   if (threadIdx.x == 0) *a.total = carry;
 }
 
-// SIGMA: also write the uncertainties of each record (9-head maps).
-template <int NH, bool SIGMA>
+// SIGMA: also write the uncertainties of each record (9-head maps).  STORED: the detections
+// come from the count pass's ballots (a.flag_words) instead of the maps' neighbourhoods.
+template <int NH, bool SIGMA, bool STORED>
 __global__ void __launch_bounds__(kDecodeThreads) k_decode_write(DecodeArgs a) {
   __shared__ unsigned warp_cnt[kPxPerThread][kDecodeThreads / 32];
   const long long q0 = (long long)blockIdx.x * kDecodePxPerBlock;
@@ -153,13 +161,18 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode_write(DecodeArgs a) {
   PxLoc loc[kPxPerThread];
   bool flag[kPxPerThread];
   dec_locate(a, q0, loc);
-  dec_flags<NH>(a, loc, flag);
+  if (!STORED) dec_flags<NH>(a, loc, flag);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   unsigned bal[kPxPerThread];
 #pragma unroll
   for (int k = 0; k < kPxPerThread; ++k) {
-    bal[k] = __ballot_sync(0xffffffffu, flag[k]);
+    if (STORED) {
+      bal[k] = a.flag_words[((size_t)blockIdx.x * kPxPerThread + k) * (kDecodeThreads / 32) + warp];
+      flag[k] = (bal[k] >> lane) & 1u;
+    } else {
+      bal[k] = __ballot_sync(0xffffffffu, flag[k]);
+    }
     if (lane == 0) warp_cnt[k][warp] = __popc(bal[k]);
   }
   __syncthreads();
@@ -213,12 +226,17 @@ cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int* launches) {
   else
     k_decode_count<kHeads><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
   k_decode_scan<<<1, 1024, 0, s>>>(a, nb);
-  if (a.nh == kMaxHeads && a.out_sigma)
-    k_decode_write<kMaxHeads, true><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
-  else if (a.nh == kMaxHeads)
-    k_decode_write<kMaxHeads, false><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
-  else
-    k_decode_write<kHeads, false><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+  const bool st = a.flag_words != nullptr;
+  if (a.nh == kMaxHeads && a.out_sigma) {
+    if (st) k_decode_write<kMaxHeads, true, true><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+    else k_decode_write<kMaxHeads, true, false><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+  } else if (a.nh == kMaxHeads) {
+    if (st) k_decode_write<kMaxHeads, false, true><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+    else k_decode_write<kMaxHeads, false, false><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+  } else {
+    if (st) k_decode_write<kHeads, false, true><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+    else k_decode_write<kHeads, false, false><<<(unsigned)nb, kDecodeThreads, 0, s>>>(a);
+  }
   if (launches) *launches += 3;
   return cudaGetLastError();
 }

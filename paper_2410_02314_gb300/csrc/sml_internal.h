@@ -30,6 +30,9 @@ struct DecodeArgs {
   unsigned long long* total;  // running count (device); updated by the scan kernel
   unsigned int* block_counts;  // [nblocks]
   unsigned long long* block_offsets;  // [nblocks]
+  // [nblocks][kDecodePxPerBlock / 32] detection ballots of the count pass, reused by the write
+  // pass; NULL: the write pass evaluates the detections again
+  unsigned int* flag_words = nullptr;
 };
 
 constexpr int kDecodeThreads = 256;
