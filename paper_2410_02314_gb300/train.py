@@ -157,6 +157,9 @@ class DilatedLocNet(torch.nn.Module):
         super().__init__()
         if weights.bn is not None:
             raise ValueError("train a net without BatchNorm (fold it first)")
+        if spec.dcd or spec.unet or spec.n_heads != synth.N_HEADS or spec.in_ch != 1:
+            raise ValueError("training covers the plain dilated stack with the five position heads and one input "
+                             "frame (no dense blocks, U-Net, uncertainty heads or three-frame input)")
         self.spec = spec
         self.w = torch.nn.ParameterList([torch.nn.Parameter(torch.tensor(a, dtype=torch.float32)) for a in weights.conv_w])
         self.b = torch.nn.ParameterList([torch.nn.Parameter(torch.tensor(a, dtype=torch.float32)) for a in weights.conv_b])
@@ -168,8 +171,10 @@ class DilatedLocNet(torch.nn.Module):
         s = json.loads(spec_json)
         spec = synth.NetSpec(in_ch=s.get("in_ch", 1), channels=s["channels"], dilations=tuple(s["dilations"]),
                              precision=s.get("precision", "fp32"), in_scale=s.get("in_scale", 1e-3),
-                             z_scale=s.get("z_scale", 1000.0), ph_scale=s.get("ph_scale", 10000.0))
-        return cls(spec, synth.unpack_blob(blob)[1])
+                             z_scale=s.get("z_scale", 1000.0), ph_scale=s.get("ph_scale", 10000.0),
+                             dcd=s.get("dcd"), unet=int((s.get("unet") or {}).get("levels", 0)),
+                             n_heads=len(s.get("heads", synth.HEAD_NAMES[: synth.N_HEADS])))
+        return cls(spec, synth.unpack_blob(blob, spec)[1])
 
     def features(self, frames, gain=1.0, offset=100.0):
         x = sml_train_ingest(frames.contiguous(), gain, offset, self.spec.in_scale).unsqueeze(-1)

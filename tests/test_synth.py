@@ -66,3 +66,18 @@ def test_training_targets():
     m = tgt[:, 0] > 0.5
     assert m.sum() <= em.x.size
     assert np.all(np.abs(tgt[:, 1][m]) <= 0.5 + 1e-6) and np.all(np.abs(tgt[:, 2][m]) <= 0.5 + 1e-6)
+
+
+def test_training_net_refuses_topologies_it_cannot_train():
+    """The training kernels cover the plain stack with five heads and one input frame; other
+    specs are refused when the trainable net is built, not trained wrongly."""
+    import pytest
+
+    from paper_2410_02314_gb300.train import DilatedLocNet
+
+    plain = synth.NetSpec(in_ch=1, channels=16, dilations=(1, 2, 1))
+    DilatedLocNet.from_blob(plain.to_json(), synth.pack_blob(plain, synth.init_weights(plain, 1)))
+    for kw in (dict(dcd={"growth": 16, "blocks": [[2]]}), dict(unet=1), dict(n_heads=9), dict(in_ch=3)):
+        spec = synth.NetSpec(**{**plain.__dict__, **kw})
+        with pytest.raises(ValueError):
+            DilatedLocNet.from_blob(spec.to_json(), synth.pack_blob(spec, synth.init_weights(spec, 1)))
