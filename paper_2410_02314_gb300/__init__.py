@@ -61,6 +61,7 @@ EXPORTS = (
     "sml_reader_stats",
     "sml_reader_close",
     "sml_localize_file",
+    "sml_sim_frames",
 )
 SML_KERNEL_LAYER1, SML_KERNEL_CONV, SML_KERNEL_CONV_HEADS, SML_KERNEL_DECODE = 0, 1, 2, 3
 
@@ -149,6 +150,9 @@ def lib():
         L.sml_localize_file.argtypes = [P, ctypes.c_char_p, LL, I, I, I, ctypes.POINTER(_Camera),
                                         ctypes.POINTER(_Thresholds), I, P, S, ctypes.POINTER(S), ctypes.POINTER(IoStats)]
         L.sml_localize_file.restype = I
+        L.sml_sim_frames.argtypes = [P, P, P, P, P, LL, P, I, I, I, I, F, ctypes.POINTER(_Camera), ctypes.c_ulonglong,
+                                     LL, I, P, P]
+        L.sml_sim_frames.restype = I
         _lib = L
     return _lib
 
@@ -231,6 +235,35 @@ def sml_localize(ctx, frames, p_min, gain=1.0, offset=100.0, gain_map=None, offs
     if hasattr(out_arr, "data_ptr"):
         return out_arr[: n.value * RECORD_DTYPE.itemsize]
     return out_arr[: n.value]
+
+
+def sml_sim_frames(emitters, T, H, W, astig=False, sigma0=1.3, gain=1.0, offset=100.0, gain_map=None,
+                   offset_map=None, seed=0, frame0=0, noise=True, d_adu=None, d_mu=None):
+    """Simulated frames on the device (include/sml_sim.h).  emitters: an object with numpy
+    arrays frame, x, y, z, photons (one entry per emitter) and bg (one per frame), e.g.
+    synth.Emitters.  Returns d_adu: a CUDA int16 tensor [T,H,W] holding the uint16 ADU bits
+    (view it as uint16 on the host), allocated unless given; d_mu (optional CUDA float32
+    [T,H,W]) receives the expected image."""
+    import torch
+
+    fr = np.ascontiguousarray(emitters.frame, dtype=np.int32)
+    xs = np.ascontiguousarray(emitters.x, dtype=np.float32)
+    ys = np.ascontiguousarray(emitters.y, dtype=np.float32)
+    zs = np.ascontiguousarray(emitters.z, dtype=np.float32)
+    ph = np.ascontiguousarray(emitters.photons, dtype=np.float32)
+    bg = np.ascontiguousarray(emitters.bg, dtype=np.float32)
+    if bg.size != T:
+        raise ValueError("bg needs one entry per frame")
+    if d_adu is None:
+        d_adu = torch.empty((T, H, W), dtype=torch.int16, device="cuda")
+    cam = _camera(gain, offset, gain_map, offset_map)
+    code = lib().sml_sim_frames(fr.ctypes.data, xs.ctypes.data, ys.ctypes.data, zs.ctypes.data, ph.ctypes.data,
+                                int(fr.size), bg.ctypes.data, int(T), int(H), int(W), int(bool(astig)), float(sigma0),
+                                ctypes.byref(cam), int(seed) & 0xFFFFFFFFFFFFFFFF, int(frame0), int(bool(noise)),
+                                _ptr(d_adu), _ptr(d_mu))
+    if code != SML_OK:
+        raise SmlError(code, "sml_sim_frames failed")
+    return d_adu
 
 
 def sml_num_heads(ctx) -> int:
