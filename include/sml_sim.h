@@ -41,7 +41,8 @@ extern "C" {
  * offset, or device maps [H][W].  noise = 0 gives adu from mu without Poisson noise.
  * frame0: index of the call's first frame in its stack (the noise of a frame depends only
  * on seed, frame0 + t and the pixel).  Synchronous.  Errors: SML_ERR_BAD_ARG (sizes, frame
- * indices, NULL pointers, non-positive sigma0 or gain), SML_ERR_OOM, SML_ERR_CUDA.
+ * indices, NULL pointers, non-positive sigma0 or gain, 2^31 or more emitters or 16 x 16 tiles
+ * in one call), SML_ERR_OOM, SML_ERR_CUDA.
  */
 int sml_sim_frames(const int32_t* frame, const float* x, const float* y, const float* z, const float* photons,
                    long long n, const float* bg, int T, int H, int W, int astig, float sigma0, const sml_camera* cam,

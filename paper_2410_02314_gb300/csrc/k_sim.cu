@@ -160,6 +160,7 @@ extern "C" int sml_sim_frames(const int32_t* frame, const float* x, const float*
   if (T == 0) return SML_OK;
   const int ntx = (W + kTile - 1) / kTile, nty = (H + kTile - 1) / kTile;
   const long long nbins = (long long)T * ntx * nty;
+  if (nbins >= (1LL << 31) || n >= (1LL << 31)) return SML_ERR_BAD_ARG;  // tile bins and offsets are 32-bit
   // widths, PSF window and tile bins on the host
   std::vector<SimEmitter> em((size_t)n);
   std::vector<int> key((size_t)n);
