@@ -146,3 +146,40 @@ def test_full_topology_full_size_sampled():
     want, want_sig = oracle.decode(maps, 0.5, net.z_scale, net.ph_scale, with_sigma=True)
     recs, sig = loc.localize_sigma(w.frames, 0.5, capacity=4_000_000)
     assert recs.tobytes() == want.tobytes() and sig.tobytes() == want_sig.tobytes()
+
+
+def test_full_topology_with_three_frame_input_across_chunk_edges():
+    """Dense blocks + U-Net + nine heads with the three-frame input: chunks of two frames read
+    their neighbours; maps equal the single-chunk run bit for bit and match the bf16 oracle."""
+    spec = synth.NetSpec(in_ch=3, channels=16, dilations=(1, 1), precision="bf16", n_heads=9, unet=2,
+                         dcd={"growth": 16, "blocks": [[2, 4]]})
+    blob = synth.pack_blob(spec, synth.init_weights(spec, 41))
+    T, H, W = 5, 40, 70
+    rng = np.random.default_rng(43)
+    frames = rng.integers(95, 900, (T, H, W)).astype(np.uint16)
+    cam = synth.Camera(2.0, 100.0)
+    one, got = _maps(sml.Localizer(spec.to_json(), blob), frames, cam, 9)
+    small = json.dumps(dict(json.loads(spec.to_json()), chunk_px=2 * H * W))
+    two, _ = _maps(sml.Localizer(small, blob), frames, cam, 9)
+    assert np.array_equal(one, two)
+    net = oracle.Net(spec.to_json(), blob)
+    refq = oracle.forward(oracle.quantized(net, "bf16"), frames, gain=2.0, offset=100.0, quant="bf16")
+    assert max(_err(got, refq, range(5))) <= 2e-2 * depth_scale(net)
+
+
+def test_stack_file_pipeline_on_the_full_topology(tmp_path):
+    """The stack-file pipeline (reader thread, pinned ring, overlapped copies) runs any one-frame
+    net: its records equal one sml_localize call on the same frames."""
+    spec = synth.NetSpec(in_ch=1, channels=16, dilations=(1, 1), precision="bf16", n_heads=9, unet=2,
+                         dcd={"growth": 16, "blocks": [[2, 4]]})
+    blob = synth.pack_blob(spec, synth.init_weights(spec, 47))
+    T, H, W = 37, 64, 96
+    rng = np.random.default_rng(5)
+    em = synth.emitters_density(rng, T, H, W, 2.0)
+    frames = synth.simulate(em, T, H, W, synth.Camera(1.0, 100.0), False, rng)
+    path = tmp_path / "stack.raw"
+    frames.tofile(path)
+    loc = sml.Localizer(spec.to_json(), blob)
+    recs, _ = loc.localize_file(str(path), T, H, W, 0.5, batch=8)
+    want = loc.localize(frames, 0.5)
+    assert len(want) > 0 and recs.tobytes() == want.tobytes()
