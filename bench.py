@@ -530,11 +530,26 @@ def main():
            "peak_gbs": pk["hbm_gbs"], "algorithmic_frac": bytes_launch / avg_conv_s / 1e9 / pk["hbm_gbs"]}
     if traffic is not None:
         hbm.update({"achieved_gbs": traffic / avg_conv_s / 1e9, "frac": traffic / avg_conv_s / 1e9 / pk["hbm_gbs"]})
-    roofline = {"bound": "tensor" if args.precision != "fp32" else "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "kernel": "k_dconv_tc (middle layers)"
-                if args.precision != "fp32" else "k_dconv_f32 (middle layers)", "peak_kind": peak_note,
-                "flops_per_launch": flops_launch, "launches": conv_n, "avg_launch_ms": avg_conv_s * 1000,
-                "hbm": hbm}
+    compute = {"achieved_tflops": achieved, "peak_tflops": peak, "frac": achieved / peak, "peak_kind": peak_note,
+               "flops_per_launch": flops_launch}
+    # the roofline's bound: HBM when the launch's intensity (FLOP per algorithmic byte) is below
+    # the ridge (compute peak / copy bandwidth), else the compute unit
+    kernel = "k_dconv_tc (middle layers)" if args.precision != "fp32" else "k_dconv_f32 (middle layers)"
+    if flops_launch / bytes_launch < peak * 1e12 / (pk["hbm_gbs"] * 1e9):
+        roofline = {"bound": "hbm", "achieved": hbm["algorithmic_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": hbm["algorithmic_frac"], "traffic": traffic, "kernel": kernel,
+                    "peak_kind": f"copy bandwidth ({pk_kind})", "algorithmic_bytes_per_launch": bytes_launch,
+                    "launches": conv_n, "avg_launch_ms": avg_conv_s * 1000,
+                    "intensity_flop_per_byte": flops_launch / bytes_launch,
+                    "ridge_flop_per_byte": peak * 1e3 / pk["hbm_gbs"], "compute": compute}
+        if "frac" in hbm:
+            roofline["traffic_frac"] = hbm["frac"]
+    else:
+        roofline = {"bound": "tensor" if args.precision != "fp32" else "alu", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+                    "peak_kind": peak_note, "flops_per_launch": flops_launch, "launches": conv_n,
+                    "avg_launch_ms": avg_conv_s * 1000, "intensity_flop_per_byte": flops_launch / bytes_launch,
+                    "ridge_flop_per_byte": peak * 1e3 / pk["hbm_gbs"], "hbm": hbm}
     breakdown = {"layer1_ms": l1_ms / args.steps, "conv_ms": conv_ms / args.steps,
                  "conv_heads_ms": heads_ms / args.steps, "decode_ms": dec_ms / args.steps}
 
