@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "sml_internal.h"
@@ -26,73 +27,128 @@ struct L1Params {
 };
 
 constexpr int kL1Tile = 128;     // pixels of one image row per block (and threads per block)
-constexpr int kL1Rows = 4;       // image rows per block
 constexpr int kL1Px = 8;         // pixels per thread: columns pg + 16*p, p < kL1Px
 constexpr int kL1ChGroups = 8;   // a thread computes C/8 output channels
-constexpr int kL1Span = kL1Tile + 2 * 64;  // staged input pixels per row (dilation <= 64)
+constexpr int kL1MaxD = 64;      // largest layer-1 dilation
+constexpr int kL1Batch = 4;      // staged rows whose loads are in flight together
 
-// Dynamic shared memory of one block: staged inputs [kL1Rows][3][IN_CH][kL1Span] floats,
-// then the padded output tile [kL1Tile][C*OB + 16] bytes.
-template <int C, int OUT, int IN_CH>
-constexpr size_t l1_smem_bytes() {
-  return (size_t)kL1Rows * 3 * IN_CH * kL1Span * 4 + (size_t)kL1Tile * (C * (OUT == 0 ? 4 : (OUT == 1 ? 2 : 1)) + 16);
+// Output rows per block: 16 for the small dilations of a first layer, whose input rows
+// overlap (16 + 2d staged rows for 16 output rows), else 4.
+__host__ __device__ constexpr int l1_rows(int d) { return d <= 4 ? 16 : 4; }
+
+// Staged input rows of a block: output row r (< R = l1_rows(d)) reads image rows
+// i0 + r + (ky-1)d.  For d < R these overlap, and the block stages the R + 2d distinct rows
+// i0 - d .. i0 + R - 1 + d once (staged row r + ky d); otherwise all 3R are distinct (staged
+// row ky R + r).
+__host__ __device__ constexpr int l1_stage_rows(int d) { return d < l1_rows(d) ? l1_rows(d) + 2 * d : 3 * l1_rows(d); }
+__device__ __forceinline__ int l1_srow(int r, int ky, int d) {
+  return d < l1_rows(d) ? r + ky * d : ky * l1_rows(d) + r;
+}
+__device__ __forceinline__ int l1_stage_image_row(int sr, int i0, int d) {
+  const int R = l1_rows(d);
+  return d < R ? i0 - d + sr : i0 + sr % R + (sr / R - 1) * d;
 }
 
-// One block: a 128-pixel strip of kL1Rows rows of one frame.  Thread (pg = lane % 16,
+// Dynamic shared memory of one block: staged inputs [l1_stage_rows(d)][IN_CH][128 + 2d] as
+// float pairs (each value twice, the operand of a packed two-channel FMA), then the padded
+// output tile [kL1Tile][C*OB + 16] bytes.
+template <int C, int OUT, int IN_CH>
+constexpr size_t l1_smem_bytes(int d) {
+  return (size_t)l1_stage_rows(d) * IN_CH * (kL1Tile + 2 * d) * 8 +
+         (size_t)kL1Tile * (C * (OUT == 0 ? 4 : (OUT == 1 ? 2 : 1)) + 16);
+}
+
+// One block: a 128-pixel strip of l1_rows(d) rows of one frame.  Thread (pg = lane % 16,
 // cg = 2*warp + lane / 16) computes channels cg*C/8 .. +C/8 for the strip's pixels pg + 16p.
 // FMAs take their weights from registers (with constant-bank weight operands they ran at half
-// the rate).  The dilated input rows of every output row of the block (IN_CH input channels:
-// the frame itself, or frames t-1, t, t+1) go through the camera transform into shared memory
-// first, one global round trip per block.  FMA order: bias, then input channel, then taps
-// (ky, kx) row-major.  Outputs are staged in shared memory (rows padded by 16 bytes against
-// bank conflicts) so that the stores to HBM are whole 16-byte chunks, consecutive across
-// threads.
+// the rate), two channels per packed FMA (__ffma2_rn: each lane one fmaf, so the arithmetic is
+// that of the scalar FMA chain).  The distinct dilated input rows of the block (IN_CH input
+// channels: the frame itself, or frames t-1, t, t+1) go through the camera transform into
+// shared memory first, one global round trip per block, kL1Batch rows of loads in flight at a
+// time.  FMA order: bias, then input channel, then taps (ky, kx) row-major.  Outputs are
+// staged in shared memory (rows padded by 16 bytes against bank conflicts) so that the stores
+// to HBM are whole 16-byte chunks, consecutive across threads.
 template <int C, int OUT, int IN_CH>
 __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restrict__ frames, int H, int W, int d,
                                                        int t0, int t_first, int t_last, CamArgs cam,
                                                        const __grid_constant__ L1Params prm, float out_scale,
                                                        void* __restrict__ out, int out_ct) {
   constexpr int CPT = C / kL1ChGroups;
+  constexpr int CP = CPT / 2;                             // channel pairs per thread
   constexpr int OB = OUT == 0 ? 4 : (OUT == 1 ? 2 : 1);  // output bytes per channel
   constexpr int OS = C * OB + 16;                        // staged bytes per pixel
+  static_assert(CPT % 2 == 0, "channels per thread come in pairs");
   extern __shared__ __align__(16) uint8_t l1_smem[];
-  float(*xs)[3][IN_CH][kL1Span] = reinterpret_cast<float(*)[3][IN_CH][kL1Span]>(l1_smem);
-  uint8_t* ot = l1_smem + (size_t)kL1Rows * 3 * IN_CH * kL1Span * 4;
-  const int j0 = blockIdx.x * kL1Tile, t = t0 + blockIdx.z, i0 = blockIdx.y * kL1Rows;
+  const int span = kL1Tile + 2 * d, nsr = l1_stage_rows(d), R = l1_rows(d);
+  float2* xs = reinterpret_cast<float2*>(l1_smem);  // [nsr][IN_CH][span]
+  uint8_t* ot = l1_smem + (size_t)nsr * IN_CH * span * 8;
+  const int j0 = blockIdx.x * kL1Tile, t = t0 + blockIdx.z, i0 = blockIdx.y * R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int pg = lane & 15, cg = 2 * warp + (lane >> 4);
-  const int span = kL1Tile + 2 * d;
+  // a staged row is at most 2 * kL1Tile pixels (span <= 256): two elements per thread
 #pragma unroll
   for (int ci = 0; ci < IN_CH; ++ci) {
     const int tf = IN_CH == 1 ? t : t + ci - 1;  // source frame of input channel ci
     const bool have = tf >= t_first && tf <= t_last;
     const uint16_t* f = frames + (ptrdiff_t)tf * H * W;
+    for (int sr0 = 0; sr0 < nsr; sr0 += kL1Batch) {
+      float adu[kL1Batch][2], g[kL1Batch][2], o[kL1Batch][2];
+      bool in[kL1Batch][2];
 #pragma unroll
-    for (int r = 0; r < kL1Rows; ++r)
+      for (int u = 0; u < kL1Batch; ++u)
 #pragma unroll
-      for (int ky = 0; ky < 3; ++ky)
-        for (int c = threadIdx.x; c < span; c += kL1Tile)
-          xs[r][ky][ci][c] = have ? cam_input(f, H, W, i0 + r + (ky - 1) * d, j0 - d + c, cam) : 0.0f;
-  }
-  float w[IN_CH == 1 ? CPT : 1][9], bias[CPT];
+        for (int k = 0; k < 2; ++k) {
+          const int sr = sr0 + u, c = threadIdx.x + k * kL1Tile;
+          const int ii = l1_stage_image_row(sr, i0, d), jj = j0 - d + c;
+          in[u][k] = have && sr < nsr && c < span && ii >= 0 && ii < H && jj >= 0 && jj < W;
+          const size_t px = in[u][k] ? (size_t)ii * W + jj : 0;
+          adu[u][k] = in[u][k] ? (float)f[px] : 0.0f;
+          g[u][k] = cam.gain_map && in[u][k] ? cam.gain_map[px] : cam.gain;
+          o[u][k] = cam.offset_map && in[u][k] ? cam.offset_map[px] : cam.offset;
+        }
 #pragma unroll
-  for (int c = 0; c < CPT; ++c) {
-    bias[c] = prm.b[cg * CPT + c];
-    if (IN_CH == 1) {
+      for (int u = 0; u < kL1Batch; ++u)
 #pragma unroll
-      for (int k = 0; k < 9; ++k) w[IN_CH == 1 ? c : 0][k] = prm.w[(cg * CPT + c) * 9 + k];
+        for (int k = 0; k < 2; ++k) {
+          const int sr = sr0 + u, c = threadIdx.x + k * kL1Tile;
+          if (sr < nsr && c < span) {
+            // zero outside the frame (the first layer's "same" zero padding)
+            const float v = in[u][k] ? cam_transform(adu[u][k], o[u][k], g[u][k], cam.in_scale) : 0.0f;
+            xs[((size_t)sr * IN_CH + ci) * span + c] = make_float2(v, v);
+          }
+        }
     }
   }
+  float2 bias[CP];
+#pragma unroll
+  for (int q = 0; q < CP; ++q) bias[q] = make_float2(prm.b[cg * CPT + 2 * q], prm.b[cg * CPT + 2 * q + 1]);
+  // weights of channel pair q, input channel ci, tap k
+  auto wpair = [&](int q, int ci, int k) {
+    return make_float2(prm.w[((cg * CPT + 2 * q) * IN_CH + ci) * 9 + k], prm.w[((cg * CPT + 2 * q + 1) * IN_CH + ci) * 9 + k]);
+  };
+  float2 w[IN_CH == 1 ? CP : 1][9];
+  if (IN_CH == 1) {
+#pragma unroll
+    for (int q = 0; q < CP; ++q)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) w[IN_CH == 1 ? q : 0][k] = wpair(q, 0, k);
+  }
   const int npx = W - j0 < kL1Tile ? W - j0 : kL1Tile;  // valid pixels of the strip
-  for (int r = 0; r < kL1Rows; ++r) {
+  for (int r = 0; r < R; ++r) {
     const int i = i0 + r;
     if (i >= H) break;
     __syncthreads();  // xs is filled; the previous row's ot is written out
+    const float2* xr[3];  // staged rows of the three vertical taps
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) xr[ky] = xs + (size_t)l1_srow(r, ky, d) * IN_CH * span;
     // ReLU, quantise and stage one pixel's CPT outputs
-    auto stage = [&](int px, const float (&acc)[CPT]) {
+    auto stage = [&](int px, const float2 (&acc)[CP]) {
       float a[CPT];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) a[c] = fmaxf(acc[c], 0.0f);
+      for (int q = 0; q < CP; ++q) {
+        a[2 * q] = fmaxf(acc[q].x, 0.0f);
+        a[2 * q + 1] = fmaxf(acc[q].y, 0.0f);
+      }
       uint8_t* dst = ot + (size_t)px * OS + cg * CPT * OB;
       if (OUT == 0) {
 #pragma unroll
@@ -114,46 +170,46 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
 #pragma unroll
       for (int p = 0; p < kL1Px; ++p) {
         const int px = pg + 16 * p;
-        float x[9];
+        float2 x[9];
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-          for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xs[r][ky][0][px + kx * d];
-        float acc[CPT];
+          for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xr[ky][px + kx * d];
+        float2 acc[CP];
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          float a = bias[c];
+        for (int q = 0; q < CP; ++q) {
+          float2 a = bias[q];
 #pragma unroll
-          for (int k = 0; k < 9; ++k) a = fmaf(w[IN_CH == 1 ? c : 0][k], x[k], a);
-          acc[c] = a;
+          for (int k = 0; k < 9; ++k) a = __ffma2_rn(w[IN_CH == 1 ? q : 0][k], x[k], a);
+          acc[q] = a;
         }
         stage(px, acc);
       }
     } else {  // input channel outer, so each channel's weights are loaded once per row
-      float acc[kL1Px][CPT];
+      float2 acc[kL1Px][CP];
 #pragma unroll
       for (int p = 0; p < kL1Px; ++p)
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[p][c] = bias[c];
+        for (int q = 0; q < CP; ++q) acc[p][q] = bias[q];
 #pragma unroll
       for (int ci = 0; ci < IN_CH; ++ci) {
-        float wc[CPT][9];
+        float2 wc[CP][9];
 #pragma unroll
-        for (int c = 0; c < CPT; ++c)
+        for (int q = 0; q < CP; ++q)
 #pragma unroll
-          for (int k = 0; k < 9; ++k) wc[c][k] = prm.w[((cg * CPT + c) * IN_CH + ci) * 9 + k];
+          for (int k = 0; k < 9; ++k) wc[q][k] = wpair(q, ci, k);
 #pragma unroll
         for (int p = 0; p < kL1Px; ++p) {
           const int px = pg + 16 * p;
-          float x[9];
+          float2 x[9];
 #pragma unroll
           for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-            for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xs[r][ky][ci][px + kx * d];
+            for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xr[ky][(size_t)ci * span + px + kx * d];
 #pragma unroll
-          for (int c = 0; c < CPT; ++c)
+          for (int q = 0; q < CP; ++q)
 #pragma unroll
-            for (int k = 0; k < 9; ++k) acc[p][c] = fmaf(wc[c][k], x[k], acc[p][c]);
+            for (int k = 0; k < 9; ++k) acc[p][q] = __ffma2_rn(wc[q][k], x[k], acc[p][q]);
         }
       }
 #pragma unroll
@@ -296,16 +352,17 @@ template <int C, int OUT, int IN_CH>
 static cudaError_t launch_l1(const uint16_t* frames, int T, int H, int W, int d, int t_first, int t_last,
                              const CamArgs& cam, const L1Params& prm, float out_scale, void* out, int out_ct,
                              cudaStream_t s) {
-  constexpr size_t smem = l1_smem_bytes<C, OUT, IN_CH>();
-  static bool configured = false;  // opt in to more than 48 KB once per instantiation
+  const size_t smem = l1_smem_bytes<C, OUT, IN_CH>(d);
+  static bool configured = false;  // opt in to the largest dilation's size once per instantiation
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_ingest_l1<C, OUT, IN_CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)std::max(l1_smem_bytes<C, OUT, IN_CH>(4),
+                                                       l1_smem_bytes<C, OUT, IN_CH>(kL1MaxD)));
     if (e != cudaSuccess) return e;
     configured = true;
   }
   for (int t0 = 0; t0 < T; t0 += 65535) {
-    dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + kL1Rows - 1) / kL1Rows, (unsigned)(T - t0 < 65535 ? T - t0 : 65535)),
+    dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + l1_rows(d) - 1) / l1_rows(d), (unsigned)(T - t0 < 65535 ? T - t0 : 65535)),
         block(kL1Tile);
     k_ingest_l1<C, OUT, IN_CH><<<grid, block, smem, s>>>(frames, H, W, d, t0, t_first, t_last, cam, prm, out_scale, out,
                                                          out_ct);
@@ -331,7 +388,7 @@ cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d,
                              const float* b1, int C, int in_ch, int t_first, int t_last, int prec, float out_scale,
                              void* out, int out_ct, cudaStream_t s) {
   if ((long long)T * H * W == 0) return cudaSuccess;
-  if (d > 64 || C > 64 || (in_ch != 1 && in_ch != 3)) return cudaErrorInvalidValue;
+  if (d < 1 || d > kL1MaxD || C > 64 || (in_ch != 1 && in_ch != 3)) return cudaErrorInvalidValue;
   if (t_first > 0 || t_last < T - 1) return cudaErrorInvalidValue;
   if (out_ct < C || out_ct % 16) return cudaErrorInvalidValue;
   // w1/b1 are host copies here: they travel as a kernel parameter

@@ -55,15 +55,10 @@ struct CamArgs {
 // h = 20 (where exp(h) is still far from overflow) and h itself above (the rest is < 2e-9 h).
 __device__ __forceinline__ float softplus_f(float h) { return h > 20.0f ? h : log1pf(expf(h)); }
 
-// Network input of pixel (i, j) of one frame: (adu - offset) / gain * in_scale, each step one
-// IEEE rounding; zero outside the frame (the first layer's "same" zero padding).
-__device__ __forceinline__ float cam_input(const uint16_t* __restrict__ f, int H, int W, int i, int j,
-                                           const CamArgs& cam) {
-  if (i < 0 || i >= H || j < 0 || j >= W) return 0.0f;
-  size_t px = (size_t)i * W + j;
-  float g = cam.gain_map ? cam.gain_map[px] : cam.gain;
-  float o = cam.offset_map ? cam.offset_map[px] : cam.offset;
-  return __fmul_rn(__fdiv_rn(__fsub_rn((float)f[px], o), g), cam.in_scale);
+// Network input of one pixel from its ADU value and its camera offset and gain:
+// (adu - offset) / gain * in_scale, each step one IEEE rounding.
+__device__ __forceinline__ float cam_transform(float adu, float offset, float gain, float in_scale) {
+  return __fmul_rn(__fdiv_rn(__fsub_rn(adu, offset), gain), in_scale);
 }
 #endif
 

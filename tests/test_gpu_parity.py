@@ -214,6 +214,31 @@ def test_dilation_larger_than_tile_margin(stages):
     check_quantized("bf16", js, blob, frames, cam, maps, logits)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("d1,in_ch", [(2, 1), (3, 3), (4, 1), (5, 3), (64, 1)])
+def test_first_layer_dilation(prec, d1, in_ch):
+    """The first layer at dilations below the block height (its input rows overlap and are
+    staged once) and above it, on a frame with a ragged 128-pixel strip and a ragged row block,
+    with per-pixel camera maps; single- and three-frame input."""
+    rng = np.random.default_rng(11 + d1)
+    spec = synth.NetSpec(in_ch=in_ch, channels=32, dilations=(d1, 1), precision=prec)
+    blob = synth.pack_blob(spec, synth.init_weights(spec, 6))
+    T, H, W = 3, 71, 150
+    frames = rng.integers(90, 900, (T, H, W)).astype(np.uint16)
+    cam = synth.Camera(1.0, 100.0, gain_map=rng.uniform(0.5, 2.0, (H, W)).astype(np.float32),
+                       offset_map=rng.uniform(80.0, 120.0, (H, W)).astype(np.float32))
+    js = spec.to_json()
+    loc, maps, logits = gpu_maps(js, blob, frames, cam)
+    if prec == "bf16":
+        check_quantized("bf16", js, blob, frames, cam, maps, logits)
+    else:
+        net = oracle.Net(js, blob)
+        ref = oracle.forward(net, frames, gain=cam.gain, offset=cam.offset, gain_map=cam.gain_map.astype(np.float64),
+                             offset_map=cam.offset_map.astype(np.float64))
+        assert max(map_errors(maps, logits, ref)) <= TOL["fp32"]
+    loc.close()
+
+
 # ----------------------------------------------------------------------------- decode
 
 
