@@ -525,7 +525,9 @@ def main():
     else:
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         peak_note = "fp32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz (derived, not measured)"
-    traffic = profiled_traffic(args.precision, {"batched": "batched256", "dcd": "dcd256"}.get(args.workload, ""))
+    # the committed ncu figures are for full launches of 256 frames of 256x256 (16,777,216 px)
+    traffic = (profiled_traffic(args.precision, {"batched": "batched256", "dcd": "dcd256"}.get(args.workload, ""))
+               if px_per_launch == 256 * 256 * 256 else None)
     hbm = {"algorithmic_bytes_per_launch": bytes_launch, "algorithmic_gbs": bytes_launch / avg_conv_s / 1e9,
            "peak_gbs": pk["hbm_gbs"], "algorithmic_frac": bytes_launch / avg_conv_s / 1e9 / pk["hbm_gbs"]}
     if traffic is not None:

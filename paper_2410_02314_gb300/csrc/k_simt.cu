@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
   for (int ci = 0; ci < IN_CH; ++ci) {
     const int tf = IN_CH == 1 ? t : t + ci - 1;  // source frame of input channel ci
     const bool have = tf >= t_first && tf <= t_last;
-    const uint16_t* f = frames + (ptrdiff_t)tf * H * W;
+    const uint16_t* f = have ? frames + (ptrdiff_t)tf * H * W : frames;  // not read unless have
     for (int sr0 = 0; sr0 < nsr; sr0 += kL1Batch) {
       float adu[kL1Batch][2], g[kL1Batch][2], o[kL1Batch][2];
       bool in[kL1Batch][2];
