@@ -487,3 +487,29 @@ def test_three_frame_context_across_chunk_edges(prec):
     host = loc2.localize(frames, 0.5, gain=2.0, offset=100.0)
     dev = loc2.localize(torch.from_numpy(frames).cuda(), 0.5, gain=2.0, offset=100.0)
     assert len(one) > 0 and one.tobytes() == host.tobytes() == dev.tobytes()
+
+
+@pytest.mark.parametrize("in_ch", [1, 3])
+def test_large_host_stacks_equal_device_frames(in_ch):
+    """Host frames staged to the device per chunk give the device-frame records byte for
+    byte: 150 frames of 256x256 as one chunk and as chunks of 64 frames (a short tail; with
+    three-frame input each chunk also reads its neighbours' edge frames), from pageable and
+    from pinned host memory."""
+    import json
+
+    rng = np.random.default_rng(47 + in_ch)
+    spec = synth.NetSpec(in_ch=in_ch, channels=16, dilations=(1, 2, 1), precision="bf16")
+    js = spec.to_json()
+    blob = synth.pack_blob(spec, synth.init_weights(spec, 13))
+    T, H, W = 150, 256, 256
+    frames = rng.integers(95, 700, (T, H, W)).astype(np.uint16)
+    kw = dict(gain=2.0, offset=100.0, capacity=T * H * W // 4)  # random-init net on noise: many maxima
+    ref = sml.Localizer(js, blob).localize(torch.from_numpy(frames).cuda(), 0.5, **kw)
+    assert len(ref) > 0
+    pinned = torch.from_numpy(frames).pin_memory()
+    for chunk_frames in (256, 64):
+        loc = sml.Localizer(json.dumps(dict(json.loads(js), chunk_px=chunk_frames * H * W)), blob)
+        assert loc.localize(frames, 0.5, **kw).tobytes() == ref.tobytes(), chunk_frames
+        assert loc.localize(pinned, 0.5, **kw).tobytes() == ref.tobytes(), chunk_frames
+        assert loc.localize(torch.from_numpy(frames).cuda(), 0.5, **kw).tobytes() == ref.tobytes(), chunk_frames
+        loc.close()
