@@ -2,7 +2,7 @@
 INFRASTRUCTURE ONLY (tests/ and bench.py import it; the product never does).
 
 This is the classical localization method the learned network is compared with, and the
-judge of localization error: the CRLB (Sec. 4.1.1) bounds the variance of any unbiased
+yardstick of localization error: the CRLB (Sec. 4.1.1) bounds the variance of any unbiased
 estimator, and an efficient MLE reaches it.
 
 Model (pixel-integrated Gaussian, unit pixels, pixel (i, j) centred on integer indices):
