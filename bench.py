@@ -66,6 +66,12 @@ def conv_class_work(spec, px, elem_bytes):
     return flops, nbytes, launches
 
 
+def roofline_bound(flops, nbytes, compute_peak_tflops, hbm_gbs):
+    """The roofline's bound of a launch: "hbm" when its intensity (FLOP per algorithmic byte)
+    lies below the ridge (compute peak / copy bandwidth), else "compute"."""
+    return "hbm" if flops / nbytes < compute_peak_tflops * 1e12 / (hbm_gbs * 1e9) else "compute"
+
+
 def algorithmic_flops_per_px(spec):
     C, L = spec.channels, spec.L
     return 2 * (9 * C + (L - 1) * 9 * C * C + 5 * C)
@@ -537,7 +543,7 @@ def main():
     # the roofline's bound: HBM when the launch's intensity (FLOP per algorithmic byte) is below
     # the ridge (compute peak / copy bandwidth), else the compute unit
     kernel = "k_dconv_tc (middle layers)" if args.precision != "fp32" else "k_dconv_f32 (middle layers)"
-    if flops_launch / bytes_launch < peak * 1e12 / (pk["hbm_gbs"] * 1e9):
+    if roofline_bound(flops_launch, bytes_launch, peak, pk["hbm_gbs"]) == "hbm":
         roofline = {"bound": "hbm", "achieved": hbm["algorithmic_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": hbm["algorithmic_frac"], "traffic": traffic, "kernel": kernel,
                     "peak_kind": f"copy bandwidth ({pk_kind})", "algorithmic_bytes_per_launch": bytes_launch,

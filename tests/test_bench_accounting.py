@@ -1,0 +1,68 @@
+"""The work accounting behind bench.py's roofline figures, against per-pixel counts made by
+hand from each net's layer plan (a 3x3 conv from ci to co channels is 2*9*ci*co FLOP per
+pixel of its level and reads ci, writes co channels there)."""
+import importlib.util
+import os
+
+import pytest
+
+from paper_2410_02314_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+PX = 256 * 256 * 256  # one chunk of the batched workload
+
+
+def test_plain_48_channel_net(bench):
+    # middle layers 2..7 of the 8-layer net: 6 convs 48 -> 48
+    flops, nbytes, launches = bench.conv_class_work(synth.spec_48(), PX, 2)
+    assert launches == 6
+    assert flops == 6 * 41472 * PX  # 2*9*48*48
+    assert nbytes == 6 * 192 * PX  # (48 + 48) channels x 2 bytes
+    assert bench.conv_class_work(synth.spec_48(), PX, 1)[1] == 6 * 96 * PX  # e4m3
+    # whole step: layer 1 (1 -> 48), 7 convs 48 -> 48, heads 48 -> 5
+    assert bench.algorithmic_flops_per_px(synth.spec_48()) == 291648
+
+
+def test_dense_block_net(bench):
+    # per block: dense layers 32/48/64/80 -> 16 and a transition 96 -> 32; four blocks
+    flops, nbytes, launches = bench.conv_class_work(synth.spec_dcd(), PX, 2)
+    assert launches == 20
+    assert flops == 4 * (18 * 16 * (32 + 48 + 64 + 80) + 18 * 96 * 32) * PX  # 479 232 per px
+    assert nbytes == 4 * ((48 + 64 + 80 + 96) + (96 + 32)) * 2 * PX  # 3 328 B per px
+    assert nbytes == 55834574848
+
+
+def test_full_topology_adds_the_unet_stage(bench):
+    # level 1 (px/4): down conv 32 -> 32; at full resolution: up conv 64 -> 32; pool reads 32
+    # at full and writes 32 at px/4, upsample the reverse.  Level 2 likewise at px/16 and px/4.
+    _, dcd_bytes, dcd_launches = bench.conv_class_work(synth.spec_dcd(), PX, 2)
+    flops, nbytes, launches = bench.conv_class_work(synth.spec_dilatedloc(), PX, 2)
+    assert launches == dcd_launches + 8
+    lv1 = 64 / 4 + 96 + 64 * (1 / 4 + 1)
+    lv2 = 64 / 16 + 96 / 4 + 64 * (1 / 16 + 1 / 4)
+    assert lv1 + lv2 == 240
+    assert nbytes == dcd_bytes + 240 * 2 * PX  # 3 808 B per px
+    unet_flops = 18 * 32 * 32 * (1 / 4 + 1 / 16) + 18 * 64 * 32 * (1 + 1 / 4)
+    dcd_flops = bench.conv_class_work(synth.spec_dcd(), PX, 2)[0]
+    assert flops == pytest.approx(dcd_flops + unet_flops * PX, rel=1e-12)
+
+
+def test_roofline_bound(bench):
+    # BF16 middle layer: 41 472 FLOP over 192 B = 216 FLOP/B, below the ridge 1702.5 / 6.6735 = 255
+    assert bench.roofline_bound(41472.0, 192.0, 1702.5, 6673.5) == "hbm"
+    # FP8: 432 FLOP/B against 2 x 1702.5 / 6.6735 = 510
+    assert bench.roofline_bound(41472.0, 96.0, 3405.0, 6673.5) == "hbm"
+    # FP32 SIMT: 108 FLOP/B against 80.5 / 6.6735 = 12
+    assert bench.roofline_bound(41472.0, 384.0, 80.5, 6673.5) == "compute"
+    # a dense contraction far above the ridge
+    assert bench.roofline_bound(1e6, 100.0, 1702.5, 6673.5) == "compute"
