@@ -353,14 +353,12 @@ static cudaError_t launch_l1(const uint16_t* frames, int T, int H, int W, int d,
                              const CamArgs& cam, const L1Params& prm, float out_scale, void* out, int out_ct,
                              cudaStream_t s) {
   const size_t smem = l1_smem_bytes<C, OUT, IN_CH>(d);
-  static bool configured = false;  // opt in to the largest dilation's size once per instantiation
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_ingest_l1<C, OUT, IN_CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max(l1_smem_bytes<C, OUT, IN_CH>(4),
-                                                       l1_smem_bytes<C, OUT, IN_CH>(kL1MaxD)));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // opt in to more than 48 KB on the current device, to the largest size any dilation takes
+  // (the same value on every launch: no host state, and no race between threads or devices)
+  cudaError_t e = cudaFuncSetAttribute(
+      k_ingest_l1<C, OUT, IN_CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)std::max(l1_smem_bytes<C, OUT, IN_CH>(4), l1_smem_bytes<C, OUT, IN_CH>(kL1MaxD)));
+  if (e != cudaSuccess) return e;
   for (int t0 = 0; t0 < T; t0 += 65535) {
     dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + l1_rows(d) - 1) / l1_rows(d), (unsigned)(T - t0 < 65535 ? T - t0 : 65535)),
         block(kL1Tile);
@@ -420,13 +418,11 @@ static cudaError_t launch_f32_impl(const F32LayerArgs& a, const float* hw, const
   if (a.ci < 4 || a.ci % 4 || a.ci * CO > kF32MaxWeights || a.in_ct < a.ci || a.in_ct % 4) return cudaErrorInvalidValue;
   if (!HEADS && (a.out_off < 0 || a.out_off % 4 || a.out_off + CO > a.out_ct || a.out_ct % 4)) return cudaErrorInvalidValue;
   size_t smem = sizeof(float) * 9 * a.ci * CO;
-  static bool configured = false;  // opt in to the largest weight image once per instantiation
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_dconv_f32<CO, HEADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(float) * 9 * kF32MaxWeights);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // the weight image may exceed 48 KB: opt in on the current device to the largest image
+  // (the same value on every launch)
+  cudaError_t e = cudaFuncSetAttribute(k_dconv_f32<CO, HEADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(float) * 9 * kF32MaxWeights);
+  if (e != cudaSuccess) return e;
   long long npx = (long long)a.T * a.H * a.W;
   if (npx == 0) return cudaSuccess;
   k_dconv_f32<CO, HEADS><<<grid_for(npx), kSimtThreads, smem, s>>>(a, hw, hb, nh, maps, logits);

@@ -43,6 +43,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "sml_internal.h"
@@ -759,6 +760,7 @@ size_t tc_smem_bytes(uint32_t bimg_bytes, int seg, int nstages, uint32_t stage_b
 }
 
 constexpr size_t kSmemBudget = 227 * 1024;
+std::mutex g_tc_launch_mutex;  // serialises attribute-set + launch of the conv kernels
 
 // Row sizes of a layer with ci input channels at dilation d.
 struct TcSizes {
@@ -833,6 +835,10 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   a.nstages = nst;
   size_t smem = tc_smem_bytes(z.bimg_bytes, Cfg::SEG, nst, z.stage_bytes);
   if (smem > kSmemBudget) return cudaErrorInvalidConfiguration;
+  // the limit is this launch's size, which differs between the layers that share the
+  // runtime-K instance: set and launch under one lock, so that contexts on several host
+  // threads never launch under another launch's smaller limit
+  std::lock_guard<std::mutex> lock(g_tc_launch_mutex);
   cudaError_t e = cudaFuncSetAttribute(k_dconv_tc<CI, CO, PREC, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
