@@ -68,3 +68,35 @@ def test_release_out_of_order_is_refused(tmp_path):
     assert L.sml_reader_release(h, ptrs[0]) == sml.SML_OK
     assert L.sml_reader_release(h, ptrs[1]) == sml.SML_OK
     L.sml_reader_close(h)
+
+
+def test_ring_back_pressure_and_timeout(tmp_path):
+    """With both buffers of a 2-buffer ring handed out, the reader cannot read the third batch:
+    sml_reader_next times out (SML_ERR_CUDA, as documented) until the first buffer comes back,
+    and the third batch then holds the right frames.  Closing with batches still out ends the
+    reader thread."""
+    import ctypes
+
+    frames = np.arange(5 * 3 * 4, dtype=np.uint16).reshape(5, 3, 4)
+    p = tmp_path / "ring.raw"
+    write_stack(p, frames)
+    L = sml.lib()
+    h = ctypes.c_void_p()
+    assert L.sml_reader_open(os.fsencode(str(p)), 0, 5, 3, 4, 2, 2, ctypes.byref(h)) == sml.SML_OK
+
+    def nxt(timeout_ms):
+        q, n, first = ctypes.c_void_p(), ctypes.c_int(0), ctypes.c_longlong(0)
+        code = L.sml_reader_next(h, ctypes.byref(q), ctypes.byref(n), ctypes.byref(first), timeout_ms)
+        return code, q.value, n.value, first.value
+
+    c0, p0, n0, f0 = nxt(10000)
+    c1, p1, n1, f1 = nxt(10000)
+    assert (c0, n0, f0, c1, n1, f1) == (sml.SML_OK, 2, 0, sml.SML_OK, 2, 2)
+    assert nxt(50)[0] == sml.SML_ERR_CUDA  # batch 2 needs buffer 0 back
+    assert L.sml_reader_release(h, ctypes.c_void_p(p0)) == sml.SML_OK
+    c2, p2, n2, f2 = nxt(10000)
+    assert (c2, p2, n2, f2) == (sml.SML_OK, p0, 1, 4)
+    got = np.ctypeslib.as_array(ctypes.cast(p2, ctypes.POINTER(ctypes.c_uint16)), shape=(1, 3, 4))
+    assert np.array_equal(got, frames[4:5])
+    assert nxt(10)[2] == 0  # past the last batch: no frames
+    L.sml_reader_close(h)  # batches 1 and 2 still out
