@@ -77,56 +77,102 @@ def algorithmic_flops_per_px(spec):
     return 2 * (9 * C + (L - 1) * 9 * C * C + 5 * C)
 
 
-class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+CLOCK_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+
+def _smi_time(text):
+    """nvidia-smi's timestamp field (local time, e.g. 2026/12/04 01:53:02.123) as a datetime,
+    or None if it does not parse."""
+    import datetime
+
+    for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+        try:
+            return datetime.datetime.strptime(text.strip(), fmt)
+        except ValueError:
+            pass
+    return None
+
+
+def parse_clock_samples(lines, begin=None, end=None):
+    """Summary of nvidia-smi samples (timestamp, index, clocks.sm, clocks.max.sm, power.draw,
+    active reasons, then the four reasons of CLOCK_REASONS).  With begin/end (local
+    datetimes of the timed region) only the samples taken inside it count; if none does (a
+    region shorter than the sampling period) or the timestamps do not parse, all samples
+    count and "window" says so."""
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            sm, mx = float(parts[2]), float(parts[3])
+        except ValueError:
+            continue
+        active = [n for n, v in zip(CLOCK_REASONS, parts[6:10]) if v.lower().startswith("active")]
+        rows.append((_smi_time(parts[0]), sm, mx, active))
+    if not rows:
+        return None
+    inside = [r for r in rows if begin is not None and r[0] is not None and begin <= r[0] <= end]
+    use, window = (inside, "timed region") if inside else (rows, "around the timed region")
+    return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+            "samples": len(use), "window": window,
+            "reasons": sorted({n for r in use for n in r[3]})}
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples (every 50 ms) around the timed region; the
+    summary keeps the samples stamped inside it."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.begin = self.end = None
         import tempfile
 
         self.path = os.path.join(tempfile.gettempdir(), f"sml_bench_clocks_gpu{index}_{os.getpid()}.csv")
 
     def start(self):
+        """Start sampling and wait (at most 3 s) until the first sample is written."""
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+
+    def mark_begin(self):
+        import datetime
+
+        self.begin = datetime.datetime.now()
+
+    def mark_end(self):
+        import datetime
+
+        self.end = datetime.datetime.now()
 
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+        with open(self.path) as f:
+            return parse_clock_samples(f.readlines(), self.begin, self.end)
 
 
 def kernel_source_hash():
@@ -501,7 +547,14 @@ def main():
 
     clk = ClockSampler(local)
     clk.start()
-    times = replicas.timed_region(lambda: timed(args.steps, profile=True), dist, torch.cuda.synchronize)
+
+    def timed_marked():
+        clk.mark_begin()
+        out = timed(args.steps, profile=True)  # ends with a device synchronise
+        clk.mark_end()
+        return out
+
+    times = replicas.timed_region(timed_marked, dist, torch.cuda.synchronize)
     clocks = clk.stop()
     ms = replicas.max_over_ranks(statistics.mean(times), dist, dev)
     value = replicas.whole_job_rate(T_FRAMES, ms / 1000.0, world)

@@ -66,3 +66,34 @@ def test_roofline_bound(bench):
     assert bench.roofline_bound(41472.0, 384.0, 80.5, 6673.5) == "compute"
     # a dense contraction far above the ridge
     assert bench.roofline_bound(1e6, 100.0, 1702.5, 6673.5) == "compute"
+
+
+def _smi_line(ts, sm, reasons=("Not Active",) * 4):
+    # timestamp, index, clocks.sm, clocks.max.sm, power.draw, active mask, four reasons
+    return ", ".join([ts, "0", str(sm), "2070", "900.5", "0x0000000000000000", *reasons])
+
+
+def test_clock_samples_inside_the_timed_region(bench):
+    import datetime
+
+    lines = [_smi_line("2026/12/04 01:53:02.000", 1400),  # idle, before the region
+             _smi_line("2026/12/04 01:53:02.150", 2070),
+             _smi_line("2026/12/04 01:53:02.200", 2070, ("Not Active", "Not Active", "Not Active", "Active")),
+             _smi_line("2026/12/04 01:53:02.250", 2055),
+             _smi_line("2026/12/04 01:53:02.400", 1100)]  # after the region
+    t = lambda s: datetime.datetime(2026, 12, 4, 1, 53, 2, int(s * 1e6))
+    got = bench.parse_clock_samples(lines, t(0.1), t(0.3))
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "samples": 3, "window": "timed region",
+                   "reasons": ["sw_power_cap"]}
+
+
+def test_clock_samples_fall_back_to_all_when_none_is_inside(bench):
+    import datetime
+
+    lines = [_smi_line("2026/12/04 01:53:02.000", 2070), "garbage", _smi_line("not a time", 2070,
+                                                                               ("Active",) + ("Not Active",) * 3)]
+    t = lambda s: datetime.datetime(2026, 12, 4, 1, 53, 2, int(s * 1e6))
+    got = bench.parse_clock_samples(lines, t(0.5), t(0.6))
+    assert got["samples"] == 2 and got["window"] == "around the timed region"
+    assert got["reasons"] == ["hw_slowdown"]
+    assert bench.parse_clock_samples([], None, None) is None
