@@ -97,3 +97,27 @@ def test_clock_samples_fall_back_to_all_when_none_is_inside(bench):
     assert got["samples"] == 2 and got["window"] == "around the timed region"
     assert got["reasons"] == ["hw_slowdown"]
     assert bench.parse_clock_samples([], None, None) is None
+
+
+def test_clock_sampler_with_a_stand_in_nvidia_smi(bench, tmp_path, monkeypatch):
+    """The sampler's process handling end to end, with a shell script in place of nvidia-smi
+    that prints one timestamped sample every 50 ms: it starts before the region, the region's
+    samples are kept, and stop() ends the sampling process."""
+    import time
+
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\nwhile true; do\n"
+                    "  echo \"$(date +'%Y/%m/%d %H:%M:%S.%3N'), 0, 2070, 2070, 850.0, 0x0, Not Active, Not Active, "
+                    "Not Active, Not Active\"\n  sleep 0.05\ndone\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    clk = bench.ClockSampler(0)
+    clk.start()
+    assert clk.proc is not None and os.path.getsize(clk.path) > 0  # sampling is live before the region
+    clk.mark_begin()
+    time.sleep(0.4)
+    clk.mark_end()
+    got = clk.stop()
+    assert clk.proc.poll() is not None
+    assert got["window"] == "timed region" and 3 <= got["samples"] <= 12
+    assert got["sm_mhz"] == 2070.0 and got["reasons"] == []
