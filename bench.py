@@ -66,10 +66,85 @@ def conv_class_work(spec, px, elem_bytes):
     return flops, nbytes, launches
 
 
-def roofline_bound(flops, nbytes, compute_peak_tflops, hbm_gbs):
-    """The roofline's bound of a launch: "hbm" when its intensity (FLOP per algorithmic byte)
-    lies below the ridge (compute peak / copy bandwidth), else "compute"."""
-    return "hbm" if flops / nbytes < compute_peak_tflops * 1e12 / (hbm_gbs * 1e9) else "compute"
+def measure_peaks(dev, n=8192, reps=5):
+    """Dense peaks measured here, next to the measured BF16 and copy figures: FP8 e4m3
+    through torch._scaled_mm (cuBLASLt, 2 n^3 FLOP per call) and FP32 through torch.matmul
+    with TF32 off (cuBLAS SGEMM on the FMA pipes), best of `reps` calls (burst), CUDA events."""
+    import torch
+
+    def best(fn, flops):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            t.append(a.elapsed_time(b) / 1000.0)
+        return flops / min(t) / 1e12
+
+    out = {"how": f"best of {reps} calls, {n}^3: fp8 torch._scaled_mm (e4m3 x e4m3 -> bf16), fp32 torch.matmul "
+                  f"with TF32 off (SGEMM)"}
+    x = torch.randn(n, n, device=dev, dtype=torch.bfloat16)
+    y = torch.randn(n, n, device=dev, dtype=torch.bfloat16)
+    try:
+        a8 = x.to(torch.float8_e4m3fn)
+        b8 = y.to(torch.float8_e4m3fn).t().contiguous().t()
+        one = torch.ones((), device=dev)
+        out["fp8_tflops"] = best(lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16),
+                                 2 * n ** 3)
+        del a8, b8
+    except Exception as e:  # recorded, and the FP8 roofline then says which peak it used
+        out["fp8_error"] = repr(e)[:200]
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        xf, yf = x.float(), y.float()
+        out["fp32_tflops"] = best(lambda: torch.matmul(xf, yf), 2 * n ** 3)
+        del xf, yf
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    del x, y
+    torch.cuda.empty_cache()
+    return out
+
+
+def conv_roofline(spec, precision, px_per_launch, conv_ms, conv_n, pk, live, traffic):
+    """Roofline of the dominant kernel, the middle-layer conv (k_dconv_tc; k_dconv_f32 in FP32).
+    It is a dense contraction, so the tensor pipe bounds it (the ALU pipes for the FP32 SIMT
+    path): achieved = the layer's FLOPs per launch (2 x 9 x Cin x Cout per pixel x the
+    launch's pixels) / the mean launch time (CUDA events on the launching stream); peak = the
+    burst dense peak of the launch's operand type: BF16 the measured cuBLAS figure,
+    FP8 and FP32 measured here (measure_peaks).  The HBM side is reported beside it: the
+    layer's activation bytes (Cin + Cout per pixel, read once and written once) over the
+    launch time against the measured copy bandwidth, and the DRAM bytes ncu counted."""
+    elem = {"bf16": 2, "fp8": 1, "fp32": 4}[precision]
+    fl, nb, n_launch = conv_class_work(spec, px_per_launch, elem)
+    flops_launch, bytes_launch = fl / n_launch, nb / n_launch
+    avg_s = conv_ms / max(conv_n, 1) / 1000.0
+    achieved = flops_launch / avg_s / 1e12
+    if precision == "bf16":
+        peak, peak_kind = pk["bf16_tflops"], f"bf16 dense burst, cuBLAS ({'measured' if 'when' in pk else 'fallback'})"
+    elif precision == "fp8" and live.get("fp8_tflops"):
+        peak, peak_kind = live["fp8_tflops"], "fp8 e4m3 dense burst, measured here (torch._scaled_mm)"
+    elif precision == "fp8":
+        peak, peak_kind = 2.0 * pk["bf16_tflops"], "fp8 = 2 x measured bf16 burst (nominal 4.5/2.25 ratio)"
+    else:
+        peak, peak_kind = live.get("fp32_tflops", 80.5), "fp32 FMA, measured here (SGEMM)"
+    kernel = "k_dconv_tc (middle layers)" if precision != "fp32" else "k_dconv_f32 (middle layers)"
+    hbm = {"bytes_per_launch": bytes_launch, "gbs": bytes_launch / avg_s / 1e9, "peak_gbs": pk["hbm_gbs"],
+           "frac": bytes_launch / avg_s / 1e9 / pk["hbm_gbs"],
+           "note": "the layer's own activation bytes (input and output once each); the method's algorithmic bytes "
+                   "are the frames in and the records out (about 2.5 B/px for the whole path)"}
+    if traffic is not None:
+        hbm.update({"dram_gbs": traffic / avg_s / 1e9, "dram_frac": traffic / avg_s / 1e9 / pk["hbm_gbs"]})
+    return {"bound": "tensor" if precision != "fp32" else "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "kernel": kernel, "peak_kind": peak_kind,
+            "flops_per_launch": flops_launch, "px_per_launch": px_per_launch, "launches": conv_n,
+            "avg_launch_ms": avg_s * 1000, "hbm": hbm}
 
 
 def algorithmic_flops_per_px(spec):
@@ -216,94 +291,205 @@ def cpu_baseline(w, budget_s=12.0):
                       f"float64 forward + float32 decode, {el:.1f} s"}
 
 
-def serving_run(args, spec_json, blob, dev, capacity_px_per_s, load=0.8, n_requests=24, slots=3):
-    """Mixed stacks 100x512^2, 50x1024^2, 20x2048^2 uint16 (3:2:1), sCMOS astigmatic frames,
-    Poisson arrivals at `load` x the measured pixel capacity; continuous batching over
-    `slots` contexts.  Frames of each size come from a small simulated pool (same content
-    for requests of the same size)."""
-    import numpy as np
-    import torch
-
-    from paper_2410_02314_gb300 import serve, synth
-
-    rng = np.random.default_rng(6)
-    pool = {}
-    for T, S in ((100, 512), (50, 1024), (20, 2048)):
-        w = synth.workload_large_fov(T=1, H=S, W=S, seed=60 + S)
-        pool[S] = (torch.from_numpy(np.repeat(w.frames, T, axis=0)).pin_memory(), w.cam)
-    kinds = rng.choice([512, 1024, 2048], size=n_requests, p=[0.5, 1 / 3, 1 / 6])
-    mean_px = np.mean([pool[k][0].numel() for k in kinds])
-    rate = load * capacity_px_per_s / mean_px
-    arrivals = serve.poisson_arrivals(n_requests, rate, rng)
-    reqs = []
-    for k, (kind, t) in enumerate(zip(kinds, arrivals)):
-        fr, cam = pool[int(kind)]
-        reqs.append(serve.Request(rid=k, frames=fr, arrival=float(t), gain=cam.gain, offset=cam.offset,
-                                  gain_map=torch.from_numpy(cam.gain_map).to(dev),
-                                  offset_map=torch.from_numpy(cam.offset_map).to(dev)))
-    ex = serve.GpuExecutor(spec_json, blob, slots=slots, device=dev.index or 0)
-    ex.warm([(512, 512), (1024, 1024), (2048, 2048)], max_request=(20, 2048, 2048))
-    sch = serve.Scheduler(ex, hbm_budget=48 << 30)
-    rep = serve.report(sch.run(reqs))
-    rep.update({"load": load, "arrival_rate_per_s": rate, "slots": slots, "max_queue": sch.max_queue,
-                "mix": "100x512^2 : 50x1024^2 : 20x2048^2 = 3:2:1, sCMOS astigmatic"})
-    return rep
-
-
-def large_fov_run(dev, stream, flush, frames=256, sim_batch=16, reps=3):
-    """Large field of view: `frames` distinct 2048x2048 sCMOS frames (per-pixel gain N(2,0.1)
-    and offset N(100,5) maps resident on the device, 2 emitters/um^2, astigmatic PSF with
-    z ~ U(-600,600) nm, Poisson noise), simulated on the device by the library's frame
-    simulator in batches of `sim_batch` frames, then localized as one resident stack (the
-    library runs it as chunks of 2^24 pixels, 4 frames), BF16 and FP8, 48-channel 8-layer net."""
+def serving_pool(dev, seed=6):
+    """Distinct sCMOS astigmatic frames for the serving stream, simulated on the device by the
+    library's frame simulator (2 emitters/um^2, per-pixel gain/offset maps) and kept in pinned
+    host memory: 2T frames per request size (T = 100, 50, 20 for 512^2, 1024^2, 2048^2)."""
     import numpy as np
     import torch
 
     import paper_2410_02314_gb300 as sml
     from paper_2410_02314_gb300 import synth
 
-    H = W = 2048
-    rng = np.random.default_rng(4)
+    rng = np.random.default_rng(seed)
+    pool = {}
+    for T, S in ((100, 512), (50, 1024), (20, 2048)):
+        cam = synth.scmos_camera(rng, S, S)
+        d_gain, d_off = torch.from_numpy(cam.gain_map).to(dev), torch.from_numpy(cam.offset_map).to(dev)
+        em = synth.emitters_density(rng, 2 * T, S, S, 2.0, astig=True)
+        d_adu = sml.sml_sim_frames(em, 2 * T, S, S, astig=True, gain_map=d_gain, offset_map=d_off, seed=seed + S)
+        torch.cuda.synchronize()
+        host = d_adu.cpu().pin_memory()  # int16 tensor holding the uint16 ADU bits
+        pool[S] = (T, host, cam, d_gain, d_off)
+        del d_adu
+    torch.cuda.empty_cache()
+    return pool
+
+
+def serving_run(spec_json, blob, dev, capacity_px_per_s, pool, load=0.8, n_requests=200, slots=3):
+    """Mixed stacks 100x512^2, 50x1024^2, 20x2048^2 uint16 (3:2:1), Poisson arrivals at
+    `load` x the measured pixel capacity; continuous batching over `slots` contexts whose
+    workspaces for the three sizes are created before the timed stream.  Each request's
+    frames are a window of T consecutive frames at a random start in its size's pool of 2T
+    distinct simulated frames.  The HBM budget is the device's free memory at the start plus
+    what the slots hold, minus a 4 GiB reserve."""
+    import numpy as np
+    import torch
+
+    from paper_2410_02314_gb300 import serve
+
+    rng = np.random.default_rng(int(load * 1000))
+    kinds = rng.choice([512, 1024, 2048], size=n_requests, p=[0.5, 1 / 3, 1 / 6])
+    mean_px = np.mean([pool[int(k)][0] * int(k) * int(k) for k in kinds])
+    rate = load * capacity_px_per_s / mean_px
+    arrivals = serve.poisson_arrivals(n_requests, rate, rng)
+    reqs = []
+    for k, (kind, t) in enumerate(zip(kinds, arrivals)):
+        T, host, cam, d_gain, d_off = pool[int(kind)]
+        o = int(rng.integers(0, T + 1))
+        reqs.append(serve.Request(rid=k, frames=host[o : o + T], arrival=float(t), gain=cam.gain, offset=cam.offset,
+                                  gain_map=d_gain, offset_map=d_off))
+    ex = serve.GpuExecutor(spec_json, blob, slots=slots, device=dev.index or 0)
+    ex.warm([(512, 512), (1024, 1024), (2048, 2048)], max_request=(20, 2048, 2048))
+    sch = serve.Scheduler(ex, reserve=4 << 30)
+    rep = serve.report(sch.run(reqs))
+    rep.update({"load": load, "arrival_rate_per_s": rate, "slots": slots, "max_queue": sch.max_queue,
+                "hbm_budget_bytes": sch.budget, "resident_bytes": ex.resident_bytes(),
+                "peak_accounted_bytes": sch.peak_in_use,
+                "mix": "100x512^2 : 50x1024^2 : 20x2048^2 = 3:2:1, sCMOS astigmatic, distinct frames per request"})
+    for loc in ex.locs:
+        loc.close()
+    return rep
+
+
+LFOV_FRAMES, LFOV_HW = 1000, 2048
+
+
+def large_fov_frames(dev, frames=LFOV_FRAMES, sim_batch=16, seed=4):
+    """The large field-of-view stack: `frames` distinct 2048x2048 sCMOS frames (per-pixel gain
+    N(2,0.1) and offset N(100,5) maps resident on the device, 2 emitters/um^2, astigmatic PSF
+    with z ~ U(-600,600) nm, Poisson noise), simulated on the device by the library's frame
+    simulator in batches of `sim_batch` frames.  Returns (device int16 [T,H,W] holding the
+    uint16 ADU bits, camera, device gain map, device offset map, emitters per frame,
+    simulated frames/s)."""
+    import numpy as np
+    import torch
+
+    import paper_2410_02314_gb300 as sml
+    from paper_2410_02314_gb300 import synth
+
+    H = W = LFOV_HW
+    rng = np.random.default_rng(seed)
     cam = synth.scmos_camera(rng, H, W)
     d_gain, d_off = torch.from_numpy(cam.gain_map).to(dev), torch.from_numpy(cam.offset_map).to(dev)
     d_frames = torch.empty((frames, H, W), dtype=torch.int16, device=dev)
     n_em = 0
     t_sim = time.perf_counter()
     for c in range(0, frames, sim_batch):
-        em = synth.emitters_density(rng, sim_batch, H, W, 2.0, astig=True)
+        nb = min(sim_batch, frames - c)
+        em = synth.emitters_density(rng, nb, H, W, 2.0, astig=True)
         n_em += em.x.size
-        sml.sml_sim_frames(em, sim_batch, H, W, astig=True, gain_map=d_gain, offset_map=d_off, seed=4, frame0=c,
-                           d_adu=d_frames[c : c + sim_batch])
+        sml.sml_sim_frames(em, nb, H, W, astig=True, gain_map=d_gain, offset_map=d_off, seed=seed, frame0=c,
+                           d_adu=d_frames[c : c + nb])
     torch.cuda.synchronize()
-    t_sim = time.perf_counter() - t_sim
+    return d_frames, cam, d_gain, d_off, n_em / frames, frames / (time.perf_counter() - t_sim)
+
+
+def large_fov_cpu_baseline(net, frame, cam, budget_s=10.0, block=256):
+    """The oracle (float64 forward + float32 decode) on blocks of `block` x `block` pixels of
+    one 2048x2048 frame, each computed with its receptive-field halo (forward_window), as
+    many as fit the time budget; frames/s extrapolated per pixel to whole frames."""
+    import numpy as np
+
+    import oracle
+
+    H, W = frame.shape
+    done_px, nblk, t0 = 0, 0, time.perf_counter()
+    rng = np.random.default_rng(0)
+    while True:
+        i0, j0 = (int(v) * block for v in rng.integers(0, H // block, 2))
+        hd = oracle.forward_window(net, frame[None], i0, i0 + block, j0, j0 + block, cam.gain, cam.offset,
+                                   cam.gain_map.astype(np.float64), cam.offset_map.astype(np.float64))
+        oracle.decode(oracle.maps_f32(hd), P_MIN, net.z_scale, net.ph_scale)
+        done_px += block * block
+        nblk += 1
+        el = time.perf_counter() - t0
+        if el > budget_s:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": done_px / el / (H * W), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nblk} blocks of {block}x{block} px of one {H}x{W} frame (each with its {net.R}-px receptive "
+                      f"halo), float64 forward + float32 decode, {el:.1f} s; extrapolated per pixel to whole frames"}
+
+
+def large_fov_line(dev, stream, flush, prec, lf, steps, warmup, pk, live, with_e2e=True, with_cpu=True):
+    """The large field-of-view configuration as a bench line: the 1000-frame 2048x2048 stack
+    (resident in HBM) through the 48-channel 8-layer net in `prec` (bf16 or fp8), one step =
+    one sml_localize_async call over all frames (the library runs chunks of 4 frames);
+    L2 flushed between steps.  Adds the middle-layer conv roofline, the end-to-end rate
+    through sml_localize with pinned host frames and records, the oracle's extrapolated
+    rate and the clocks."""
+    import torch
+
+    import oracle
+    import paper_2410_02314_gb300 as sml
+    from paper_2410_02314_gb300 import synth
+
+    d_frames, cam, d_gain, d_off, em_per_frame, sim_fps = lf
+    T, H, W = (int(x) for x in d_frames.shape)
     spec = synth.spec_48("bf16")
     blob = synth.pack_blob(spec, synth.init_weights(spec, 1004))
     camk = {"gain": cam.gain, "offset": cam.offset, "gain_map": d_gain, "offset_map": d_off}
-    cap = frames * H * W // 4
+    js = spec.to_json()
+    if prec == "fp8":  # activation scales from a bf16 calibration pass over the first 4 frames
+        js = sml.calibrate_fp8(js, blob, d_frames[:4], **camk)
+    loc = sml.Localizer(js, blob)
+    cap = T * 300000  # random-init nets detect about 170-230 k local maxima per frame
     d_out = torch.empty(cap * 24, dtype=torch.uint8, device=dev)
     d_n = torch.zeros(1, dtype=torch.int64, device=dev)
-    res = {"workload": f"{frames} distinct {H}x{W} sCMOS frames simulated on the device (astigmatic, 2 emitters/um^2, "
-                       f"per-pixel gain/offset maps)", "l2": "flushed between calls",
-           "simulated_frames_per_s": frames / t_sim, "emitters_per_frame": n_em / frames}
-    for prec in ("bf16", "fp8"):
-        js = spec.to_json()
-        if prec == "fp8":
-            js = sml.calibrate_fp8(js, blob, d_frames[:1], **camk)
-        loc = sml.Localizer(js, blob)
+    for _ in range(max(1, warmup)):
         loc.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream, **camk)
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-        for a, b in ev:
+    torch.cuda.synchronize()
+    launches = loc.last_launch_count
+    clk = ClockSampler(dev.index or 0)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sml.sml_profile_enable(loc.ctx, True)
+    clk.mark_begin()
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        loc.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream, **camk)
+        b.record(stream)
+    torch.cuda.synchronize()
+    clk.mark_end()
+    clocks = clk.stop()
+    sml.sml_profile_enable(loc.ctx, False)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    conv_ms, conv_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_CONV)
+    n_rec = int(d_n.item())
+    px_per_launch = 4 * H * W
+    res = {"metric": "frames/s", "value": T / (ms / 1000), "unit": "frames/s", "steps": steps, "warmup": warmup,
+           "ms_per_step": ms, "dtype": prec,
+           "config": {"workload": f"large_fov_{T}x{H}x{W}_scmos_astig_48ch_8layer", "frames_per_step": T,
+                      "frames": f"{T} distinct frames simulated on the device (astigmatic, 2 emitters/um^2, "
+                                f"per-pixel gain/offset maps), {em_per_frame:.0f} emitters per frame",
+                      "chunk": "4 frames (16,777,216 px) per launch", "l2": "flushed between steps (512 MB write)"},
+           "mpix_per_s": T * H * W / (ms / 1000) / 1e6, "records_per_frame": n_rec / T,
+           "gpu_launches": launches * steps, "simulated_frames_per_s": sim_fps,
+           "roofline": conv_roofline(spec, prec, px_per_launch, conv_ms, conv_n, pk, live,
+                                     profiled_traffic(prec, "large_fov")),
+           "clocks": clocks}
+    if with_e2e:
+        host_frames = d_frames.cpu().pin_memory()
+        host_out = torch.empty(cap * 24, dtype=torch.uint8).pin_memory()
+        e2e_t = []
+        for k in range(3):
             flush.zero_()
-            a.record(stream)
-            loc.localize_async(d_frames, P_MIN, d_out, d_n, stream=stream, **camk)
-            b.record(stream)
-        torch.cuda.synchronize()
-        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
-        res[f"{prec}_frames_per_s"] = frames / (ms / 1000)
-        res[f"{prec}_gpx_per_s"] = frames * H * W / (ms / 1000) / 1e9
-        res[f"{prec}_records_per_frame"] = int(d_n.item()) / frames
-        loc.close()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            recs = sml.sml_localize(loc.ctx, host_frames, P_MIN, out=host_out, **camk)
+            if k:
+                e2e_t.append(time.perf_counter() - t0)
+        e2e_s = statistics.mean(e2e_t)
+        res["e2e"] = {"value": T / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": int(host_frames.numel() * 2),
+                      "d2h_bytes_per_step": int(recs.numel() + 8), "steps": len(e2e_t)}
+        del host_frames, host_out
+    if with_cpu:
+        net = oracle.Net(js, blob)
+        frame0 = d_frames[0].cpu().numpy().view("uint16")
+        res["cpu_baseline"] = large_fov_cpu_baseline(net, frame0, cam)
+    loc.close()
     return res
 
 
@@ -457,9 +643,10 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
     ap.add_argument("--frames", type=int, default=T_FRAMES,
                     help="frames per step (default 256; smaller stacks for profiler captures)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "dcd", "dilatedloc"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "dcd", "dilatedloc", "large_fov"],
                     help="batched: the 48-channel 8-layer net; dcd: the 22-layer dense-block net; dilatedloc: the "
-                         "full topology (dense blocks, U-Net, uncertainty heads); dcd and dilatedloc run fp32/bf16")
+                         "full topology (dense blocks, U-Net, uncertainty heads); dcd and dilatedloc run fp32/bf16; "
+                         "large_fov: 1000 distinct 2048x2048 sCMOS frames, bf16 or fp8, one GPU")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk-px", type=int, default=0)
     ap.add_argument("--tc-stages", type=int, default=0)
@@ -494,8 +681,21 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    if args.workload != "batched" and args.precision == "fp8":
+    if args.workload in ("dcd", "dilatedloc") and args.precision == "fp8":
         raise SystemExit("the dense-block and full-topology nets run in fp32 or bf16")
+    if args.workload == "large_fov":
+        if world > 1 or args.precision == "fp32":
+            raise SystemExit("the large field-of-view line runs on one GPU in bf16 or fp8")
+        flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+        lf = large_fov_frames(dev)
+        live = measure_peaks(dev)
+        line = large_fov_line(dev, torch.cuda.current_stream(), flush, args.precision, lf, args.steps, args.warmup,
+                              peaks()[0], live, with_cpu=not args.no_cpu_baseline)
+        line.update({"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                     "data": "synthetic", "peaks_measured": live})
+        line["config"]["parallelism"] = "replicas1"
+        print(json.dumps(line), flush=True)
+        return
 
     def workload(prec, d_frames=None):
         make = {"batched": synth.workload_batched, "dcd": synth.workload_dcd,
@@ -559,58 +759,20 @@ def main():
     ms = replicas.max_over_ranks(statistics.mean(times), dist, dev)
     value = replicas.whole_job_rate(T_FRAMES, ms / 1000.0, world)
 
+    live_peaks = measure_peaks(dev)  # FP8 and FP32 dense peaks, after the timed region
     # dominant kernel: the middle-layer tensor-core (or FP32) conv, timed on its stream
     conv_ms, conv_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_CONV)
     heads_ms, heads_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_CONV_HEADS)
     l1_ms, l1_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_LAYER1)
     dec_ms, dec_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_DECODE)
-    C = w.spec.channels
     chunk_px = json.loads(spec_json).get("chunk_px", 1 << 24)
     frames_per_chunk = max(1, chunk_px // (H * W))
     px_per_launch = min(frames_per_chunk, T_FRAMES) * H * W
     pk, pk_kind = peaks()
-    # per launch: the conv-class FLOPs and bytes of one chunk spread over its launches (all
-    # equal for a plain stack)
-    fl, nb, n_launch = conv_class_work(w.spec, px_per_launch, {"bf16": 2, "fp8": 1, "fp32": 4}[args.precision])
-    flops_launch, bytes_launch = fl / n_launch, nb / n_launch
-    avg_conv_s = conv_ms / max(conv_n, 1) / 1000.0
-    achieved = flops_launch / avg_conv_s / 1e12
-    if args.precision == "bf16":
-        peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
-        peak_note = f"bf16 dense sustained ({pk_kind})"
-    elif args.precision == "fp8":
-        peak = 2.0 * pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
-        peak_note = f"fp8 = 2 x bf16 sustained ({pk_kind}) by the nominal 4.5/2.25 ratio"
-    else:
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12
-        peak_note = "fp32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz (derived, not measured)"
     # the committed ncu figures are for full launches of 256 frames of 256x256 (16,777,216 px)
     traffic = (profiled_traffic(args.precision, {"batched": "batched256", "dcd": "dcd256"}.get(args.workload, ""))
                if px_per_launch == 256 * 256 * 256 else None)
-    hbm = {"algorithmic_bytes_per_launch": bytes_launch, "algorithmic_gbs": bytes_launch / avg_conv_s / 1e9,
-           "peak_gbs": pk["hbm_gbs"], "algorithmic_frac": bytes_launch / avg_conv_s / 1e9 / pk["hbm_gbs"]}
-    if traffic is not None:
-        hbm.update({"achieved_gbs": traffic / avg_conv_s / 1e9, "frac": traffic / avg_conv_s / 1e9 / pk["hbm_gbs"]})
-    compute = {"achieved_tflops": achieved, "peak_tflops": peak, "frac": achieved / peak, "peak_kind": peak_note,
-               "flops_per_launch": flops_launch}
-    # the roofline's bound: HBM when the launch's intensity (FLOP per algorithmic byte) is below
-    # the ridge (compute peak / copy bandwidth), else the compute unit
-    kernel = "k_dconv_tc (middle layers)" if args.precision != "fp32" else "k_dconv_f32 (middle layers)"
-    if roofline_bound(flops_launch, bytes_launch, peak, pk["hbm_gbs"]) == "hbm":
-        roofline = {"bound": "hbm", "achieved": hbm["algorithmic_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": hbm["algorithmic_frac"], "traffic": traffic, "kernel": kernel,
-                    "peak_kind": f"copy bandwidth ({pk_kind})", "algorithmic_bytes_per_launch": bytes_launch,
-                    "launches": conv_n, "avg_launch_ms": avg_conv_s * 1000,
-                    "intensity_flop_per_byte": flops_launch / bytes_launch,
-                    "ridge_flop_per_byte": peak * 1e3 / pk["hbm_gbs"], "compute": compute}
-        if "frac" in hbm:
-            roofline["traffic_frac"] = hbm["frac"]
-    else:
-        roofline = {"bound": "tensor" if args.precision != "fp32" else "alu", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
-                    "peak_kind": peak_note, "flops_per_launch": flops_launch, "launches": conv_n,
-                    "avg_launch_ms": avg_conv_s * 1000, "intensity_flop_per_byte": flops_launch / bytes_launch,
-                    "ridge_flop_per_byte": peak * 1e3 / pk["hbm_gbs"], "hbm": hbm}
+    roofline = conv_roofline(w.spec, args.precision, px_per_launch, conv_ms, conv_n, pk, live_peaks, traffic)
     breakdown = {"layer1_ms": l1_ms / args.steps, "conv_ms": conv_ms / args.steps,
                  "conv_heads_ms": heads_ms / args.steps, "decode_ms": dec_ms / args.steps}
 
@@ -658,11 +820,16 @@ def main():
 
     serving = None
     if not args.no_serve and world == 1:  # arrival rates at 0.5, 0.8 and 0.95 of the measured capacity
-        serving = [serving_run(args, spec_json, w.blob, dev, capacity_px_per_s=value * H * W, load=ld)
-                   for ld in (0.5, 0.8, 0.95)]
+        pool = serving_pool(dev)
+        serving = [serving_run(spec_json, w.blob, dev, value * H * W, pool, load=ld) for ld in (0.5, 0.8, 0.95)]
+        del pool
     large_fov = small = file_pipe = dcd = None
     if not args.no_extra and world == 1:
-        large_fov = large_fov_run(dev, stream, flush)
+        lf = large_fov_frames(dev)
+        large_fov = {p: large_fov_line(dev, stream, flush, p, lf, 3, 1, pk, live_peaks, with_cpu=(p == "bf16"))
+                     for p in ("bf16", "fp8")}
+        del lf
+        torch.cuda.empty_cache()
         small = small_latency_run(dev, stream)
         file_pipe = file_pipeline_run(spec_json, w.blob, w.frames, w.cam)
         dcd = ({k: topology_run(dev, stream, flush, k) for k in TOPOLOGIES} if args.workload == "batched" else None)
@@ -697,6 +864,7 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "e2e": e2e,
         "roofline": roofline,
+        "peaks_measured": live_peaks,
         "kernel_ms_per_step": breakdown,
         "cpu_baseline": cpu,
         "clocks": clocks,

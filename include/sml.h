@@ -89,7 +89,7 @@ typedef struct {
  *   in_ch 1 (one frame per output frame) or 3 (frames t-1, t, t+1 as the first layer's
  *   input channels, the three-frame temporal context of Sec. 3.1; zero where t-1 or t+1 lies
  *   outside the frames of the call; chunk edges inside a call read the neighbouring frames);
- *   channels in {16,32,48,64}; 2..16 layers with dilations 1..64;
+ *   channels in {16,32,48,64}; 2..32 layers with dilations 1..64;
  *   "heads": 5 names (p, dx, dy, z, N: probability logit, sub-pixel offsets, zhat, Nhat) or
  *   9 (those and the uncertainty heads sx, sy, sz, sN, Sec. 3.2; each sigma map is
  *   softplus(h) = log(1 + exp(h)) of its raw head); default 5;
@@ -111,8 +111,9 @@ typedef struct {
  *   has_bn, gamma[C], beta[C], mean[C], var[C] f32 and eps f32; then the heads
  *   Wh[n_heads][C] f32 and bh[n_heads] f32 (head order: p logit, dx, dy, zhat, Nhat, then
  *   sx, sy, sz, sN).  BatchNorm is folded into the conv weights here.
- *   Nets with dense blocks use version 2: header "<8s7I32i" with reserved = growth and the
- *   32 dilations of every conv layer in execution order; layer l's W is [Cout_l][Cin_l][3][3]
+ *   Nets with dense blocks or a U-Net, and plain stacks of more than 16 layers, use version 2:
+ *   header "<8s7I32i" with reserved = growth (0 without dense blocks) and the 32 dilations of
+ *   every conv layer in execution order; layer l's W is [Cout_l][Cin_l][3][3]
  *   with the channel counts of the dcd plan; no BatchNorm.
  * out: receives the context (owned by the caller, freed with sml_destroy).
  * Errors: SML_ERR_BAD_SPEC, SML_ERR_BAD_WEIGHTS, SML_ERR_UNSUPPORTED, SML_ERR_OOM, SML_ERR_CUDA.
@@ -143,6 +144,37 @@ int sml_localize(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, cons
 
 /* Number of output heads of the context's net: 5, or 9 with the uncertainty heads. */
 int sml_num_heads(const sml_ctx* ctx);
+
+/* Number of conv layers of the context's net in execution order (the length of an fp8 net
+ * spec's "act_scales"; dense blocks and a U-Net add their layers to the spec's dilations). */
+int sml_num_layers(const sml_ctx* ctx);
+
+/*
+ * sml_workspace_bytes -- device memory of the context's per-frame-size workspace ("plan":
+ * activation buffers of one chunk, maps, decode scratch, staging of host frames and camera
+ * maps).  A call on frames of a new H x W allocates such a plan and keeps it for later calls
+ * of that size (up to 4 sizes; the least recently used is then freed after its last call's
+ * work on that call's stream has finished).  Host only, no device call.
+ * plan_bytes (or NULL): bytes of a plan for H x W; plan_resident (or NULL): 1 if the context
+ * holds one now, else 0; resident_bytes (or NULL): bytes of all plans the context holds.
+ * Weights and the per-call record staging of host outputs are not counted.
+ * Errors: SML_ERR_BAD_ARG.
+ */
+int sml_workspace_bytes(const sml_ctx* ctx, int H, int W, size_t* plan_bytes, int* plan_resident,
+                        size_t* resident_bytes);
+
+/*
+ * sml_error_word -- the stream-ordered status of the context's asynchronous work.  Every
+ * mbarrier wait of the tensor-core conv kernels is bounded (2 s); a kernel that gives up sets
+ * the context's device error word and returns early, leaving its outputs incomplete.  The
+ * synchronous calls check the word and fail with SML_ERR_CUDA; sml_localize_async,
+ * sml_forward_maps and sml_decode_maps cannot.  This call enqueues on `stream`, after the work
+ * already enqueued there, a copy of the word into d_word (device int: 0 = every kernel of the
+ * context finished its work, nonzero = one gave up) and clears the word.  Call it after the
+ * asynchronous calls whose results are about to be used, on their stream.
+ * Errors: SML_ERR_BAD_ARG, SML_ERR_CUDA.
+ */
+int sml_error_word(sml_ctx* ctx, int* d_word, void* stream);
 
 /*
  * sml_localize_sigma -- sml_localize plus the uncertainties of every detection, for nets
@@ -201,6 +233,20 @@ int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, in
                         float* amax);
 
 /*
+ * sml_calibrate_fp8 -- activation scales for the "fp8" precision (per-layer activation scale,
+ * per-output-channel weight scales).  Runs sml_activation_amax on an fp32 or bf16 context of
+ * the net over the calibration frames (d_frames: device [T][H][W] uint16, T >= 1; camera as in
+ * sml_activation_amax) and writes to act_scales (host float[L], L = the net's conv layers):
+ * act_scales[0] = 1 (layer 0 reads the frames) and, for l >= 1,
+ * act_scales[l] = max(amax[l], 1e-6) * margin / 448 (448 = the largest finite e4m3 value;
+ * margin > 0 leaves headroom above the calibration maximum, 1 = none), in float32.  These
+ * are the "act_scales" of an fp8 net spec of the same net.  Synchronous.
+ * Errors: SML_ERR_BAD_ARG (T < 1, margin <= 0), and those of sml_activation_amax.
+ */
+int sml_calibrate_fp8(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam,
+                      float margin, float* act_scales);
+
+/*
  * sml_decode_maps_static -- the decode of sml_decode_maps for callers that cannot allocate
  * device memory.  This entry point has no counterpart in the paper; it exists for callers
  * that must not call cudaMalloc/cudaFree while they run: an acquisition loop sharing the GPU
@@ -218,7 +264,8 @@ int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, in
  * T*H*W <= 16,777,216 pixels (e.g. 256 frames of 256 x 256); larger calls return
  * SML_ERR_UNSUPPORTED without touching any buffer.  The first call on a device looks up the
  * array's device address (with that device current); make that first call before any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU (other streams,
+ * capture.  A call in a new CUDA context of the device (after cudaDeviceReset, for instance)
+ * looks the address up again; make that call before any capture too.  All calls share the array: calls whose work overlaps on the GPU (other streams,
  * other host threads) race and must be serialised by the caller.
  * Errors: SML_ERR_BAD_ARG, SML_ERR_UNSUPPORTED, SML_ERR_CUDA.
  */

@@ -26,6 +26,16 @@ extern "C" {
 
 int sml_debug_umma(const void* d_a, const void* d_b, float* d_d, int n, int k, int kind, int d_col, void* stream);
 
+/*
+ * sml_debug_set_error_word: host-side fault injection for tests of the error paths.  Writes
+ * value into the context's device error word (synchronously, with no kernel involved), as
+ * a tensor-core kernel does when one of its bounded waits gives up.  The next synchronous
+ * call then fails with SML_ERR_CUDA, and sml_error_word reports it to asynchronous callers.
+ * Returns SML_OK, SML_ERR_BAD_ARG or SML_ERR_CUDA.
+ */
+struct sml_ctx;
+int sml_debug_set_error_word(struct sml_ctx* ctx, int value);
+
 #ifdef __cplusplus
 }
 #endif

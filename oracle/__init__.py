@@ -103,7 +103,8 @@ def _ptr(a):
 class Net:
     """Network description parsed from a JSON net spec and an SMLW weight blob.
 
-    Plain stacks (version-1 blobs): L conv layers of C channels with the spec's dilations.
+    Plain stacks: L conv layers of C channels with the spec's dilations (version-1 blobs up to
+    16 layers, version 2 with reserved = 0 for 17 to 32).
     Nets with dense connection dilated blocks (spec key "dcd", version-2 blobs; Sec. 3.2.1):
     a stem conv (dilations[0], in_ch -> C); per block, dense layers whose input is the block
     input and every earlier output of the block concatenated (C + j*growth channels, growth
@@ -141,7 +142,8 @@ class Net:
         else:
             self.growth = 0
             self.layers = [(self.in_ch if l == 0 else C, C, d, "plain") for l, d in enumerate(self.plain_dil)]
-            fmt, version = "<8s7I16i", 1
+            # plain stacks beyond 16 layers carry their 17..32 dilations in the version-2 header
+            fmt, version = ("<8s7I16i", 1) if len(self.layers) <= 16 else ("<8s7I32i", 2)
         unet = s.get("unet")
         self.unet = int(unet["levels"]) if unet else 0
         if self.unet:

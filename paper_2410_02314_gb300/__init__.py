@@ -39,6 +39,9 @@ EXPORTS = (
     "sml_last_error",
     "sml_localize",
     "sml_num_heads",
+    "sml_num_layers",
+    "sml_workspace_bytes",
+    "sml_error_word",
     "sml_localize_sigma",
     "sml_localize_async",
     "sml_forward_maps",
@@ -46,9 +49,11 @@ EXPORTS = (
     "sml_decode_maps_static",
     "sml_last_launch_count",
     "sml_activation_amax",
+    "sml_calibrate_fp8",
     "sml_profile_enable",
     "sml_profile_read",
     "sml_debug_umma",
+    "sml_debug_set_error_word",
     "sml_train_ingest",
     "sml_train_conv_fwd",
     "sml_train_conv_bwd_work_bytes",
@@ -114,6 +119,12 @@ def lib():
         L.sml_localize.restype = I
         L.sml_num_heads.argtypes = [P]
         L.sml_num_heads.restype = I
+        L.sml_num_layers.argtypes = [P]
+        L.sml_num_layers.restype = I
+        L.sml_workspace_bytes.argtypes = [P, I, I, ctypes.POINTER(S), ctypes.POINTER(I), ctypes.POINTER(S)]
+        L.sml_workspace_bytes.restype = I
+        L.sml_error_word.argtypes = [P, P, P]
+        L.sml_error_word.restype = I
         L.sml_localize_sigma.argtypes = [P, P, I, I, I, ctypes.POINTER(_Camera), ctypes.POINTER(_Thresholds), P, P, S,
                                          ctypes.POINTER(S)]
         L.sml_localize_sigma.restype = I
@@ -130,12 +141,16 @@ def lib():
         L.sml_last_launch_count.restype = I
         L.sml_activation_amax.argtypes = [P, P, I, I, I, ctypes.POINTER(_Camera), P]
         L.sml_activation_amax.restype = I
+        L.sml_calibrate_fp8.argtypes = [P, P, I, I, I, ctypes.POINTER(_Camera), F, P]
+        L.sml_calibrate_fp8.restype = I
         L.sml_profile_enable.argtypes = [P, I]
         L.sml_profile_enable.restype = I
         L.sml_profile_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]
         L.sml_profile_read.restype = I
         L.sml_debug_umma.argtypes = [P, P, P, I, I, I, I, P]
         L.sml_debug_umma.restype = I
+        L.sml_debug_set_error_word.argtypes = [P, I]
+        L.sml_debug_set_error_word.restype = I
         LL = ctypes.c_longlong
         L.sml_reader_open.argtypes = [ctypes.c_char_p, LL, I, I, I, I, I, ctypes.POINTER(P)]
         L.sml_reader_open.restype = I
@@ -270,6 +285,24 @@ def sml_num_heads(ctx) -> int:
     return lib().sml_num_heads(ctx)
 
 
+def sml_num_layers(ctx) -> int:
+    return lib().sml_num_layers(ctx)
+
+
+def sml_workspace_bytes(ctx, H, W):
+    """(bytes of a plan for H x W frames, whether the context holds it now, bytes of all plans
+    the context holds)."""
+    pb, res, tot = ctypes.c_size_t(0), ctypes.c_int(0), ctypes.c_size_t(0)
+    _check(ctx, lib().sml_workspace_bytes(ctx, int(H), int(W), ctypes.byref(pb), ctypes.byref(res), ctypes.byref(tot)))
+    return int(pb.value), bool(res.value), int(tot.value)
+
+
+def sml_error_word(ctx, d_word, stream=None):
+    """Enqueue the copy of the context's device error word into d_word (CUDA int32 tensor) and
+    clear it (stream ordered)."""
+    _check(ctx, lib().sml_error_word(ctx, _ptr(d_word), _stream(stream)))
+
+
 def sml_localize_sigma(ctx, frames, p_min, gain=1.0, offset=100.0, gain_map=None, offset_map=None, capacity=None):
     """sml_localize plus the uncertainties of each record (9-head nets): returns (records,
     sigmas) as numpy arrays of RECORD_DTYPE and SIGMA_DTYPE, sigmas[k] belonging to records[k]."""
@@ -397,20 +430,29 @@ def sml_activation_amax(ctx, d_frames, gain=1.0, offset=100.0, gain_map=None, of
     return out
 
 
+def sml_calibrate_fp8(ctx, d_frames, margin=1.0, gain=1.0, offset=100.0, gain_map=None, offset_map=None):
+    """Activation scales of the fp8 precision from a calibration pass (numpy float32 [L])."""
+    T, H, W = (int(s) for s in d_frames.shape)
+    out = np.zeros(64, dtype=np.float32)
+    cam = _camera(gain, offset, gain_map, offset_map)
+    _check(ctx, lib().sml_calibrate_fp8(ctx, _ptr(d_frames), T, H, W, ctypes.byref(cam), float(margin),
+                                        out.ctypes.data))
+    return out
+
+
 def calibrate_fp8(net_spec: str, weights: bytes, d_frames, margin=1.0, **cam):
-    """FP8 net spec from a bf16 calibration pass: act_scales[l] = margin * amax[l] / 448."""
+    """The fp8 net spec of a net: its act_scales come from sml_calibrate_fp8 on a bf16 context
+    of the same net over the calibration frames."""
     import json
 
     spec = json.loads(net_spec)
-    L = len(spec["dilations"])
-    cal = dict(spec, precision="bf16")
-    ctx = sml_create(json.dumps(cal), weights)
+    ctx = sml_create(json.dumps(dict(spec, precision="bf16")), weights)
     try:
-        amax = sml_activation_amax(ctx, d_frames, **cam)[:L]
+        L = sml_num_layers(ctx)
+        scales = sml_calibrate_fp8(ctx, d_frames, margin, **cam)[:L]
     finally:
         sml_destroy(ctx)
-    scales = [1.0] + [max(float(a), 1e-6) * margin / 448.0 for a in amax[1:]]
-    return json.dumps(dict(spec, precision="fp8", act_scales=scales))
+    return json.dumps(dict(spec, precision="fp8", act_scales=[float(x) for x in scales]))
 
 
 def sml_profile_enable(ctx, on: bool):

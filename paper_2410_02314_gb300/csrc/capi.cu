@@ -18,6 +18,7 @@
 
 #include <chrono>
 
+#include "../../include/sml_debug.h"
 #include "../../include/sml_io.h"
 #include "../../include/sml_train.h"
 #include "sml_internal.h"
@@ -170,6 +171,8 @@ struct Plan {
   unsigned* flag_words = nullptr;  // decode: the count pass's detection ballots
   uint16_t* frames = nullptr;  // staging for host frames
   float* cam_maps = nullptr;   // staging for host camera maps [2][H][W]
+  cudaEvent_t done = nullptr;  // recorded on the stream of every call that used the plan
+  size_t bytes = 0;            // device bytes of the buffers above
   CUtensorMap tmap[kMaxLayers];  // per layer, over its input buffer: one box per row (width depends on d)
 };
 
@@ -297,6 +300,7 @@ int upload(sml_ctx* ctx, T** dst, const void* src, size_t bytes) {
 }
 
 void free_plan(Plan& p) {
+  if (p.done) cudaEventDestroy(p.done);
   for (void* a : p.act) cudaFree(a);
   cudaFree(p.maps);
   cudaFree(p.block_counts);
@@ -360,6 +364,43 @@ struct ProfScope {
 
 constexpr size_t kMaxPlans = 4;
 
+// Device buffers of a plan for frames of H x W: the chunk (Tc frames of at most chunk_px
+// pixels together), the activation buffers of every resolution level, the maps, the decode
+// scratch, and the staging of host frames (with the context frames) and host camera maps.
+struct PlanSizes {
+  int Tc = 1;
+  size_t act[kMaxBufs] = {0};
+  size_t maps = 0, counts = 0, offsets = 0, flags = 0, frames = 0, cam = 0;
+  size_t total() const {
+    size_t t = maps + counts + offsets + flags + frames + cam;
+    for (size_t a : act) t += a;
+    return t;
+  }
+};
+
+PlanSizes plan_sizes(const sml_ctx* ctx, int H, int W) {
+  PlanSizes z;
+  const long long hw = (long long)H * W;
+  z.Tc = (int)std::max(1LL, ctx->chunk_px / hw);
+  const size_t npx = (size_t)z.Tc * hw;
+  for (int b = 0; b < ctx->nbuf; ++b)
+    z.act[b] = (size_t)z.Tc * level_dim(H, ctx->buf[b].level) * level_dim(W, ctx->buf[b].level) * ctx->buf[b].ct *
+               act_elem_bytes(ctx->prec);
+  z.maps = npx * ctx->nh * sizeof(float);
+  z.counts = decode_blocks(npx) * sizeof(unsigned);
+  z.offsets = decode_blocks(npx) * sizeof(unsigned long long);
+  z.flags = decode_blocks(npx) * (kDecodePxPerBlock / 32) * sizeof(unsigned);
+  z.frames = (size_t)(z.Tc + 2) * hw * sizeof(uint16_t);  // + context frames
+  z.cam = 2 * hw * sizeof(float);
+  return z;
+}
+
+// Marks the end of a call's use of the current plan on its stream: a later eviction of the
+// plan waits for this point only (not for the whole device).
+void plan_used(sml_ctx* ctx, cudaStream_t s) {
+  if (ctx->plan && ctx->plan->done) cudaEventRecord(ctx->plan->done, s);
+}
+
 int get_plan(sml_ctx* ctx, int H, int W) {
   ++ctx->plan_clock;
   for (auto& q : ctx->plans)
@@ -372,33 +413,35 @@ int get_plan(sml_ctx* ctx, int H, int W) {
     size_t victim = 0;
     for (size_t k = 1; k < ctx->plans.size(); ++k)
       if (ctx->plans[k]->last_use < ctx->plans[victim]->last_use) victim = k;
-    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    cudaDeviceSynchronize();  // the plan's buffers may still be in use by async calls
-    free_plan(*ctx->plans[victim]);
+    // its buffers may still be in use by the last call that used it, on that call's stream
+    Plan& v = *ctx->plans[victim];
+    if (v.done) SML_CUDA(cudaEventSynchronize(v.done), "plan eviction");
+    free_plan(v);
     ctx->plans.erase(ctx->plans.begin() + victim);
   }
   std::unique_ptr<Plan> np(new Plan());
   Plan& p = *np;
-  long long hw = (long long)H * W;
-  int Tc = (int)std::max(1LL, ctx->chunk_px / hw);
-  size_t npx = (size_t)Tc * hw;
+  const PlanSizes z = plan_sizes(ctx, H, W);
+  const int Tc = z.Tc;
   int r;
   for (int b = 0; b < ctx->nbuf; ++b) {
-    const size_t px = (size_t)Tc * level_dim(H, ctx->buf[b].level) * level_dim(W, ctx->buf[b].level);
-    if ((r = dev_alloc(ctx, &p.act[b], px * ctx->buf[b].ct * act_elem_bytes(ctx->prec)))) {
+    if ((r = dev_alloc(ctx, &p.act[b], z.act[b]))) {
       free_plan(p);
       return r;
     }
   }
-  if ((r = dev_alloc(ctx, &p.maps, npx * ctx->nh * sizeof(float))) ||
-      (r = dev_alloc(ctx, &p.block_counts, decode_blocks(npx) * sizeof(unsigned))) ||
-      (r = dev_alloc(ctx, &p.block_offsets, decode_blocks(npx) * sizeof(unsigned long long))) ||
-      (r = dev_alloc(ctx, &p.flag_words, decode_blocks(npx) * (kDecodePxPerBlock / 32) * sizeof(unsigned))) ||
-      (r = dev_alloc(ctx, &p.frames, (size_t)(Tc + 2) * hw * sizeof(uint16_t))) ||  // + context frames
-      (r = dev_alloc(ctx, &p.cam_maps, 2 * hw * sizeof(float)))) {
+  if ((r = dev_alloc(ctx, &p.maps, z.maps)) || (r = dev_alloc(ctx, &p.block_counts, z.counts)) ||
+      (r = dev_alloc(ctx, &p.block_offsets, z.offsets)) || (r = dev_alloc(ctx, &p.flag_words, z.flags)) ||
+      (r = dev_alloc(ctx, &p.frames, z.frames)) || (r = dev_alloc(ctx, &p.cam_maps, z.cam))) {
     free_plan(p);
     return r;
   }
+  cudaError_t e = cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return cuda_fail(ctx, e, "plan event");
+  }
+  p.bytes = z.total();
   if (ctx->prec != kFP32) {
     for (int l = 1; l < ctx->L; ++l) {
       const LayerDesc& y = ctx->lay[l];
@@ -602,6 +645,7 @@ int localize_device(sml_ctx* ctx, const uint16_t* d_frames, bool frames_on_host,
     ProfScope ps(ctx, SML_KERNEL_DECODE, s);
     SML_CUDA(launch_decode(da, s, &ctx->launches), "decode");
   }
+  plan_used(ctx, s);
   return SML_OK;
 }
 
@@ -644,7 +688,7 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
   if (dc == root.obj.end() || dc->second.kind == JVal::kNull) {
     // plain stack: layer l reads buffer (l-1) & 1 and writes buffer l & 1
     ctx->L = (int)dil.size();
-    if (ctx->L < 2 || ctx->L > 16) return fail(nullptr, SML_ERR_BAD_SPEC, "need 2..16 layers");
+    if (ctx->L < 2 || ctx->L > kMaxLayers) return fail(nullptr, SML_ERR_BAD_SPEC, "need 2..%d layers", kMaxLayers);
     ctx->ct = C;
     for (int l = 0; l < ctx->L; ++l) {
       LayerDesc& y = ctx->lay[l];
@@ -811,13 +855,14 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
   return SML_OK;
 }
 
-// Weight blob: header "<8s7I16i" (version 1, plain stacks) or "<8s7I32i" (version 2, nets
-// with dense blocks: reserved = growth, dil[32] = every layer's dilation in execution order);
+// Weight blob: header "<8s7I16i" (version 1, plain stacks of up to 16 layers) or "<8s7I32i"
+// (version 2: nets with dense blocks or a U-Net, reserved = growth, and plain stacks of 17..32
+// layers, reserved = 0; dil[32] = every layer's dilation in execution order);
 // then per layer W[cout][cin][3][3], b[cout] (+ BatchNorm, version 1 only) and the heads.
 // Checks the header against the spec and the size; host only (runs before any device call).
 int check_blob(const sml_ctx* ctx, const void* blob, size_t bytes, size_t* hdr_out, int* has_bn_out) {
   const uint8_t* b = static_cast<const uint8_t*>(blob);
-  const bool v2 = ctx->growth > 0 || ctx->unet > 0;
+  const bool v2 = ctx->growth > 0 || ctx->unet > 0 || ctx->L > 16;  // plain stacks of 17..32 layers: version 2
   const int ndil = v2 ? 32 : 16;
   const size_t hdr_bytes = 8 + 7 * 4 + (size_t)ndil * 4;
   if (!blob || bytes < hdr_bytes || memcmp(b, "SMLW0001", 8) != 0)
@@ -1061,6 +1106,31 @@ int sml_localize(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, cons
 
 int sml_num_heads(const sml_ctx* ctx) { return ctx ? ctx->nh : 0; }
 
+int sml_num_layers(const sml_ctx* ctx) { return ctx ? ctx->L : 0; }
+
+int sml_workspace_bytes(const sml_ctx* ctx, int H, int W, size_t* plan_bytes, int* plan_resident,
+                        size_t* resident_bytes) {
+  if (!ctx || H < 1 || W < 1 || H > 16384 || W > 16384) return SML_ERR_BAD_ARG;
+  if (plan_bytes) *plan_bytes = plan_sizes(ctx, H, W).total();
+  int res = 0;
+  size_t tot = 0;
+  for (const auto& q : ctx->plans) {
+    tot += q->bytes;
+    if (q->H == H && q->W == W) res = 1;
+  }
+  if (plan_resident) *plan_resident = res;
+  if (resident_bytes) *resident_bytes = tot;
+  return SML_OK;
+}
+
+int sml_error_word(sml_ctx* ctx, int* d_word, void* stream) {
+  if (!ctx || !d_word) return SML_ERR_BAD_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SML_CUDA(cudaMemcpyAsync(d_word, ctx->d_err, sizeof(int), cudaMemcpyDeviceToDevice, s), "error word");
+  SML_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s), "clear error word");
+  return SML_OK;
+}
+
 int sml_localize_sigma(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, const sml_camera* cam,
                        const sml_thresholds* thr, sml_record* out, sml_sigma* out_sigma, size_t capacity,
                        size_t* n_out) {
@@ -1107,6 +1177,7 @@ int sml_forward_maps(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W
                            d_maps + (size_t)t0 * ctx->nh * fpx, d_logits ? d_logits + (size_t)t0 * fpx : nullptr, s)))
       return r;
   }
+  plan_used(ctx, s);
   return SML_OK;
 }
 
@@ -1144,6 +1215,7 @@ int sml_decode_maps(sml_ctx* ctx, const float* d_maps, int T, int H, int W, cons
     ProfScope ps(ctx, SML_KERNEL_DECODE, s);
     SML_CUDA(launch_decode(da, s, &ctx->launches), "decode");
   }
+  plan_used(ctx, s);
   return SML_OK;
 }
 
@@ -1202,11 +1274,27 @@ int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, in
                            nullptr, s, d_amax)))
       return r;
   }
+  plan_used(ctx, s);
   unsigned h[kMaxLayers];
   SML_CUDA(cudaMemcpyAsync(h, d_amax, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H amax");
   SML_CUDA(cudaStreamSynchronize(s), "amax");
   for (int l = 1; l < ctx->L; ++l) memcpy(&amax[l], &h[l], sizeof(float));
   return check_device_error(ctx);
+}
+
+int sml_calibrate_fp8(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam, float margin,
+                      float* act_scales) {
+  if (!ctx) return SML_ERR_BAD_ARG;
+  if (!act_scales || !(margin > 0.0f) || !std::isfinite(margin)) return fail(ctx, SML_ERR_BAD_ARG, "bad argument");
+  if (T < 1) return fail(ctx, SML_ERR_BAD_ARG, "calibration needs at least one frame");
+  float amax[kMaxLayers] = {0};
+  int r = sml_activation_amax(ctx, d_frames, T, H, W, cam, amax);
+  if (r) return r;
+  // e4m3 holds magnitudes up to 448: scale = margin * amax / 448, with amax floored at 1e-6
+  // (a layer input that is zero on every calibration frame keeps a usable scale)
+  act_scales[0] = 1.0f;  // layer 0 reads the frames, not stored activations
+  for (int l = 1; l < ctx->L; ++l) act_scales[l] = std::max(amax[l], 1e-6f) * margin / 448.0f;
+  return SML_OK;
 }
 
 // ------------------------------------------------------------------ training (sml_train.h)
@@ -1246,6 +1334,14 @@ int sml_train_heads_loss(const float* a, const float* tgt, int B, int H, int W, 
   if (work_bytes < train_heads_work_bytes(B, H, W, C)) return SML_ERR_BAD_ARG;
   return train_status(train_heads_loss(a, tgt, B, H, W, C, hw, hb, h, loss, da ? grad_scale : nullptr, da, dhw, dhb,
                                        work, static_cast<cudaStream_t>(stream)));
+}
+
+// Debug entry (include/sml_debug.h): host-side injection of a device-side failure report.
+int sml_debug_set_error_word(sml_ctx* ctx, int value) {
+  if (!ctx) return SML_ERR_BAD_ARG;
+  SML_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  SML_CUDA(cudaMemcpy(ctx->d_err, &value, sizeof(int), cudaMemcpyHostToDevice), "set error word");
+  return SML_OK;
 }
 
 // Debug entry (include/sml_debug.h): one UMMA tile through the conv kernel's descriptor helpers.

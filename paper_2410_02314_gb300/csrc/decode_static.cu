@@ -32,19 +32,51 @@ struct StaticScratch {
 
 static __device__ __align__(256) StaticScratch g_scratch;
 
-// Device address of g_scratch, looked up once per device (with that device current).
+// Device address of g_scratch, looked up with the device current on the first call and again
+// whenever the current CUDA context's unique ID differs from the one of the last look-up:
+// after cudaDeviceReset (or a release of the primary context) the module is loaded anew in a
+// new context and the array may live elsewhere.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 StaticScratch* g_addr[kMaxDevices] = {nullptr};
+unsigned long long g_addr_ctx[kMaxDevices] = {0};
+
+typedef CUresult (*PFN_ctxGetCurrent_t)(CUcontext*);
+typedef CUresult (*PFN_ctxGetId_t)(CUcontext, unsigned long long*);
+
+template <typename F>
+F driver_fn(const char* name) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    return reinterpret_cast<F>(p);
+  return nullptr;
+}
+
+// Unique ID of the calling thread's current context (0 if none is current yet).
+bool current_ctx_id(unsigned long long* id) {
+  static PFN_ctxGetCurrent_t get_cur = driver_fn<PFN_ctxGetCurrent_t>("cuCtxGetCurrent");
+  static PFN_ctxGetId_t get_id = driver_fn<PFN_ctxGetId_t>("cuCtxGetId");
+  CUcontext cur = nullptr;
+  if (!get_cur || !get_id || get_cur(&cur) != CUDA_SUCCESS) return false;
+  *id = 0;
+  return !cur || get_id(cur, id) == CUDA_SUCCESS;
+}
 
 int scratch_address(StaticScratch** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SML_ERR_CUDA;
+  unsigned long long id = 0;
+  if (!current_ctx_id(&id)) return SML_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  if (id == 0 || !g_addr[dev] || g_addr_ctx[dev] != id) {
+    // the look-up also makes the device's primary context current when none was
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return SML_ERR_CUDA;
+    if (!current_ctx_id(&id) || id == 0) return SML_ERR_CUDA;
     g_addr[dev] = static_cast<StaticScratch*>(p);
+    g_addr_ctx[dev] = id;
   }
   *out = g_addr[dev];
   return SML_OK;

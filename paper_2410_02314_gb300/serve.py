@@ -2,13 +2,21 @@
 continuous batching on one GPU.
 
 * Weights and per-size workspaces stay resident: each slot is one library context (its own
-  workspace and TMA descriptors, cached per frame size) driving its own CUDA stream.
+  workspace and TMA descriptors, kept per frame size) driving its own CUDA stream.
 * Admission: requests wait in arrival order and start as soon as a slot is free and their
-  device memory (frames + record buffer) fits the HBM budget next to the requests already
-  running.  Requests that arrive while others run are admitted the moment a slot and memory
-  free up, and their kernels interleave with the running ones on the device.
+  device memory fits the HBM budget next to what is already held.  The budget counts
+  everything the serving loop holds on the device: every slot's resident workspaces (one
+  per frame size a slot has run, reported by the library) and record buffers, plus, per
+  running request, its frames and records; a request whose frame size is new to its slot
+  is also charged the workspace the library will allocate for it.  The budget defaults to
+  the device's free memory at the start of the run plus what the slots already hold, minus
+  a reserve.  Requests that arrive while others run are admitted the moment a slot and
+  memory free up, and their kernels interleave with the running ones on the device.
 * Each request's records are the same alone and in the mix: every frame is computed
   independently and deterministically (no reduction depends on what else is on the GPU).
+* A kernel that gave up on one of its bounded waits sets its context's error word; the
+  executor reads the word with each request's record count and fails that request
+  (Request.error) instead of returning incomplete records.
 * Latency is measured from arrival to records in host memory; the report gives p50 / p99
   latency and sustained frames/s.
 
@@ -38,6 +46,8 @@ class Request:
     admitted: float = -1.0
     done: float = -1.0
     records: object = None
+    error: str | None = None  # set when the request failed on the device
+    slot: int = -1
 
     @property
     def shape(self):
@@ -57,7 +67,9 @@ def record_capacity(T, H, W):
     return max(16, (T * ((H + 1) // 2) * ((W + 1) // 2)))
 
 
-def device_bytes(req: Request):
+def request_bytes(req: Request):
+    """Device bytes a running request holds beyond its slot's resident state: its frames, its
+    record buffer and its count."""
     T, H, W = req.shape
     return T * H * W * 2 + record_capacity(T, H, W) * 24 + 16
 
@@ -65,25 +77,44 @@ def device_bytes(req: Request):
 class Scheduler:
     """FIFO admission under a slot count and an HBM byte budget; executor-agnostic.
 
-    An executor provides: slots (int), start(slot, req) and poll(slot) -> bool (True once
-    the request on that slot has finished and its records are in req.records)."""
+    An executor provides: slots (int); start(slot, req); poll(slot) -> bool (True once the
+    request on that slot has finished: its records are in req.records, or req.error says why
+    it failed); resident_bytes() (device bytes every slot holds between requests: workspaces
+    and record buffers); plan_bytes(slot, shape) (workspace a request of that (T, H, W) shape
+    adds on that slot: 0 if the slot holds one for H x W); and, for a budget derived from the
+    device, memory_budget(reserve)."""
 
-    def __init__(self, executor, hbm_budget: int, clock=time.perf_counter):
+    def __init__(self, executor, hbm_budget: int | None = None, reserve: int = 4 << 30, clock=time.perf_counter):
         self.ex = executor
-        self.budget = int(hbm_budget)
+        self.budget = int(hbm_budget) if hbm_budget is not None else int(executor.memory_budget(reserve))
         self.clock = clock
         self.in_use = 0
         self.peak_in_use = 0
         self.max_queue = 0
+        self.failed = 0
+
+    def _need(self, slot, r):
+        return request_bytes(r) + self.ex.plan_bytes(slot, r.shape)
+
+    def _pick_slot(self, free, r):
+        """A free slot that already holds the request's workspace, else the first free slot."""
+        for k, slot in enumerate(free):
+            if self.ex.plan_bytes(slot, r.shape) == 0:
+                return k
+        return 0
 
     def run(self, requests, idle_sleep=5e-5):
         reqs = sorted(requests, key=lambda r: r.arrival)
+        base = self.ex.resident_bytes()
         for r in reqs:
-            if device_bytes(r) > self.budget:
-                raise ValueError(f"request {r.rid} needs {device_bytes(r)} bytes, above the HBM budget {self.budget}")
+            need = min(self._need(s, r) for s in range(self.ex.slots))
+            if base + need > self.budget:
+                raise ValueError(f"request {r.rid} needs {need} bytes next to the {base} resident, above the HBM "
+                                 f"budget {self.budget}")
         waiting = collections.deque()
         free = list(range(self.ex.slots))
         running = {}  # slot -> request
+        transient = 0  # bytes of the running requests
         nxt = 0
         t0 = self.clock()
         done = 0
@@ -94,20 +125,30 @@ class Scheduler:
                 waiting.append(reqs[nxt])
                 nxt += 1
             self.max_queue = max(self.max_queue, len(waiting))
-            while waiting and free and self.in_use + device_bytes(waiting[0]) <= self.budget:
-                r = waiting.popleft()
-                slot = free.pop(0)
-                self.in_use += device_bytes(r)
-                self.peak_in_use = max(self.peak_in_use, self.in_use)
+            while waiting and free:
+                r = waiting[0]
+                k = self._pick_slot(free, r)
+                slot = free[k]
+                plan = self.ex.plan_bytes(slot, r.shape)
+                if self.ex.resident_bytes() + plan + transient + request_bytes(r) > self.budget:
+                    break
+                waiting.popleft()
+                free.pop(k)
+                transient += request_bytes(r)
+                r.slot = slot
                 r.admitted = self.clock() - t0
-                self.ex.start(slot, r)
+                self.ex.start(slot, r)  # allocates the new workspace, if any
                 running[slot] = r
+                self.in_use = self.ex.resident_bytes() + transient
+                self.peak_in_use = max(self.peak_in_use, self.in_use)
                 progressed = True
             for slot in list(running):
                 if self.ex.poll(slot):
                     r = running.pop(slot)
                     r.done = self.clock() - t0
-                    self.in_use -= device_bytes(r)
+                    transient -= request_bytes(r)
+                    self.in_use = self.ex.resident_bytes() + transient
+                    self.failed += r.error is not None
                     free.append(slot)
                     done += 1
                     progressed = True
@@ -131,7 +172,11 @@ def report(reqs):
         "frames_per_s": frames / span,
         "mpix_per_s": px / span / 1e6,
         "span_s": span,
+        "failed": sum(r.error is not None for r in reqs),
     }
+
+
+MAX_PLANS = 4  # frame sizes whose workspace a library context keeps (least recently used freed first)
 
 
 class GpuExecutor:
@@ -152,8 +197,9 @@ class GpuExecutor:
         # once they are large enough)
         self.d_out = [None] * slots
         self.h_out = [None] * slots
-        self.h_n = [torch.empty(1, dtype=torch.int64, pin_memory=True) for _ in range(slots)]
-        self.d_n = [torch.zeros(1, dtype=torch.int64, device=self.dev) for _ in range(slots)]
+        self.h_n = [torch.empty(2, dtype=torch.int64, pin_memory=True) for _ in range(slots)]
+        # count (element 0) and the context's error word (low half of element 1)
+        self.d_n = [torch.zeros(2, dtype=torch.int64, device=self.dev) for _ in range(slots)]
 
     def _buffers(self, slot, cap):
         torch = self.torch
@@ -163,8 +209,8 @@ class GpuExecutor:
         return self.d_out[slot], self.h_out[slot]
 
     def warm(self, shapes, max_request=None):
-        """Create each slot's workspace for the given frame sizes (and, if given, record buffers
-        for the largest request shape (T, H, W)) before timing."""
+        """Create each slot's workspace for the given frame sizes (at most MAX_PLANS) and, if
+        given, record buffers for the largest request shape (T, H, W) before timing."""
         torch = self.torch
         for slot, (loc, st) in enumerate(zip(self.locs, self.streams)):
             for (H, W) in shapes:
@@ -176,7 +222,34 @@ class GpuExecutor:
                 self._buffers(slot, record_capacity(*max_request))
         torch.cuda.synchronize(self.dev)
 
+    def resident_bytes(self):
+        """Workspaces every slot's context holds (the library's own count) and the slots'
+        record buffers."""
+        from . import sml_workspace_bytes
+
+        ws = sum(sml_workspace_bytes(loc.ctx, 1, 1)[2] for loc in self.locs)
+        return ws + sum(0 if d is None else d.numel() for d in self.d_out)
+
+    def plan_bytes(self, slot, shape):
+        """Device bytes a request of shape (T, H, W) adds to what the slot keeps: the library's
+        workspace for H x W if the slot's context holds none (the library's own figure; the
+        plan it may free in exchange is not credited), and the growth of the slot's record
+        buffer if the request needs a larger one."""
+        from . import sml_workspace_bytes
+
+        T, H, W = shape
+        pb, res, _ = sml_workspace_bytes(self.locs[slot].ctx, H, W)
+        have = 0 if self.d_out[slot] is None else self.d_out[slot].numel()
+        return (0 if res else pb) + max(0, record_capacity(T, H, W) * 24 - have)
+
+    def memory_budget(self, reserve):
+        """The device's free memory now, plus what the slots already hold, minus `reserve`."""
+        free, _ = self.torch.cuda.mem_get_info(self.dev)
+        return free + self.resident_bytes() - reserve
+
     def start(self, slot, r: Request):
+        from . import sml_error_word
+
         torch = self.torch
         st = self.streams[slot]
         T, H, W = r.shape
@@ -185,8 +258,11 @@ class GpuExecutor:
         d_n, h_n = self.d_n[slot], self.h_n[slot]
         with torch.cuda.stream(st):
             d_frames = r.frames.to(self.dev, non_blocking=True)
-        self.locs[slot].localize_async(d_frames, r.p_min, d_out[: cap * 24], d_n, gain=r.gain, offset=r.offset,
+            d_n[1:].zero_()
+        self.locs[slot].localize_async(d_frames, r.p_min, d_out[: cap * 24], d_n[:1], gain=r.gain, offset=r.offset,
                                        gain_map=r.gain_map, offset_map=r.offset_map, stream=st)
+        # the context's error word after this request's kernels, next to its count
+        sml_error_word(self.locs[slot].ctx, d_n[1:].view(torch.int32)[:1], stream=st)
         with torch.cuda.stream(st):
             h_n.copy_(d_n, non_blocking=True)
             ev = torch.cuda.Event()
@@ -200,6 +276,8 @@ class GpuExecutor:
             return False
         if s["phase"] == 1:  # count known: copy exactly the records back
             n = int(s["h_n"][0])
+            if int(s["h_n"][1]) != 0:
+                return self._fail(slot, "a kernel gave up on a bounded wait; the request's records are incomplete")
             st = self.streams[slot]
             h_out = self.h_out[slot]
             with torch.cuda.stream(st):
@@ -216,26 +294,58 @@ class GpuExecutor:
         self.state[slot] = None
         return True
 
+    def _fail(self, slot, why):
+        r = self.state[slot]["req"]
+        r.error = why
+        r.records = None
+        self.state[slot] = None
+        return True
+
 
 class FakeExecutor:
-    """Host-only executor with a fixed service time per frame (for testing the scheduler)."""
+    """Host-only executor with a fixed service time per frame (for testing the scheduler).
+    It models the library's per-slot workspaces: a frame size new to a slot costs
+    plan_cost(H, W) bytes, kept until the slot's MAX_PLANS-th newer size evicts it.
+    fail_rids: requests whose device work reports an error."""
 
-    def __init__(self, slots, s_per_frame, clock):
+    def __init__(self, slots, s_per_frame, clock, plan_cost=lambda H, W: 0, fail_rids=()):
         self.slots = slots
         self.s_per_frame = s_per_frame
         self.clock = clock
+        self.plan_cost = plan_cost
+        self.fail_rids = set(fail_rids)
         self.busy_until = [None] * slots
         self.reqs = [None] * slots
+        self.plans = [collections.OrderedDict() for _ in range(slots)]  # (H, W) -> bytes, LRU first
         self.concurrent_peak = 0
 
+    def resident_bytes(self):
+        return sum(sum(p.values()) for p in self.plans)
+
+    def plan_bytes(self, slot, shape):
+        _, H, W = shape
+        return 0 if (H, W) in self.plans[slot] else self.plan_cost(H, W)
+
     def start(self, slot, r):
+        _, H, W = r.shape
+        p = self.plans[slot]
+        if (H, W) in p:
+            p.move_to_end((H, W))
+        else:
+            if len(p) >= MAX_PLANS:
+                p.popitem(last=False)
+            p[(H, W)] = self.plan_cost(H, W)
         self.busy_until[slot] = self.clock() + r.nframes * self.s_per_frame
         self.reqs[slot] = r
         self.concurrent_peak = max(self.concurrent_peak, sum(b is not None for b in self.busy_until))
 
     def poll(self, slot):
         if self.busy_until[slot] is not None and self.clock() >= self.busy_until[slot]:
-            self.reqs[slot].records = np.zeros(0)
+            r = self.reqs[slot]
+            if r.rid in self.fail_rids:
+                r.error = "injected device error"
+            else:
+                r.records = np.zeros(0)
             self.busy_until[slot] = None
             return True
         return False

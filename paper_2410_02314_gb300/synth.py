@@ -208,13 +208,18 @@ def init_weights(spec: NetSpec, seed: int, bn: bool = False) -> Weights:
 
 
 def pack_blob(spec: NetSpec, w: Weights) -> bytes:
-    """Serialise weights into an SMLW blob (little endian, float32 payload).  Plain stacks use
-    version 1 (dil[16]); nets with dense blocks or a U-Net version 2 (reserved = growth, dil[32] = every
-    layer's dilation in execution order)."""
+    """Serialise weights into an SMLW blob (little endian, float32 payload).  Plain stacks of up
+    to 16 layers use version 1 (dil[16]); nets with dense blocks or a U-Net, and plain stacks of
+    17 to 32 layers, version 2 (reserved = growth, dil[32] = every layer's dilation in execution
+    order)."""
     L, C = spec.L, spec.channels
     has_bn = 1 if w.bn is not None else 0
     nh = int(np.asarray(w.head_b).size)
-    if spec.dcd or spec.unet:
+    if spec.dcd or spec.unet or L > MAX_LAYERS:
+        if has_bn:
+            raise ValueError("version-2 blobs carry no BatchNorm")
+        if L > MAX_LAYERS_V2:
+            raise ValueError(f"{L} conv layers (at most {MAX_LAYERS_V2})")
         dil = [d for _, _, d in spec.layers()] + [0] * (MAX_LAYERS_V2 - L)
         growth = int(spec.dcd["growth"]) if spec.dcd else 0
         parts = [struct.pack(HEADER_FMT_V2, MAGIC, 2, L, C, spec.in_ch, nh, has_bn, growth, *dil)]
@@ -234,7 +239,7 @@ def pack_blob(spec: NetSpec, w: Weights) -> bytes:
 
 def unpack_blob(blob: bytes, spec: NetSpec | None = None) -> tuple[dict, Weights]:
     """Parse an SMLW blob back into float64 arrays (header dict, Weights).  A version-2 blob
-    (dense blocks) needs its spec for the layers' channel counts."""
+    (dense blocks, a U-Net or more than 16 layers) needs its spec for the layers' channel counts."""
     head = struct.unpack_from(HEADER_FMT, blob, 0)
     if head[0] != MAGIC:
         raise ValueError("bad magic")

@@ -57,15 +57,26 @@ def test_full_topology_adds_the_unet_stage(bench):
     assert flops == pytest.approx(dcd_flops + unet_flops * PX, rel=1e-12)
 
 
-def test_roofline_bound(bench):
-    # BF16 middle layer: 41 472 FLOP over 192 B = 216 FLOP/B, below the ridge 1702.5 / 6.6735 = 255
-    assert bench.roofline_bound(41472.0, 192.0, 1702.5, 6673.5) == "hbm"
-    # FP8: 432 FLOP/B against 2 x 1702.5 / 6.6735 = 510
-    assert bench.roofline_bound(41472.0, 96.0, 3405.0, 6673.5) == "hbm"
-    # FP32 SIMT: 108 FLOP/B against 80.5 / 6.6735 = 12
-    assert bench.roofline_bound(41472.0, 384.0, 80.5, 6673.5) == "compute"
-    # a dense contraction far above the ridge
-    assert bench.roofline_bound(1e6, 100.0, 1702.5, 6673.5) == "compute"
+def test_conv_roofline_is_the_tensor_pipe(bench):
+    """The conv's roofline is the tensor pipe (a dense contraction; the ALU pipes in FP32):
+    achieved = 41 472 FLOP per pixel x the launch's pixels / the mean launch time, against the
+    burst peak of the launch's operand type; the HBM figures ride along."""
+    pk = {"hbm_gbs": 6787.9, "bf16_tflops": 1936.3, "bf16_tflops_sustained": 1724.3, "when": "x"}
+    live = {"fp8_tflops": 3510.0, "fp32_tflops": 69.5}
+    # 120 launches summing 74.82 ms: 0.6235 ms each
+    r = bench.conv_roofline(synth.spec_48(), "bf16", PX, 74.82, 120, pk, live, 3.33e9)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s" and r["peak"] == 1936.3
+    assert r["achieved"] == pytest.approx(41472 * PX / 0.6235e-3 / 1e12, rel=1e-9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1936.3, rel=1e-12)
+    assert 0.57 < r["frac"] < 0.60  # 1 116 TFLOP/s
+    assert r["hbm"]["bytes_per_launch"] == 192 * PX
+    assert r["hbm"]["dram_gbs"] == pytest.approx(3.33e9 / 0.6235e-3 / 1e9, rel=1e-9)
+    r8 = bench.conv_roofline(synth.spec_48(), "fp8", PX, 60.0, 120, pk, live, None)
+    assert r8["bound"] == "tensor" and r8["peak"] == 3510.0 and r8["hbm"]["bytes_per_launch"] == 96 * PX
+    r8b = bench.conv_roofline(synth.spec_48(), "fp8", PX, 60.0, 120, pk, {}, None)
+    assert r8b["peak"] == 2 * 1936.3  # no FP8 measurement: the nominal ratio, stated
+    r32 = bench.conv_roofline(synth.spec_48(), "fp32", PX, 600.0, 6, pk, live, None)
+    assert r32["bound"] == "alu" and r32["peak"] == 69.5
 
 
 def _smi_line(ts, sm, reasons=("Not Active",) * 4):

@@ -3,10 +3,12 @@
 The library checks spec and blob before it touches a device, so a malformed or unsupported
 request is refused the same way with or without a GPU."""
 import json
+import struct
 
 import pytest
 import torch
 
+import oracle
 import paper_2410_02314_gb300 as sml
 from paper_2410_02314_gb300 import synth
 
@@ -188,3 +190,25 @@ def test_valid_unet_nets_reach_the_device_check():
                dict(levels=2, C=48)):
         _, js, blob = _unet(**kw)
         assert _code(js, blob) == sml.SML_ERR_CUDA, kw
+
+
+# ----------------------------------------------------------------------------- deep plain stacks
+
+
+def test_plain_stacks_beyond_16_layers_use_the_version_2_blob():
+    """Plain stacks of 17..32 layers carry every dilation in the version-2 header (reserved =
+    0); they pass the host checks, 33 layers do not, and a blob of another depth is refused."""
+    deep = synth.NetSpec(in_ch=1, channels=48, dilations=(1,) + (1, 2, 4, 8, 16, 8, 4) * 4, precision="bf16")
+    assert deep.L == 29
+    blob = synth.pack_blob(deep, synth.init_weights(deep, 3))
+    assert struct.unpack_from("<8s7I", blob, 0)[1] == 2
+    net = oracle.Net(deep.to_json(), blob)
+    assert net.L == 29 and net.dil == list(deep.dilations)
+    if not torch.cuda.is_available():
+        assert _code(deep.to_json(), blob) == sml.SML_ERR_CUDA
+    too_deep = synth.NetSpec(in_ch=1, channels=16, dilations=(1,) * 33, precision="bf16")
+    assert _code(too_deep.to_json(), blob) == sml.SML_ERR_BAD_SPEC
+    shorter = synth.NetSpec(in_ch=1, channels=48, dilations=deep.dilations[:-1], precision="bf16")
+    assert _code(shorter.to_json(), blob) == sml.SML_ERR_BAD_WEIGHTS
+    with pytest.raises(ValueError):
+        synth.pack_blob(deep, synth.init_weights(deep, 3, bn=True))

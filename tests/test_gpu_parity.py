@@ -13,6 +13,8 @@ boundary (one ulp of that element, attenuated downstream):
   * decode: bit-exact (same bytes) when both sides decode the same float32 maps;
   * the fused localize call equals the decode of the maps the same network produced.
 """
+import json
+
 import numpy as np
 import pytest
 import torch
@@ -361,6 +363,53 @@ def test_batched_256_full_size_sampled(prec):
     assert recs.tobytes() == want.tobytes()
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_batched_256_full_frames(prec):
+    """Whole frames 0, 127 and 255 of the benchmark batch (256 frames of 256x256, run as the
+    bench runs it: one 16.8-Mpixel chunk), every pixel of all 5 maps, against the oracle's
+    forward of those frames: float64 (FP32 <= 1e-4, BF16 <= 3e-2) and, for BF16, the bf16
+    mode (max <= 2e-2, RMS <= 2e-3)."""
+    w = synth.workload_batched(precision=prec)
+    js = with_precision(w, prec)
+    loc, maps, logits = gpu_maps(js, w.blob, w.frames, w.cam)
+    sel = [0, 127, 255]
+    m, lg = maps[sel], logits[sel]
+    fr = np.ascontiguousarray(w.frames[sel])
+    if prec == "fp32":
+        e = map_errors(m, lg, oracle.forward(oracle.Net(js, w.blob), fr, w.cam.gain, w.cam.offset))
+        print("fp32 full frames vs float64", np.round(e, 8))
+        assert max(e) <= TOL["fp32"]
+    else:
+        check_quantized(prec, js, w.blob, fr, w.cam, m, lg)
+    loc.close()
+
+
+_F64_2048 = {}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_large_fov_2048_whole_frame(prec):
+    """One whole 2048x2048 sCMOS frame (per-pixel gain and offset maps, astigmatic emitters at
+    2 per um^2), every pixel of all 5 maps, from a two-frame call in the large field-of-view
+    configuration, against the oracle's forward of that frame: float64 and the quantized mode
+    of the precision (BF16: max <= 2e-2, RMS <= 2e-3, float64 <= 3e-2; FP8 with the oracle's
+    activation scales: max <= 1e-1, RMS <= 2e-2, float64 <= 0.4 max and 0.08 RMS)."""
+    w = synth.workload_large_fov(T=2, precision="bf16")
+    net = oracle.Net(w.spec.to_json(), w.blob)
+    gm, om = w.cam.gain_map.astype(np.float64), w.cam.offset_map.astype(np.float64)
+    js, scales = w.spec.to_json(), None
+    if prec == "fp8":
+        scales = oracle.act_scales(net, w.frames[:1, 700:956, 900:1156], w.cam.gain, w.cam.offset,
+                                   gm[700:956, 900:1156], om[700:956, 900:1156])
+        js = json.dumps(dict(json.loads(js), precision="fp8", act_scales=scales))
+    loc, maps, logits = gpu_maps(js, w.blob, w.frames, w.cam)
+    fr = np.ascontiguousarray(w.frames[1:2])
+    if "ref" not in _F64_2048:
+        _F64_2048["ref"] = oracle.forward(net, fr, w.cam.gain, w.cam.offset, gm, om)
+    check_quantized(prec, js, w.blob, fr, w.cam, maps[1:2], logits[1:2], scales=scales, full=_F64_2048["ref"])
+    loc.close()
+
+
 # ----------------------------------------------------------------------------- FP8
 
 
@@ -397,6 +446,28 @@ def test_activation_amax_matches_oracle_activations():
     for l in range(1, net.L):
         ref = acts[:, l - 1].max()
         assert abs(amax[l] - ref) <= 1e-4 * ref, (l, amax[l], ref)
+
+
+def test_calibrate_fp8_scales_follow_the_oracle_activations():
+    """sml_calibrate_fp8 on an FP32 context: act_scales[0] = 1 and act_scales[l] = margin *
+    amax[l] / 448 with amax[l] the oracle's largest activation entering layer l (within the
+    FP32 map tolerance); calibrate_fp8 puts exactly those scales into the fp8 spec."""
+    w = synth.workload_small()
+    ctx = sml.sml_create(w.spec.to_json(), w.blob)
+    d = torch.from_numpy(w.frames).cuda()
+    for margin in (1.0, 1.25):
+        sc = sml.sml_calibrate_fp8(ctx, d, margin, gain=w.cam.gain, offset=w.cam.offset)
+        net = oracle.Net(w.spec.to_json(), w.blob)
+        ref = oracle.act_scales(net, w.frames, w.cam.gain, w.cam.offset)
+        assert sc[0] == 1.0
+        for l in range(1, net.L):
+            assert abs(sc[l] - margin * ref[l]) <= 1e-4 * margin * ref[l], (l, sc[l], ref[l])
+    assert sml.sml_num_layers(ctx) == net.L
+    with pytest.raises(sml.SmlError):
+        sml.sml_calibrate_fp8(ctx, d, 0.0, gain=w.cam.gain, offset=w.cam.offset)
+    sml.sml_destroy(ctx)
+    js = json.loads(sml.calibrate_fp8(w.spec.to_json(), w.blob, d, 1.25, gain=w.cam.gain, offset=w.cam.offset))
+    assert js["precision"] == "fp8" and len(js["act_scales"]) == net.L and js["act_scales"][0] == 1.0
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])

@@ -60,17 +60,16 @@ def _gpu_records(js, blob, frames, cam, p_min):
 
 # (config, precision): gates (max lateral RMSE nm, min Jaccard), a few times the values measured
 # on a GB300: small FP32 0.0 nm / 1.0, BF16 0.07 / 0.968; batched FP32 0.0002 / 1.0, BF16
-# 0.19 / 0.929, FP8 3.0 / 0.358; large-FOV crop BF16 0.31 / 0.893, FP8 5.7 / 0.245 (random-init
-# p maps hover at the threshold, so many FP8 detections flip; on a trained net FP8 keeps a
-# record Jaccard of 0.86-0.89, tests/test_gpu_train.py)
+# 0.19 / 0.929; large-FOV crop BF16 0.31 / 0.893.  FP8 records are gated on the trained net
+# only (tests/test_gpu_train.py): random-init p maps hover at the threshold, so the record
+# Jaccard of FP8 against float64 here (0.25-0.36 measured) says nothing a gate could hold
+# to; FP8's maps are gated against the oracle in tests/test_gpu_parity.py.
 CASES = {
     ("small_64", "fp32"): (0.01, 0.999),
     ("small_64", "bf16"): (0.5, 0.9),
     ("batched_256", "fp32"): (0.01, 0.999),
     ("batched_256", "bf16"): (1.0, 0.85),
-    ("batched_256", "fp8"): (10.0, 0.25),
     ("large_fov_512", "bf16"): (1.5, 0.8),
-    ("large_fov_512", "fp8"): (15.0, 0.15),
 }
 
 

@@ -27,7 +27,7 @@ def make_net(C, dil, seed=7, in_ch=1, bn=False, positive=False, zero_bias=False)
         w.conv_b = [np.zeros_like(b) for b in w.conv_b]
         w.head_b = np.zeros_like(w.head_b)
     blob = synth.pack_blob(spec, w)
-    return spec, blob, oracle.Net(spec.to_json(), blob), synth.blob_f32_weights(blob)
+    return spec, blob, oracle.Net(spec.to_json(), blob), synth.blob_f32_weights(blob, spec)
 
 
 def torch_reference(x0, w, dil, bn=None, eps=1e-5):
@@ -46,7 +46,9 @@ def torch_reference(x0, w, dil, bn=None, eps=1e-5):
 
 @pytest.mark.parametrize(
     "C,dil,H,W",
-    [(3, (1, 2, 4), 9, 11), (4, (1, 2, 4, 8, 4, 1), 13, 12), (2, (3, 5), 7, 16), (3, (16, 1), 10, 9)],
+    [(3, (1, 2, 4), 9, 11), (4, (1, 2, 4, 8, 4, 1), 13, 12), (2, (3, 5), 7, 16), (3, (16, 1), 10, 9),
+     # a plain stack of 20 layers: the version-2 blob of stacks beyond 16 layers
+     (2, (1, 2, 1, 3) * 5, 9, 10)],
 )
 def test_forward_matches_torch_conv2d(C, dil, H, W):
     _, _, net, w = make_net(C, dil)
