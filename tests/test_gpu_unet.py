@@ -1,11 +1,10 @@
 """GPU parity of nets with the U-Net fine stage (Sec. 3.2; two upsampling stages, Sec. 4.2)
 through the C ABI: 2x2 max pooling and nearest upsampling kernels between resolution
 levels, convs on the half- and quarter-resolution buffers, the skip concatenation as an
-offset store.  FP32 against float64 (<= 1e-4); BF16 against the oracle's bf16 mode (max
-<= 2e-2, RMS <= 2e-3) and float64 (<= 3e-2), each scaled by sqrt(n / 7) for n > 7
-tensor-core layers (independent one-ulp rounding flips accumulate with depth; the base gates
-are those of the 8-layer net's 7); records bit-exact against the oracle's decode of the GPU
-maps."""
+offset store.  FP32 against float64 (<= 1e-4); BF16 against the oracle's bf16 mode (max and
+RMS) and float64 (max) under the depth gate of tests/gpu_gates.py (the measured error grows
+linearly with the number of tensor-core layers); records bit-exact against the oracle's
+decode of the GPU maps."""
 import json
 
 import numpy as np
@@ -14,6 +13,7 @@ import torch
 
 import oracle
 import paper_2410_02314_gb300 as sml
+from gpu_gates import bf16_gate
 from paper_2410_02314_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -42,9 +42,9 @@ def _maps(loc, frames, cam, nh):
     return m, got
 
 
-def depth_scale(net):
-    """sqrt(n / 7) for n > 7 tensor-core layers (all conv layers after the first)."""
-    return float(np.sqrt(max(1.0, (net.L - 1) / 7.0)))
+def gate(net, kind):
+    """The BF16 depth gate for this net's tensor-core layers (all conv layers after the first)."""
+    return bf16_gate(net.L - 1, kind)
 
 
 def _err(got, ref, ks):
@@ -96,8 +96,7 @@ def test_unet_maps_and_records_match_oracle(prec, C, levels, dcd, dil, nh, size)
         eq, rq = _err(got, refq, range(5)), _rms(got, refq, range(5))
         print(prec, C, levels, dcd is not None, "vs quantized", np.round(eq, 5), "rms", np.round(rq, 6), "vs float64",
               np.round(e, 4))
-        k = depth_scale(net)
-        assert max(eq) <= 2e-2 * k and max(rq) <= 2e-3 * k and max(e) <= 3e-2 * k
+        assert max(eq) <= gate(net, "q_max") and max(rq) <= gate(net, "q_rms") and max(e) <= gate(net, "f64_max")
     if nh == 9:
         want, want_sig = oracle.decode(maps, 0.5, net.z_scale, net.ph_scale, with_sigma=True)
         recs, sig = loc.localize_sigma(frames, 0.5, gain=cam.gain, offset=cam.offset, gain_map=cam.gain_map,
@@ -140,9 +139,9 @@ def test_full_topology_full_size_sampled():
         refq = oracle.forward_window(qnet, w.frames[t : t + 1], i0, i0 + 24, j0, j0 + 24, quant="bf16")
         worst = max(worst, max(_err(blk, ref, range(5))))
         worst_q = max(worst_q, max(_err(blk, refq, range(5))))
-    k = depth_scale(net)
-    print("full topology sampled worst", worst, "vs quantized", worst_q, "depth scale", k)
-    assert worst <= 3e-2 * k and worst_q <= 2e-2 * k
+    print("full topology sampled worst", worst, "vs quantized", worst_q, "gates", gate(net, "f64_max"),
+          gate(net, "q_max"))
+    assert worst <= gate(net, "f64_max") and worst_q <= gate(net, "q_max")
     want, want_sig = oracle.decode(maps, 0.5, net.z_scale, net.ph_scale, with_sigma=True)
     recs, sig = loc.localize_sigma(w.frames, 0.5, capacity=4_000_000)
     assert recs.tobytes() == want.tobytes() and sig.tobytes() == want_sig.tobytes()
@@ -164,7 +163,7 @@ def test_full_topology_with_three_frame_input_across_chunk_edges():
     assert np.array_equal(one, two)
     net = oracle.Net(spec.to_json(), blob)
     refq = oracle.forward(oracle.quantized(net, "bf16"), frames, gain=2.0, offset=100.0, quant="bf16")
-    assert max(_err(got, refq, range(5))) <= 2e-2 * depth_scale(net)
+    assert max(_err(got, refq, range(5))) <= gate(net, "q_max")
 
 
 def test_stack_file_pipeline_on_the_full_topology(tmp_path):
