@@ -340,7 +340,7 @@ def serving_run(spec_json, blob, dev, capacity_px_per_s, pool, load=0.8, n_reque
         reqs.append(serve.Request(rid=k, frames=host[o : o + T], arrival=float(t), gain=cam.gain, offset=cam.offset,
                                   gain_map=d_gain, offset_map=d_off))
     ex = serve.GpuExecutor(spec_json, blob, slots=slots, device=dev.index or 0)
-    ex.warm([(512, 512), (1024, 1024), (2048, 2048)], max_request=(20, 2048, 2048))
+    ex.warm([(100, 512, 512), (50, 1024, 1024), (20, 2048, 2048)], max_request=(20, 2048, 2048))
     sch = serve.Scheduler(ex, reserve=4 << 30)
     rep = serve.report(sch.run(reqs))
     rep.update({"load": load, "arrival_rate_per_s": rate, "slots": slots, "max_queue": sch.max_queue,
@@ -519,6 +519,49 @@ def small_latency_run(dev, stream, calls=50):
     res = {"workload": "4 x 64x64 frames, 32-channel 6-layer net, FP32", "us_per_call": us,
            "launches_per_call": loc.last_launch_count, "records_per_call": int(d_n.item())}
     loc.close()
+    return res
+
+
+def training_run(dev, steps=20, warmup=3):
+    """The training configuration: the 48-channel 8-layer net on batches of 256 astigmatic
+    64x64 patches (0-10 emitters each), Adam on FP32 master weights; one step = forward, loss,
+    backward and the optimizer update.  BF16 (tensor-core forward, input gradient and weight
+    gradient) and FP32 (SIMT) on the same device-simulated batches (a fresh batch per step,
+    simulated before the timed region).  Device time per step with CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_2410_02314_gb300 import synth
+    from paper_2410_02314_gb300.train import DilatedLocNet, device_batch
+
+    spec = synth.spec_48("fp32")
+    rng = np.random.default_rng(5)
+    batches = [device_batch(rng, 256, 64, 64, max_emitters=10, frame0=k * 256) for k in range(warmup + steps)]
+    res = {"workload": "256 patches of 64x64 per step (astigmatic, 0-10 emitters), 48-channel 8-layer net, Adam",
+           "batches": "simulated on the device before the timed region, one per step"}
+    for prec in ("bf16", "fp32"):
+        net = DilatedLocNet(spec, synth.init_weights(spec, 11), precision=prec).to(dev)
+        opt = torch.optim.Adam(net.parameters(), lr=1e-3)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k, (frames, tgt) in enumerate(batches):
+            a = b = None
+            if k >= warmup:
+                a, b = ev[k - warmup]
+                a.record()
+            opt.zero_grad(set_to_none=True)
+            loss = net.loss(frames, tgt)
+            loss.backward()
+            opt.step()
+            if b is not None:
+                b.record()
+        torch.cuda.synchronize()
+        ms = statistics.mean(x.elapsed_time(y) for x, y in ev)
+        res[f"{prec}_steps_per_s"] = 1000.0 / ms
+        res[f"{prec}_ms_per_step"] = ms
+        res[f"{prec}_final_loss"] = float(loss.item())
+        if prec == "bf16":
+            res["bf16_device_error"] = net.device_error()
+    res["bf16_speedup_vs_fp32"] = res["bf16_steps_per_s"] / res["fp32_steps_per_s"]
     return res
 
 
@@ -823,8 +866,9 @@ def main():
         pool = serving_pool(dev)
         serving = [serving_run(spec_json, w.blob, dev, value * H * W, pool, load=ld) for ld in (0.5, 0.8, 0.95)]
         del pool
-    large_fov = small = file_pipe = dcd = None
+    large_fov = small = file_pipe = dcd = training = None
     if not args.no_extra and world == 1:
+        training = training_run(dev)
         lf = large_fov_frames(dev)
         large_fov = {p: large_fov_line(dev, stream, flush, p, lf, 3, 1, pk, live_peaks, with_cpu=(p == "bf16"))
                      for p in ("bf16", "fp8")}
@@ -873,6 +917,7 @@ def main():
         "small_latency": small,
         "file_pipeline": file_pipe,
         "topologies": dcd,
+        "training": training,
         **extra,
     }
     print(json.dumps(line), flush=True)

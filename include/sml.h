@@ -104,7 +104,13 @@ typedef struct {
  *   "fp8" (e4m3 activations and weights, FP32 accumulation; needs "act_scales": one
  *   positive float per conv layer, the scale of that layer's input activations).
  *   Optional tuning: "chunk_px": pixels per device chunk (default 2^24); "tc_stages": TMA
- *   ring depth of the tensor-core conv (0 = as deep as shared memory allows, else 4..16).
+ *   ring depth of the tensor-core conv (0 = as deep as shared memory allows, else 4..16);
+ *   "fp8_pair_rows": 1 (default) loads FP8 activations of even-width frames as 32-byte pixel
+ *   pairs, 0 as 16-byte rows (the same bytes land in shared memory; results are identical).
+ *   Failure-path tests only: "debug_poison_cta": c makes CTA c of every tensor-core conv
+ *   launch load no data, so that its waits run out after "debug_wait_ns" (1e6..2e9)
+ *   nanoseconds and the call reports SML_ERR_CUDA (the kernels' give-up path, with no copy of
+ *   that CTA in flight).
  * weights: an SMLW blob (host memory, read during the call only):
  *   header "<8s7I16i": magic "SMLW0001", version 1, L, C, in_ch, n_heads (5 or 9), has_bn,
  *   reserved, dilations[16]; then per layer l: W[C][Cin_l][3][3] f32, b[C] f32 and, if
@@ -152,15 +158,17 @@ int sml_num_layers(const sml_ctx* ctx);
 /*
  * sml_workspace_bytes -- device memory of the context's per-frame-size workspace ("plan":
  * activation buffers of one chunk, maps, decode scratch, staging of host frames and camera
- * maps).  A call on frames of a new H x W allocates such a plan and keeps it for later calls
- * of that size (up to 4 sizes; the least recently used is then freed after its last call's
- * work on that call's stream has finished).  Host only, no device call.
- * plan_bytes (or NULL): bytes of a plan for H x W; plan_resident (or NULL): 1 if the context
- * holds one now, else 0; resident_bytes (or NULL): bytes of all plans the context holds.
- * Weights and the per-call record staging of host outputs are not counted.
- * Errors: SML_ERR_BAD_ARG.
+ * maps).  A call on T frames of H x W uses a plan whose chunk holds min(T, chunk_px / (H W))
+ * frames (at least one): it keeps the plan of that frame size if its chunk is at least that
+ * large, and otherwise allocates one (freeing a smaller plan of the size, and the least
+ * recently used plan when it holds 4 sizes, each after its last call's work on that call's
+ * stream).  Host only, no device call.
+ * plan_bytes (or NULL): bytes of the plan a call on T frames of H x W uses; plan_resident (or
+ * NULL): 1 if the context holds it now (no allocation), else 0; resident_bytes (or NULL):
+ * bytes of all plans the context holds.  Weights and the per-call record staging of host
+ * outputs are not counted.  Errors: SML_ERR_BAD_ARG.
  */
-int sml_workspace_bytes(const sml_ctx* ctx, int H, int W, size_t* plan_bytes, int* plan_resident,
+int sml_workspace_bytes(const sml_ctx* ctx, int T, int H, int W, size_t* plan_bytes, int* plan_resident,
                         size_t* resident_bytes);
 
 /*

@@ -27,6 +27,21 @@ extern "C" {
 int sml_debug_umma(const void* d_a, const void* d_b, float* d_d, int n, int k, int kind, int d_col, void* stream);
 
 /*
+ * sml_debug_umma_mn: one tensor-core product D = A B^T with both operands MN-major, the
+ * operand layout of the weight-gradient contraction (its K runs over pixels): A is M x K,
+ * B is N x K, bf16.  d_a / d_b hold shared-memory images (a_bytes / b_bytes, multiples of
+ * 1024) of 32-byte-swizzled planes: plane g of A covers rows 16g..16g+15 of A, one 32-byte
+ * line per k (element (m, k) at logical byte g*a_plane + k*32 + (m%16)*2, then bit 4 of
+ * the byte offset XOR bit 7: the 32-byte swizzle); B likewise with b_plane, its k-th line
+ * at line b_shift + k (the descriptor starts b_shift lines into the planes).  M 64 or 128,
+ * N 16..256 (multiple of 16), K a positive multiple of 16; a_plane, b_plane multiples of
+ * 256.  d_d: float32 [128][n], TMEM lane l in row l (lanes the MMA does not write read 0).
+ * Synchronises the stream.  Returns SML_OK, SML_ERR_BAD_ARG or SML_ERR_CUDA.
+ */
+int sml_debug_umma_mn(const void* d_a, const void* d_b, float* d_d, int m, int n, int k, int a_bytes, int b_bytes,
+                      int a_plane, int b_plane, int b_shift, void* stream);
+
+/*
  * sml_debug_set_error_word: host-side fault injection for tests of the error paths.  Writes
  * value into the context's device error word (synchronously, with no kernel involved), as
  * a tensor-core kernel does when one of its bounded waits gives up.  The next synchronous

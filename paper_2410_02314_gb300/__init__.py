@@ -54,12 +54,22 @@ EXPORTS = (
     "sml_profile_read",
     "sml_debug_umma",
     "sml_debug_set_error_word",
+    "sml_debug_umma_mn",
     "sml_train_ingest",
     "sml_train_conv_fwd",
     "sml_train_conv_bwd_work_bytes",
     "sml_train_conv_bwd",
     "sml_train_heads_work_bytes",
     "sml_train_heads_loss",
+    "sml_train_bf16_bimg_bytes",
+    "sml_train_bf16_pack",
+    "sml_train_bf16_layer0",
+    "sml_train_bf16_conv_fwd",
+    "sml_train_bf16_conv_dgrad",
+    "sml_train_bf16_wgrad_work_bytes",
+    "sml_train_bf16_conv_wgrad",
+    "sml_train_bf16_heads_loss",
+    "sml_train_bf16_l0_wgrad",
     "sml_reader_open",
     "sml_reader_next",
     "sml_reader_release",
@@ -121,7 +131,7 @@ def lib():
         L.sml_num_heads.restype = I
         L.sml_num_layers.argtypes = [P]
         L.sml_num_layers.restype = I
-        L.sml_workspace_bytes.argtypes = [P, I, I, ctypes.POINTER(S), ctypes.POINTER(I), ctypes.POINTER(S)]
+        L.sml_workspace_bytes.argtypes = [P, I, I, I, ctypes.POINTER(S), ctypes.POINTER(I), ctypes.POINTER(S)]
         L.sml_workspace_bytes.restype = I
         L.sml_error_word.argtypes = [P, P, P]
         L.sml_error_word.restype = I
@@ -151,6 +161,8 @@ def lib():
         L.sml_debug_umma.restype = I
         L.sml_debug_set_error_word.argtypes = [P, I]
         L.sml_debug_set_error_word.restype = I
+        L.sml_debug_umma_mn.argtypes = [P, P, P, I, I, I, I, I, I, I, I, P]
+        L.sml_debug_umma_mn.restype = I
         LL = ctypes.c_longlong
         L.sml_reader_open.argtypes = [ctypes.c_char_p, LL, I, I, I, I, I, ctypes.POINTER(P)]
         L.sml_reader_open.restype = I
@@ -289,11 +301,12 @@ def sml_num_layers(ctx) -> int:
     return lib().sml_num_layers(ctx)
 
 
-def sml_workspace_bytes(ctx, H, W):
-    """(bytes of a plan for H x W frames, whether the context holds it now, bytes of all plans
-    the context holds)."""
+def sml_workspace_bytes(ctx, T, H, W):
+    """(bytes of the plan a call on T frames of H x W uses, whether the context holds it now,
+    bytes of all plans the context holds)."""
     pb, res, tot = ctypes.c_size_t(0), ctypes.c_int(0), ctypes.c_size_t(0)
-    _check(ctx, lib().sml_workspace_bytes(ctx, int(H), int(W), ctypes.byref(pb), ctypes.byref(res), ctypes.byref(tot)))
+    _check(ctx, lib().sml_workspace_bytes(ctx, int(T), int(H), int(W), ctypes.byref(pb), ctypes.byref(res),
+                                          ctypes.byref(tot)))
     return int(pb.value), bool(res.value), int(tot.value)
 
 

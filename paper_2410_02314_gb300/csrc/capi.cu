@@ -174,6 +174,7 @@ struct Plan {
   cudaEvent_t done = nullptr;  // recorded on the stream of every call that used the plan
   size_t bytes = 0;            // device bytes of the buffers above
   CUtensorMap tmap[kMaxLayers];  // per layer, over its input buffer: one box per row (width depends on d)
+  bool pair_rows[kMaxLayers] = {false};  // FP8 layers whose map loads 32-byte pixel pairs
 };
 
 // One conv layer of the net in execution order: cin -> cout channels at dilation d.  Layer 0
@@ -222,6 +223,11 @@ struct sml_ctx {
   float act_scale[kMaxLayers] = {0};
   long long chunk_px = 1 << 24;
   int tc_stages = 0;  // "tc_stages": TMA ring depth, 0 = as deep as shared memory allows
+  // failure-path tests ("debug_wait_ns", "debug_poison_cta"): a shorter give-up time of the
+  // tensor-core kernels' waits, and one CTA of every conv launch whose producer loads nothing
+  unsigned long long debug_wait_ns = 0;
+  int debug_poison_cta = -1;
+  bool fp8_pair_rows = true;  // "fp8_pair_rows": 0 keeps 16-byte TMA rows for FP8 (comparison runs)
   // device weights
   std::vector<float> w1, b1;  // layer 1 [C][in_ch][9], [C] (host: passed to the kernel by value)
   float* wf32[kMaxLayers] = {nullptr};  // [9][cin][cout]
@@ -324,15 +330,22 @@ int level_dim(int n, int level) {
 // tensor (group row, W, g_in, H, Tc) with the buffer's strides and loads boxes (group row,
 // tc_box_width(d) pixels, g_in, 1, 1): one input row segment per box, BF16 rows with the
 // 32-byte swizzle.  Pixels left of 0 or right of W-1, and rows outside [0,H), are filled with
-// zeros by TMA.
-int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W, int d, int g_in, int gt) {
+// zeros by TMA.  FP8 frames of even width are read as 32-byte pixel pairs instead (pairs =
+// true): tensor (pair of group rows, W/2, g_in, H, Tc), boxes of tc_box_width(d)/2 pairs,
+// which land in shared memory byte for byte as the 16-byte rows would (a TMA row of 16 bytes
+// moves a half sector; a pair row a whole one).
+int encode_act_map(sml_ctx* ctx, CUtensorMap* m, void* base, int Tc, int H, int W, int d, int g_in, int gt,
+                   bool pairs = false) {
   PFN_encodeTiled_t enc = get_encoder();
   if (!enc) return fail(ctx, SML_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const bool bf16 = ctx->prec == kBF16;
+  if (pairs && (bf16 || W % 2)) return fail(ctx, SML_ERR_CUDA, "pixel-pair rows need fp8 and an even width");
   const cuuint64_t rowb = bf16 ? 32 : 16;
-  cuuint64_t dims[5] = {16ull, (cuuint64_t)W, (cuuint64_t)g_in, (cuuint64_t)H, (cuuint64_t)Tc};
-  cuuint64_t strides[4] = {rowb, rowb * W, rowb * W * gt, rowb * W * gt * H};
-  cuuint32_t box[5] = {16u, (cuuint32_t)tc_box_width(d), (cuuint32_t)g_in, 1u, 1u};
+  cuuint64_t dims[5] = {pairs ? 32ull : 16ull, (cuuint64_t)(pairs ? W / 2 : W), (cuuint64_t)g_in, (cuuint64_t)H,
+                        (cuuint64_t)Tc};
+  cuuint64_t strides[4] = {pairs ? 32ull : rowb, rowb * W, rowb * W * gt, rowb * W * gt * H};
+  cuuint32_t box[5] = {pairs ? 32u : 16u, (cuuint32_t)(pairs ? tc_box_width(d) / 2 : tc_box_width(d)),
+                       (cuuint32_t)g_in, 1u, 1u};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 5, base, dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, bf16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -364,6 +377,13 @@ struct ProfScope {
 
 constexpr size_t kMaxPlans = 4;
 
+// Frames per chunk of a call on T frames of H x W: as many as chunk_px pixels hold (at least
+// one), and no more than the call has.
+int chunk_frames_for(const sml_ctx* ctx, int T, int H, int W) {
+  const long long tmax = std::max(1LL, ctx->chunk_px / ((long long)H * W));
+  return (int)std::max(1LL, std::min<long long>(T, tmax));
+}
+
 // Device buffers of a plan for frames of H x W: the chunk (Tc frames of at most chunk_px
 // pixels together), the activation buffers of every resolution level, the maps, the decode
 // scratch, and the staging of host frames (with the context frames) and host camera maps.
@@ -378,10 +398,10 @@ struct PlanSizes {
   }
 };
 
-PlanSizes plan_sizes(const sml_ctx* ctx, int H, int W) {
+PlanSizes plan_sizes(const sml_ctx* ctx, int H, int W, int Tc) {
   PlanSizes z;
   const long long hw = (long long)H * W;
-  z.Tc = (int)std::max(1LL, ctx->chunk_px / hw);
+  z.Tc = Tc;
   const size_t npx = (size_t)z.Tc * hw;
   for (int b = 0; b < ctx->nbuf; ++b)
     z.act[b] = (size_t)z.Tc * level_dim(H, ctx->buf[b].level) * level_dim(W, ctx->buf[b].level) * ctx->buf[b].ct *
@@ -401,14 +421,27 @@ void plan_used(sml_ctx* ctx, cudaStream_t s) {
   if (ctx->plan && ctx->plan->done) cudaEventRecord(ctx->plan->done, s);
 }
 
-int get_plan(sml_ctx* ctx, int H, int W) {
+// The plan for a call on T frames of H x W: the context's plan of that frame size if its
+// chunk holds the call's chunk, else a new one (replacing a smaller plan of the size, and
+// evicting the least recently used plan beyond kMaxPlans sizes).  A plan's chunk holds
+// min(T, chunk_px / (H W)) frames of the call that created it, so small calls get small plans.
+int get_plan(sml_ctx* ctx, int H, int W, int T) {
   ++ctx->plan_clock;
-  for (auto& q : ctx->plans)
-    if (q->H == H && q->W == W) {
-      q->last_use = ctx->plan_clock;
-      ctx->plan = q.get();
+  const int want = chunk_frames_for(ctx, T, H, W);
+  for (size_t k = 0; k < ctx->plans.size(); ++k) {
+    Plan& q = *ctx->plans[k];
+    if (q.H != H || q.W != W) continue;
+    if (q.Tc >= want) {
+      q.last_use = ctx->plan_clock;
+      ctx->plan = &q;
       return SML_OK;
     }
+    // too small for this call: freed after the last call that used it, then re-planned
+    if (q.done) SML_CUDA(cudaEventSynchronize(q.done), "plan resize");
+    free_plan(q);
+    ctx->plans.erase(ctx->plans.begin() + k);
+    break;
+  }
   if (ctx->plans.size() >= kMaxPlans) {  // evict the least recently used plan
     size_t victim = 0;
     for (size_t k = 1; k < ctx->plans.size(); ++k)
@@ -421,7 +454,7 @@ int get_plan(sml_ctx* ctx, int H, int W) {
   }
   std::unique_ptr<Plan> np(new Plan());
   Plan& p = *np;
-  const PlanSizes z = plan_sizes(ctx, H, W);
+  const PlanSizes z = plan_sizes(ctx, H, W, want);
   const int Tc = z.Tc;
   int r;
   for (int b = 0; b < ctx->nbuf; ++b) {
@@ -445,8 +478,10 @@ int get_plan(sml_ctx* ctx, int H, int W) {
   if (ctx->prec != kFP32) {
     for (int l = 1; l < ctx->L; ++l) {
       const LayerDesc& y = ctx->lay[l];
-      if ((r = encode_act_map(ctx, &p.tmap[l], p.act[y.in_buf], Tc, level_dim(H, y.level), level_dim(W, y.level), y.d,
-                              y.cin / 16, ctx->buf[y.in_buf].ct / 16))) {
+      const int Wl = level_dim(W, y.level);
+      p.pair_rows[l] = ctx->prec == kFP8 && Wl % 2 == 0 && ctx->fp8_pair_rows;
+      if ((r = encode_act_map(ctx, &p.tmap[l], p.act[y.in_buf], Tc, level_dim(H, y.level), Wl, y.d, y.cin / 16,
+                              ctx->buf[y.in_buf].ct / 16, p.pair_rows[l]))) {
         free_plan(p);
         return r;
       }
@@ -556,6 +591,9 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, FrameRange fr,
       a.co = y.cout;
       a.prec = ctx->prec;
       a.err = ctx->d_err;
+      a.wait_ns = ctx->debug_wait_ns;
+      a.poison_cta = ctx->debug_poison_cta;
+      a.pair_rows = p.pair_rows[l] ? 1 : 0;
       SML_CUDA(launch_dconv_tc(a, last, ctx->num_sms, s), "tensor-core conv");
     }
     ++ctx->launches;
@@ -608,7 +646,7 @@ int make_cam(sml_ctx* ctx, const sml_camera* cam, CamArgs* out) {
 int localize_device(sml_ctx* ctx, const uint16_t* d_frames, bool frames_on_host, int T, int H, int W, const CamArgs& cam,
                     float p_min, sml_record* d_out, size_t capacity, unsigned long long* d_n, cudaStream_t s,
                     sml_sigma* d_sigma = nullptr) {
-  int r = get_plan(ctx, H, W);
+  int r = get_plan(ctx, H, W, T);
   if (r) return r;
   Plan& p = *ctx->plan;
   SML_CUDA(cudaMemsetAsync(d_n, 0, sizeof(unsigned long long), s), "memset count");
@@ -664,6 +702,11 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
   ctx->ph_scale = (float)num("ph_scale", 10000.0);
   ctx->chunk_px = (long long)num("chunk_px", (double)(1 << 24));
   ctx->tc_stages = (int)num("tc_stages", 0);
+  ctx->fp8_pair_rows = num("fp8_pair_rows", 1.0) != 0.0;
+  ctx->debug_wait_ns = (unsigned long long)num("debug_wait_ns", 0.0);
+  ctx->debug_poison_cta = (int)num("debug_poison_cta", -1.0);
+  if (ctx->debug_poison_cta >= 0 && (ctx->debug_wait_ns < 1000000ull || ctx->debug_wait_ns > 2000000000ull))
+    return fail(nullptr, SML_ERR_BAD_SPEC, "debug_poison_cta needs debug_wait_ns in [1e6, 2e9]");
   if (ctx->tc_stages < 0 || (ctx->tc_stages > 0 && ctx->tc_stages < 4) || ctx->tc_stages > 16)
     return fail(nullptr, SML_ERR_BAD_SPEC, "tc_stages must be 0 (as deep as shared memory allows) or 4..16");
 
@@ -1052,7 +1095,7 @@ int localize_sync(sml_ctx* ctx, const uint16_t* frames, int T, int H, int W, con
   *n_out = 0;
   if (T == 0) return SML_OK;
   SML_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-  if ((r = get_plan(ctx, H, W))) return r;
+  if ((r = get_plan(ctx, H, W, T))) return r;
   cudaStream_t s = ctx->stream;
   const size_t hw = (size_t)H * W;
   // camera maps given in host memory are staged once per call
@@ -1108,15 +1151,16 @@ int sml_num_heads(const sml_ctx* ctx) { return ctx ? ctx->nh : 0; }
 
 int sml_num_layers(const sml_ctx* ctx) { return ctx ? ctx->L : 0; }
 
-int sml_workspace_bytes(const sml_ctx* ctx, int H, int W, size_t* plan_bytes, int* plan_resident,
+int sml_workspace_bytes(const sml_ctx* ctx, int T, int H, int W, size_t* plan_bytes, int* plan_resident,
                         size_t* resident_bytes) {
-  if (!ctx || H < 1 || W < 1 || H > 16384 || W > 16384) return SML_ERR_BAD_ARG;
-  if (plan_bytes) *plan_bytes = plan_sizes(ctx, H, W).total();
+  if (!ctx || T < 1 || H < 1 || W < 1 || H > 16384 || W > 16384) return SML_ERR_BAD_ARG;
+  const int want = chunk_frames_for(ctx, T, H, W);
+  if (plan_bytes) *plan_bytes = plan_sizes(ctx, H, W, want).total();
   int res = 0;
   size_t tot = 0;
   for (const auto& q : ctx->plans) {
     tot += q->bytes;
-    if (q->H == H && q->W == W) res = 1;
+    if (q->H == H && q->W == W && q->Tc >= want) res = 1;
   }
   if (plan_resident) *plan_resident = res;
   if (resident_bytes) *resident_bytes = tot;
@@ -1168,7 +1212,7 @@ int sml_forward_maps(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W
   CamArgs ca;
   if ((r = make_cam(ctx, cam, &ca))) return r;
   if (T == 0) return SML_OK;
-  if ((r = get_plan(ctx, H, W))) return r;
+  if ((r = get_plan(ctx, H, W, T))) return r;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t fpx = (size_t)H * W;
   for (int t0 = 0; t0 < T; t0 += ctx->plan->Tc) {
@@ -1191,7 +1235,7 @@ int sml_decode_maps(sml_ctx* ctx, const float* d_maps, int T, int H, int W, cons
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   SML_CUDA(cudaMemsetAsync(d_n_out, 0, sizeof(unsigned long long), s), "memset count");
   if (T == 0) return SML_OK;
-  if ((r = get_plan(ctx, H, W))) return r;
+  if ((r = get_plan(ctx, H, W, T))) return r;
   Plan& p = *ctx->plan;
   const size_t fpx = (size_t)H * W;
   for (int t0 = 0; t0 < T; t0 += p.Tc) {
@@ -1261,7 +1305,7 @@ int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, in
   if ((r = make_cam(ctx, cam, &ca))) return r;
   for (int l = 0; l < ctx->L; ++l) amax[l] = 0.0f;
   if (T == 0) return SML_OK;
-  if ((r = get_plan(ctx, H, W))) return r;
+  if ((r = get_plan(ctx, H, W, T))) return r;
   cudaStream_t s = ctx->stream;
   unsigned* d_amax = nullptr;
   if ((r = dev_alloc(ctx, &d_amax, kMaxLayers * sizeof(unsigned)))) return r;
@@ -1336,6 +1380,152 @@ int sml_train_heads_loss(const float* a, const float* tgt, int B, int H, int W, 
                                        work, static_cast<cudaStream_t>(stream)));
 }
 
+// ------------------------------------------------------------------ BF16 training (sml_train.h)
+}  // extern "C"
+
+namespace {
+
+// SMs of the current device (cached per device).
+int current_num_sms() {
+  static int sms[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+  return sms[dev];
+}
+
+// TMA map over row-planar bf16 activations [B][H][C/16][W][16] with one box per image row:
+// `box_px` pixels (128 + 2d rounded up to 32 for the conv's input rows, or 128 for the
+// weight gradient's dz rows) by all C/16 groups; 32-byte swizzle; zero fill out of bounds.
+bool encode_rp_map(CUtensorMap* m, const void* base, int B, int H, int W, int C, int box_px) {
+  PFN_encodeTiled_t enc = get_encoder();
+  if (!enc) return false;
+  const int G = C / 16;
+  cuuint64_t dims[5] = {16ull, (cuuint64_t)W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)B};
+  cuuint64_t strides[4] = {32ull, 32ull * W, 32ull * W * G, 32ull * W * G * H};
+  cuuint32_t box[5] = {16u, (cuuint32_t)box_px, (cuuint32_t)G, 1u, 1u};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool train_bf16_dims_ok(int B, int H, int W, int C, int d) {
+  return B >= 0 && H >= 1 && W >= 1 && H <= 16384 && W <= 16384 && d >= 1 && d <= 64 &&
+         (C == 16 || C == 32 || C == 48) && (long long)B * H * W < (1LL << 31);
+}
+
+// The plain-layer conv of BF16 training: forward (bias from b_dev) or input gradient.
+int train_bf16_conv(const void* in, const void* mask, int B, int H, int W, int C, int d, const void* bimg,
+                    const float* b_dev, void* out, int* d_err, bool dgrad, void* stream) {
+  if (!in || !bimg || !out || !d_err || (dgrad ? !mask : !b_dev) || !train_bf16_dims_ok(B, H, W, C, d))
+    return SML_ERR_BAD_ARG;
+  if (B == 0) return SML_OK;
+  CUtensorMap tm;
+  if (!encode_rp_map(&tm, in, B, H, W, C, tc_box_width(d))) return SML_ERR_CUDA;
+  TcLayerArgs a{};
+  a.tmap = &tm;
+  a.stages = 0;
+  a.bimg = bimg;
+  a.bias = nullptr;
+  a.bias_dev = dgrad ? nullptr : b_dev;
+  a.mask = mask;
+  a.out_inv_scale = 1.0f;
+  a.out = out;
+  a.out_g0 = 0;
+  a.out_gt = C / 16;
+  a.T = B;
+  a.H = H;
+  a.W = W;
+  a.d = d;
+  a.prec = kBF16;
+  a.ci = a.co = C;
+  a.err = d_err;
+  return train_status(launch_dconv_tc_train(a, dgrad, current_num_sms(), static_cast<cudaStream_t>(stream)));
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sml_train_bf16_bimg_bytes(int C) { return (C == 16 || C == 32 || C == 48) ? tc_bimg_bytes(C, C, kBF16) : 0; }
+
+int sml_train_bf16_pack(const float* w, int C, void* bimg_fwd, void* bimg_dgrad, void* stream) {
+  if (!w || !bimg_fwd || !bimg_dgrad || (C != 16 && C != 32 && C != 48)) return SML_ERR_BAD_ARG;
+  return train_status(launch_pack_bimg_bf16(w, C, C, bimg_fwd, bimg_dgrad, static_cast<cudaStream_t>(stream)));
+}
+
+int sml_train_bf16_layer0(const uint16_t* frames, int B, int H, int W, float gain, float offset, float in_scale,
+                          const float* w0, const float* b0, int C, int d, void* a0, void* stream) {
+  if (!frames || !w0 || !b0 || !a0 || !(gain > 0.0f) || !train_bf16_dims_ok(B, H, W, C, d)) return SML_ERR_BAD_ARG;
+  if (B == 0) return SML_OK;
+  CamArgs cam{gain, offset, in_scale, nullptr, nullptr};
+  return train_status(launch_ingest_l1_devw(frames, B, H, W, d, cam, w0, b0, C, a0, static_cast<cudaStream_t>(stream)));
+}
+
+int sml_train_bf16_conv_fwd(const void* x, int B, int H, int W, int C, int d, const void* bimg_fwd, const float* b,
+                            void* y, int* d_err, void* stream) {
+  return train_bf16_conv(x, nullptr, B, H, W, C, d, bimg_fwd, b, y, d_err, false, stream);
+}
+
+int sml_train_bf16_conv_dgrad(const void* dz, const void* x, int B, int H, int W, int C, int d, const void* bimg_dgrad,
+                              void* dz_in, int* d_err, void* stream) {
+  return train_bf16_conv(dz, x, B, H, W, C, d, bimg_dgrad, nullptr, dz_in, d_err, true, stream);
+}
+
+size_t sml_train_bf16_wgrad_work_bytes(int C) {
+  const int sms = current_num_sms();
+  return (C == 16 || C == 32 || C == 48) && sms > 0 ? train_wgrad_tc_work_bytes(C, sms) : 0;
+}
+
+int sml_train_bf16_conv_wgrad(const void* x, const void* dz, int B, int H, int W, int C, int d, float* dw, float* db,
+                              void* work, size_t work_bytes, int* d_err, void* stream) {
+  if (!x || !dz || !dw || !db || !work || !d_err || !train_bf16_dims_ok(B, H, W, C, d)) return SML_ERR_BAD_ARG;
+  const int sms = current_num_sms();
+  if (sms <= 0) return SML_ERR_CUDA;
+  if (work_bytes < train_wgrad_tc_work_bytes(C, sms)) return SML_ERR_BAD_ARG;
+  CUtensorMap tm_dz, tm_x;
+  if (!encode_rp_map(&tm_dz, dz, B > 0 ? B : 1, H, W, C, kTileM) ||
+      !encode_rp_map(&tm_x, x, B > 0 ? B : 1, H, W, C, tc_box_width(d)))
+    return SML_ERR_CUDA;
+  return train_status(launch_wgrad_tc(&tm_dz, &tm_x, B, H, W, C, d, static_cast<float*>(work), sms, dw, db, d_err,
+                                      static_cast<cudaStream_t>(stream)));
+}
+
+int sml_train_bf16_heads_loss(const void* a, const float* tgt, int B, int H, int W, int C, const float* hw,
+                              const float* hb, float* h, float* loss, const float* grad_scale, void* dz, float* dhw,
+                              float* dhb, void* work, size_t work_bytes, void* stream) {
+  if (B < 1 || H < 1 || W < 1 || !a || !tgt || !hw || !hb || !h || !loss || !work) return SML_ERR_BAD_ARG;
+  if (C != 16 && C != 32 && C != 48 && C != 64) return SML_ERR_BAD_ARG;
+  if (dz && (!grad_scale || !dhw || !dhb)) return SML_ERR_BAD_ARG;
+  if (work_bytes < train_heads_work_bytes(B, H, W, C)) return SML_ERR_BAD_ARG;
+  return train_status(train_heads_loss_rp(a, tgt, B, H, W, C, hw, hb, h, loss, dz ? grad_scale : nullptr, dz, dhw, dhb,
+                                          work, static_cast<cudaStream_t>(stream)));
+}
+
+int sml_train_bf16_l0_wgrad(const float* x0, const void* dz0, int B, int H, int W, int C, int d, float* dw, float* db,
+                            void* work, size_t work_bytes, void* stream) {
+  if (!x0 || !dz0 || !dw || !db || !work || !train_bf16_dims_ok(B, H, W, C, d)) return SML_ERR_BAD_ARG;
+  if (work_bytes < train_conv_work_bytes(B, H, W, 1, C)) return SML_ERR_BAD_ARG;
+  return train_status(train_l0_wgrad_rp(x0, dz0, B, H, W, C, d, dw, db, work, static_cast<cudaStream_t>(stream)));
+}
+
+// Debug entry (include/sml_debug.h): one UMMA with both operands MN-major.
+int sml_debug_umma_mn(const void* d_a, const void* d_b, float* d_d, int m, int n, int k, int a_bytes, int b_bytes,
+                      int a_plane, int b_plane, int b_shift, void* stream) {
+  static int* d_err = nullptr;
+  if (!d_a || !d_b || !d_d) return SML_ERR_BAD_ARG;
+  if (!d_err && cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) return SML_ERR_OOM;
+  cudaMemset(d_err, 0, sizeof(int));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_umma_mn_selftest(d_a, d_b, d_d, m, n, k, a_bytes, b_bytes, a_plane, b_plane, b_shift, d_err, s);
+  if (e == cudaErrorInvalidValue) return SML_ERR_BAD_ARG;
+  if (e != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return SML_ERR_CUDA;
+  int h = 0;
+  cudaMemcpy(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  return h ? SML_ERR_CUDA : SML_OK;
+}
+
 // Debug entry (include/sml_debug.h): host-side injection of a device-side failure report.
 int sml_debug_set_error_word(sml_ctx* ctx, int value) {
   if (!ctx) return SML_ERR_BAD_ARG;
@@ -1405,7 +1595,7 @@ extern "C" int sml_localize_file(sml_ctx* ctx, const char* path, long long offse
   if (T == 0) return SML_OK;
   const auto t_start = std::chrono::steady_clock::now();
   SML_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-  if ((r = get_plan(ctx, H, W))) return r;
+  if ((r = get_plan(ctx, H, W, std::min(T, batch)))) return r;
   cudaStream_t s = ctx->stream;
   const size_t hw = (size_t)H * W;
   if (ca.gain_map && !is_device_ptr(ca.gain_map)) {

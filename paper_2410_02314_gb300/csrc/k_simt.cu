@@ -68,11 +68,16 @@ constexpr size_t l1_smem_bytes(int d) {
 // time.  FMA order: bias, then input channel, then taps (ky, kx) row-major.  Outputs are
 // staged in shared memory (rows padded by 16 bytes against bank conflicts) so that the stores
 // to HBM are whole 16-byte chunks, consecutive across threads.
-template <int C, int OUT, int IN_CH>
+// DEVW (training): the weights and bias come from device memory (wdev [C][IN_CH][9], bdev [C])
+// instead of the by-value parameter, so that an optimizer step on the device needs no copy
+// to the host before the next forward.
+template <int C, int OUT, int IN_CH, bool DEVW = false>
 __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restrict__ frames, int H, int W, int d,
                                                        int t0, int t_first, int t_last, CamArgs cam,
                                                        const __grid_constant__ L1Params prm, float out_scale,
-                                                       void* __restrict__ out, int out_ct) {
+                                                       void* __restrict__ out, int out_ct,
+                                                       const float* __restrict__ wdev = nullptr,
+                                                       const float* __restrict__ bdev = nullptr) {
   constexpr int CPT = C / kL1ChGroups;
   constexpr int CP = CPT / 2;                             // channel pairs per thread
   constexpr int OB = OUT == 0 ? 4 : (OUT == 1 ? 2 : 1);  // output bytes per channel
@@ -121,10 +126,14 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
   }
   float2 bias[CP];
 #pragma unroll
-  for (int q = 0; q < CP; ++q) bias[q] = make_float2(prm.b[cg * CPT + 2 * q], prm.b[cg * CPT + 2 * q + 1]);
+  for (int q = 0; q < CP; ++q) {
+    const float* b = DEVW ? bdev : prm.b;
+    bias[q] = make_float2(b[cg * CPT + 2 * q], b[cg * CPT + 2 * q + 1]);
+  }
   // weights of channel pair q, input channel ci, tap k
   auto wpair = [&](int q, int ci, int k) {
-    return make_float2(prm.w[((cg * CPT + 2 * q) * IN_CH + ci) * 9 + k], prm.w[((cg * CPT + 2 * q + 1) * IN_CH + ci) * 9 + k]);
+    const float* w = DEVW ? wdev : prm.w;
+    return make_float2(w[((cg * CPT + 2 * q) * IN_CH + ci) * 9 + k], w[((cg * CPT + 2 * q + 1) * IN_CH + ci) * 9 + k]);
   };
   float2 w[IN_CH == 1 ? CP : 1][9];
   if (IN_CH == 1) {
@@ -368,6 +377,25 @@ static cudaError_t launch_l1(const uint16_t* frames, int T, int H, int W, int d,
   return cudaGetLastError();
 }
 
+// BF16 training's first layer: weights from device memory, bf16 row-planar output.
+template <int C>
+static cudaError_t launch_l1_devw(const uint16_t* frames, int T, int H, int W, int d, const CamArgs& cam,
+                                  const float* wdev, const float* bdev, void* out, cudaStream_t s) {
+  const size_t smem = l1_smem_bytes<C, 1, 1>(d);
+  cudaError_t e = cudaFuncSetAttribute(k_ingest_l1<C, 1, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)std::max(l1_smem_bytes<C, 1, 1>(4), l1_smem_bytes<C, 1, 1>(kL1MaxD)));
+  if (e != cudaSuccess) return e;
+  L1Params prm;
+  memset(&prm, 0, sizeof(prm));
+  for (int t0 = 0; t0 < T; t0 += 65535) {
+    dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + l1_rows(d) - 1) / l1_rows(d), (unsigned)(T - t0 < 65535 ? T - t0 : 65535)),
+        block(kL1Tile);
+    k_ingest_l1<C, 1, 1, true><<<grid, block, smem, s>>>(frames, H, W, d, t0, 0, T - 1, cam, prm, 1.0f, out, C, wdev,
+                                                         bdev);
+  }
+  return cudaGetLastError();
+}
+
 template <int C>
 static cudaError_t launch_l1_prec(const uint16_t* frames, int T, int H, int W, int d, int in_ch, int t_first,
                                   int t_last, const CamArgs& cam, const L1Params& prm, int prec, float out_scale,
@@ -380,6 +408,18 @@ static cudaError_t launch_l1_prec(const uint16_t* frames, int T, int H, int W, i
   if (prec == kFP32) return launch_l1<C, 0, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, out_ct, s);
   if (prec == kBF16) return launch_l1<C, 1, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, out_ct, s);
   return launch_l1<C, 2, 3>(frames, T, H, W, d, t_first, t_last, cam, prm, out_scale, out, out_ct, s);
+}
+
+cudaError_t launch_ingest_l1_devw(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1_dev,
+                                  const float* b1_dev, int C, void* out, cudaStream_t s) {
+  if ((long long)T * H * W == 0) return cudaSuccess;
+  if (d < 1 || d > kL1MaxD) return cudaErrorInvalidValue;
+  switch (C) {
+    case 16: return launch_l1_devw<16>(frames, T, H, W, d, cam, w1_dev, b1_dev, out, s);
+    case 32: return launch_l1_devw<32>(frames, T, H, W, d, cam, w1_dev, b1_dev, out, s);
+    case 48: return launch_l1_devw<48>(frames, T, H, W, d, cam, w1_dev, b1_dev, out, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1,

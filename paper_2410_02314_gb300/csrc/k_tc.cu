@@ -47,6 +47,7 @@
 #include <type_traits>
 
 #include "sml_internal.h"
+#include "tc_ptx.cuh"
 
 namespace sml {
 
@@ -58,186 +59,6 @@ constexpr int kMinStages = 4;  // the handoff protocol needs a ring of at least 
 constexpr int kTmemCols = 512;
 constexpr int kMaxSeg = 6;
 constexpr int kMaxStages = 16;
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait for the phase with the given parity.  Fails fast once any role of the CTA
-// has given up (abort flag in shared memory).
-__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
-  unsigned long long t0 = gtimer();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63u) == 0) {
-      if (*abort_flag) return false;
-      if (gtimer() - t0 > kWaitLimitNs) {
-        *abort_flag = 1;
-        atomicExch(err, 1);
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
-  return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, err, abort_flag);
-}
-
-// Bounded wait for this thread's own asynchronous work (TMA loads, MMAs) to land before the
-// CTA releases the memory it writes.  Unlike mbar_wait it keeps waiting after another role
-// has aborted: that work completes whatever the other roles did.
-__device__ __noinline__ bool mbar_wait_own(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
-  unsigned long long t0 = gtimer();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63u) == 0 && gtimer() - t0 > kWaitLimitNs) {
-      *abort_flag = 1;
-      atomicExch(err, 1);
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// Shared-memory matrix descriptor, K-major.
-//   bits 0-13 start >> 4, 16-29 LBO >> 4 (K-direction core-matrix stride, no-swizzle only),
-//   32-45 SBO >> 4 (M/N-direction 8-row-group stride), 46-48 = 0b001, 49-51 base offset = 0,
-//   61-63 layout: 0 = no swizzle, 6 = 32-byte swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout = 0) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
-}
-
-// Instruction descriptor: D = F32, A/B K-major, dense.  kind::f16 with BF16 inputs
-// (a/b format 1), kind::tf32 (format 2) or kind::f8f6f4 with E4M3 inputs (format 0).
-__host__ __device__ constexpr uint32_t operand_format(int prec) { return prec == kBF16 ? 1u : (prec == kTF32 ? 2u : 0u); }
-__host__ __device__ constexpr uint32_t instr_desc(int prec, int M, int N) {
-  return (1u << 4) | (operand_format(prec) << 7) | (operand_format(prec) << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-template <int PREC>
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if (PREC == kBF16) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-  } else if (PREC == kTF32) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-  }
-}
-
-// Issued by a whole converged warp; only the lane with leader != 0 issues (no divergence).
-template <int PREC>
-__device__ __forceinline__ void umma_if(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t leader) {
-  if (PREC == kBF16) {
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %5, 0;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-        "@q tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(leader), "r"(1u)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %5, 0;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-        "@q tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(leader), "r"(1u)
-        : "memory");
-  }
-}
-__device__ __forceinline__ void umma_commit_if(uint32_t bar, uint32_t leader) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t"
-      "@q tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(bar),
-      "r"(leader)
-      : "memory");
-}
-// Named barriers 1 and 2 (0 is __syncthreads) carry the waiter -> MMA handoffs: the waiter
-// warp arrives, the MMA warp syncs (64 threads each time).
-__device__ __forceinline__ void named_arrive(uint32_t id) { asm volatile("bar.arrive %0, 64;" ::"r"(id) : "memory"); }
-__device__ __forceinline__ void named_sync(uint32_t id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
-
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
-      : "memory");
-}
-
-// max(x, 0) of two floats rounded to bf16 (round to nearest even) and packed, low half = lo.
-__device__ __forceinline__ uint32_t bf16x2_relu(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
-}
-
-// 32 lanes x 32 bits, 16 consecutive columns per thread.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
-}
-// 32 lanes x 32 bits, 16 consecutive columns per thread (store).
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
-      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
-      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Kernel arguments; bias, dequantisation factors and head weights travel by value so the
 // epilogue's FMAs read them from the constant bank.
@@ -262,6 +83,17 @@ struct TcKArgs {
   int nks, g_in, g_planes;
   uint32_t bimg_bytes;
   int out_g0, out_gt;
+  const float* bias_dev;  // device [co] bias (BF16 training), read instead of bias[] when set
+  const uint8_t* mask;    // DGRAD: the lower layer's activations, laid out like out
+  // Failure-path test settings: the give-up time of the waits on other roles (kWaitLimitNs
+  // unless a test shortens it) and a CTA whose producer issues no load at all (-1: none), so
+  // that its consumers' waits run out with no copy of that CTA in flight
+  unsigned long long wait_ns;
+  int poison_cta;
+  // FP8 rows loaded as 32-byte pixel pairs (frames of even width): the box starts at pixel
+  // j0 - d - pair_off (pair_off = d & 1 keeps the start even) and the A operand pair_off
+  // pixels into the box; -1: one 16-byte row per pixel
+  int pair_off;
   int* err;
 };
 
@@ -339,7 +171,7 @@ __device__ __forceinline__ void heads_out(const TcKArgs& a, const float (&v)[CO]
   }
 }
 
-template <int CI, int CO, int PREC, bool LAST>
+template <int CI, int CO, int PREC, bool LAST, bool DGRAD = false>
 __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant__ CUtensorMap tmap, const TcKArgs a) {
   using Cfg = TcCfg<CI, CO, PREC>;
   // K-dependent sizes: compile-time constants, or the arguments' values for CI = 0
@@ -412,7 +244,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
   // accumulator start values: every row position holds the bias (in accumulator units)
   float acc0[CO];
 #pragma unroll
-  for (int c = 0; c < CO; ++c) acc0[c] = PREC == kFP8 ? a.bias[c] / a.deq[c] : a.bias[c];
+  for (int c = 0; c < CO; ++c)
+    acc0[c] = PREC == kFP8 ? a.bias[c] / a.deq[c] : (DGRAD ? 0.0f : (a.bias_dev ? a.bias_dev[c] : a.bias[c]));
   if (warp < kEpiWarps) {
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
     for (int k = 0; k < SEG; ++k)
@@ -430,20 +263,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
       const uint32_t nst = (uint32_t)a.nstages;
       uint32_t st = 0, ph = 0, issued = 0;  // stage, phase of its current use, loads issued
-      bool ok = true;
+      bool ok = (int)blockIdx.x != a.poison_cta;  // a poisoned CTA loads nothing (failure-path test)
       for (uint32_t u = u_begin; u < u_end && ok; ++u) {
         int t, j0, phi, q;
         const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
         for (int kk = 0; kk < n_out + 2 && n_out > 0; ++kk) {
           // the slot was released by the MMA that read its previous load (skip on first use)
-          if (issued >= nst && !mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1u, a.err, s_abort)) {
+          if (issued >= nst && !mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1u, a.err, s_abort, a.wait_ns)) {
             ok = false;
             break;
           }
           const uint32_t fb = smem_u32(&full_bar[st]);
           mbar_expect_tx(fb, a.tx_bytes);
           const int row = phi + (q * SEG + kk - 1) * a.d;
-          tma_load_5d(smem_u32(s_stage + (size_t)st * a.stage_bytes), &tmap, 0, j0 - a.d, 0, row, t, fb);
+          const int x0 = PREC == kFP8 && a.pair_off >= 0 ? (j0 - a.d - a.pair_off) / 2 : j0 - a.d;
+          tma_load_5d(smem_u32(s_stage + (size_t)st * a.stage_bytes), &tmap, 0, x0, 0, row, t, fb);
           ++issued;
           if (++st == nst) {
             st = 0;
@@ -474,8 +308,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       // is advanced by plain addition, which cannot carry out of the field because every
       // shared-memory address is below 256 KB.
       // BF16: 32-byte swizzled rows, one plane per K step; FP8: 16-byte rows, two planes per step
-      const uint64_t a_desc0 = PREC == kBF16 ? smem_desc(smem_u32(s_stage), 16u, 256u, 6u)
-                                             : smem_desc(smem_u32(s_stage), a.plane_stride, 128u);
+      const uint64_t a_desc0 =
+          PREC == kBF16 ? smem_desc(smem_u32(s_stage), 16u, 256u, 6u)
+                        : smem_desc(smem_u32(s_stage) + 16u * (uint32_t)(a.pair_off > 0 ? a.pair_off : 0),
+                                    a.plane_stride, 128u);
       const uint64_t b_desc0 = smem_desc(smem_u32(s_bimg), 128u, 256u);
       // A offsets in 16-byte units: tap kx starts kx*d pixel rows later, K step ks one plane
       // (BF16) or two planes (FP8) further
@@ -581,8 +417,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
           }
           const int k1 = k0 + hand_rows < n_out + 2 ? k0 + hand_rows : n_out + 2;
           for (int kk = k0; kk < k1; ++kk) {
-            mbar_wait(smem_u32(&full_bar[st]), ph, a.err, s_abort);
-            if (kk < n_out && ((used >> kk) & 1u)) mbar_wait(smem_u32(&acce_bar[kk]), (par >> kk) & 1u, a.err, s_abort);
+            mbar_wait(smem_u32(&full_bar[st]), ph, a.err, s_abort, a.wait_ns);
+            if (kk < n_out && ((used >> kk) & 1u)) mbar_wait(smem_u32(&acce_bar[kk]), (par >> kk) & 1u, a.err, s_abort, a.wait_ns);
             if (++st == nst) {
               st = 0;
               ph ^= 1u;
@@ -613,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
 #pragma unroll 1
       for (int k = 0; k < n_out; ++k) {
-        if (!mbar_wait(smem_u32(&accf_bar[k]), (fpar >> k) & 1u, a.err, s_abort)) {
+        if (!mbar_wait(smem_u32(&accf_bar[k]), (fpar >> k) & 1u, a.err, s_abort, a.wait_ns)) {
           ok = false;
           break;
         }
@@ -648,6 +484,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
             heads_out<CO, kHeads>(a, v, t, px, plane);
           else
             heads_out<CO, kMaxHeads>(a, v, t, px, plane);
+        } else if (PREC == kBF16 && DGRAD) {
+          // input gradient of the layer below: dz = v * [a > 0] with a that layer's (ReLU) output
+#pragma unroll
+          for (int gq = 0; gq < Cfg::GO; ++gq) {
+            const size_t off = ((((size_t)t * a.H + i) * out_gt + out_g0 + gq) * a.W + j) * 32;
+            const uint4* mp = reinterpret_cast<const uint4*>(a.mask + off);
+            uint4 mk[2] = {__ldcs(mp), __ldcs(mp + 1)};
+            const uint32_t* mw = reinterpret_cast<const uint32_t*>(mk);
+            uint4 o[2];
+            uint32_t* ow = reinterpret_cast<uint32_t*>(o);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) ow[e] = bf16x2_masked(v[16 * gq + 2 * e], v[16 * gq + 2 * e + 1], mw[e]);
+            uint4* dst = reinterpret_cast<uint4*>(a.out + off);
+            __stcs(dst, o[0]);
+            __stcs(dst + 1, o[1]);
+          }
         } else if (PREC == kBF16) {
 #pragma unroll
           for (int gq = 0; gq < Cfg::GO; ++gq) {
@@ -751,6 +603,82 @@ __global__ void __launch_bounds__(128, 1) k_umma_selftest(const uint8_t* A, cons
   }
 }
 
+// One M x N x K product with both operands MN-major (the layout of the weight-gradient
+// contraction, whose K is pixels): A and B arrive as host-built images of 32-byte-swizzled
+// planes, plane g = [K rows][16 elements of M (or N) 16g..16g+15] (the row-planar stage
+// layout read along its pixels), planes a_plane / b_plane bytes apart; B's descriptor starts
+// b_shift rows into its planes (the tap shift of the contraction).  D: all 128 TMEM lanes x N
+// columns read back as float32 [128][N] (for M = 64, the lanes the MMA did not write read
+// back whatever TMEM held; the caller finds the data layout).
+__global__ void __launch_bounds__(128, 1) k_umma_mn_selftest(const uint8_t* A, const uint8_t* B, float* D, int M,
+                                                             int N, int K, int a_bytes, int b_bytes, int a_plane,
+                                                             int b_plane, int b_shift, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + ((a_bytes + 1023) & ~1023);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + ((b_bytes + 1023) & ~1023));
+  volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(bar + 1);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
+  for (int k = threadIdx.x; k < a_bytes / 16; k += 128) reinterpret_cast<uint4*>(sA)[k] = reinterpret_cast<const uint4*>(A)[k];
+  for (int k = threadIdx.x; k < b_bytes / 16; k += 128) reinterpret_cast<uint4*>(sB)[k] = reinterpret_cast<const uint4*>(B)[k];
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(bar), 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void*)s_tmem)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *s_tmem;
+  {  // zero the accumulator columns of every lane, so lanes the MMA does not write read 0
+    float z[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) z[k] = 0.0f;
+    const int warp = threadIdx.x >> 5;
+    for (int c = 0; c < N; c += 16) tmem_st16(tmem + ((uint32_t)(warp * 32) << 16) + c, z);
+    tmem_st_wait();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (threadIdx.x == 0) {
+    // kind::f16, bf16 inputs, F32 accumulate, A and B MN-major (bits 15, 16)
+    const uint32_t idesc = instr_desc(kBF16, M, N) | (1u << 15) | (1u << 16);
+    for (int ks = 0; ks < K / 16; ++ks) {
+      const uint64_t ad = smem_desc(smem_u32(sA) + ks * 512, (uint32_t)a_plane, 256u, 6u);
+      const uint64_t bd = smem_desc(smem_u32(sB) + (b_shift + ks * 16) * 32, (uint32_t)b_plane, 256u, 6u);
+      umma<kBF16>(tmem, ad, bd, idesc, 1u);
+    }
+    umma_commit(smem_u32(bar));
+  }
+  __syncwarp();
+  bool ok = mbar_wait(smem_u32(bar), 0, err, s_abort);
+  fence_after_sync();
+  const int warp = threadIdx.x >> 5;
+  if (ok) {
+    for (int c = 0; c < N; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+      tmem_ld_wait();
+      for (int k = 0; k < 16; ++k) D[(size_t)threadIdx.x * N + c + k] = v[k];
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
 size_t tc_smem_bytes(uint32_t bimg_bytes, int seg, int nstages, uint32_t stage_bytes) {
   size_t b = 1024;                                 // alignment slack
   b += (bimg_bytes + 1023u) & ~1023u;              // weights
@@ -782,7 +710,7 @@ TcSizes tc_sizes(int ci, int co, int d, int prec) {
 
 int tc_seg(int co) { return (512 / co - 4) < kMaxSeg ? (512 / co - 4) : kMaxSeg; }
 
-template <int CI, int CO, int PREC, bool LAST>
+template <int CI, int CO, int PREC, bool LAST, bool DGRAD = false>
 cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   using Cfg = TcCfg<CI, CO, PREC>;
   const int ci = CI > 0 ? CI : la.ci;
@@ -790,7 +718,7 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   TcKArgs a{};
   a.bimg = static_cast<const uint8_t*>(la.bimg);
   for (int c = 0; c < CO; ++c) {
-    a.bias[c] = la.bias[c];
+    a.bias[c] = la.bias ? la.bias[c] : 0.0f;
     a.deq[c] = la.deq ? la.deq[c] : 1.0f;
   }
   if (LAST) {
@@ -825,6 +753,12 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   a.stage_bytes = z.stage_bytes;
   a.out_g0 = la.out_g0;
   a.out_gt = la.out_gt;
+  a.bias_dev = la.bias_dev;
+  a.mask = static_cast<const uint8_t*>(la.mask);
+  a.wait_ns = la.wait_ns ? la.wait_ns : kWaitLimitNs;
+  a.poison_cta = la.poison_cta;
+  a.pair_off = (PREC == kFP8 && la.pair_rows) ? (la.d & 1) : -1;
+  if (DGRAD && (!a.mask || PREC != kBF16 || LAST)) return cudaErrorInvalidValue;
   if (CI > 0 && !LAST && (la.out_g0 != 0 || la.out_gt != Cfg::GO)) return cudaErrorInvalidValue;
   if (!LAST && (la.out_g0 < 0 || la.out_g0 + Cfg::GO > la.out_gt)) return cudaErrorInvalidValue;
   a.err = la.err;
@@ -839,11 +773,11 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   // runtime-K instance: set and launch under one lock, so that contexts on several host
   // threads never launch under another launch's smaller limit
   std::lock_guard<std::mutex> lock(g_tc_launch_mutex);
-  cudaError_t e = cudaFuncSetAttribute(k_dconv_tc<CI, CO, PREC, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_dconv_tc<CI, CO, PREC, LAST, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   long long grid = (long long)a.units < (long long)num_sms ? (long long)a.units : (long long)num_sms;
-  k_dconv_tc<CI, CO, PREC, LAST><<<(unsigned)grid, kThreads, smem, s>>>(*la.tmap, a);
+  k_dconv_tc<CI, CO, PREC, LAST, DGRAD><<<(unsigned)grid, kThreads, smem, s>>>(*la.tmap, a);
   return cudaGetLastError();
 }
 
@@ -922,6 +856,35 @@ cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaSt
     case 64: return launch_tc_impl<0, 64, kBF16, false>(a, num_sms, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_dconv_tc_train(const TcLayerArgs& a, bool dgrad, int num_sms, cudaStream_t s) {
+  if (a.prec != kBF16 || a.ci != a.co || a.out_g0 != 0 || a.out_gt != a.co / 16) return cudaErrorInvalidValue;
+  switch (a.co) {
+    case 16: return dgrad ? launch_tc_impl<16, 16, kBF16, false, true>(a, num_sms, s) : launch_tc_impl<16, 16, kBF16, false>(a, num_sms, s);
+    case 32: return dgrad ? launch_tc_impl<32, 32, kBF16, false, true>(a, num_sms, s) : launch_tc_impl<32, 32, kBF16, false>(a, num_sms, s);
+    case 48: return dgrad ? launch_tc_impl<48, 48, kBF16, false, true>(a, num_sms, s) : launch_tc_impl<48, 48, kBF16, false>(a, num_sms, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_umma_mn_selftest(const void* A, const void* B, float* D, int M, int N, int K, int a_bytes,
+                                    int b_bytes, int a_plane, int b_plane, int b_shift, int* err, cudaStream_t s) {
+  if ((M != 64 && M != 128) || N < 16 || N > 256 || N % 16 || K < 16 || K % 16 || a_bytes % 1024 || b_bytes % 1024 ||
+      a_plane % 256 || b_plane % 256 || b_shift < 0)
+    return cudaErrorInvalidValue;
+  // the operands' descriptors stay inside the images: A reads M/16 planes of K rows, B M/16
+  // planes of b_shift + K rows
+  if ((long long)(M / 16 - 1) * a_plane + (long long)K * 32 > a_bytes ||
+      (long long)(N / 16 - 1) * b_plane + (long long)(b_shift + K) * 32 > b_bytes)
+    return cudaErrorInvalidValue;
+  const size_t smem = 1024 + (size_t)a_bytes + (size_t)b_bytes + 64;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_umma_mn_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_umma_mn_selftest<<<1, 128, smem, s>>>(static_cast<const uint8_t*>(A), static_cast<const uint8_t*>(B), D, M, N, K,
+                                          a_bytes, b_bytes, a_plane, b_plane, b_shift, err);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_umma_selftest(const void* A, const void* B, float* D, int N, int K, int prec, int d_col, int* err,

@@ -7,6 +7,8 @@
 // Reductions over pixels (weight, bias and head gradients, the loss) go through per-block
 // partial sums and a second kernel that adds them in block order, so every result is
 // deterministic.
+#include <cuda_bf16.h>
+
 #include <cstring>
 
 #include "sml_internal.h"
@@ -73,9 +75,11 @@ struct WgCfg {
   static constexpr int NOUT = CO * K + CO;  // dw then db
 };
 
-template <int CI, int CO>
+// RP = true: dy holds dz itself, as bf16 row-planar activations [B][H][CO/16][W][16] (the ReLU
+// mask already applied; y unused) -- the first layer's gradient in BF16 training.
+template <int CI, int CO, bool RP = false>
 __global__ void __launch_bounds__(WgCfg<CI, CO>::THREADS) k_wgrad_partial(const float* __restrict__ x,
-                                                                          const float* __restrict__ dy,
+                                                                          const void* __restrict__ dy,
                                                                           const float* __restrict__ y, int B, int H,
                                                                           int W, int d, long long px_per_block,
                                                                           float* __restrict__ partial) {
@@ -106,8 +110,13 @@ __global__ void __launch_bounds__(WgCfg<CI, CO>::THREADS) k_wgrad_partial(const 
           xs[p][k] = v;
         } else {
           int o = k - Cfg::K;
-          size_t src = (size_t)q * CO + o;
-          v = y[src] > 0.0f ? dy[src] : 0.0f;
+          if (RP) {
+            const size_t src = ((((size_t)t * H + i) * (CO / 16) + o / 16) * W + j) * 16 + (o % 16);
+            v = __bfloat162float(static_cast<const __nv_bfloat16*>(dy)[src]);
+          } else {
+            const size_t src = (size_t)q * CO + o;
+            v = y[src] > 0.0f ? static_cast<const float*>(dy)[src] : 0.0f;
+          }
           zs[p][o] = v;
         }
       } else {
@@ -173,12 +182,15 @@ __global__ void __launch_bounds__(kHThreads) k_count_targets(const float* __rest
 
 // Per pixel: heads, loss terms and (optionally) gradients.  Partial layout per block:
 // [0] BCE sum, [1] L2 sum, [2 .. 2+5C) dhw, [2+5C .. 2+5C+5) dhb.
-template <int C>
-__global__ void __launch_bounds__(kHThreads) k_heads_loss(const float* __restrict__ a, const float* __restrict__ tgt,
-                                                          int B, int HW, const float* __restrict__ hw,
+// RP = true (BF16 training): a holds bf16 row-planar activations [B][H][C/16][W][16], and da
+// receives dz = (d loss / d a) * [a > 0] (the last conv layer's ReLU mask applied), rounded to
+// bf16, in the same layout.
+template <int C, bool RP = false>
+__global__ void __launch_bounds__(kHThreads) k_heads_loss(const void* __restrict__ a, const float* __restrict__ tgt,
+                                                          int B, int HW, int W, const float* __restrict__ hw,
                                                           const float* __restrict__ hb, float* __restrict__ h,
                                                           const float* __restrict__ nt_partial, int nt_blocks,
-                                                          const float* __restrict__ grad_scale, float* __restrict__ da,
+                                                          const float* __restrict__ grad_scale, void* __restrict__ da,
                                                           float* __restrict__ partial) {
   extern __shared__ float sm[];
   float* s_a = sm;                       // [kHThreads][C]
@@ -200,10 +212,18 @@ __global__ void __launch_bounds__(kHThreads) k_heads_loss(const float* __restric
   float dh[kHeads] = {0, 0, 0, 0, 0};
   if (q < npx) {
     long long b = q / HW, px = q - b * HW;
-    const float* ap = a + (size_t)q * C;
     float av[C];
+    // row-planar: group g of pixel (b, i, j) at (((b H + i) G + g) W + j) x 16 elements
+    const size_t rp0 = RP ? (((size_t)b * (HW / W) + px / W) * (C / 16) * W + px % W) * 16 : 0;
+    if (RP) {
+      const __nv_bfloat16* ap = static_cast<const __nv_bfloat16*>(a);
 #pragma unroll
-    for (int c = 0; c < C; ++c) av[c] = ap[c];
+      for (int c = 0; c < C; ++c) av[c] = __bfloat162float(ap[rp0 + (size_t)(c / 16) * W * 16 + (c % 16)]);
+    } else {
+      const float* ap = static_cast<const float*>(a) + (size_t)q * C;
+#pragma unroll
+      for (int c = 0; c < C; ++c) av[c] = ap[c];
+    }
     float hv[kHeads];
 #pragma unroll
     for (int k = 0; k < kHeads; ++k) {
@@ -226,13 +246,16 @@ __global__ void __launch_bounds__(kHThreads) k_heads_loss(const float* __restric
       dh[k] = 2.0f * e * inv_nt * gs;
     }
     if (da) {
-      float* dp = da + (size_t)q * C;
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         float s = 0.0f;
 #pragma unroll
         for (int k = 0; k < kHeads; ++k) s = fmaf(s_hw[k * C + c], dh[k], s);
-        dp[c] = s;
+        if (RP)
+          static_cast<__nv_bfloat16*>(da)[rp0 + (size_t)(c / 16) * W * 16 + (c % 16)] =
+              __float2bfloat16_rn(av[c] > 0.0f ? s : 0.0f);
+        else
+          static_cast<float*>(da)[(size_t)q * C + c] = s;
       }
     }
 #pragma unroll
@@ -325,9 +348,9 @@ cudaError_t conv_bwd_impl(const float* x, const float* y, const float* dy, int B
   return cudaGetLastError();
 }
 
-template <int C>
-cudaError_t heads_impl(const float* a, const float* tgt, int B, int H, int W, const float* hw, const float* hb,
-                       float* h, float* loss, const float* gscale, float* da, float* dhw, float* dhb, float* work,
+template <int C, bool RP = false>
+cudaError_t heads_impl(const void* a, const float* tgt, int B, int H, int W, const float* hw, const float* hb,
+                       float* h, float* loss, const float* gscale, void* da, float* dhw, float* dhb, float* work,
                        cudaStream_t s) {
   const int HW = H * W;
   long long npx = (long long)B * HW;
@@ -335,10 +358,11 @@ cudaError_t heads_impl(const float* a, const float* tgt, int B, int H, int W, co
   float* nt_partial = work;
   float* partial = work + kNtBlocks;
   size_t smem = sizeof(float) * kHThreads * (C + kHeads + 2);
-  cudaError_t e = cudaFuncSetAttribute(k_heads_loss<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_heads_loss<C, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_count_targets<<<kNtBlocks, kHThreads, 0, s>>>(tgt, B, HW, nt_partial);
-  k_heads_loss<C><<<nb, kHThreads, smem, s>>>(a, tgt, B, HW, hw, hb, h, nt_partial, kNtBlocks, gscale, da, partial);
+  k_heads_loss<C, RP><<<nb, kHThreads, smem, s>>>(a, tgt, B, HW, W, hw, hb, h, nt_partial, kNtBlocks, gscale, da,
+                                                  partial);
   int nout = 2 + kHeads * C + kHeads;
   k_heads_reduce<<<(nout + 255) / 256, 256, 0, s>>>(partial, nb, C, npx, nt_partial, kNtBlocks, loss, dhw, dhb);
   return cudaGetLastError();
@@ -408,6 +432,37 @@ cudaError_t train_heads_loss(const float* a, const float* tgt, int B, int H, int
 #define HL(CC) return heads_impl<CC>(a, tgt, B, H, W, hw, hb, h, loss, gscale, da, dhw, dhb, wk, s)
   SML_CH_SWITCH(C, HL)
 #undef HL
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t train_heads_loss_rp(const void* a, const float* tgt, int B, int H, int W, int C, const float* hw,
+                                const float* hb, float* h, float* loss, const float* gscale, void* dz, float* dhw,
+                                float* dhb, void* work, cudaStream_t s) {
+  if ((long long)B * H * W == 0) return cudaErrorInvalidValue;
+  float* wk = static_cast<float*>(work);
+#define HR(CC) return heads_impl<CC, true>(a, tgt, B, H, W, hw, hb, h, loss, gscale, dz, dhw, dhb, wk, s)
+  SML_CH_SWITCH(C, HR)
+#undef HR
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t train_l0_wgrad_rp(const float* x0, const void* dz0, int B, int H, int W, int C, int d, float* dw,
+                              float* db, void* work, cudaStream_t s) {
+  const long long npx = (long long)B * H * W;
+  if (npx == 0) return cudaSuccess;
+  float* wk = static_cast<float*>(work);
+#define W0(CO)                                                                                     \
+  {                                                                                                \
+    using Cfg = WgCfg<1, CO>;                                                                      \
+    long long ppb = (npx + kWgBlocks - 1) / kWgBlocks;                                             \
+    ppb = (ppb + kWgPx - 1) / kWgPx * kWgPx;                                                       \
+    const int nb = (int)((npx + ppb - 1) / ppb);                                                   \
+    k_wgrad_partial<1, CO, true><<<nb, Cfg::THREADS, 0, s>>>(x0, dz0, nullptr, B, H, W, d, ppb, wk); \
+    k_wgrad_reduce<1, CO><<<(Cfg::NOUT + 255) / 256, 256, 0, s>>>(wk, nb, dw, db);                 \
+    return cudaGetLastError();                                                                     \
+  }
+  SML_CH_SWITCH(C, W0)
+#undef W0
   return cudaErrorInvalidValue;
 }
 

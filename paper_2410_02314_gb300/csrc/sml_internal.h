@@ -75,6 +75,11 @@ cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d,
                              const float* b1, int C, int in_ch, int t_first, int t_last, int prec, float out_scale,
                              void* out, int out_ct, cudaStream_t s);
 
+// BF16 training: the same first layer (in_ch = 1, bf16 row-planar output with C channels)
+// with w1 [C][1][9] and b1 [C] in DEVICE memory.
+cudaError_t launch_ingest_l1_devw(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1_dev,
+                                  const float* b1_dev, int C, void* out, cudaStream_t s);
+
 // Max of n post-ReLU activations (fp32 or bf16 buffer) into *out (float bits, atomicMax).
 cudaError_t launch_amax(const void* x, size_t n, int prec, unsigned* out, cudaStream_t s);
 
@@ -126,13 +131,30 @@ struct TcLayerArgs {
   int T, H, W, d, prec;
   int ci, co;               // input channels read (groups 0..ci/16-1 of the input buffer), outputs
   int* err;                 // device error word (wait timeouts)
+  const float* bias_dev = nullptr;  // BF16 training: device bias [co], used instead of `bias`
+  const void* mask = nullptr;       // input gradient: the lower layer's activations (layout of out)
+  unsigned long long wait_ns = 0;   // failure-path tests: give-up time of the waits (0 = 2 s)
+  int poison_cta = -1;              // failure-path tests: a CTA whose producer loads nothing
+  int pair_rows = 0;                // FP8: the map loads 32-byte pixel pairs (even W; see encode_act_map)
 };
 cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaStream_t s);
+// BF16 training, plain C -> C layers: the forward conv (bias from a.bias_dev) or, with dgrad,
+// the input gradient dz_in = conv(dz; mirrored transposed weights) * [a.mask > 0] (no bias).
+cudaError_t launch_dconv_tc_train(const TcLayerArgs& a, bool dgrad, int num_sms, cudaStream_t s);
 size_t tc_bimg_bytes(int ci, int co, int prec);
 void tc_pack_bimg(const float* w_tap_ci_co /*[9][ci][co]*/, int ci, int co, int prec, const float* w_scale, void* dst);
 int tc_box_width(int d);
 // Whether a ci -> co layer at dilation d fits the tensor-core conv's shared memory.
 bool tc_layer_fits(int ci, int co, int d, int prec);
+
+// --- BF16 training on the tensor cores (k_train_tc.cu) -----------------------------------
+size_t train_wgrad_tc_work_bytes(int C, int num_sms);
+// FP32 w [cout][cin][3][3] -> bf16 B images of the conv: forward and mirrored-transposed (dgrad).
+cudaError_t launch_pack_bimg_bf16(const float* w, int cin, int cout, void* fwd, void* dgrad, cudaStream_t s);
+// dw [C][C][3][3], db [C] of a C -> C layer from dz (tm_dz: 128-pixel row boxes) and the
+// layer input x (tm_x: the conv's row boxes for dilation d); partial: train_wgrad_tc_work_bytes.
+cudaError_t launch_wgrad_tc(const CUtensorMap* tm_dz, const CUtensorMap* tm_x, int T, int H, int W, int C, int d,
+                            float* partial, int num_sms, float* dw, float* db, int* err, cudaStream_t s);
 
 // --- training (k_train.cu) -------------------------------------------------------------
 size_t train_conv_work_bytes(int B, int H, int W, int cin, int cout);
@@ -146,9 +168,19 @@ cudaError_t train_heads_loss(const float* a, const float* tgt, int B, int H, int
                              float* dhb, void* work, cudaStream_t s);
 cudaError_t train_ingest(const uint16_t* f, long long n, float gain, float offset, float in_scale, float* x0,
                          cudaStream_t s);
+// BF16 training: heads + loss from bf16 row-planar activations, writing dz (masked, bf16
+// row-planar); first-layer weight gradient from bf16 row-planar dz0 and the fp32 input x0.
+cudaError_t train_heads_loss_rp(const void* a, const float* tgt, int B, int H, int W, int C, const float* hw,
+                                const float* hb, float* h, float* loss, const float* gscale, void* dz, float* dhw,
+                                float* dhb, void* work, cudaStream_t s);
+cudaError_t train_l0_wgrad_rp(const float* x0, const void* dz0, int B, int H, int W, int C, int d, float* dw,
+                              float* db, void* work, cudaStream_t s);
 
 // Debug: one 128 x N x K UMMA through the same descriptor helpers (exposed for tests).
 cudaError_t launch_umma_selftest(const void* a, const void* b, float* d, int N, int K, int prec, int d_col, int* err,
                                  cudaStream_t s);
+// Debug: one M x N x K product with both operands MN-major (32-byte-swizzled planes).
+cudaError_t launch_umma_mn_selftest(const void* A, const void* B, float* D, int M, int N, int K, int a_bytes,
+                                    int b_bytes, int a_plane, int b_plane, int b_shift, int* err, cudaStream_t s);
 
 }  // namespace sml

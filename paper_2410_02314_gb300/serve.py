@@ -209,13 +209,14 @@ class GpuExecutor:
         return self.d_out[slot], self.h_out[slot]
 
     def warm(self, shapes, max_request=None):
-        """Create each slot's workspace for the given frame sizes (at most MAX_PLANS) and, if
-        given, record buffers for the largest request shape (T, H, W) before timing."""
+        """Create each slot's workspace for the given request shapes (T, H, W), at most
+        MAX_PLANS frame sizes, and, if given, record buffers for the largest request shape
+        before timing."""
         torch = self.torch
         for slot, (loc, st) in enumerate(zip(self.locs, self.streams)):
-            for (H, W) in shapes:
-                fr = torch.zeros((1, H, W), dtype=torch.uint16, device=self.dev)
-                out = torch.empty(record_capacity(1, H, W) * 24, dtype=torch.uint8, device=self.dev)
+            for (T, H, W) in shapes:
+                fr = torch.zeros((T, H, W), dtype=torch.uint16, device=self.dev)
+                out = torch.empty(record_capacity(T, H, W) * 24, dtype=torch.uint8, device=self.dev)
                 n = torch.zeros(1, dtype=torch.int64, device=self.dev)
                 loc.localize_async(fr, 0.5, out, n, stream=st)
             if max_request is not None:
@@ -227,7 +228,7 @@ class GpuExecutor:
         record buffers."""
         from . import sml_workspace_bytes
 
-        ws = sum(sml_workspace_bytes(loc.ctx, 1, 1)[2] for loc in self.locs)
+        ws = sum(sml_workspace_bytes(loc.ctx, 1, 1, 1)[2] for loc in self.locs)
         return ws + sum(0 if d is None else d.numel() for d in self.d_out)
 
     def plan_bytes(self, slot, shape):
@@ -238,7 +239,7 @@ class GpuExecutor:
         from . import sml_workspace_bytes
 
         T, H, W = shape
-        pb, res, _ = sml_workspace_bytes(self.locs[slot].ctx, H, W)
+        pb, res, _ = sml_workspace_bytes(self.locs[slot].ctx, T, H, W)
         have = 0 if self.d_out[slot] is None else self.d_out[slot].numel()
         return (0 if res else pb) + max(0, record_capacity(T, H, W) * 24 - have)
 

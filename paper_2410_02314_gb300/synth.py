@@ -480,18 +480,13 @@ def workload_large_fov(T=2, H=2048, W=2048, precision="bf16", seed=4) -> Workloa
 # --------------------------------------------------------------------------- training data
 
 
-def training_batch(rng, B=256, H=64, W=64, max_emitters=10, astig=True, z_scale=1000.0, ph_scale=10000.0,
-                   min_emitters=0):
-    """Simulated training patches and per-pixel targets.
-
-    Returns (frames u16 [B,H,W], targets f32 [B,5,H,W], emitters).  Target channel 0 is 1 at
-    the pixel containing an emitter (brighter one wins a shared pixel); channels 1-4 hold
-    dx, dy (emitter minus pixel centre, px), z / z_scale and photons / ph_scale there.
-    """
+def training_emitters(rng, B=256, H=64, W=64, max_emitters=10, astig=True, min_emitters=0) -> Emitters:
+    """Emitters of a batch of training patches: U{min..max} per patch, uniform positions,
+    z ~ U(-600, 600) nm (astigmatic), photons LogNormal(ln 3000, 0.5), background U(50, 200)."""
     counts = rng.integers(min_emitters, max_emitters + 1, B)
     n = int(counts.sum())
     x, y = _uniform_positions(rng, n, H, W)
-    em = Emitters(
+    return Emitters(
         frame=np.repeat(np.arange(B, dtype=np.int32), counts),
         x=x,
         y=y,
@@ -499,18 +494,38 @@ def training_batch(rng, B=256, H=64, W=64, max_emitters=10, astig=True, z_scale=
         photons=rng.lognormal(math.log(3000.0), 0.5, n),
         bg=rng.uniform(50.0, 200.0, B),
     )
+
+
+def training_target_entries(em: Emitters, H: int, W: int, z_scale=1000.0, ph_scale=10000.0):
+    """The nonzero entries of the per-pixel targets [B,5,H,W] of a batch, as (flat indices,
+    float32 values): channel 0 is 1 at the pixel containing an emitter (the brighter emitter
+    wins a shared pixel); channels 1-4 hold dx, dy (emitter minus pixel centre, px),
+    z / z_scale and photons / ph_scale there."""
+    j = np.clip(np.rint(em.x).astype(np.int64), 0, W - 1)
+    i = np.clip(np.rint(em.y).astype(np.int64), 0, H - 1)
+    f = em.frame.astype(np.int64)
+    order = np.argsort(em.photons, kind="stable")  # ascending: the last write of a pixel is the brightest
+    px = (f * 5 * H + i) * W + j  # flat index of channel 0
+    last = {}
+    for k in order:
+        last[px[k]] = k
+    win = np.array(sorted(last.values()), dtype=np.int64)
+    idx = np.concatenate([px[win] + c * H * W for c in range(5)])
+    val = np.concatenate([np.ones(win.size), em.x[win] - j[win], em.y[win] - i[win], em.z[win] / z_scale,
+                          em.photons[win] / ph_scale]).astype(np.float32)
+    return idx, val
+
+
+def training_batch(rng, B=256, H=64, W=64, max_emitters=10, astig=True, z_scale=1000.0, ph_scale=10000.0,
+                   min_emitters=0):
+    """Simulated training patches and per-pixel targets.
+
+    Returns (frames u16 [B,H,W], targets f32 [B,5,H,W], emitters, camera); targets as
+    training_target_entries describes them."""
+    em = training_emitters(rng, B, H, W, max_emitters, astig, min_emitters)
     cam = Camera(1.0, 100.0)
     frames = simulate(em, B, H, W, cam, astig, rng)
     tgt = np.zeros((B, 5, H, W), dtype=np.float32)
-    best = np.full((B, H, W), -1.0)
-    j = np.clip(np.rint(em.x).astype(np.int64), 0, W - 1)
-    i = np.clip(np.rint(em.y).astype(np.int64), 0, H - 1)
-    for k in np.argsort(em.photons):  # ascending: brighter emitters overwrite dimmer ones
-        f = em.frame[k]
-        best[f, i[k], j[k]] = em.photons[k]
-        tgt[f, 0, i[k], j[k]] = 1.0
-        tgt[f, 1, i[k], j[k]] = em.x[k] - j[k]
-        tgt[f, 2, i[k], j[k]] = em.y[k] - i[k]
-        tgt[f, 3, i[k], j[k]] = em.z[k] / z_scale
-        tgt[f, 4, i[k], j[k]] = em.photons[k] / ph_scale
+    idx, val = training_target_entries(em, H, W, z_scale, ph_scale)
+    tgt.reshape(-1)[idx] = val
     return frames, tgt, em, cam

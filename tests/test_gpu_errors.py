@@ -60,7 +60,7 @@ def test_serving_fails_the_request_that_saw_the_error():
         fr = synth.simulate(em, 2, 64, 64, synth.Camera(), False, rng)
         reqs.append(serve.Request(rid=k, frames=torch.from_numpy(fr).pin_memory(), arrival=0.0))
     ex = serve.GpuExecutor(spec.to_json(), blob, slots=1)
-    ex.warm([(64, 64)])
+    ex.warm([(2, 64, 64)])
     assert sml.lib().sml_debug_set_error_word(ex.locs[0].ctx, 1) == sml.SML_OK
     sch = serve.Scheduler(ex, 1 << 34)
     out = sch.run(reqs)
@@ -69,3 +69,29 @@ def test_serving_fails_the_request_that_saw_the_error():
     for r in out[1:]:
         assert r.records.tobytes() == alone.localize(r.frames.numpy(), r.p_min).tobytes()
     assert sch.failed == 1
+
+
+def test_a_conv_whose_waits_run_out_reports_it():
+    """The kernels' own give-up path, in the form that leaves nothing in flight: with the test
+    settings debug_poison_cta = 0 and debug_wait_ns = 5 ms, CTA 0 of every tensor-core conv
+    launch loads no data, so its consumers' bounded waits run out; the kernel sets the error
+    word, finishes its row sequence without waiting, drains its own MMAs, frees TMEM and
+    returns.  The call reports SML_ERR_CUDA; a context without the settings then gives the
+    usual records on the same device."""
+    import json
+
+    w = synth.workload_small(precision="bf16")
+    js = json.loads(w.spec.to_json())
+    bad = sml.Localizer(json.dumps(dict(js, debug_poison_cta=0, debug_wait_ns=5e6)), w.blob)
+    with pytest.raises(sml.SmlError) as e:
+        bad.localize(w.frames, 0.5, gain=w.cam.gain, offset=w.cam.offset)
+    assert e.value.code == sml.SML_ERR_CUDA and "timed out" in str(e.value)
+    bad.close()
+    good = sml.Localizer(w.spec.to_json(), w.blob)
+    recs = good.localize(w.frames, 0.5, gain=w.cam.gain, offset=w.cam.offset)
+    again = good.localize(w.frames, 0.5, gain=w.cam.gain, offset=w.cam.offset)
+    assert len(recs) > 0 and recs.tobytes() == again.tobytes()
+    good.close()
+    with pytest.raises(sml.SmlError) as e:  # the test setting needs a short, bounded wait
+        sml.Localizer(json.dumps(dict(js, debug_poison_cta=0)), w.blob)
+    assert e.value.code == sml.SML_ERR_BAD_SPEC

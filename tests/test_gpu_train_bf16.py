@@ -1,0 +1,164 @@
+"""BF16 training on the tensor cores (include/sml_train.h, BF16 section).
+
+Per kernel, against float64 PyTorch of the same bf16 inputs: the forward conv, the input
+gradient (transposed conv with the lower layer's ReLU mask) and the weight/bias gradient
+contraction (tcgen05 with MN-major operands).  Whole network: the loss and every gradient
+against the oracle's exact float64 gradient (itself pinned to central finite differences,
+tests/test_oracle_grad.py), and a net trained in BF16 on fresh device-simulated batches of
+the training configuration (256 patches of 64x64, 48-channel 8-layer net) against the method
+without a network."""
+import time
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+import oracle
+from paper_2410_02314_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def to_rp(x):
+    """NCHW float -> row-planar bf16 [B][H][C/16][W][16] (CUDA)."""
+    B, C, H, W = x.shape
+    return x.reshape(B, C // 16, 16, H, W).permute(0, 3, 1, 4, 2).contiguous().to(torch.bfloat16).cuda()
+
+
+def from_rp(a):
+    """Row-planar [B][H][G][W][16] -> NCHW float64 (CPU)."""
+    B, H, G, W, _ = a.shape
+    return a.permute(0, 2, 4, 1, 3).reshape(B, 16 * G, H, W).double().cpu()
+
+
+def bf16(x):
+    return x.to(torch.bfloat16).double()
+
+
+@pytest.mark.parametrize("C,d,B,H,W", [(48, 1, 2, 20, 40), (48, 4, 3, 33, 150), (32, 16, 2, 40, 130), (16, 2, 1, 9, 17)])
+def test_bf16_conv_kernels_match_float64(C, d, B, H, W):
+    """Forward, input gradient and weight gradient of one C -> C layer (dilation d, ragged
+    frames wider than one 128-pixel strip) against float64 PyTorch on the same bf16 values:
+    the outputs differ only by FP32 accumulation and the final bf16 rounding (1 ulp)."""
+    from paper_2410_02314_gb300 import train as T
+
+    g = torch.Generator().manual_seed(C + d)
+    x = torch.relu(torch.randn(B, C, H, W, generator=g, dtype=torch.float64))
+    w = (torch.rand(C, C, 3, 3, generator=g, dtype=torch.float64) - 0.5) * 2 * (6.0 / (9 * C)) ** 0.5
+    b = (torch.rand(C, generator=g, dtype=torch.float64) - 0.5) * 0.2
+    dz = torch.randn(B, C, H, W, generator=g, dtype=torch.float64) * (torch.rand(B, C, H, W, generator=g) > 0.4)
+    xq, wq, dzq = bf16(x), bf16(w), bf16(dz)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    fwd, dg = T.sml_train_bf16_pack(w.float().cuda().contiguous())
+    # forward
+    y = from_rp(T.sml_train_bf16_conv_fwd(to_rp(x), fwd, b.float().cuda(), d, err))
+    ref = torch.relu(F.conv2d(xq, wq, b.float().double(), padding=d, dilation=d))
+    assert (y - ref).abs().max().item() <= 2 ** -8 * ref.abs().max().item() + 1e-6
+    # input gradient of the layer below: conv_transpose of dz, masked by x > 0
+    dzin = from_rp(T.sml_train_bf16_conv_dgrad(to_rp(dz), to_rp(x), dg, d, err))
+    ref_in = F.conv_transpose2d(dzq, wq, padding=d, dilation=d) * (xq > 0)
+    assert (dzin - ref_in).abs().max().item() <= 2 ** -8 * ref_in.abs().max().item() + 1e-6
+    # weight and bias gradient
+    dw, db = T.sml_train_bf16_conv_wgrad(to_rp(x), to_rp(dz), d, err)
+    xr = xq.clone().requires_grad_(True)
+    wr = wq.clone().requires_grad_(True)
+    br = torch.zeros(C, dtype=torch.float64, requires_grad=True)
+    (F.conv2d(xr, wr, br, padding=d, dilation=d) * dzq).sum().backward()
+    e_w = (dw.double().cpu() - wr.grad).abs().max().item() / wr.grad.abs().max().item()
+    e_b = (db.double().cpu() - br.grad).abs().max().item() / br.grad.abs().max().item()
+    print(C, d, "wgrad rel err", e_w, "bias", e_b)
+    assert e_w <= 1e-5 and e_b <= 1e-5
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+
+
+def _loss_and_grads(net, frames, tgt):
+    for p in net.parameters():
+        p.grad = None
+    loss = net.loss(torch.from_numpy(frames).cuda(), torch.from_numpy(tgt).cuda())
+    loss.backward()
+    g = [p.grad.detach().double().cpu().numpy().ravel() for p in net.w] + \
+        [p.grad.detach().double().cpu().numpy().ravel() for p in net.b] + \
+        [net.hw.grad.double().cpu().numpy().ravel(), net.hb.grad.double().cpu().numpy().ravel()]
+    return float(loss.item()), g
+
+
+@pytest.mark.parametrize("C,dil,B,H,W", [(16, (1, 2, 4), 3, 20, 24), (48, (1, 2, 4, 8, 16, 8, 4, 1), 4, 64, 64)])
+def test_bf16_gradients_match_oracle(C, dil, B, H, W):
+    """The whole network in BF16 (forward, heads + loss, backward) against the oracle's
+    float64 loss and gradient: per parameter group, the normalised max error and the cosine
+    between the gradients; the FP32 SIMT path on the same batch is printed beside it."""
+    from paper_2410_02314_gb300.train import DilatedLocNet
+
+    spec = synth.NetSpec(in_ch=1, channels=C, dilations=dil)
+    blob = synth.pack_blob(spec, synth.init_weights(spec, 3))
+    rng = np.random.default_rng(1)
+    frames, tgt, _, _ = synth.training_batch(rng, B=B, H=H, W=W, max_emitters=6)
+    onet = oracle.Net(spec.to_json(), blob)
+    x0 = oracle.ingest(frames, 1.0, 100.0, in_scale=onet.in_scale)
+    val, gw, gb, ghw, ghb, _ = oracle.loss_grad(onet, x0, tgt)
+    ref = [gw, gb, ghw, ghb]
+    out = {}
+    for prec in ("bf16", "fp32"):
+        net = DilatedLocNet.from_blob(spec.to_json(), blob, precision=prec).cuda()
+        loss, g = _loss_and_grads(net, frames, tgt)
+        groups = [np.concatenate(g[: len(dil)]), np.concatenate(g[len(dil) : 2 * len(dil)]), g[-2], g[-1]]
+        rel = [float(np.abs(a - r).max() / max(np.abs(r).max(), 1e-12)) for a, r in zip(groups, ref)]
+        cos = [float(a @ r / max(np.linalg.norm(a) * np.linalg.norm(r), 1e-30)) for a, r in zip(groups, ref)]
+        out[prec] = (abs(loss - val) / abs(val), rel, cos)
+        print(prec, C, len(dil), "loss rel err", out[prec][0], "grad max rel err (w, b, hw, hb)", np.round(rel, 5),
+              "cos", np.round(cos, 6))
+        if prec == "bf16":
+            assert not net.device_error()
+    loss_e, rel, cos = out["bf16"]
+    assert loss_e <= 1e-2
+    assert max(rel) <= 0.1 and min(cos) >= 0.995
+    assert max(out["fp32"][1]) <= 1e-4
+
+
+def test_bf16_training_on_device_batches_beats_mle():
+    """Training configuration: the 48-channel 8-layer net, BF16 forward and backward with FP32
+    masters (Adam), fresh batches of 256 astigmatic 64x64 patches per step from the device
+    simulator.  The trained net (BF16 inference) against local maxima + Gaussian MLE on held-out
+    frames at high density; steps per second of BF16 and FP32 training on the same batches."""
+    import paper_2410_02314_gb300 as sml
+    from paper_2410_02314_gb300.train import DilatedLocNet, device_batch, train
+
+    from test_gpu_train import _evaluate
+
+    spec = synth.NetSpec(in_ch=1, channels=48, dilations=(1, 2, 4, 8, 16, 8, 4, 1))
+    # throughput: 20 steps each on the same device batch
+    rates = {}
+    for prec in ("bf16", "fp32"):
+        net = DilatedLocNet(spec, synth.init_weights(spec, 11), precision=prec).cuda()
+        opt = torch.optim.Adam(net.parameters(), lr=1e-3)
+        frames, tgt = device_batch(np.random.default_rng(0), 256, 64, 64, max_emitters=10)
+        for k in range(23):
+            if k == 3:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            opt.zero_grad(set_to_none=True)
+            net.loss(frames, tgt).backward()
+            opt.step()
+        torch.cuda.synchronize()
+        rates[prec] = 20 / (time.perf_counter() - t0)
+    print("training steps/s (256 x 64x64 patches, 48-ch 8-layer):", rates)
+    net = DilatedLocNet(spec, synth.init_weights(spec, 11), precision="bf16").cuda()
+    hist = train(net, steps=1500, batch=256, patch=64, lr=1e-3, log_every=250, seed=5, max_emitters=40, fresh=True)
+    print("bf16 training loss", hist)
+    assert hist[-1][1] < 0.5 * hist[0][1]
+    js, blob = net.to_blob("bf16")
+    loc = sml.Localizer(js, blob)
+    best, base = _evaluate(loc, np.random.default_rng(1234), 32, 20, 40)
+    print("high density | bf16-trained net (p_min=%s)" % best[0], best[1], "| local max + MLE (thr=%s)" % base[0], base[1])
+    assert best[1]["jaccard"] > base[1]["jaccard"]
+    assert rates["bf16"] > rates["fp32"]
