@@ -686,10 +686,11 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
     ap.add_argument("--frames", type=int, default=T_FRAMES,
                     help="frames per step (default 256; smaller stacks for profiler captures)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "dcd", "dilatedloc", "large_fov"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "dcd", "dilatedloc", "large_fov", "training"],
                     help="batched: the 48-channel 8-layer net; dcd: the 22-layer dense-block net; dilatedloc: the "
                          "full topology (dense blocks, U-Net, uncertainty heads); dcd and dilatedloc run fp32/bf16; "
-                         "large_fov: 1000 distinct 2048x2048 sCMOS frames, bf16 or fp8, one GPU")
+                         "large_fov: 1000 distinct 2048x2048 sCMOS frames, bf16 or fp8, one GPU; training: "
+                         "BF16 and FP32 training steps (256 patches of 64x64), one GPU")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk-px", type=int, default=0)
     ap.add_argument("--tc-stages", type=int, default=0)
@@ -726,6 +727,16 @@ def main():
 
     if args.workload in ("dcd", "dilatedloc") and args.precision == "fp8":
         raise SystemExit("the dense-block and full-topology nets run in fp32 or bf16")
+    if args.workload == "training":
+        if world > 1:
+            raise SystemExit("the training line runs on one GPU")
+        tr = training_run(dev, steps=args.steps, warmup=max(3, args.warmup))
+        line = {"metric": "training steps/s", "value": tr["bf16_steps_per_s"], "unit": "steps/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": tr["bf16_ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": "training_256x64x64_48ch_8layer", "parallelism": "replicas1"}, "training": tr}
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "large_fov":
         if world > 1 or args.precision == "fp32":
             raise SystemExit("the large field-of-view line runs on one GPU in bf16 or fp8")

@@ -86,6 +86,50 @@ __device__ __forceinline__ void dec_flags(const DecodeArgs& a, const PxLoc (&loc
   }
 }
 
+// The same flags as dec_flags, with the horizontal neighbours taken from the adjacent lanes:
+// the 32 lanes of a warp hold 32 consecutive pixels in raster order, so each lane loads only
+// its own column at rows i-1, i, i+1 and shuffles the columns j-1 and j+1 in; lanes 0 and 31
+// load the column just outside the warp's run.  A neighbour outside the frame (j = 0 or
+// j = W-1, where the adjacent lane holds the next or previous row) reads as -inf, as in
+// dec_flags.
+template <int NH>
+__device__ __forceinline__ void dec_flags_shfl(const DecodeArgs& a, const PxLoc (&loc)[kPxPerThread],
+                                               bool (&flag)[kPxPerThread]) {
+  const size_t plane = (size_t)a.H * a.W;
+  const int lane = threadIdx.x & 31;
+  float col[kPxPerThread][3], edge[kPxPerThread][3];
+#pragma unroll
+  for (int k = 0; k < kPxPerThread; ++k) {
+    const float* p = a.maps + (size_t)loc[k].t * NH * plane;
+    const int je = lane == 0 ? loc[k].j - 1 : loc[k].j + 1;
+    const bool edge_lane = lane == 0 || lane == 31;
+#pragma unroll
+    for (int di = -1; di <= 1; ++di) {
+      const int ii = loc[k].i + di;
+      const bool in = loc[k].valid && ii >= 0 && ii < a.H;
+      col[k][di + 1] = in ? __ldg(p + (size_t)ii * a.W + loc[k].j) : -INFINITY;
+      edge[k][di + 1] = edge_lane && in && je >= 0 && je < a.W ? __ldg(p + (size_t)ii * a.W + je) : -INFINITY;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kPxPerThread; ++k) {
+    float l[3], r[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      l[q] = __shfl_up_sync(0xffffffffu, col[k][q], 1);
+      r[q] = __shfl_down_sync(0xffffffffu, col[k][q], 1);
+      if (lane == 0) l[q] = edge[k][q];
+      if (lane == 31) r[q] = edge[k][q];
+      if (loc[k].j == 0) l[q] = -INFINITY;
+      if (loc[k].j == a.W - 1) r[q] = -INFINITY;
+    }
+    const float c = col[k][1];
+    // strict against earlier neighbours (row i-1, and the left one), >= against later ones
+    flag[k] = loc[k].valid && c > a.p_min && c > l[0] && c > col[k][0] && c > r[0] && c > l[1] && c >= r[1] &&
+              c >= l[2] && c >= col[k][2] && c >= r[2];
+  }
+}
+
 // NH: channels of the maps (5, or 9 with the uncertainty maps).
 template <int NH>
 __global__ void __launch_bounds__(kDecodeThreads) k_decode_count(DecodeArgs a) {
@@ -94,7 +138,7 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode_count(DecodeArgs a) {
   PxLoc loc[kPxPerThread];
   bool flag[kPxPerThread];
   dec_locate(a, q0, loc);
-  dec_flags<NH>(a, loc, flag);
+  dec_flags_shfl<NH>(a, loc, flag);
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned cnt = 0;
 #pragma unroll

@@ -15,6 +15,7 @@ import torch
 import torch.nn.functional as F
 
 import oracle
+from bf16_emulation import bf16_emulation
 from paper_2410_02314_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -92,37 +93,71 @@ def _loss_and_grads(net, frames, tgt):
     return float(loss.item()), g
 
 
+def _groups(net, L):
+    g = [np.concatenate([p.grad.detach().double().cpu().numpy().ravel() for p in net.w]),
+         np.concatenate([p.grad.detach().double().cpu().numpy().ravel() for p in net.b]),
+         net.hw.grad.double().cpu().numpy().ravel(), net.hb.grad.double().cpu().numpy().ravel()]
+    return g
+
+
+def _cmp(got, ref):
+    rel = [float(np.abs(a - r).max() / max(np.abs(r).max(), 1e-30)) for a, r in zip(got, ref)]
+    cos = [float(a @ r / max(np.linalg.norm(a) * np.linalg.norm(r), 1e-30)) for a, r in zip(got, ref)]
+    return rel, cos
+
+
+# Gates of the BF16 path against the float64 oracle, from tests/measure_bf16_grad_error.py on a
+# GB300 (18 nets: C = 16, 32, 48 with 3, 6, 8 layers, 6 weight seeds each): worst loss error
+# 9.0e-4; conv weight and bias gradients worst normalised max error 0.177, worst cosine 0.985;
+# head gradients worst 0.0061.  The spread comes from the bf16 forward itself: ReLU masks of
+# near-zero pre-activations differ from float64 and route the gradient differently (some seeds
+# agree to 0.3 %, others to 17 %).  Gates: 1.5 x the worst (cosine: 1.5 x its distance to 1).
+F64_LOSS, F64_CONV_MAX, F64_CONV_COS, F64_HEAD_MAX = 1.4e-3, 0.27, 0.978, 0.01
+
+
 @pytest.mark.parametrize("C,dil,B,H,W", [(16, (1, 2, 4), 3, 20, 24), (48, (1, 2, 4, 8, 16, 8, 4, 1), 4, 64, 64)])
-def test_bf16_gradients_match_oracle(C, dil, B, H, W):
-    """The whole network in BF16 (forward, heads + loss, backward) against the oracle's
-    float64 loss and gradient: per parameter group, the normalised max error and the cosine
-    between the gradients; the FP32 SIMT path on the same batch is printed beside it."""
+def test_bf16_gradients_match_oracle_and_emulation(C, dil, B, H, W):
+    """The whole network in BF16 (forward, heads + loss, backward): against the oracle's
+    float64 loss and gradient (itself pinned to finite differences) under the measured gates
+    above, and against a float64 emulation of the same bf16 roundings, which isolates the
+    kernels from the bf16 numerics; the FP32 SIMT path on the same batch is checked too."""
     from paper_2410_02314_gb300.train import DilatedLocNet
 
     spec = synth.NetSpec(in_ch=1, channels=C, dilations=dil)
-    blob = synth.pack_blob(spec, synth.init_weights(spec, 3))
+    wts = synth.init_weights(spec, 3)
+    blob = synth.pack_blob(spec, wts)
+    wts = synth.blob_f32_weights(blob, spec)
     rng = np.random.default_rng(1)
     frames, tgt, _, _ = synth.training_batch(rng, B=B, H=H, W=W, max_emitters=6)
     onet = oracle.Net(spec.to_json(), blob)
     x0 = oracle.ingest(frames, 1.0, 100.0, in_scale=onet.in_scale)
     val, gw, gb, ghw, ghb, _ = oracle.loss_grad(onet, x0, tgt)
-    ref = [gw, gb, ghw, ghb]
-    out = {}
+    ref64 = [gw, gb, ghw, ghb]
+    val_e, ref_e = bf16_emulation(frames, tgt, spec, wts)
+    res = {}
     for prec in ("bf16", "fp32"):
         net = DilatedLocNet.from_blob(spec.to_json(), blob, precision=prec).cuda()
-        loss, g = _loss_and_grads(net, frames, tgt)
-        groups = [np.concatenate(g[: len(dil)]), np.concatenate(g[len(dil) : 2 * len(dil)]), g[-2], g[-1]]
-        rel = [float(np.abs(a - r).max() / max(np.abs(r).max(), 1e-12)) for a, r in zip(groups, ref)]
-        cos = [float(a @ r / max(np.linalg.norm(a) * np.linalg.norm(r), 1e-30)) for a, r in zip(groups, ref)]
-        out[prec] = (abs(loss - val) / abs(val), rel, cos)
-        print(prec, C, len(dil), "loss rel err", out[prec][0], "grad max rel err (w, b, hw, hb)", np.round(rel, 5),
-              "cos", np.round(cos, 6))
+        for p in net.parameters():
+            p.grad = None
+        loss = net.loss(torch.from_numpy(frames).cuda(), torch.from_numpy(tgt).cuda())
+        loss.backward()
+        got = _groups(net, len(dil))
+        res[prec] = (float(loss.item()), got)
+        rel, cos = _cmp(got, ref64)
+        print(prec, C, len(dil), "vs float64: loss", abs(loss.item() - val) / abs(val), "grad max (w, b, hw, hb)",
+              np.round(rel, 5), "cos", np.round(cos, 6))
         if prec == "bf16":
             assert not net.device_error()
-    loss_e, rel, cos = out["bf16"]
-    assert loss_e <= 1e-2
-    assert max(rel) <= 0.1 and min(cos) >= 0.995
-    assert max(out["fp32"][1]) <= 1e-4
+            rel_e, cos_e = _cmp(got, ref_e)
+            print("bf16 vs bf16 emulation: loss", abs(loss.item() - val_e) / abs(val_e), "grad max", np.round(rel_e, 5),
+                  "cos", np.round(cos_e, 7))
+            assert abs(loss.item() - val) <= F64_LOSS * abs(val)
+            assert max(rel[:2]) <= F64_CONV_MAX and min(cos[:2]) >= F64_CONV_COS and max(rel[2:]) <= F64_HEAD_MAX
+            res["emulation"] = (abs(loss.item() - val_e) / abs(val_e), rel_e, cos_e)
+        else:
+            assert abs(loss.item() - val) <= 1e-5 * abs(val) and max(rel) <= 1e-4
+    loss_e, rel_e, cos_e = res["emulation"]
+    assert loss_e <= 1e-4 and max(rel_e) <= 0.05 and min(cos_e) >= 0.999
 
 
 def test_bf16_training_on_device_batches_beats_mle():
