@@ -251,9 +251,11 @@ class ClockSampler:
 
 
 def kernel_source_hash():
+    """sha256[:16] of the conv kernel's sources (k_tc.cu and the inline-PTX helpers it includes)."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2410_02314_gb300", "csrc", "k_tc.cu"), "rb") as f:
-        h.update(f.read())
+    for name in ("k_tc.cu", "tc_ptx.cuh"):
+        with open(os.path.join(ROOT, "paper_2410_02314_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -264,7 +266,7 @@ def profiled_traffic(precision, workload="batched256"):
     if not os.path.exists(p):
         return None
     text = open(p).read()
-    m_hash = re.search(r"k_tc\.cu sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    m_hash = re.search(r"conv kernel sources sha256\[:16\]:\s*([0-9a-f]{16})", text)
     m_bytes = re.search(r"dram bytes per full launch:\s*([0-9.e+]+)", text)
     if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
         return None
@@ -698,6 +700,8 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the large-FOV and small-config measurements")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the FP8/FP32 peak measurement (profiler captures: its GEMMs would join the launch list)")
     args = ap.parse_args()
     T_FRAMES = args.frames
     if args.impl == "reference":
@@ -813,7 +817,7 @@ def main():
     ms = replicas.max_over_ranks(statistics.mean(times), dist, dev)
     value = replicas.whole_job_rate(T_FRAMES, ms / 1000.0, world)
 
-    live_peaks = measure_peaks(dev)  # FP8 and FP32 dense peaks, after the timed region
+    live_peaks = {} if args.no_peaks else measure_peaks(dev)  # FP8 and FP32 dense peaks, after the timed region
     # dominant kernel: the middle-layer tensor-core (or FP32) conv, timed on its stream
     conv_ms, conv_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_CONV)
     heads_ms, heads_n = sml.sml_profile_read(loc.ctx, sml.SML_KERNEL_CONV_HEADS)

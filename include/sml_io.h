@@ -62,7 +62,9 @@ void sml_reader_close(sml_reader* r);
 /* Localize a whole stack file in batches of `batch` frames (see the pipeline above).
  * Records go to `out` (host memory, `capacity` records) in (frame, row, column) order with
  * frame = index in the stack, exactly as sml_localize on all T frames returns them.
- * Requires a one-frame input net (in_ch = 1); three-frame nets get SML_ERR_UNSUPPORTED.
+ * Three-frame nets (in_ch = 3) read the frame before and after each batch from the
+ * neighbouring batches (copied on the device), so their records too equal sml_localize on
+ * all T frames; each batch is then localized once its successor has been read.
  * CAPACITY sets *n_out to the needed count (records beyond capacity are not written).
  * stats may be NULL. */
 int sml_localize_file(sml_ctx* ctx, const char* path, long long offset, int T, int H, int W, const sml_camera* cam,

@@ -501,9 +501,11 @@ int get_plan(sml_ctx* ctx, int H, int W, int T) {
 struct FrameRange {
   int first, last;  // relative to the chunk's first frame
 };
-FrameRange chunk_frames(const sml_ctx* ctx, int T, int t0, int tc) {
+// before / after: the frame just before / after the call's T frames exists too (a stack
+// processed in batches, whose neighbours are real frames of the stack).
+FrameRange chunk_frames(const sml_ctx* ctx, int T, int t0, int tc, bool before = false, bool after = false) {
   if (ctx->in_ch == 1) return {0, tc - 1};
-  return {t0 > 0 ? -1 : 0, t0 + tc < T ? tc : tc - 1};
+  return {(t0 > 0 || before) ? -1 : 0, (t0 + tc < T || after) ? tc : tc - 1};
 }
 
 // One chunk of frames through the network: maps [tc][5][H][W] (+ optional logits).  d_frames
@@ -645,7 +647,7 @@ int make_cam(sml_ctx* ctx, const sml_camera* cam, CamArgs* out) {
 // Whole call on device-resident frames: chunks of whole frames, one running record count.
 int localize_device(sml_ctx* ctx, const uint16_t* d_frames, bool frames_on_host, int T, int H, int W, const CamArgs& cam,
                     float p_min, sml_record* d_out, size_t capacity, unsigned long long* d_n, cudaStream_t s,
-                    sml_sigma* d_sigma = nullptr) {
+                    sml_sigma* d_sigma = nullptr, bool before = false, bool after = false) {
   int r = get_plan(ctx, H, W, T);
   if (r) return r;
   Plan& p = *ctx->plan;
@@ -654,7 +656,7 @@ int localize_device(sml_ctx* ctx, const uint16_t* d_frames, bool frames_on_host,
   for (int t0 = 0; t0 < T; t0 += p.Tc) {
     int tc = std::min(p.Tc, T - t0);
     const uint16_t* f = d_frames + (size_t)t0 * fpx;
-    const FrameRange fr = chunk_frames(ctx, T, t0, tc);
+    const FrameRange fr = chunk_frames(ctx, T, t0, tc, before, after);
     if (frames_on_host) {  // the chunk and its context frames, staged into the plan's buffer
       const size_t n = (size_t)(fr.last - fr.first + 1) * fpx;
       SML_CUDA(cudaMemcpyAsync(p.frames, f + (ptrdiff_t)fr.first * (ptrdiff_t)fpx, n * sizeof(uint16_t),
@@ -1560,7 +1562,8 @@ namespace {
 struct FilePipe {
   sml_reader* reader = nullptr;
   cudaStream_t copy = nullptr;
-  cudaEvent_t h2d[2] = {nullptr, nullptr}, cnt[2] = {nullptr, nullptr}, d2h[2] = {nullptr, nullptr};
+  cudaEvent_t h2d[2] = {nullptr, nullptr}, cnt[2] = {nullptr, nullptr}, d2h[2] = {nullptr, nullptr},
+              comp[2] = {nullptr, nullptr};
   uint8_t* dev = nullptr;                 // frames[2] | records[2] | counts[2]
   unsigned long long* h_cnt = nullptr;    // pinned, 2 counts
   ~FilePipe() {
@@ -1569,6 +1572,7 @@ struct FilePipe {
       if (h2d[k]) cudaEventDestroy(h2d[k]);
       if (cnt[k]) cudaEventDestroy(cnt[k]);
       if (d2h[k]) cudaEventDestroy(d2h[k]);
+      if (comp[k]) cudaEventDestroy(comp[k]);
     }
     if (copy) cudaStreamDestroy(copy);
     if (dev) cudaFree(dev);
@@ -1587,7 +1591,6 @@ extern "C" int sml_localize_file(sml_ctx* ctx, const char* path, long long offse
   int r;
   if (!path || !n_out || (capacity > 0 && !out) || batch < 1 || offset < 0) return fail(ctx, SML_ERR_BAD_ARG, "bad argument");
   if ((r = check_dims(ctx, T, H, W)) || (r = check_thr(ctx, thr))) return r;
-  if (ctx->in_ch != 1) return fail(ctx, SML_ERR_UNSUPPORTED, "stack files need a one-frame input net (in_ch = 1)");
   CamArgs ca;
   if ((r = make_cam(ctx, cam, &ca))) return r;
   *n_out = 0;
@@ -1606,8 +1609,14 @@ extern "C" int sml_localize_file(sml_ctx* ctx, const char* path, long long offse
     SML_CUDA(cudaMemcpyAsync(ctx->plan->cam_maps + hw, ca.offset_map, hw * 4, cudaMemcpyHostToDevice, s), "H2D offset map");
     ca.offset_map = ctx->plan->cam_maps + hw;
   }
+  // Three-frame nets (in_ch = 3) need the frame before and after each batch.  Each frame slot
+  // then holds [previous batch's last frame | the batch | next batch's first frame], the two
+  // context frames copied on the device from the neighbouring slot, and a batch is localized
+  // one batch later, once its successor has arrived.
+  const bool ctx3 = ctx->in_ch == 3;
+  const int ext = ctx3 ? 2 : 0;  // context frames per slot
   FilePipe fp;
-  const size_t frame_bytes = (size_t)batch * hw * sizeof(uint16_t);
+  const size_t frame_bytes = (size_t)(batch + ext) * hw * sizeof(uint16_t);
   // a detection is a strict local maximum: at most one per 2x2 block of a frame
   const size_t rec_cap = (size_t)batch * ((H + 1) / 2) * ((W + 1) / 2);
   const size_t rec_bytes = rec_cap * sizeof(sml_record);
@@ -1623,8 +1632,10 @@ extern "C" int sml_localize_file(sml_ctx* ctx, const char* path, long long offse
     SML_CUDA(cudaEventCreateWithFlags(&fp.h2d[k], cudaEventDisableTiming), "event");
     SML_CUDA(cudaEventCreateWithFlags(&fp.cnt[k], cudaEventDisableTiming), "event");
     SML_CUDA(cudaEventCreateWithFlags(&fp.d2h[k], cudaEventDisableTiming), "event");
+    SML_CUDA(cudaEventCreateWithFlags(&fp.comp[k], cudaEventDisableTiming), "event");
   }
-  if ((r = sml_reader_open(path, offset, T, H, W, batch, 3, &fp.reader)))
+  // one batch more in flight when batches wait for their successor
+  if ((r = sml_reader_open(path, offset, T, H, W, batch, ctx3 ? 4 : 3, &fp.reader)))
     return fail(ctx, r, "cannot read %d frames of %dx%d from %s at offset %lld", T, H, W, path, offset);
 
   struct Done {
@@ -1633,14 +1644,15 @@ extern "C" int sml_localize_file(sml_ctx* ctx, const char* path, long long offse
   };
   std::vector<Done> done;
   size_t total = 0, written = 0;
-  struct Pending {
-    int slot = -1;
-    long long first = 0;
+  struct Batch {
+    int slot = -1, nf = 0;
+    long long k = 0, first = 0;
     const uint16_t* host = nullptr;
-  } pend;
+  };
+  Batch wait_comp, wait_fin;  // read but not yet localized (three-frame nets); localized, records pending
   // records of a finished batch: count (host waits for its compute), then an async D2H on
   // the copy stream, which overlaps the next batch's compute
-  auto finish = [&](const Pending& p) -> int {
+  auto finish = [&](const Batch& p) -> int {
     SML_CUDA(cudaEventSynchronize(fp.cnt[p.slot]), "batch count");
     int rr = sml_reader_release(fp.reader, p.host);  // its H2D finished before its compute
     if (rr) return fail(ctx, rr, "reader release");
@@ -1654,6 +1666,23 @@ extern "C" int sml_localize_file(sml_ctx* ctx, const char* path, long long offse
     total += n;
     return SML_OK;
   };
+  // localize a batch whose frames (and context frames) are on the device; `after`: the
+  // frame after the batch is in its slot
+  auto compute = [&](const Batch& b, bool after) -> int {
+    SML_CUDA(cudaStreamWaitEvent(s, fp.h2d[b.slot], 0), "wait H2D");
+    if (b.k >= 2) SML_CUDA(cudaStreamWaitEvent(s, fp.d2h[b.slot], 0), "wait D2H");
+    const uint16_t* f = d_frames[b.slot] + (ctx3 ? hw : 0);
+    int rr = localize_device(ctx, f, false, b.nf, H, W, ca, thr->p_min, d_rec[b.slot], rec_cap, d_n + b.slot, s, nullptr,
+                             ctx3 && b.first > 0, after);
+    if (rr) return rr;
+    SML_CUDA(cudaMemcpyAsync(fp.h_cnt + b.slot, d_n + b.slot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
+             "D2H count");
+    SML_CUDA(cudaEventRecord(fp.cnt[b.slot], s), "event");
+    SML_CUDA(cudaEventRecord(fp.comp[b.slot], s), "event");
+    if (wait_fin.slot >= 0 && (rr = finish(wait_fin))) return rr;
+    wait_fin = b;
+    return SML_OK;
+  };
   for (long long k = 0;; ++k) {
     const uint16_t* hp = nullptr;
     int nf = 0;
@@ -1662,23 +1691,41 @@ extern "C" int sml_localize_file(sml_ctx* ctx, const char* path, long long offse
       return fail(ctx, r, "reading %s failed or timed out", path);
     if (nf == 0) break;
     const int slot = (int)(k & 1);
+    // the slot's previous batch (k - 2) has been localized before its frames are replaced
+    if (k >= 2) SML_CUDA(cudaStreamWaitEvent(fp.copy, fp.comp[slot], 0), "wait compute");
     // the copy stream is in order: this H2D follows the D2H that last read d_rec[slot]
-    SML_CUDA(cudaMemcpyAsync(d_frames[slot], hp, (size_t)nf * hw * sizeof(uint16_t), cudaMemcpyHostToDevice, fp.copy),
+    SML_CUDA(cudaMemcpyAsync(d_frames[slot] + (ctx3 ? hw : 0), hp, (size_t)nf * hw * sizeof(uint16_t),
+                             cudaMemcpyHostToDevice, fp.copy),
              "H2D frames");
+    if (ctx3 && wait_comp.slot >= 0) {  // context frames between this batch and the previous one
+      uint16_t* prev = d_frames[wait_comp.slot];
+      SML_CUDA(cudaMemcpyAsync(d_frames[slot], prev + (size_t)wait_comp.nf * hw, hw * sizeof(uint16_t),
+                               cudaMemcpyDeviceToDevice, fp.copy),
+               "context frame");
+      SML_CUDA(cudaMemcpyAsync(prev + (size_t)(wait_comp.nf + 1) * hw, d_frames[slot] + hw, hw * sizeof(uint16_t),
+                               cudaMemcpyDeviceToDevice, fp.copy),
+               "context frame");
+    }
     SML_CUDA(cudaEventRecord(fp.h2d[slot], fp.copy), "event");
-    SML_CUDA(cudaStreamWaitEvent(s, fp.h2d[slot], 0), "wait H2D");
-    if (k >= 2) SML_CUDA(cudaStreamWaitEvent(s, fp.d2h[slot], 0), "wait D2H");
-    if ((r = localize_device(ctx, d_frames[slot], false, nf, H, W, ca, thr->p_min, d_rec[slot], rec_cap, d_n + slot, s)))
-      return r;
-    SML_CUDA(cudaMemcpyAsync(fp.h_cnt + slot, d_n + slot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
-             "D2H count");
-    SML_CUDA(cudaEventRecord(fp.cnt[slot], s), "event");
-    if (pend.slot >= 0 && (r = finish(pend))) return r;
-    pend.slot = slot;
-    pend.first = first;
-    pend.host = hp;
+    Batch b;
+    b.slot = slot;
+    b.nf = nf;
+    b.k = k;
+    b.first = first;
+    b.host = hp;
+    if (!ctx3) {
+      if ((r = compute(b, false))) return r;
+      continue;
+    }
+    if (wait_comp.slot >= 0) {
+      // its tail frame came with this batch's copies (later on the copy stream)
+      SML_CUDA(cudaStreamWaitEvent(s, fp.h2d[slot], 0), "wait context");
+      if ((r = compute(wait_comp, true))) return r;
+    }
+    wait_comp = b;
   }
-  if (pend.slot >= 0 && (r = finish(pend))) return r;
+  if (ctx3 && wait_comp.slot >= 0 && (r = compute(wait_comp, false))) return r;
+  if (wait_fin.slot >= 0 && (r = finish(wait_fin))) return r;
   SML_CUDA(cudaStreamSynchronize(fp.copy), "D2H records");
   SML_CUDA(cudaStreamSynchronize(s), "localize");
   if ((r = check_device_error(ctx))) return r;

@@ -9,7 +9,7 @@
 // box of the row-planar activations ([T][H][G][W][16 channels], G = C/16) lands as G planes
 // of [pixel][16 channels] with the 32-byte swizzle, which is the canonical MN-major SW32
 // operand (planes = atoms along M/N, LBO = plane stride; 8 pixels per atom along K, SBO =
-// 256 B).  A = dZ of one 128-pixel row strip (M = 128: the C output channels, the planes
+// 256 B).  A = dZ of one 128-pixel row strip (M = 64: the C output channels, the planes
 // beyond them zero), B = X of the row i + (ky-1)d, its descriptor started (kx-1)d+d pixel
 // lines into a box that begins d pixels left of the strip (the tap shift along K).  Each of
 // the 9 taps accumulates into its own C TMEM columns; one more MMA per K step against a
@@ -38,13 +38,14 @@ struct WgKArgs {
   uint32_t units;         // T * H * NS
   uint32_t x_plane;       // bytes of one plane of an X row box
   uint32_t x_slot;        // bytes of one X row slot (G planes, 1024-aligned)
-  uint32_t stage_bytes;   // dZ slot (8 planes of 4 KB) + 3 X slots
+  uint32_t stage_bytes;   // dZ slot (M/16 planes of 4 KB) + 3 X slots
   float* partial;         // [gridDim.x][C][wg_cols(C)]
   int* err;
 };
 
-constexpr uint32_t kDzPlane = kTileM * 32;  // 128 pixels x 32 bytes
-constexpr uint32_t kDzSlot = 8 * kDzPlane;  // M = 128: 8 planes
+constexpr int kWgM = 64;                        // MMA M: the output channels, padded to 64
+constexpr uint32_t kDzPlane = kTileM * 32;       // 128 pixels x 32 bytes
+constexpr uint32_t kDzSlot = (kWgM / 16) * kDzPlane;  // M / 16 planes of 16 channels
 
 template <int C>
 __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constant__ CUtensorMap tm_dz,
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constan
   // set-up: zero the dZ planes beyond the C channels (M padding), the ones plane, barriers, TMEM
   for (int s = 0; s < kWgStages; ++s) {
     uint4* z = reinterpret_cast<uint4*>(s_stage + (size_t)s * a.stage_bytes + (size_t)G * kDzPlane);
-    for (int k = threadIdx.x; k < (int)((8 - G) * kDzPlane / 16); k += kWgThreads) z[k] = make_uint4(0, 0, 0, 0);
+    for (int k = threadIdx.x; k < (int)((kWgM / 16 - G) * kDzPlane / 16); k += kWgThreads) z[k] = make_uint4(0, 0, 0, 0);
   }
   for (int k = threadIdx.x; k < 1024 / 16; k += kWgThreads)
     reinterpret_cast<uint4*>(s_ones)[k] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
@@ -134,9 +135,9 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constan
     }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------ MMA issuer (single thread)
-    // bf16 x bf16 -> f32, M = 128, A and B MN-major (instruction descriptor bits 15, 16)
-    const uint32_t idesc_c = instr_desc(kBF16, kTileM, C) | (1u << 15) | (1u << 16);
-    const uint32_t idesc_1 = instr_desc(kBF16, kTileM, 16) | (1u << 15) | (1u << 16);
+    // bf16 x bf16 -> f32, M = 64, A and B MN-major (instruction descriptor bits 15, 16)
+    const uint32_t idesc_c = instr_desc(kBF16, kWgM, C) | (1u << 15) | (1u << 16);
+    const uint32_t idesc_1 = instr_desc(kBF16, kWgM, 16) | (1u << 15) | (1u << 16);
     const uint64_t ones = smem_desc(smem_u32(s_ones), 256u, 256u, 6u);
     uint32_t st = 0, ph = 0;
     bool issued = false;
@@ -173,13 +174,16 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constan
   const bool ok = mbar_wait_own(smem_u32(&done_bar[0]), 0, a.err, s_abort);
   fence_after_sync();
   if (ok && !*s_abort) {
-    const int co = warp * 32 + lane;  // TMEM lane = output channel (M row)
-    float* dst = a.partial + ((size_t)blockIdx.x * C + (co < C ? co : 0)) * COLS;
+    // an M = 64 MMA writes D row 16w + t to TMEM lane 32w + t (t < 16): lanes 0-15 of each
+    // warp's quarter hold output channels 16w .. 16w + 15
+    const int co = warp * 16 + lane;
+    const bool mine = lane < 16 && co < C;
+    float* dst = a.partial + ((size_t)blockIdx.x * C + (mine ? co : 0)) * COLS;
     for (int c = 0; c < COLS; c += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
       tmem_ld_wait();
-      if (co < C) {
+      if (mine) {
 #pragma unroll
         for (int k = 0; k < 16; ++k) dst[c + k] = v[k];
       }

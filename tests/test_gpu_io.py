@@ -54,10 +54,20 @@ def test_file_pipeline_scmos_maps_and_capacity(tmp_path):
     assert e.value.code == sml.SML_ERR_CAPACITY and e.value.needed == len(want)
 
 
-def test_file_pipeline_rejects_context_nets(tmp_path):
-    spec = synth.NetSpec(in_ch=3, channels=16, dilations=(1, 2, 1), precision="bf16")
+@pytest.mark.parametrize("prec,batch,T", [("fp32", 4, 9), ("bf16", 3, 10), ("bf16", 1, 4), ("bf16", 64, 7),
+                                          ("bf16", 5, 5)])
+def test_file_pipeline_with_three_frame_nets_equals_one_call(tmp_path, prec, batch, T):
+    """Three-frame input (frames t-1, t, t+1 as channels, Sec. 3.1): each batch takes its
+    context frames from the neighbouring batches (device copies, one batch of delay), so the
+    records equal one sml_localize call on all frames byte for byte, for batch sizes that split
+    the stack unevenly, one frame per batch, and a single batch."""
+    spec = synth.NetSpec(in_ch=3, channels=16 if prec == "fp32" else 32, dilations=(1, 2, 4, 1), precision=prec)
     blob = synth.pack_blob(spec, synth.init_weights(spec, 3))
-    path = _stack(tmp_path, np.zeros((2, 32, 32), np.uint16))
-    with pytest.raises(sml.SmlError) as e:
-        sml.Localizer(spec.to_json(), blob).localize_file(path, 2, 32, 32, 0.5)
-    assert e.value.code == sml.SML_ERR_UNSUPPORTED
+    w = synth.workload_small(T=T, precision=prec)
+    path = _stack(tmp_path, w.frames, header=32)
+    loc = sml.Localizer(spec.to_json(), blob)
+    want = loc.localize(w.frames, 0.3, gain=w.cam.gain, offset=w.cam.offset)
+    got, st = loc.localize_file(path, T, 64, 64, 0.3, batch=batch, gain=w.cam.gain, offset=w.cam.offset, file_offset=32)
+    assert len(want) > 10
+    assert got.tobytes() == want.tobytes()
+    assert st["frames"] == T
