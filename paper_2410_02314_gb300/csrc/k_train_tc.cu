@@ -11,9 +11,10 @@
 // operand (planes = atoms along M/N, LBO = plane stride; 8 pixels per atom along K, SBO =
 // 256 B).  A = dZ of one 128-pixel row strip (M = 64: the C output channels, the planes
 // beyond them zero), B = X of the row i + (ky-1)d, its descriptor started (kx-1)d+d pixel
-// lines into a box that begins d pixels left of the strip (the tap shift along K).  Each of
-// the 9 taps accumulates into its own C TMEM columns; one more MMA per K step against a
-// plane of ones accumulates sum_p dZ (the bias gradient).  The accumulators stay in TMEM
+// lines into a box that begins d pixels left of the strip (the tap shift along K).  The three
+// X rows of a unit sit in consecutive planes, so one MMA of N = 3C covers the three vertical
+// taps of a horizontal tap; each tap accumulates into its own C TMEM columns (kx-major), and
+// one more MMA per K step against a plane of ones accumulates sum_p dZ (the bias gradient).  The accumulators stay in TMEM
 // across all the work units of a CTA (a contiguous range of row strips); each CTA writes its
 // partial sums, and a second kernel adds the partials in CTA order (deterministic).
 #include <cuda_bf16.h>
@@ -37,7 +38,7 @@ struct WgKArgs {
   int NS;                 // 128-pixel strips per row
   uint32_t units;         // T * H * NS
   uint32_t x_plane;       // bytes of one plane of an X row box
-  uint32_t x_slot;        // bytes of one X row slot (G planes, 1024-aligned)
+  uint32_t x_slot;        // bytes of one X row slot (G planes; the 3 slots are contiguous)
   uint32_t stage_bytes;   // dZ slot (M/16 planes of 4 KB) + 3 X slots
   float* partial;         // [gridDim.x][C][wg_cols(C)]
   int* err;
@@ -135,10 +136,19 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constan
     }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------ MMA issuer (single thread)
-    // bf16 x bf16 -> f32, M = 64, A and B MN-major (instruction descriptor bits 15, 16)
-    const uint32_t idesc_c = instr_desc(kBF16, kWgM, C) | (1u << 15) | (1u << 16);
+    // bf16 x bf16 -> f32, M = 64, A and B MN-major (instruction descriptor bits 15, 16).  The
+    // three X row slots of a stage are contiguous planes (x_slot = G planes), so one B operand
+    // of N = 3C spans the rows of all three vertical taps: its 16-channel atoms are (ky, group)
+    // in order, x_plane apart.  Per K step: one MMA per horizontal tap, plus the ones MMA.
+    const uint32_t idesc_c = instr_desc(kBF16, kWgM, 3 * C) | (1u << 15) | (1u << 16);
     const uint32_t idesc_1 = instr_desc(kBF16, kWgM, 16) | (1u << 15) | (1u << 16);
     const uint64_t ones = smem_desc(smem_u32(s_ones), 256u, 256u, 6u);
+    // descriptors of stage 0, K step 0; a K step adds 16 pixel lines (512 B, 32 in the
+    // descriptor's 16-byte address field), a stage adds stage_bytes
+    const uint64_t a0 = smem_desc(smem_u32(s_stage), kDzPlane, 256u, 6u);
+    uint64_t b0[3];
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) b0[kx] = smem_desc(smem_u32(s_stage) + kDzSlot + (uint32_t)(kx * a.d) * 32u, a.x_plane, 256u, 6u);
     uint32_t st = 0, ph = 0;
     bool issued = false;
     for (uint32_t u = u_begin; u < u_end; ++u) {
@@ -147,16 +157,12 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constan
       const int j0 = (int)(u % (uint32_t)a.NS) * kTileM;
       const int valid = a.W - j0 < kTileM ? a.W - j0 : kTileM;
       const int nk = (valid + 15) / 16;  // K steps that hold pixels of the frame
-      const uint32_t base = smem_u32(s_stage + (size_t)st * a.stage_bytes);
+      const uint64_t st16 = (uint64_t)((st * a.stage_bytes) >> 4);
       for (int ks = 0; ks < nk; ++ks) {
-        const uint64_t ad = smem_desc(base + (uint32_t)ks * 512u, kDzPlane, 256u, 6u);
+        const uint64_t off = st16 + (uint64_t)(ks * 32);
+        const uint64_t ad = a0 + off;
 #pragma unroll
-        for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-          for (int kx = 0; kx < 3; ++kx) {
-            const uint32_t b_addr = base + kDzSlot + (uint32_t)ky * a.x_slot + (uint32_t)(kx * a.d + ks * 16) * 32u;
-            umma<kBF16>(tmem + (uint32_t)((ky * 3 + kx) * C), ad, smem_desc(b_addr, a.x_plane, 256u, 6u), idesc_c, 1u);
-          }
+        for (int kx = 0; kx < 3; ++kx) umma<kBF16>(tmem + (uint32_t)(kx * 3 * C), ad, b0[kx] + off, idesc_c, 1u);
         umma<kBF16>(tmem + (uint32_t)(9 * C), ad, ones, idesc_1, 1u);
       }
       umma_commit(smem_u32(&empty_bar[st]));
@@ -209,9 +215,9 @@ __global__ void k_wgrad_reduce(const float* __restrict__ partial, int nblk, floa
   for (int b = 0; b < nblk; ++b) s += partial[((size_t)b * C + co) * COLS + c];
   if (c == 9 * C) {
     db[co] = s;
-  } else {
-    const int tap = c / C, ci = c % C;
-    dw[((size_t)co * C + ci) * 9 + tap] = s;
+  } else {  // column kx * 3C + ky * C + ci
+    const int kx = c / (3 * C), ky = (c % (3 * C)) / C, ci = c % C;
+    dw[((size_t)co * C + ci) * 9 + ky * 3 + kx] = s;
   }
 }
 
@@ -266,7 +272,7 @@ cudaError_t launch_wgrad_tc(const CUtensorMap* tm_dz, const CUtensorMap* tm_x, i
   if (units >= (1LL << 31)) return cudaErrorInvalidValue;
   a.units = (uint32_t)units;
   a.x_plane = (uint32_t)tc_box_width(d) * 32u;
-  a.x_slot = ((uint32_t)(C / 16) * a.x_plane + 1023u) & ~1023u;
+  a.x_slot = (uint32_t)(C / 16) * a.x_plane;  // a multiple of 1024 (x_plane is): the slots are contiguous planes
   a.stage_bytes = kDzSlot + 3u * a.x_slot;
   a.partial = partial;
   a.err = err;

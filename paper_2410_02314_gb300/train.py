@@ -378,6 +378,59 @@ class DilatedLocNet(torch.nn.Module):
         return spec.to_json(), synth.pack_blob(spec, w)
 
 
+class GraphedStep:
+    """One training step (forward, loss, backward, Adam update) captured once in a CUDA graph
+    and replayed: the host then issues one launch per step instead of the ~100 kernel launches
+    and library calls of the step, whose host-side cost otherwise exceeds their device time
+    at the training batch size.  The batch is copied into the graph's static input tensors
+    before each replay; the optimizer runs with capturable state on the device.
+
+        step = GraphedStep(net, frames_shape, lr=1e-3)
+        loss = step(frames, targets)   # a device scalar (no synchronisation)
+    """
+
+    def __init__(self, net: "DilatedLocNet", frames_shape, lr: float = 1e-3, warmup: int = 2, gain=1.0,
+                 offset=100.0):
+        dev = net.hw.device
+        B, H, W = frames_shape
+        self.net = net
+        self.frames = torch.zeros((B, H, W), dtype=torch.int16, device=dev)
+        self.tgt = torch.zeros((B, 5, H, W), dtype=torch.float32, device=dev)
+        self.opt = torch.optim.Adam(net.parameters(), lr=lr, capturable=True)
+        if net.precision == "bf16" and getattr(net, "_err", None) is None:
+            net._err = torch.zeros(1, dtype=torch.int32, device=dev)
+        saved = [p.detach().clone() for p in net.parameters()]
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):  # warm-up outside the graph (allocator, optimizer state)
+            for _ in range(max(1, warmup)):
+                self.opt.zero_grad(set_to_none=True)
+                net.loss(self.frames, self.tgt, gain, offset).backward()
+                self.opt.step()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        # the warm-up steps must not count: parameters and optimizer state back to the start,
+        # in place (the graph captures these tensors' addresses)
+        with torch.no_grad():
+            for p, v in zip(net.parameters(), saved):
+                p.copy_(v)
+            for st in self.opt.state.values():
+                for v in st.values():
+                    if torch.is_tensor(v):
+                        v.zero_()
+        self.graph = torch.cuda.CUDAGraph()
+        self.opt.zero_grad(set_to_none=True)
+        with torch.cuda.graph(self.graph):
+            self.loss = net.loss(self.frames, self.tgt, gain, offset)
+            self.loss.backward()
+            self.opt.step()
+
+    def __call__(self, frames, tgt):
+        self.frames.copy_(frames.view(torch.int16), non_blocking=True)
+        self.tgt.copy_(tgt, non_blocking=True)
+        self.graph.replay()
+        return self.loss
+
+
 def device_batch(rng, B, H, W, max_emitters=10, min_emitters=0, z_scale=1000.0, ph_scale=10000.0, seed=5, frame0=0,
                  device="cuda"):
     """A fresh batch of training patches: emitters drawn on the host, frames rendered on the

@@ -197,3 +197,31 @@ def test_bf16_training_on_device_batches_beats_mle():
     print("high density | bf16-trained net (p_min=%s)" % best[0], best[1], "| local max + MLE (thr=%s)" % base[0], base[1])
     assert best[1]["jaccard"] > base[1]["jaccard"]
     assert rates["bf16"] > rates["fp32"]
+
+
+def test_graphed_training_step_matches_eager():
+    """The BF16 training step captured in a CUDA graph (GraphedStep) replays the eager steps on
+    the same batches: with the same optimizer arithmetic (Adam with its state on the device,
+    as the graph needs it) the losses and parameters after five steps are the same."""
+    from paper_2410_02314_gb300.train import DilatedLocNet, GraphedStep, device_batch
+
+    spec = synth.NetSpec(in_ch=1, channels=32, dilations=(1, 2, 4, 1))
+    rng = np.random.default_rng(3)
+    batches = [device_batch(rng, 16, 48, 48, max_emitters=6, frame0=16 * k) for k in range(5)]
+    eager = DilatedLocNet(spec, synth.init_weights(spec, 5), precision="bf16").cuda()
+    opt = torch.optim.Adam(eager.parameters(), lr=1e-3, capturable=True)
+    losses_e = []
+    for frames, tgt in batches:
+        opt.zero_grad(set_to_none=True)
+        loss = eager.loss(frames, tgt)
+        loss.backward()
+        opt.step()
+        losses_e.append(float(loss.item()))
+    graphed = DilatedLocNet(spec, synth.init_weights(spec, 5), precision="bf16").cuda()
+    step = GraphedStep(graphed, (16, 48, 48), lr=1e-3)
+    losses_g = [float(step(frames, tgt).item()) for frames, tgt in batches]
+    print("eager", losses_e, "graphed", losses_g)
+    assert np.allclose(losses_g, losses_e, rtol=1e-6, atol=0)
+    for a, b in zip(eager.parameters(), graphed.parameters()):
+        assert torch.allclose(a, b, rtol=1e-6, atol=1e-9)
+    assert not graphed.device_error()
