@@ -27,6 +27,9 @@ using namespace sml;
 
 namespace {
 
+// The training kernels read and write activations 16 bytes at a time.
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 // ------------------------------------------------------------------ tiny JSON reader
 struct JVal {
   enum Kind { kNull, kNum, kStr, kArr, kObj, kBool } kind = kNull;
@@ -1377,6 +1380,7 @@ int sml_train_heads_loss(const float* a, const float* tgt, int B, int H, int W, 
                          float* dhb, void* work, size_t work_bytes, void* stream) {
   if (B < 1 || H < 1 || W < 1 || !a || !tgt || !hw || !hb || !h || !loss || !work) return SML_ERR_BAD_ARG;
   if (da && (!grad_scale || !dhw || !dhb)) return SML_ERR_BAD_ARG;
+  if (!aligned16(a) || (da && !aligned16(da))) return SML_ERR_BAD_ARG;
   if (work_bytes < train_heads_work_bytes(B, H, W, C)) return SML_ERR_BAD_ARG;
   return train_status(train_heads_loss(a, tgt, B, H, W, C, hw, hb, h, loss, da ? grad_scale : nullptr, da, dhw, dhb,
                                        work, static_cast<cudaStream_t>(stream)));
@@ -1500,6 +1504,7 @@ int sml_train_bf16_heads_loss(const void* a, const float* tgt, int B, int H, int
   if (B < 1 || H < 1 || W < 1 || !a || !tgt || !hw || !hb || !h || !loss || !work) return SML_ERR_BAD_ARG;
   if (C != 16 && C != 32 && C != 48 && C != 64) return SML_ERR_BAD_ARG;
   if (dz && (!grad_scale || !dhw || !dhb)) return SML_ERR_BAD_ARG;
+  if (!aligned16(a) || (dz && !aligned16(dz))) return SML_ERR_BAD_ARG;
   if (work_bytes < train_heads_work_bytes(B, H, W, C)) return SML_ERR_BAD_ARG;
   return train_status(train_heads_loss_rp(a, tgt, B, H, W, C, hw, hb, h, loss, dz ? grad_scale : nullptr, dz, dhw, dhb,
                                           work, static_cast<cudaStream_t>(stream)));
@@ -1507,7 +1512,7 @@ int sml_train_bf16_heads_loss(const void* a, const float* tgt, int B, int H, int
 
 int sml_train_bf16_l0_wgrad(const float* x0, const void* dz0, int B, int H, int W, int C, int d, float* dw, float* db,
                             void* work, size_t work_bytes, void* stream) {
-  if (!x0 || !dz0 || !dw || !db || !work || !train_bf16_dims_ok(B, H, W, C, d)) return SML_ERR_BAD_ARG;
+  if (!x0 || !dz0 || !dw || !db || !work || !train_bf16_dims_ok(B, H, W, C, d) || !aligned16(dz0)) return SML_ERR_BAD_ARG;
   if (work_bytes < train_conv_work_bytes(B, H, W, 1, C)) return SML_ERR_BAD_ARG;
   return train_status(train_l0_wgrad_rp(x0, dz0, B, H, W, C, d, dw, db, work, static_cast<cudaStream_t>(stream)));
 }

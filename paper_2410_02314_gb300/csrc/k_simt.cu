@@ -68,16 +68,12 @@ constexpr size_t l1_smem_bytes(int d) {
 // time.  FMA order: bias, then input channel, then taps (ky, kx) row-major.  Outputs are
 // staged in shared memory (rows padded by 16 bytes against bank conflicts) so that the stores
 // to HBM are whole 16-byte chunks, consecutive across threads.
-// DEVW (training): the weights and bias come from device memory (wdev [C][IN_CH][9], bdev [C])
-// instead of the by-value parameter, so that an optimizer step on the device needs no copy
-// to the host before the next forward.
-template <int C, int OUT, int IN_CH, bool DEVW = false>
+// (The BF16 one-frame case runs k_l1_rp_bf16 below, which stores from registers.)
+template <int C, int OUT, int IN_CH>
 __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restrict__ frames, int H, int W, int d,
                                                        int t0, int t_first, int t_last, CamArgs cam,
                                                        const __grid_constant__ L1Params prm, float out_scale,
-                                                       void* __restrict__ out, int out_ct,
-                                                       const float* __restrict__ wdev = nullptr,
-                                                       const float* __restrict__ bdev = nullptr) {
+                                                       void* __restrict__ out, int out_ct) {
   constexpr int CPT = C / kL1ChGroups;
   constexpr int CP = CPT / 2;                             // channel pairs per thread
   constexpr int OB = OUT == 0 ? 4 : (OUT == 1 ? 2 : 1);  // output bytes per channel
@@ -127,12 +123,12 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
   float2 bias[CP];
 #pragma unroll
   for (int q = 0; q < CP; ++q) {
-    const float* b = DEVW ? bdev : prm.b;
+    const float* b = prm.b;
     bias[q] = make_float2(b[cg * CPT + 2 * q], b[cg * CPT + 2 * q + 1]);
   }
   // weights of channel pair q, input channel ci, tap k
   auto wpair = [&](int q, int ci, int k) {
-    const float* w = DEVW ? wdev : prm.w;
+    const float* w = prm.w;
     return make_float2(w[((cg * CPT + 2 * q) * IN_CH + ci) * 9 + k], w[((cg * CPT + 2 * q + 1) * IN_CH + ci) * 9 + k]);
   };
   float2 w[IN_CH == 1 ? CP : 1][9];
@@ -252,6 +248,96 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
   }
 }
 
+// The BF16 first layer of a one-frame net, stored straight from registers.  A block has
+// G = C/16 warps and covers a 128-pixel strip of l1_rows(d) output rows of one frame; warp g
+// writes channel group g: lane pair (2u, 2u+1) takes pixels u + 16p (p < 8), the even lane
+// channels 0..7 of the group and the odd lane 8..15, so each thread ends a pixel with one
+// 16-byte store and one warp store covers 16 whole 32-byte pixel rows.  Staging (camera
+// transform of the block's distinct dilated input rows), FMA order (bias, then taps (ky, kx)
+// row-major, each lane of the packed FMA one fmaf), ReLU and rounding are those of
+// k_ingest_l1, so both give the same bits.  DEVW: weights and bias from device memory.
+template <int C, bool DEVW>
+__global__ void __launch_bounds__(C * 2) k_l1_rp_bf16(const uint16_t* __restrict__ frames, int H, int W, int d, int t0,
+                                                      CamArgs cam, const __grid_constant__ L1Params prm,
+                                                      void* __restrict__ out, int out_ct,
+                                                      const float* __restrict__ wdev, const float* __restrict__ bdev) {
+  constexpr int NT = C * 2;  // threads: 32 per 16-channel group
+  extern __shared__ __align__(16) uint8_t l1_smem[];
+  const int span = kL1Tile + 2 * d, nsr = l1_stage_rows(d), R = l1_rows(d);
+  float2* xs = reinterpret_cast<float2*>(l1_smem);  // [nsr][span]
+  const int j0 = blockIdx.x * kL1Tile, t = t0 + blockIdx.z, i0 = blockIdx.y * R;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int half = lane & 1, u = lane >> 1;
+  const uint16_t* f = frames + (ptrdiff_t)t * H * W;
+  // staging: kL1Batch elements per thread with their loads in flight together
+  const int nst = nsr * span;
+  for (int e0 = threadIdx.x; e0 < nst; e0 += kL1Batch * NT) {
+    float adu[kL1Batch], gn[kL1Batch], of[kL1Batch];
+    bool in[kL1Batch];
+#pragma unroll
+    for (int k = 0; k < kL1Batch; ++k) {
+      const int e = e0 + k * NT, sr = e / span, c = e - sr * span;
+      const int ii = l1_stage_image_row(sr, i0, d), jj = j0 - d + c;
+      in[k] = e < nst && ii >= 0 && ii < H && jj >= 0 && jj < W;
+      const size_t px = in[k] ? (size_t)ii * W + jj : 0;
+      adu[k] = in[k] ? (float)f[px] : 0.0f;
+      gn[k] = cam.gain_map && in[k] ? cam.gain_map[px] : cam.gain;
+      of[k] = cam.offset_map && in[k] ? cam.offset_map[px] : cam.offset;
+    }
+#pragma unroll
+    for (int k = 0; k < kL1Batch; ++k) {
+      const int e = e0 + k * NT;
+      if (e < nst) {
+        // zero outside the frame (the first layer's "same" zero padding)
+        const float v = in[k] ? cam_transform(adu[k], of[k], gn[k], cam.in_scale) : 0.0f;
+        xs[e] = make_float2(v, v);
+      }
+    }
+  }
+  const int c0 = g * 16 + half * 8;  // first channel of this thread
+  const float* wsrc = DEVW ? wdev : prm.w;
+  const float* bsrc = DEVW ? bdev : prm.b;
+  float2 w[4][9], bias[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    bias[q] = make_float2(bsrc[c0 + 2 * q], bsrc[c0 + 2 * q + 1]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) w[q][k] = make_float2(wsrc[(c0 + 2 * q) * 9 + k], wsrc[(c0 + 2 * q + 1) * 9 + k]);
+  }
+  __syncthreads();
+  const int npx = W - j0 < kL1Tile ? W - j0 : kL1Tile;  // valid pixels of the strip
+  const int gt = out_ct / 16;                            // groups per pixel row of the buffer
+  for (int r = 0; r < R; ++r) {
+    const int i = i0 + r;
+    if (i >= H) break;
+    const float2* xr[3];
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) xr[ky] = xs + (size_t)l1_srow(r, ky, d) * span;
+    uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(out) +
+                                          ((((size_t)t * H + i) * gt + g) * W + j0) * 32 + half * 16);
+#pragma unroll
+    for (int p = 0; p < kL1Px; ++p) {
+      const int px = u + 16 * p;
+      float2 x[9];
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xr[ky][px + kx * d];
+      uint4 o;
+      uint32_t* ow = reinterpret_cast<uint32_t*>(&o);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float2 a = bias[q];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a = __ffma2_rn(w[q][k], x[k], a);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(fmaxf(a.x, 0.0f), fmaxf(a.y, 0.0f));
+        ow[q] = *reinterpret_cast<uint32_t*>(&h2);
+      }
+      if (px < npx) dst[(size_t)px * 2] = o;
+    }
+  }
+}
+
 // Heads of one pixel from its CO final activations (one fully unrolled loop per head count).
 template <int CO, int NH>
 __device__ __forceinline__ void f32_heads_out(const float (&acc)[CO], const float* __restrict__ hw,
@@ -357,43 +443,51 @@ inline unsigned grid_for(long long npx) { return (unsigned)((npx + kSimtThreads 
 
 }  // namespace
 
+// The register-store BF16 first layer (k_l1_rp_bf16): its staged rows take at most 26 KB.
+template <int C, bool DEVW>
+static cudaError_t launch_l1_rp_bf16(const uint16_t* frames, int T, int H, int W, int d, const CamArgs& cam,
+                                     const L1Params& prm, void* out, int out_ct, const float* wdev, const float* bdev,
+                                     cudaStream_t s) {
+  const size_t smem = (size_t)l1_stage_rows(d) * (kL1Tile + 2 * d) * 8;
+  for (int t0 = 0; t0 < T; t0 += 65535) {
+    dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + l1_rows(d) - 1) / l1_rows(d), (unsigned)(T - t0 < 65535 ? T - t0 : 65535));
+    k_l1_rp_bf16<C, DEVW><<<grid, C * 2, smem, s>>>(frames, H, W, d, t0, cam, prm, out, out_ct, wdev, bdev);
+  }
+  return cudaGetLastError();
+}
+
 template <int C, int OUT, int IN_CH>
 static cudaError_t launch_l1(const uint16_t* frames, int T, int H, int W, int d, int t_first, int t_last,
                              const CamArgs& cam, const L1Params& prm, float out_scale, void* out, int out_ct,
                              cudaStream_t s) {
-  const size_t smem = l1_smem_bytes<C, OUT, IN_CH>(d);
-  // opt in to more than 48 KB on the current device, to the largest size any dilation takes
-  // (the same value on every launch: no host state, and no race between threads or devices)
-  cudaError_t e = cudaFuncSetAttribute(
-      k_ingest_l1<C, OUT, IN_CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)std::max(l1_smem_bytes<C, OUT, IN_CH>(4), l1_smem_bytes<C, OUT, IN_CH>(kL1MaxD)));
-  if (e != cudaSuccess) return e;
-  for (int t0 = 0; t0 < T; t0 += 65535) {
-    dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + l1_rows(d) - 1) / l1_rows(d), (unsigned)(T - t0 < 65535 ? T - t0 : 65535)),
-        block(kL1Tile);
-    k_ingest_l1<C, OUT, IN_CH><<<grid, block, smem, s>>>(frames, H, W, d, t0, t_first, t_last, cam, prm, out_scale, out,
-                                                         out_ct);
+  if constexpr (OUT == 1 && IN_CH == 1) {
+    return launch_l1_rp_bf16<C, false>(frames, T, H, W, d, cam, prm, out, out_ct, nullptr, nullptr, s);
+  } else {
+    const size_t smem = l1_smem_bytes<C, OUT, IN_CH>(d);
+    // opt in to more than 48 KB on the current device, to the largest size any dilation takes
+    // (the same value on every launch: no host state, and no race between threads or devices)
+    cudaError_t e = cudaFuncSetAttribute(
+        k_ingest_l1<C, OUT, IN_CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)std::max(l1_smem_bytes<C, OUT, IN_CH>(4), l1_smem_bytes<C, OUT, IN_CH>(kL1MaxD)));
+    if (e != cudaSuccess) return e;
+    for (int t0 = 0; t0 < T; t0 += 65535) {
+      dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + l1_rows(d) - 1) / l1_rows(d),
+                (unsigned)(T - t0 < 65535 ? T - t0 : 65535)),
+          block(kL1Tile);
+      k_ingest_l1<C, OUT, IN_CH><<<grid, block, smem, s>>>(frames, H, W, d, t0, t_first, t_last, cam, prm, out_scale,
+                                                           out, out_ct);
+    }
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
 }
 
 // BF16 training's first layer: weights from device memory, bf16 row-planar output.
 template <int C>
 static cudaError_t launch_l1_devw(const uint16_t* frames, int T, int H, int W, int d, const CamArgs& cam,
                                   const float* wdev, const float* bdev, void* out, cudaStream_t s) {
-  const size_t smem = l1_smem_bytes<C, 1, 1>(d);
-  cudaError_t e = cudaFuncSetAttribute(k_ingest_l1<C, 1, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)std::max(l1_smem_bytes<C, 1, 1>(4), l1_smem_bytes<C, 1, 1>(kL1MaxD)));
-  if (e != cudaSuccess) return e;
   L1Params prm;
   memset(&prm, 0, sizeof(prm));
-  for (int t0 = 0; t0 < T; t0 += 65535) {
-    dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + l1_rows(d) - 1) / l1_rows(d), (unsigned)(T - t0 < 65535 ? T - t0 : 65535)),
-        block(kL1Tile);
-    k_ingest_l1<C, 1, 1, true><<<grid, block, smem, s>>>(frames, H, W, d, t0, 0, T - 1, cam, prm, 1.0f, out, C, wdev,
-                                                         bdev);
-  }
-  return cudaGetLastError();
+  return launch_l1_rp_bf16<C, true>(frames, T, H, W, d, cam, prm, out, C, wdev, bdev, s);
 }
 
 template <int C>

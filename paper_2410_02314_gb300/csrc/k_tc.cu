@@ -449,6 +449,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
 #pragma unroll 1
       for (int k = 0; k < n_out; ++k) {
+        // DGRAD: the ReLU mask of this output row is issued before the accumulator wait, so its
+        // DRAM latency overlaps the row's MMAs instead of stalling the conversion below
+        uint4 mk[DGRAD ? Cfg::GO : 1][2];
+        if (PREC == kBF16 && DGRAD) {
+          const int i = phi + (q * SEG + k) * a.d;
+          const int j = j0 + m;
+          if (j < a.W) {
+#pragma unroll
+            for (int gq = 0; gq < Cfg::GO; ++gq) {
+              const uint4* mp = reinterpret_cast<const uint4*>(
+                  a.mask + ((((size_t)t * a.H + i) * out_gt + out_g0 + gq) * a.W + j) * 32);
+              mk[gq][0] = __ldcs(mp);
+              mk[gq][1] = __ldcs(mp + 1);
+            }
+          }
+        }
         if (!mbar_wait(smem_u32(&accf_bar[k]), (fpar >> k) & 1u, a.err, s_abort, a.wait_ns)) {
           ok = false;
           break;
@@ -489,9 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
 #pragma unroll
           for (int gq = 0; gq < Cfg::GO; ++gq) {
             const size_t off = ((((size_t)t * a.H + i) * out_gt + out_g0 + gq) * a.W + j) * 32;
-            const uint4* mp = reinterpret_cast<const uint4*>(a.mask + off);
-            uint4 mk[2] = {__ldcs(mp), __ldcs(mp + 1)};
-            const uint32_t* mw = reinterpret_cast<const uint32_t*>(mk);
+            const uint32_t* mw = reinterpret_cast<const uint32_t*>(mk[gq]);
             uint4 o[2];
             uint32_t* ow = reinterpret_cast<uint32_t*>(o);
 #pragma unroll

@@ -82,6 +82,56 @@ def test_bf16_conv_kernels_match_float64(C, d, B, H, W):
     assert int(err.item()) == 0
 
 
+@pytest.mark.parametrize("C,d,B,H,W", [(48, 1, 3, 21, 37), (48, 8, 2, 64, 150), (32, 3, 5, 13, 70), (16, 2, 1, 9, 17)])
+def test_bf16_first_layer_grad_and_heads_match_float64(C, d, B, H, W):
+    """The first layer's weight and bias gradient (FP32 input, bf16 pre-activation gradient)
+    and the fused heads + loss + head gradients on bf16 activations, against float64 PyTorch
+    of the same values.  Pixel counts and row counts are ragged (no multiple of a block's
+    pixel or row step), so the kernels' partial tails are exercised."""
+    from paper_2410_02314_gb300 import train as T
+
+    g = torch.Generator().manual_seed(7 * C + d)
+    # first layer: dw[c][tap] = sum_p dz0[p][c] x0[p + off(tap)], db[c] = sum_p dz0[p][c]
+    x0 = torch.randn(B, H, W, generator=g, dtype=torch.float64).float()
+    dz0 = torch.randn(B, C, H, W, generator=g, dtype=torch.float64) * (torch.rand(B, C, H, W, generator=g) > 0.5)
+    dz0q = bf16(dz0)
+    dw, db = T.sml_train_bf16_l0_wgrad(x0.cuda(), to_rp(dz0), d)
+    wr = torch.zeros(C, 1, 3, 3, dtype=torch.float64, requires_grad=True)
+    br = torch.zeros(C, dtype=torch.float64, requires_grad=True)
+    (F.conv2d(x0.double().unsqueeze(1), wr, br, padding=d, dilation=d) * dz0q).sum().backward()
+    e_w = (dw.double().cpu() - wr.grad).abs().max().item() / wr.grad.abs().max().item()
+    e_b = (db.double().cpu() - br.grad).abs().max().item() / br.grad.abs().max().item()
+    print(C, d, "first-layer wgrad rel err", e_w, "bias", e_b)
+    assert e_w <= 1e-5 and e_b <= 1e-5
+    # heads + loss: BCE on the logit head (mean over pixels) + L2 on the other four heads over
+    # target pixels (divided by their count), gradients of 0.75 x loss
+    a = torch.relu(torch.randn(B, C, H, W, generator=g, dtype=torch.float64))
+    hw = ((torch.rand(5, C, generator=g, dtype=torch.float64) - 0.5) * 0.5).float()
+    hb = ((torch.rand(5, generator=g, dtype=torch.float64) - 0.5) * 0.5).float()
+    tgt = torch.randn(B, 5, H, W, generator=g, dtype=torch.float64).float()
+    tgt[:, 0] = (torch.rand(B, H, W, generator=g) < 0.1).float()
+    gs = torch.tensor([0.75], device="cuda")
+    h, loss, dz, dhw, dhb = T.sml_train_bf16_heads_loss(to_rp(a), tgt.cuda(), hw.cuda(), hb.cuda(), grad_scale=gs)
+    aq = bf16(a).requires_grad_(True)
+    hwr = hw.double().requires_grad_(True)
+    hbr = hb.double().requires_grad_(True)
+    hh = torch.einsum("kc,bchw->bkhw", hwr, aq) + hbr[None, :, None, None]
+    t64 = tgt.double()
+    m = t64[:, 0] > 0.5
+    lref = F.binary_cross_entropy_with_logits(hh[:, 0], t64[:, 0], reduction="sum") / (B * H * W) + \
+        ((hh[:, 1:] - t64[:, 1:]) ** 2 * m[:, None]).sum() / max(1, int(m.sum()))
+    (0.75 * lref).backward()
+    e_h = (h.double().cpu() - hh.detach()).abs().max().item() / hh.detach().abs().max().item()
+    e_l = abs(loss.item() - lref.item()) / abs(lref.item())
+    ref_dz = aq.grad * (aq.detach() > 0)
+    e_dz = (from_rp(dz) - ref_dz).abs().max().item() / ref_dz.abs().max().item()
+    e_hw = (dhw.double().cpu() - hwr.grad).abs().max().item() / hwr.grad.abs().max().item()
+    e_hb = (dhb.double().cpu() - hbr.grad).abs().max().item() / hbr.grad.abs().max().item()
+    print(C, "heads rel err: h", e_h, "loss", e_l, "dz", e_dz, "dhw", e_hw, "dhb", e_hb)
+    assert e_h <= 1e-5 and e_l <= 1e-5 and e_hw <= 1e-5 and e_hb <= 1e-5
+    assert e_dz <= 2 ** -8  # one bf16 rounding of the FP32 gradient
+
+
 def _loss_and_grads(net, frames, tgt):
     for p in net.parameters():
         p.grad = None
