@@ -1401,8 +1401,9 @@ int current_num_sms() {
 }
 
 // TMA map over row-planar bf16 activations [B][H][C/16][W][16] with one box per image row:
-// `box_px` pixels (128 + 2d rounded up to 32 for the conv's input rows, or 128 for the
-// weight gradient's dz rows) by all C/16 groups; 32-byte swizzle; zero fill out of bounds.
+// `box_px` pixels (128 + 2d rounded up to 32 for the conv's input rows; the weight
+// gradient's strip and halo widths from wgrad_tc_boxes) by all C/16 groups; 32-byte swizzle;
+// zero fill out of bounds.
 bool encode_rp_map(CUtensorMap* m, const void* base, int B, int H, int W, int C, int box_px) {
   PFN_encodeTiled_t enc = get_encoder();
   if (!enc) return false;
@@ -1491,8 +1492,10 @@ int sml_train_bf16_conv_wgrad(const void* x, const void* dz, int B, int H, int W
   if (sms <= 0) return SML_ERR_CUDA;
   if (work_bytes < train_wgrad_tc_work_bytes(C, sms)) return SML_ERR_BAD_ARG;
   CUtensorMap tm_dz, tm_x;
-  if (!encode_rp_map(&tm_dz, dz, B > 0 ? B : 1, H, W, C, kTileM) ||
-      !encode_rp_map(&tm_x, x, B > 0 ? B : 1, H, W, C, tc_box_width(d)))
+  int dz_px = 0, x_px = 0;
+  wgrad_tc_boxes(W, d, &dz_px, &x_px);
+  if (!encode_rp_map(&tm_dz, dz, B > 0 ? B : 1, H, W, C, dz_px) ||
+      !encode_rp_map(&tm_x, x, B > 0 ? B : 1, H, W, C, x_px))
     return SML_ERR_CUDA;
   return train_status(launch_wgrad_tc(&tm_dz, &tm_x, B, H, W, C, d, static_cast<float*>(work), sms, dw, db, d_err,
                                       static_cast<cudaStream_t>(stream)));

@@ -5,8 +5,8 @@
 // kernels re-lay them out while staging them in shared memory.
 //
 // Reductions over pixels (weight, bias and head gradients, the loss) go through per-block
-// partial sums and a second kernel that adds them in block order, so every result is
-// deterministic.
+// partial sums and a second kernel that adds them in an order fixed by the sizes alone, so
+// every result is deterministic.
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -134,15 +134,29 @@ __global__ void __launch_bounds__(WgCfg<CI, CO>::THREADS) k_wgrad_partial(const 
   if (r == 0) dst[CO * Cfg::K + co] = accb;
 }
 
-// Sum partials over blocks in block order; write dw in [Cout][Cin][3][3] and db.
+// Sum partials over blocks; write dw in [Cout][Cin][3][3] and db.  A block takes 32 outputs;
+// warp s adds blocks s, s + 8, ... in order and the eight slice sums are added in slice order
+// (a fixed order for given sizes).
+constexpr int kRedSlices = 8;
+
 template <int CI, int CO>
-__global__ void k_wgrad_reduce(const float* __restrict__ partial, int nblocks, float* __restrict__ dw,
-                               float* __restrict__ db) {
+__global__ void __launch_bounds__(32 * kRedSlices) k_wgrad_reduce(const float* __restrict__ partial, int nblocks,
+                                                                   float* __restrict__ dw, float* __restrict__ db) {
   using Cfg = WgCfg<CI, CO>;
-  int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= Cfg::NOUT) return;
+  __shared__ float s_sum[kRedSlices][32];
+  const int ol = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int o = blockIdx.x * 32 + ol;
+  float acc = 0.0f;
+  if (o < Cfg::NOUT) {
+#pragma unroll 4
+    for (int b = sl; b < nblocks; b += kRedSlices) acc += partial[(size_t)b * Cfg::NOUT + o];
+  }
+  s_sum[sl][ol] = acc;
+  __syncthreads();
+  if (sl != 0 || o >= Cfg::NOUT) return;
   float s = 0.0f;
-  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * Cfg::NOUT + o];
+#pragma unroll
+  for (int k = 0; k < kRedSlices; ++k) s += s_sum[k][ol];
   if (o < CO * Cfg::K) {
     int co = o / Cfg::K, k = o - co * Cfg::K, tap = k / CI, ci = k - tap * CI;
     dw[((size_t)co * CI + ci) * 9 + tap] = s;
@@ -358,6 +372,7 @@ __global__ void __launch_bounds__(kHLThreads, 3) k_heads_loss(const void* __rest
         }
       }
     }
+    if (!da) continue;  // the loss alone: no head weight gradient (a kernel-uniform branch)
     // stage the warp's pixels, then each lane adds its (k, c) pairs over them
 #pragma unroll
     for (int c = 0; c < C; ++c) xw[lane * XS + c] = av[c];
@@ -570,7 +585,7 @@ cudaError_t conv_bwd_impl(const float* x, const float* y, const float* dy, int B
   ppb = (ppb + kWgPx - 1) / kWgPx * kWgPx;
   int nb = (int)((npx + ppb - 1) / ppb);
   k_wgrad_partial<CI, CO><<<nb, Cfg::THREADS, 0, s>>>(x, dy, y, B, H, W, d, ppb, work);
-  k_wgrad_reduce<CI, CO><<<(Cfg::NOUT + 255) / 256, 256, 0, s>>>(work, nb, dw, db);
+  k_wgrad_reduce<CI, CO><<<(Cfg::NOUT + 31) / 32, 32 * kRedSlices, 0, s>>>(work, nb, dw, db);
   return cudaGetLastError();
 }
 
@@ -683,7 +698,7 @@ cudaError_t train_l0_wgrad_rp(const float* x0, const void* dz0, int B, int H, in
     const int nb = (int)(nblk < kWgBlocks ? nblk : kWgBlocks);                                  \
     k_l0_wgrad_rp<CO><<<nb, CO / 16 * 32 * kL0Slots, 0, s>>>(x0, static_cast<const __nv_bfloat16*>(dz0), B, H, W, d, \
                                                              wk);                               \
-    k_wgrad_reduce<1, CO><<<(WgCfg<1, CO>::NOUT + 255) / 256, 256, 0, s>>>(wk, nb, dw, db);     \
+    k_wgrad_reduce<1, CO><<<(WgCfg<1, CO>::NOUT + 31) / 32, 32 * kRedSlices, 0, s>>>(wk, nb, dw, db); \
     return cudaGetLastError();                                                                  \
   }
   SML_CH_SWITCH(C, W0)

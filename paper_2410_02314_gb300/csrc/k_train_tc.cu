@@ -27,7 +27,7 @@ namespace sml {
 namespace {
 
 constexpr int kWgThreads = 128;
-constexpr int kWgStages = 2;
+constexpr int kWgMaxStages = 8;
 
 // Columns of one CTA's partial sums for a layer of C channels: 9 taps x C, then 16 columns
 // holding the bias gradient (the same value 16 times).
@@ -35,18 +35,19 @@ __host__ __device__ constexpr int wg_cols(int C) { return 9 * C + 16; }
 
 struct WgKArgs {
   int T, H, W, d;
-  int NS;                 // 128-pixel strips per row
+  int S;                  // pixels per strip (the dZ box): 128, or the frame width rounded up to 32
+  int NS;                 // strips per row
   uint32_t units;         // T * H * NS
-  uint32_t x_plane;       // bytes of one plane of an X row box
+  uint32_t dz_plane;      // bytes of one plane of a dZ box (S x 32)
+  uint32_t x_plane;       // bytes of one plane of an X row box ((S + 2d rounded up to 32) x 32)
   uint32_t x_slot;        // bytes of one X row slot (G planes; the 3 slots are contiguous)
-  uint32_t stage_bytes;   // dZ slot (M/16 planes of 4 KB) + 3 X slots
+  uint32_t stage_bytes;   // dZ slot (M/16 planes) + 3 X slots
+  int nstages;            // ring stages (<= kWgMaxStages)
   float* partial;         // [gridDim.x][C][wg_cols(C)]
   int* err;
 };
 
-constexpr int kWgM = 64;                        // MMA M: the output channels, padded to 64
-constexpr uint32_t kDzPlane = kTileM * 32;       // 128 pixels x 32 bytes
-constexpr uint32_t kDzSlot = (kWgM / 16) * kDzPlane;  // M / 16 planes of 16 channels
+constexpr int kWgM = 64;  // MMA M: the output channels, padded to 64
 
 template <int C>
 __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constant__ CUtensorMap tm_dz,
@@ -56,10 +57,10 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constan
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* s_stage = smem;
-  uint8_t* s_ones = s_stage + (size_t)kWgStages * a.stage_bytes;  // 1024 B of bf16 1.0
+  uint8_t* s_ones = s_stage + (size_t)a.nstages * a.stage_bytes;  // 1024 B of bf16 1.0
   uint64_t* full_bar = reinterpret_cast<uint64_t*>(s_ones + 1024);
-  uint64_t* empty_bar = full_bar + kWgStages;
-  uint64_t* done_bar = empty_bar + kWgStages;
+  uint64_t* empty_bar = full_bar + kWgMaxStages;
+  uint64_t* done_bar = empty_bar + kWgMaxStages;
   volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(done_bar + 1);
   volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -67,14 +68,14 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constan
   const uint32_t u_end = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * a.units) / gridDim.x);
 
   // set-up: zero the dZ planes beyond the C channels (M padding), the ones plane, barriers, TMEM
-  for (int s = 0; s < kWgStages; ++s) {
-    uint4* z = reinterpret_cast<uint4*>(s_stage + (size_t)s * a.stage_bytes + (size_t)G * kDzPlane);
-    for (int k = threadIdx.x; k < (int)((kWgM / 16 - G) * kDzPlane / 16); k += kWgThreads) z[k] = make_uint4(0, 0, 0, 0);
+  for (int s = 0; s < a.nstages; ++s) {
+    uint4* z = reinterpret_cast<uint4*>(s_stage + (size_t)s * a.stage_bytes + (size_t)G * a.dz_plane);
+    for (int k = threadIdx.x; k < (int)((kWgM / 16 - G) * a.dz_plane / 16); k += kWgThreads) z[k] = make_uint4(0, 0, 0, 0);
   }
   for (int k = threadIdx.x; k < 1024 / 16; k += kWgThreads)
     reinterpret_cast<uint4*>(s_ones)[k] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kWgStages; ++s) {
+    for (int s = 0; s < a.nstages; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
@@ -105,32 +106,34 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constan
   __syncthreads();
   fence_after_sync();
 
-  const uint32_t tx = (uint32_t)G * kDzPlane + 3u * (uint32_t)G * a.x_plane;
+  const uint32_t tx = (uint32_t)G * a.dz_plane + 3u * (uint32_t)G * a.x_plane;
+  const uint32_t dz_slot = (uint32_t)(kWgM / 16) * a.dz_plane;
+  const uint32_t nst = (uint32_t)a.nstages;
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------ TMA producer
     uint32_t st = 0, ph = 0, issued = 0;
     for (uint32_t u = u_begin; u < u_end; ++u) {
       const uint32_t s_ = u % (uint32_t)a.NS, r = u / (uint32_t)a.NS;
-      const int i = (int)(r % (uint32_t)a.H), t = (int)(r / (uint32_t)a.H), j0 = (int)s_ * kTileM;
-      if (issued >= kWgStages && !mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1u, a.err, s_abort)) break;
+      const int i = (int)(r % (uint32_t)a.H), t = (int)(r / (uint32_t)a.H), j0 = (int)s_ * a.S;
+      if (issued >= nst && !mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1u, a.err, s_abort)) break;
       const uint32_t fb = smem_u32(&full_bar[st]);
       mbar_expect_tx(fb, tx);
       uint8_t* base = s_stage + (size_t)st * a.stage_bytes;
       tma_load_5d(smem_u32(base), &tm_dz, 0, j0, 0, i, t, fb);
 #pragma unroll
       for (int ky = 0; ky < 3; ++ky)
-        tma_load_5d(smem_u32(base + kDzSlot + (size_t)ky * a.x_slot), &tm_x, 0, j0 - a.d, 0, i + (ky - 1) * a.d, t, fb);
+        tma_load_5d(smem_u32(base + dz_slot + (size_t)ky * a.x_slot), &tm_x, 0, j0 - a.d, 0, i + (ky - 1) * a.d, t, fb);
       ++issued;
-      if (++st == kWgStages) {
+      if (++st == nst) {
         st = 0;
         ph ^= 1u;
       }
     }
     // no load of ours may still be landing when the CTA exits
-    const uint32_t n_drain = issued < kWgStages ? issued : kWgStages;
+    const uint32_t n_drain = issued < nst ? issued : nst;
     for (uint32_t k = 0; k < n_drain; ++k) {
       const uint32_t back = k + 1;
-      const uint32_t s2 = (st + kWgStages - (back % kWgStages)) % kWgStages;
+      const uint32_t s2 = (st + nst - (back % nst)) % nst;
       const uint32_t p2 = (back > st) ? (ph ^ 1u) : ph;
       mbar_wait_own(smem_u32(&full_bar[s2]), p2, a.err, s_abort);
     }
@@ -145,17 +148,17 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constan
     const uint64_t ones = smem_desc(smem_u32(s_ones), 256u, 256u, 6u);
     // descriptors of stage 0, K step 0; a K step adds 16 pixel lines (512 B, 32 in the
     // descriptor's 16-byte address field), a stage adds stage_bytes
-    const uint64_t a0 = smem_desc(smem_u32(s_stage), kDzPlane, 256u, 6u);
+    const uint64_t a0 = smem_desc(smem_u32(s_stage), a.dz_plane, 256u, 6u);
     uint64_t b0[3];
 #pragma unroll
-    for (int kx = 0; kx < 3; ++kx) b0[kx] = smem_desc(smem_u32(s_stage) + kDzSlot + (uint32_t)(kx * a.d) * 32u, a.x_plane, 256u, 6u);
+    for (int kx = 0; kx < 3; ++kx) b0[kx] = smem_desc(smem_u32(s_stage) + dz_slot + (uint32_t)(kx * a.d) * 32u, a.x_plane, 256u, 6u);
     uint32_t st = 0, ph = 0;
     bool issued = false;
     for (uint32_t u = u_begin; u < u_end; ++u) {
       if (!mbar_wait(smem_u32(&full_bar[st]), ph, a.err, s_abort)) break;
       fence_after_sync();
-      const int j0 = (int)(u % (uint32_t)a.NS) * kTileM;
-      const int valid = a.W - j0 < kTileM ? a.W - j0 : kTileM;
+      const int j0 = (int)(u % (uint32_t)a.NS) * a.S;
+      const int valid = a.W - j0 < a.S ? a.W - j0 : a.S;
       const int nk = (valid + 15) / 16;  // K steps that hold pixels of the frame
       const uint64_t st16 = (uint64_t)((st * a.stage_bytes) >> 4);
       for (int ks = 0; ks < nk; ++ks) {
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constan
       }
       umma_commit(smem_u32(&empty_bar[st]));
       issued = true;
-      if (++st == kWgStages) {
+      if (++st == nst) {
         st = 0;
         ph ^= 1u;
       }
@@ -203,21 +206,36 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const __grid_constan
   }
 }
 
-// dW[co][ci][ky][kx] and db[co] from the CTAs' partial sums, added in CTA order.
+// dW[co][ci][ky][kx] and db[co] from the CTAs' partial sums.  A block takes 32 outputs; warp
+// s of it adds CTAs s, s + 8, ... in order, and the eight slice sums are added in slice order:
+// a fixed order for given sizes, with eight times the loads in flight of one thread per output.
+constexpr int kRedSlices = 8;
+
 template <int C>
-__global__ void k_wgrad_reduce(const float* __restrict__ partial, int nblk, float* __restrict__ dw,
-                               float* __restrict__ db) {
+__global__ void __launch_bounds__(32 * kRedSlices) k_wgrad_reduce(const float* __restrict__ partial, int nblk,
+                                                                   float* __restrict__ dw, float* __restrict__ db) {
   constexpr int COLS = wg_cols(C);
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (co, column) of the partial sums
-  if (e >= C * (9 * C + 1)) return;
+  constexpr int NO = C * (9 * C + 1);  // (co, column) pairs of the partial sums
+  __shared__ float s_sum[kRedSlices][32];
+  const int ol = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + ol;
   const int co = e / (9 * C + 1), c = e % (9 * C + 1);
-  float s = 0.0f;
-  for (int b = 0; b < nblk; ++b) s += partial[((size_t)b * C + co) * COLS + c];
+  float acc = 0.0f;
+  if (e < NO) {
+#pragma unroll 4
+    for (int b = sl; b < nblk; b += kRedSlices) acc += partial[((size_t)b * C + co) * COLS + c];
+  }
+  s_sum[sl][ol] = acc;
+  __syncthreads();
+  if (sl != 0 || e >= NO) return;
+  float v = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kRedSlices; ++k) v += s_sum[k][ol];
   if (c == 9 * C) {
-    db[co] = s;
+    db[co] = v;
   } else {  // column kx * 3C + ky * C + ci
     const int kx = c / (3 * C), ky = (c % (3 * C)) / C, ci = c % C;
-    dw[((size_t)co * C + ci) * 9 + ky * 3 + kx] = s;
+    dw[((size_t)co * C + ci) * 9 + ky * 3 + kx] = v;
   }
 }
 
@@ -251,6 +269,15 @@ __global__ void k_pack_bimg_bf16(const float* __restrict__ w, int cin, int cout,
 
 size_t train_wgrad_tc_work_bytes(int C, int num_sms) { return (size_t)num_sms * C * wg_cols(C) * sizeof(float); }
 
+// Strip width of the weight gradient: 128 pixels, or the frame width rounded up to 32 for
+// narrower frames (training patches), so that the boxes carry little beyond the frame.  The X
+// box adds the 2d halo, rounded up to 32 pixels (1 KB planes).
+void wgrad_tc_boxes(int W, int d, int* dz_px, int* x_px) {
+  const int S = W >= kTileM ? kTileM : (W + 31) / 32 * 32;
+  *dz_px = S;
+  *x_px = (S + 2 * d + 31) / 32 * 32;
+}
+
 cudaError_t launch_pack_bimg_bf16(const float* w, int cin, int cout, void* fwd, void* dgrad, cudaStream_t s) {
   if (cin % 16 || cout % 16 || cin < 16 || cout < 16) return cudaErrorInvalidValue;
   const int n = 2 * 9 * cin * cout;
@@ -267,17 +294,25 @@ cudaError_t launch_wgrad_tc(const CUtensorMap* tm_dz, const CUtensorMap* tm_x, i
   a.H = H;
   a.W = W;
   a.d = d;
-  a.NS = (W + kTileM - 1) / kTileM;
+  int dz_px = 0, x_px = 0;
+  wgrad_tc_boxes(W, d, &dz_px, &x_px);
+  a.S = dz_px;
+  a.NS = (W + a.S - 1) / a.S;
   const long long units = (long long)T * H * a.NS;
   if (units >= (1LL << 31)) return cudaErrorInvalidValue;
   a.units = (uint32_t)units;
-  a.x_plane = (uint32_t)tc_box_width(d) * 32u;
+  a.dz_plane = (uint32_t)dz_px * 32u;
+  a.x_plane = (uint32_t)x_px * 32u;
   a.x_slot = (uint32_t)(C / 16) * a.x_plane;  // a multiple of 1024 (x_plane is): the slots are contiguous planes
-  a.stage_bytes = kDzSlot + 3u * a.x_slot;
+  a.stage_bytes = (uint32_t)(kWgM / 16) * a.dz_plane + 3u * a.x_slot;
   a.partial = partial;
   a.err = err;
-  const size_t smem = 1024 + (size_t)kWgStages * a.stage_bytes + 1024 + 8 * (2 * kWgStages + 1) + 16;
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  // as many ring stages as fit next to the fixed part (alignment slack, ones plane, barriers)
+  const size_t fixed = 1024 + 1024 + 8 * (2 * kWgMaxStages + 1) + 16;
+  const size_t avail = 227 * 1024 - fixed;
+  a.nstages = (int)std::min<size_t>(kWgMaxStages, avail / a.stage_bytes);
+  if (a.nstages < 2) return cudaErrorInvalidConfiguration;
+  const size_t smem = fixed + (size_t)a.nstages * a.stage_bytes;
   const int grid = (int)std::min<long long>(units > 0 ? units : 1, num_sms);
   cudaError_t e;
   if (units > 0) {
@@ -297,11 +332,11 @@ cudaError_t launch_wgrad_tc(const CUtensorMap* tm_dz, const CUtensorMap* tm_x, i
   } else {
     if ((e = cudaMemsetAsync(partial, 0, (size_t)C * wg_cols(C) * sizeof(float), s)) != cudaSuccess) return e;
   }
-  const int nred = C * (9 * C + 1);
+  const int nred = (C * (9 * C + 1) + 31) / 32;
   switch (C) {
-    case 16: k_wgrad_reduce<16><<<(nred + 255) / 256, 256, 0, s>>>(partial, grid, dw, db); break;
-    case 32: k_wgrad_reduce<32><<<(nred + 255) / 256, 256, 0, s>>>(partial, grid, dw, db); break;
-    default: k_wgrad_reduce<48><<<(nred + 255) / 256, 256, 0, s>>>(partial, grid, dw, db); break;
+    case 16: k_wgrad_reduce<16><<<nred, 32 * kRedSlices, 0, s>>>(partial, grid, dw, db); break;
+    case 32: k_wgrad_reduce<32><<<nred, 32 * kRedSlices, 0, s>>>(partial, grid, dw, db); break;
+    default: k_wgrad_reduce<48><<<nred, 32 * kRedSlices, 0, s>>>(partial, grid, dw, db); break;
   }
   return cudaGetLastError();
 }

@@ -149,6 +149,8 @@ bool tc_layer_fits(int ci, int co, int d, int prec);
 
 // --- BF16 training on the tensor cores (k_train_tc.cu) -----------------------------------
 size_t train_wgrad_tc_work_bytes(int C, int num_sms);
+// Box widths (pixels) of the weight gradient's dZ and X tensor maps for frames W wide.
+void wgrad_tc_boxes(int W, int d, int* dz_px, int* x_px);
 // FP32 w [cout][cin][3][3] -> bf16 B images of the conv: forward and mirrored-transposed (dgrad).
 cudaError_t launch_pack_bimg_bf16(const float* w, int cin, int cout, void* fwd, void* dgrad, cudaStream_t s);
 // dw [C][C][3][3], db [C] of a C -> C layer from dz (tm_dz: 128-pixel row boxes) and the
