@@ -68,7 +68,7 @@ constexpr size_t l1_smem_bytes(int d) {
 // time.  FMA order: bias, then input channel, then taps (ky, kx) row-major.  Outputs are
 // staged in shared memory (rows padded by 16 bytes against bank conflicts) so that the stores
 // to HBM are whole 16-byte chunks, consecutive across threads.
-// (The BF16 one-frame case runs k_l1_rp_bf16 below, which stores from registers.)
+// (The one-frame BF16 and FP8 cases run k_l1_rp below, which stores from registers.)
 template <int C, int OUT, int IN_CH>
 __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restrict__ frames, int H, int W, int d,
                                                        int t0, int t_first, int t_last, CamArgs cam,
@@ -248,20 +248,23 @@ __global__ void __launch_bounds__(kL1Tile) k_ingest_l1(const uint16_t* __restric
   }
 }
 
-// The BF16 first layer of a one-frame net, stored straight from registers.  A block has
-// G = C/16 warps and covers a 128-pixel strip of l1_rows(d) output rows of one frame; warp g
-// writes channel group g: lane pair (2u, 2u+1) takes pixels u + 16p (p < 8), the even lane
-// channels 0..7 of the group and the odd lane 8..15, so each thread ends a pixel with one
-// 16-byte store and one warp store covers 16 whole 32-byte pixel rows.  Staging (camera
+// The tensor-core precisions' first layer of a one-frame net (OUT = 1: bf16, 2: e4m3 scaled by
+// out_scale), stored straight from registers.  A block has G = C/16 warps and covers a
+// 128-pixel strip of l1_rows(d) output rows of one frame; warp g writes channel group g: lane
+// pair (2u, 2u+1) takes pixels u + 16p (p < 8), the even lane channels 0..7 of the group and
+// the odd lane 8..15, so each thread ends a pixel with one 16-byte (bf16) or 8-byte (e4m3)
+// store and one warp store covers 16 whole pixel rows of the group.  Staging (camera
 // transform of the block's distinct dilated input rows), FMA order (bias, then taps (ky, kx)
 // row-major, each lane of the packed FMA one fmaf), ReLU and rounding are those of
 // k_ingest_l1, so both give the same bits.  DEVW: weights and bias from device memory.
-template <int C, bool DEVW>
-__global__ void __launch_bounds__(C * 2) k_l1_rp_bf16(const uint16_t* __restrict__ frames, int H, int W, int d, int t0,
-                                                      CamArgs cam, const __grid_constant__ L1Params prm,
-                                                      void* __restrict__ out, int out_ct,
-                                                      const float* __restrict__ wdev, const float* __restrict__ bdev) {
-  constexpr int NT = C * 2;  // threads: 32 per 16-channel group
+template <int C, int OUT, bool DEVW>
+__global__ void __launch_bounds__(C * 2) k_l1_rp(const uint16_t* __restrict__ frames, int H, int W, int d, int t0,
+                                                 CamArgs cam, const __grid_constant__ L1Params prm, float out_scale,
+                                                 void* __restrict__ out, int out_ct, const float* __restrict__ wdev,
+                                                 const float* __restrict__ bdev) {
+  static_assert(OUT == 1 || OUT == 2, "bf16 or e4m3 row-planar output");
+  constexpr int NT = C * 2;               // threads: 32 per 16-channel group
+  constexpr int OB = OUT == 1 ? 2 : 1;    // output bytes per channel
   extern __shared__ __align__(16) uint8_t l1_smem[];
   const int span = kL1Tile + 2 * d, nsr = l1_stage_rows(d), R = l1_rows(d);
   float2* xs = reinterpret_cast<float2*>(l1_smem);  // [nsr][span]
@@ -313,8 +316,7 @@ __global__ void __launch_bounds__(C * 2) k_l1_rp_bf16(const uint16_t* __restrict
     const float2* xr[3];
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky) xr[ky] = xs + (size_t)l1_srow(r, ky, d) * span;
-    uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(out) +
-                                          ((((size_t)t * H + i) * gt + g) * W + j0) * 32 + half * 16);
+    uint8_t* dst = static_cast<uint8_t*>(out) + ((((size_t)t * H + i) * gt + g) * W + j0) * (16 * OB) + half * 8 * OB;
 #pragma unroll
     for (int p = 0; p < kL1Px; ++p) {
       const int px = u + 16 * p;
@@ -323,17 +325,26 @@ __global__ void __launch_bounds__(C * 2) k_l1_rp_bf16(const uint16_t* __restrict
       for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
         for (int kx = 0; kx < 3; ++kx) x[ky * 3 + kx] = xr[ky][px + kx * d];
-      uint4 o;
-      uint32_t* ow = reinterpret_cast<uint32_t*>(&o);
+      uint32_t ow[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         float2 a = bias[q];
 #pragma unroll
         for (int k = 0; k < 9; ++k) a = __ffma2_rn(w[q][k], x[k], a);
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(fmaxf(a.x, 0.0f), fmaxf(a.y, 0.0f));
-        ow[q] = *reinterpret_cast<uint32_t*>(&h2);
+        const float lo = fmaxf(a.x, 0.0f), hi = fmaxf(a.y, 0.0f);
+        if (OUT == 1) {
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
+          ow[q] = *reinterpret_cast<uint32_t*>(&h2);
+        } else {
+          ow[q] = __nv_cvt_float2_to_fp8x2(make_float2(lo * out_scale, hi * out_scale), __NV_SATFINITE, __NV_E4M3);
+        }
       }
-      if (px < npx) dst[(size_t)px * 2] = o;
+      if (px < npx) {
+        if (OUT == 1)
+          *reinterpret_cast<uint4*>(dst + (size_t)px * 32) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+        else
+          *reinterpret_cast<uint2*>(dst + (size_t)px * 16) = make_uint2(ow[0] | (ow[1] << 16), ow[2] | (ow[3] << 16));
+      }
     }
   }
 }
@@ -443,15 +454,15 @@ inline unsigned grid_for(long long npx) { return (unsigned)((npx + kSimtThreads 
 
 }  // namespace
 
-// The register-store BF16 first layer (k_l1_rp_bf16): its staged rows take at most 26 KB.
-template <int C, bool DEVW>
-static cudaError_t launch_l1_rp_bf16(const uint16_t* frames, int T, int H, int W, int d, const CamArgs& cam,
-                                     const L1Params& prm, void* out, int out_ct, const float* wdev, const float* bdev,
-                                     cudaStream_t s) {
+// The register-store first layer (k_l1_rp): its staged rows take at most 26 KB.
+template <int C, int OUT, bool DEVW>
+static cudaError_t launch_l1_rp(const uint16_t* frames, int T, int H, int W, int d, const CamArgs& cam,
+                                const L1Params& prm, float out_scale, void* out, int out_ct, const float* wdev,
+                                const float* bdev, cudaStream_t s) {
   const size_t smem = (size_t)l1_stage_rows(d) * (kL1Tile + 2 * d) * 8;
   for (int t0 = 0; t0 < T; t0 += 65535) {
     dim3 grid((W + kL1Tile - 1) / kL1Tile, (H + l1_rows(d) - 1) / l1_rows(d), (unsigned)(T - t0 < 65535 ? T - t0 : 65535));
-    k_l1_rp_bf16<C, DEVW><<<grid, C * 2, smem, s>>>(frames, H, W, d, t0, cam, prm, out, out_ct, wdev, bdev);
+    k_l1_rp<C, OUT, DEVW><<<grid, C * 2, smem, s>>>(frames, H, W, d, t0, cam, prm, out_scale, out, out_ct, wdev, bdev);
   }
   return cudaGetLastError();
 }
@@ -460,8 +471,8 @@ template <int C, int OUT, int IN_CH>
 static cudaError_t launch_l1(const uint16_t* frames, int T, int H, int W, int d, int t_first, int t_last,
                              const CamArgs& cam, const L1Params& prm, float out_scale, void* out, int out_ct,
                              cudaStream_t s) {
-  if constexpr (OUT == 1 && IN_CH == 1) {
-    return launch_l1_rp_bf16<C, false>(frames, T, H, W, d, cam, prm, out, out_ct, nullptr, nullptr, s);
+  if constexpr (OUT != 0 && IN_CH == 1) {
+    return launch_l1_rp<C, OUT, false>(frames, T, H, W, d, cam, prm, out_scale, out, out_ct, nullptr, nullptr, s);
   } else {
     const size_t smem = l1_smem_bytes<C, OUT, IN_CH>(d);
     // opt in to more than 48 KB on the current device, to the largest size any dilation takes
@@ -487,7 +498,7 @@ static cudaError_t launch_l1_devw(const uint16_t* frames, int T, int H, int W, i
                                   const float* wdev, const float* bdev, void* out, cudaStream_t s) {
   L1Params prm;
   memset(&prm, 0, sizeof(prm));
-  return launch_l1_rp_bf16<C, true>(frames, T, H, W, d, cam, prm, out, C, wdev, bdev, s);
+  return launch_l1_rp<C, 1, true>(frames, T, H, W, d, cam, prm, 1.0f, out, C, wdev, bdev, s);
 }
 
 template <int C>
