@@ -57,7 +57,7 @@ constexpr int kEpiWarps = 4;
 constexpr int kThreads = 224;
 constexpr int kMinStages = 4;  // the handoff protocol needs a ring of at least 2 handoff groups
 constexpr int kTmemCols = 512;
-constexpr int kMaxSeg = 6;
+constexpr int kMaxSeg = 10;
 constexpr int kMaxStages = 16;
 
 // Kernel arguments; bias, dequantisation factors and head weights travel by value so the
@@ -109,9 +109,12 @@ struct TcCfg {
   static constexpr int GP = PREC == kBF16 ? G : 2 * NKS;  // planes in shared memory (FP8: zero pad)
   static constexpr int BBLK = 3 * (CO / 8) * 256;         // bytes of one (kx, k-step) B block: N = 3 CO
   static constexpr int BIMG = 3 * NKS * BBLK;
-  // S = output rows per unit: the window of S+2 input rows needs (S+1)*CO + 3CO <= 512 columns
-  static constexpr int SEG = (512 / CO - 4) < kMaxSeg ? (512 / CO - 4) : kMaxSeg;
+  // S = output rows per unit.  Output row k accumulates at columns BASE0 - CO*k .. + CO, and an
+  // input row's MMA only writes the columns of the unit's rows it feeds, so a unit spans
+  // columns [BASE0 - CO*(S-1), BASE0 + CO) = [2 CO, (S+2) CO): S <= 512/CO - 2
+  static constexpr int SEG = (512 / CO - 2) < kMaxSeg ? (512 / CO - 2) : kMaxSeg;
   static constexpr uint32_t BASE0 = (uint32_t)(SEG + 1) * CO;  // TMEM column of output row 0
+  static_assert((SEG + 2) * CO <= 512, "a unit's accumulators fit the 512 TMEM columns");
   static constexpr uint32_t IDESC1 = instr_desc(PREC, kTileM, CO);
   static constexpr uint32_t IDESC2 = instr_desc(PREC, kTileM, 2 * CO);
   static constexpr uint32_t IDESC3 = instr_desc(PREC, kTileM, 3 * CO);
@@ -722,7 +725,7 @@ TcSizes tc_sizes(int ci, int co, int d, int prec) {
   return z;
 }
 
-int tc_seg(int co) { return (512 / co - 4) < kMaxSeg ? (512 / co - 4) : kMaxSeg; }
+int tc_seg(int co) { return (512 / co - 2) < kMaxSeg ? (512 / co - 2) : kMaxSeg; }
 
 template <int CI, int CO, int PREC, bool LAST, bool DGRAD = false>
 cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
