@@ -122,22 +122,43 @@ struct TcCfg {
 
 // Unit -> (t, phi, strip, q), q fastest: consecutive units are the next segment of the same
 // row chain (sharing two input rows) and then the neighbouring strip (sharing halo columns),
-// so with contiguous unit ranges per CTA those re-reads hit L2.  Returns the number of valid
-// output rows (<= seg).  32-bit arithmetic (unit counts stay far below 2^31).
-__device__ __forceinline__ int unit_rows(const TcKArgs& a, uint32_t u, int seg, int& t, int& j0, int& phi, int& q) {
-  const uint32_t nq = (uint32_t)a.NQ, d = (uint32_t)a.d, ns = (uint32_t)a.NS;
-  uint32_t r = u / nq;
-  q = (int)(u - r * nq);
-  uint32_t r2 = r / ns;
-  const int s = (int)(r - r2 * ns);
-  uint32_t r3 = r2 / d;
-  phi = (int)(r2 - r3 * d);
-  t = (int)r3;
-  j0 = s * kTileM;
-  const int n_class = phi < a.H ? (a.H - phi + a.d - 1) / a.d : 0;
-  const int n = n_class - q * seg;
-  return n < 0 ? 0 : (n > seg ? seg : n);
-}
+// so with contiguous unit ranges per CTA those re-reads hit L2.  Every role walks its CTA's
+// range with a cursor: the first unit is decoded with divisions, each later one by a carry
+// chain, and the residue class's row count is recomputed only when phi changes (measured: the
+// divisions of a full decode cost the issuing warp about 500 cycles per unit).  32-bit
+// arithmetic (unit counts stay far below 2^31).
+struct UnitCursor {
+  int t, phi, s, q, n_class;
+  __device__ __forceinline__ void set_class(const TcKArgs& a) { n_class = phi < a.H ? (a.H - phi + a.d - 1) / a.d : 0; }
+  __device__ __forceinline__ void init(const TcKArgs& a, uint32_t u) {
+    const uint32_t nq = (uint32_t)a.NQ, d = (uint32_t)a.d, ns = (uint32_t)a.NS;
+    const uint32_t r = u / nq;
+    q = (int)(u - r * nq);
+    const uint32_t r2 = r / ns;
+    s = (int)(r - r2 * ns);
+    const uint32_t r3 = r2 / d;
+    phi = (int)(r2 - r3 * d);
+    t = (int)r3;
+    set_class(a);
+  }
+  __device__ __forceinline__ void next(const TcKArgs& a) {
+    if (++q < a.NQ) return;
+    q = 0;
+    if (++s < a.NS) return;
+    s = 0;
+    if (++phi == a.d) {
+      phi = 0;
+      ++t;
+    }
+    set_class(a);
+  }
+  // valid output rows of the unit (<= seg) and its first pixel column
+  __device__ __forceinline__ int rows(int seg) const {
+    const int n = n_class - q * seg;
+    return n < 0 ? 0 : (n > seg ? seg : n);
+  }
+  __device__ __forceinline__ int j0() const { return s * kTileM; }
+};
 
 // The MMAs of one input row: for each horizontal tap kx and K step ks one M=128 MMA, fully
 // unrolled for a compile-time count of K steps.  The issuing warp then runs no per-MMA loop
@@ -267,9 +288,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
       const uint32_t nst = (uint32_t)a.nstages;
       uint32_t st = 0, ph = 0, issued = 0;  // stage, phase of its current use, loads issued
       bool ok = (int)blockIdx.x != a.poison_cta;  // a poisoned CTA loads nothing (failure-path test)
-      for (uint32_t u = u_begin; u < u_end && ok; ++u) {
-        int t, j0, phi, q;
-        const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
+      UnitCursor uc;
+      uc.init(a, u_begin);
+      for (uint32_t u = u_begin; u < u_end && ok; ++u, uc.next(a)) {
+        const int n_out = uc.rows(SEG), t = uc.t, j0 = uc.j0(), phi = uc.phi, q = uc.q;
         for (int kk = 0; kk < n_out + 2 && n_out > 0; ++kk) {
           // the slot was released by the MMA that read its previous load (skip on first use)
           if (issued >= nst && !mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1u, a.err, s_abort, a.wait_ns)) {
@@ -337,9 +359,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
         uint64_t a_st = a_desc0;     // descriptor of the current stage
         uint32_t hand = 0;           // handoffs taken
         bool issued = false;
-        for (uint32_t u = u_begin; u < u_end; ++u) {
-          int t, j0, phi, q;
-          const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
+        UnitCursor uc;
+        uc.init(a, u_begin);
+        for (uint32_t u = u_begin; u < u_end; ++u, uc.next(a)) {
+          const int n_out = uc.rows(SEG);
           if (n_out == 0) continue;
           for (int kk = 0; kk < n_out + 2; ++kk) {
             if ((kk & (hand_rows - 1)) == 0) {
@@ -402,9 +425,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     uint32_t used = 0, par = 0;          // row positions used before / parity of their last release
     uint32_t hand = 0;
     uint32_t g_st0 = 0, g_ph0 = 0, g_st1 = 0, g_ph1 = 0;  // first row of the last two groups (even, odd)
-    for (uint32_t u = u_begin; u < u_end; ++u) {
-      int t, j0, phi, q;
-      const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
+    UnitCursor uc;
+    uc.init(a, u_begin);
+    for (uint32_t u = u_begin; u < u_end; ++u, uc.next(a)) {
+      const int n_out = uc.rows(SEG);
       if (n_out == 0) continue;
       for (int k0 = 0; k0 < n_out + 2; k0 += hand_rows) {
         if (lane == 0) {
@@ -447,9 +471,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     const int out_gt = CI > 0 ? Cfg::GO : a.out_gt;
     const int out_g0 = CI > 0 ? 0 : a.out_g0;
     const size_t plane = (size_t)a.H * a.W;
-    for (uint32_t u = u_begin; u < u_end && ok; ++u) {
-      int t, j0, phi, q;
-      const int n_out = unit_rows(a, u, SEG, t, j0, phi, q);
+    UnitCursor uc;
+    uc.init(a, u_begin);
+    for (uint32_t u = u_begin; u < u_end && ok; ++u, uc.next(a)) {
+      const int n_out = uc.rows(SEG), t = uc.t, j0 = uc.j0(), phi = uc.phi, q = uc.q;
 #pragma unroll 1
       for (int k = 0; k < n_out; ++k) {
         // DGRAD: the ReLU mask of this output row is issued before the accumulator wait, so its
