@@ -242,19 +242,74 @@ def round_to(a, fmt):
     return out
 
 
-def quantized(net: Net, fmt):
+def input_producers(net: Net):
+    """For every conv layer in execution order, the layer that produced each of its input
+    channels (-1: the network input).  A plain layer reads its predecessor; a dense layer
+    (Sec. 3.2.1) reads the block input and the block's earlier outputs, so its channels come
+    from several layers; a transition reads the whole concatenation; a U-Net down conv reads
+    the pooled features of the level above, an up conv the level's skip features followed by
+    the upsampled deeper features (Sec. 3.2).  Pooling and upsampling move stored values, so
+    they keep the producer."""
+    prods = []
+    buf = []  # producer of each channel of the current block's concatenation
+    li = 0
+    while li < net.L:
+        cin, cout, _, kind = net.layers[li]
+        if kind == "down":
+            skips = [buf[: net.C]]
+            for _ in range(net.unet):
+                prods.append(list(skips[-1]))
+                skips.append([li] * net.C)
+                li += 1
+            up = skips.pop()
+            while skips:
+                skip = skips.pop()
+                prods.append(list(skip) + list(up))
+                up = [li] * net.C
+                li += 1
+            buf = list(up)
+            continue
+        prods.append([-1] * cin if li == 0 else list(buf[:cin]))
+        if kind == "dense":
+            buf = buf + [li] * cout
+        else:
+            buf = [li] * cout
+        li += 1
+    return [np.asarray(p, dtype=np.int64) for p in prods]
+
+
+def quantized(net: Net, fmt, scales=None):
     """Copy of net whose conv weights of layers 1..L-1 are rounded as the tensor-core path
     stores them: bf16, or e4m3 of w / s[co] times s[co] with s[co] = max |w[co,:,:,:]| / 448
-    (float32).  Layer 0 (the SIMT first layer) and the heads keep their float32 weights."""
+    (float32).  Layer 0 (the SIMT first layer) and the heads keep their float32 weights.
+    Nets with dense blocks or a U-Net in e4m3 need the activation scales (scales[l + 1]: the
+    output scale of layer l, as act_scales returns them): a layer's input channels come from
+    several layers with their own scales, so each weight is first multiplied by the scale of
+    its input channel, w'[co,ci] = w[co,ci] s_in[ci] (float32), then rounded per output channel
+    as above, and divided by s_in[ci] again, so that the float64 forward on the dequantised
+    activations computes what the tensor cores compute on the stored e4m3 codes."""
     import copy
 
     if net.bn is not None:
         raise ValueError("quantized oracle modes need a net without BatchNorm")
     q = copy.copy(net)
     if net.growth or net.unet:  # per-layer arrays (layers 1.. run on the tensor cores)
-        if fmt != "bf16":
-            raise ValueError("dense blocks and the U-Net have a bf16 quantized mode only")
-        q.layer_w = [net.layer_w[0]] + [round_to(wl, "bf16") for wl in net.layer_w[1:]]
+        if fmt == "bf16":
+            q.layer_w = [net.layer_w[0]] + [round_to(wl, "bf16") for wl in net.layer_w[1:]]
+            return q
+        if fmt != "fp8" or scales is None:
+            raise ValueError("dense blocks and the U-Net: bf16, or fp8 with the activation scales")
+        sc = np.asarray(scales, dtype=np.float32)
+        prods = input_producers(net)
+        q.layer_w = [net.layer_w[0]]
+        for li in range(1, net.L):
+            cin, cout, _, _ = net.layers[li]
+            s_in = sc[prods[li] + 1]  # float32 [cin]
+            wf = net.layer_w[li].reshape(cout, cin, 9).astype(np.float32) * s_in[None, :, None]
+            amax = np.abs(wf).max(axis=(1, 2))
+            sw = np.where(amax > 0, amax / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+            wq = round_to((wf / sw[:, None, None]).astype(np.float64), "fp8")
+            q.layer_w.append((wq * sw[:, None, None].astype(np.float64) / s_in[None, :, None].astype(np.float64)).ravel())
         return q
     w = net.conv_w.copy()
     off = net.C * net.in_ch * 9
@@ -275,8 +330,13 @@ def quantized(net: Net, fmt):
 
 def act_scales(net: Net, frames, gain=1.0, offset=100.0, gain_map=None, offset_map=None):
     """FP8 activation scales from this oracle's own float64 activations: [1] + [amax_l / 448]
-    for the inputs of layers 1..L-1 (amax over the given frames)."""
+    with amax_l the largest output of layer l = 0..L-2 over the given frames (for a plain stack
+    the inputs of layers 1..L-1)."""
     x0 = context_input(ingest(frames, gain, offset, gain_map, offset_map, net.in_scale), net.in_ch)
+    if net.growth or net.unet:
+        amax = [0.0] * net.L
+        _forward_dense(net, x0, amax=amax)
+        return [1.0] + [amax[l] / 448.0 for l in range(net.L - 1)]
     _, a = forward_x(net, x0, acts=True)
     return [1.0] + [float(a[:, l - 1].max()) / 448.0 for l in range(1, net.L)]
 
@@ -288,7 +348,7 @@ def forward_x(net: Net, x0, acts=False, quant=None, scales=None):
     (fp8: of a / scales[l]) before the layer, as the tensor-core path stores them; pass a
     net from quantized() to round the weights too."""
     if net.growth or net.unet:
-        return _forward_dense(net, x0, acts, quant)
+        return _forward_dense(net, x0, acts, quant, scales)
     lib = _load()
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     if x0.ndim == 3:
@@ -319,23 +379,32 @@ def upsample2(a, H, W):
     return a.repeat(2, axis=1).repeat(2, axis=2)[:, :H, :W]
 
 
-def _forward_dense(net: Net, x0, acts=False, quant=None):
+def _forward_dense(net: Net, x0, acts=False, quant=None, scales=None, amax=None):
     """Forward of a net with dense connection dilated blocks (Sec. 3.2.1) and/or a U-Net fine
     stage (Sec. 3.2): each conv is the C oracle's conv (float64) on a channel range of a
     buffer that concatenates the block input and the block's outputs so far; the U-Net
     pools, convolves, upsamples and concatenates with numpy.  quant "bf16" rounds every conv
     layer's stored output to bf16 (what the tensor-core path stores; pooling and upsampling
-    move stored values unchanged; the stem's input frames stay float).  Returns raw heads
-    [T,nh,H,W] (and, with acts, the last layer's activations)."""
+    move stored values unchanged; the stem's input frames stay float); quant "fp8" rounds
+    layer l's stored output a to e4m3 of a * (1 / scales[l + 1]) (float32) times scales[l + 1].
+    With amax (a list of L floats), amax[l] becomes the largest output of layer l.  Returns raw
+    heads [T,nh,H,W] (and, with acts, the last layer's activations)."""
     lib = _load()
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     if x0.ndim == 3:
         x0 = x0[:, None]
     T, cin0, H, W = x0.shape
     assert cin0 == net.in_ch
-    if quant not in (None, "fp32", "bf16"):
-        raise ValueError("dense blocks and the U-Net support the bf16 quantized mode only")
-    rnd = (lambda a: round_to(a, "bf16")) if quant == "bf16" else (lambda a: a)
+    if quant not in (None, "fp32", "bf16", "fp8") or (quant == "fp8" and scales is None):
+        raise ValueError("dense blocks and the U-Net: bf16, or fp8 with the activation scales")
+
+    def rnd(a, li):
+        if quant == "bf16":
+            return round_to(a, "bf16")
+        if quant == "fp8":
+            inv = np.float32(1.0 / scales[li + 1])
+            return round_to((a.astype(np.float32) * inv).astype(np.float64), "fp8") * scales[li + 1]
+        return a
     C, g = net.C, net.growth
     widest = max(cin for cin, _, _, _ in net.layers)
 
@@ -346,7 +415,9 @@ def _forward_dense(net: Net, x0, acts=False, quant=None):
         out = np.empty((cout, h, w), dtype=np.float64)
         lib.orc_conv(_ptr(inp), cin, h, w, _ptr(np.ascontiguousarray(net.layer_w[li])),
                      _ptr(np.ascontiguousarray(net.layer_b[li])), cout, d, _ptr(out))
-        return out if li == net.L - 1 else rnd(out)  # the last layer's output feeds the heads in FP32
+        if amax is not None:
+            amax[li] = max(amax[li], float(out.max()))
+        return out if li == net.L - 1 else rnd(out, li)  # the last layer's output feeds the heads in FP32
 
     heads = np.empty((T, net.nh, H, W), dtype=np.float64)
     last = np.empty((T, C, H, W), dtype=np.float64) if acts else None
