@@ -597,8 +597,8 @@ def topology_run(dev, stream, flush, which, reps=5):
     """The paper's topology beyond the plain stack: the 256 frames of 256x256 of the main
     workload through the 22-layer dense-block net ("dcd": 32 channels, growth 16, four blocks
     of dilations 2, 4, 8, 16 with transitions; Sec. 3.2.1) or the full topology ("dilatedloc":
-    those blocks, a two-level U-Net and the nine heads with uncertainties; Sec. 3.2), BF16 and
-    FP32.  The conv-class kernels (dense layers, transitions, U-Net convs, pools and upsamples)
+    those blocks, a two-level U-Net and the nine heads with uncertainties; Sec. 3.2), BF16, FP8
+    (scales from the library's calibration over the first 16 frames) and FP32.  The conv-class kernels (dense layers, transitions, U-Net convs, pools and upsamples)
     are timed with the library's event pairs; their algorithmic HBM bytes are one read of
     every input channel and one write of every output channel per pixel of their level."""
     import torch
@@ -609,10 +609,13 @@ def topology_run(dev, stream, flush, which, reps=5):
     name, maker = TOPOLOGIES[which]
     res = {"workload": name.format(T=T_FRAMES, H=H, W=W), "l2": "flushed between calls"}
     pk, pk_kind = peaks()
-    for prec in ("bf16", "fp32"):
-        w = getattr(synth, maker)(T=T_FRAMES, H=H, W=W, precision=prec)
-        loc = sml.Localizer(w.spec.to_json(), w.blob)
+    for prec in ("bf16", "fp8", "fp32"):
+        w = getattr(synth, maker)(T=T_FRAMES, H=H, W=W, precision="bf16" if prec == "fp8" else prec)
         d_frames = torch.from_numpy(w.frames).to(dev)
+        js = w.spec.to_json()
+        if prec == "fp8":
+            js = sml.calibrate_fp8(js, w.blob, d_frames[:16], gain=w.cam.gain, offset=w.cam.offset)
+        loc = sml.Localizer(js, w.blob)
         d_out = torch.empty(T_FRAMES * H * W // 4 * 24, dtype=torch.uint8, device=dev)
         d_n = torch.zeros(1, dtype=torch.int64, device=dev)
         for _ in range(3):
@@ -638,6 +641,11 @@ def topology_run(dev, stream, flush, which, reps=5):
                         "conv_algorithmic_bytes_per_call": nbytes, "conv_hbm_gbs": nbytes / conv_s / 1e9,
                         "conv_hbm_frac": nbytes / conv_s / 1e9 / pk["hbm_gbs"],
                         "conv_tflops": flops / conv_s / 1e12, "peak_kind": pk_kind})
+        elif prec == "fp8":
+            _, nbytes8, _ = conv_class_work(w.spec, T_FRAMES * H * W, 1)
+            conv_s = conv_ms / reps / 1000.0
+            res.update({"fp8_conv_ms_per_call": conv_ms / reps, "fp8_records_per_call": int(d_n.item()),
+                        "fp8_conv_algorithmic_bytes_per_call": nbytes8, "fp8_conv_hbm_gbs": nbytes8 / conv_s / 1e9})
         loc.close()
     return res
 
@@ -710,7 +718,7 @@ def main():
                     help="frames per step (default 256; smaller stacks for profiler captures)")
     ap.add_argument("--workload", default="batched", choices=["batched", "dcd", "dilatedloc", "large_fov", "training"],
                     help="batched: the 48-channel 8-layer net; dcd: the 22-layer dense-block net; dilatedloc: the "
-                         "full topology (dense blocks, U-Net, uncertainty heads); dcd and dilatedloc run fp32/bf16; "
+                         "full topology (dense blocks, U-Net, uncertainty heads); "
                          "large_fov: 1000 distinct 2048x2048 sCMOS frames, bf16 or fp8, one GPU; training: "
                          "BF16 and FP32 training steps (256 patches of 64x64), one GPU")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -749,8 +757,6 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    if args.workload in ("dcd", "dilatedloc") and args.precision == "fp8":
-        raise SystemExit("the dense-block and full-topology nets run in fp32 or bf16")
     if args.workload == "training":
         if world > 1:
             raise SystemExit("the training line runs on one GPU")
@@ -875,8 +881,7 @@ def main():
            "d2h_bytes_per_step": int(recs.numel() + 8)}
 
     extra = {}
-    others = [] if args.no_fp32 else [p for p in ("fp32", "bf16", "fp8")
-                                      if p != args.precision and not (args.workload != "batched" and p == "fp8")]
+    others = [] if args.no_fp32 else [p for p in ("fp32", "bf16", "fp8") if p != args.precision]
     for prec in others:  # the same batch at the other precisions, same timing method
         wo, jso = workload(prec, d_frames)
         loco = sml.Localizer(jso, wo.blob)

@@ -526,8 +526,13 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, FrameRange fr,
              "layer 1");
   }
   ++ctx->launches;
-  const size_t n_act = (size_t)tc * H * W * C;  // whole buffers of a plain stack (ct == C)
-  if (d_amax) SML_CUDA(launch_amax(p.act[0], n_act, ctx->prec, d_amax + 1, s), "amax");
+  // calibration: the maximum of every stored layer output (d_amax[l + 1] for layer l)
+  auto amax_of = [&](int l, void* buf) {
+    const LayerDesc& y = ctx->lay[l];
+    return launch_amax(buf, ctx->prec, tc, level_dim(H, y.level), level_dim(W, y.level), ctx->buf[y.out_buf].ct,
+                       y.out_off, y.cout, d_amax + l + 1, s);
+  };
+  if (d_amax) SML_CUDA(amax_of(0, p.act[ctx->lay[0].out_buf]), "amax");
   for (const Step& st : ctx->steps) {
     if (st.kind != kStepConv) {  // U-Net resolution change
       const BufDesc& bi = ctx->buf[st.in_buf];
@@ -602,7 +607,7 @@ int forward_chunk(sml_ctx* ctx, const uint16_t* d_frames, int tc, FrameRange fr,
       SML_CUDA(launch_dconv_tc(a, last, ctx->num_sms, s), "tensor-core conv");
     }
     ++ctx->launches;
-    if (d_amax && !last) SML_CUDA(launch_amax(out, n_act, ctx->prec, d_amax + l + 1, s), "amax");
+    if (d_amax && !last) SML_CUDA(amax_of(l, out), "amax");
   }
   return SML_OK;
 }
@@ -878,9 +883,6 @@ int parse_spec(sml_ctx* ctx, const char* spec) {
       ctx->act_scale[l] = (float)v.num;
     }
   }
-  if ((ctx->growth || ctx->unet) && ctx->prec == kFP8)
-    return fail(nullptr, SML_ERR_UNSUPPORTED,
-                "dcd and unet nets run in fp32 or bf16 (fp8 activation scales are per layer, not per concatenation)");
   for (int l = 1; l < ctx->L; ++l) {  // every layer must fit its kernel's shared memory
     const LayerDesc& y = ctx->lay[l];
     const bool fits = ctx->prec == kFP32 ? y.cin * y.cout <= kF32MaxWeights : tc_layer_fits(y.cin, y.cout, y.d, ctx->prec);
@@ -937,6 +939,28 @@ int check_blob(const sml_ctx* ctx, const void* blob, size_t bytes, size_t* hdr_o
   return SML_OK;
 }
 
+// The conv layer that produced each input channel of every layer (-1: the frames), from the
+// step list: a conv step writes its output channels, a pool or upsample step moves channels
+// with their producer.  Layers of dense blocks (Sec. 3.2.1) and of the U-Net (Sec. 3.2) read
+// channels of several producers.
+std::vector<std::vector<int>> input_producers(const sml_ctx* ctx) {
+  std::vector<std::vector<int>> prov(ctx->nbuf), prod(ctx->L);
+  for (int b = 0; b < ctx->nbuf; ++b) prov[b].assign(ctx->buf[b].ct, -1);
+  prod[0].assign(ctx->lay[0].cin, -1);
+  for (int c = 0; c < ctx->lay[0].cout; ++c) prov[ctx->lay[0].out_buf][ctx->lay[0].out_off + c] = 0;
+  for (const Step& st : ctx->steps) {
+    if (st.kind == kStepConv) {
+      const LayerDesc& y = ctx->lay[st.layer];
+      prod[st.layer].assign(prov[y.in_buf].begin(), prov[y.in_buf].begin() + y.cin);
+      if (st.layer < ctx->L - 1)
+        for (int c = 0; c < y.cout; ++c) prov[y.out_buf][y.out_off + c] = st.layer;
+    } else {
+      for (int c = 0; c < st.C; ++c) prov[st.out_buf][st.out_off + c] = prov[st.in_buf][c];
+    }
+  }
+  return prod;
+}
+
 int load_weights(sml_ctx* ctx, const void* blob, size_t bytes) {
   size_t hdr_bytes = 0;
   int has_bn = 0;
@@ -953,6 +977,9 @@ int load_weights(sml_ctx* ctx, const void* blob, size_t bytes) {
     off += n;
     return tmp;
   };
+  // FP8 nets with dense blocks or a U-Net fold the scale of each input channel into the weights
+  const bool fold = ctx->prec == kFP8 && (ctx->growth || ctx->unet);
+  const std::vector<std::vector<int>> prod = fold ? input_producers(ctx) : std::vector<std::vector<int>>();
   for (int l = 0; l < L; ++l) {
     const int cin = ctx->lay[l].cin, cout = ctx->lay[l].cout;
     std::vector<float> w = take((size_t)cout * cin * 9);
@@ -984,7 +1011,22 @@ int load_weights(sml_ctx* ctx, const void* blob, size_t bytes) {
         return r;
     } else {
       std::vector<float> wscale(cout, 1.0f), deq(cout, 1.0f);
-      if (ctx->prec == kFP8) {
+      if (ctx->prec == kFP8 && fold) {
+        // input channels of several producers (dense blocks, U-Net): each weight carries the
+        // scale of its input channel, w' = w s_in[ci]; the per-output-channel scale is taken
+        // over w', and the epilogue's dequantisation is that scale alone
+        std::vector<float> s_in(cin);
+        for (int ci = 0; ci < cin; ++ci) s_in[ci] = ctx->act_scale[prod[l][ci] + 1];
+        for (int tap = 0; tap < 9; ++tap)
+          for (int ci = 0; ci < cin; ++ci)
+            for (int co = 0; co < cout; ++co) t[((size_t)tap * cin + ci) * cout + co] *= s_in[ci];
+        for (int co = 0; co < cout; ++co) {
+          float amax = 0.f;
+          for (int k = 0; k < 9 * cin; ++k) amax = std::max(amax, fabsf(t[(size_t)k * cout + co]));
+          wscale[co] = amax > 0.f ? amax / 448.0f : 1.0f;
+          deq[co] = wscale[co];
+        }
+      } else if (ctx->prec == kFP8) {
         for (int co = 0; co < cout; ++co) {
           float amax = 0.f;
           for (int k = 0; k < 9 * cin; ++k) amax = std::max(amax, fabsf(t[(size_t)k * cout + co]));
@@ -1303,8 +1345,6 @@ int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, in
   int r;
   if (!amax || (T > 0 && !d_frames)) return fail(ctx, SML_ERR_BAD_ARG, "NULL argument");
   if (ctx->prec == kFP8) return fail(ctx, SML_ERR_UNSUPPORTED, "activation maxima need an fp32 or bf16 context");
-  if (ctx->growth || ctx->unet)
-    return fail(ctx, SML_ERR_UNSUPPORTED, "activation maxima are for plain stacks (fp8 calibration)");
   if ((r = check_dims(ctx, T, H, W))) return r;
   CamArgs ca;
   if ((r = make_cam(ctx, cam, &ca))) return r;

@@ -2,9 +2,10 @@
 // extraction; two upsampling stages, Sec. 4.2): 2x2 max pooling (stride 2; a window that
 // overhangs the last row or column takes the max of its in-frame pixels) and nearest 2x
 // upsampling into a channel range of a wider buffer (the concatenation of the level's skip
-// features and the upsampled ones).  Both move stored activations unchanged, so BF16 values
-// stay exactly representable; both are HBM-bound copies: every thread moves 16-byte chunks,
-// consecutive threads consecutive chunks of one output row.
+// features and the upsampled ones).  Both move stored activations unchanged, so BF16 and e4m3
+// values stay exactly representable (and e4m3 codes keep their layer's scale); both are
+// HBM-bound copies: every thread moves 16-byte chunks, consecutive threads consecutive chunks
+// of one output row.
 #include <cuda_bf16.h>
 
 #include "sml_internal.h"
@@ -25,12 +26,19 @@ __device__ __forceinline__ uint4 max4_bf16(uint4 a, uint4 b) {
   return r;
 }
 
+// e4m3 codes of post-ReLU values are never negative (sign bit clear), and for those the code
+// order is the value order, so a bytewise unsigned max is the max of the values.
+__device__ __forceinline__ uint4 max16_e4m3(uint4 a, uint4 b) {
+  return make_uint4(__vmaxu4(a.x, b.x), __vmaxu4(a.y, b.y), __vmaxu4(a.z, b.z), __vmaxu4(a.w, b.w));
+}
+
 __device__ __forceinline__ float4 max4_f32(float4 a, float4 b) {
   return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
 }
 
 // One output row (frame t, row r) per blockIdx.y step; its chunks over x.  A "chunk" is 16
-// bytes: BF16 row-planar [T][rows][groups][cols][2 chunks], FP32 NHWC [T][rows][cols][ct/4].
+// bytes: BF16 row-planar [T][rows][groups][cols][2 chunks], FP8 row-planar
+// [T][rows][groups][cols][1 chunk], FP32 NHWC [T][rows][cols][ct/4].
 struct ResampleArgs {
   const uint8_t* in;
   uint8_t* out;
@@ -40,23 +48,26 @@ struct ResampleArgs {
   int C, out_off;       // channels moved; first output channel
 };
 
-// BF16 row-planar, 2x2 max.
-__global__ void __launch_bounds__(kResampleThreads) k_pool2_bf16(const ResampleArgs a) {
+// Row-planar (BF16: NCH = 2 chunks per 16-channel group row, FP8: 1), 2x2 max.
+template <int NCH>
+__global__ void __launch_bounds__(kResampleThreads) k_pool2_rp(const ResampleArgs a) {
+  constexpr int RB = 16 * NCH;  // bytes of a group row
   const int G = a.C / 16, gin = a.in_ct / 16, gout = a.out_ct / 16, g0 = a.out_off / 16;
-  const int per_row = G * a.Wo * 2;
+  const int per_row = G * a.Wo * NCH;
   for (long long row = blockIdx.y; row < (long long)a.T * a.Ho; row += gridDim.y) {
     const int t = (int)(row / a.Ho), io = (int)(row - (long long)t * a.Ho);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < per_row; k += gridDim.x * blockDim.x) {
-      const int g = k / (2 * a.Wo), rem = k - g * 2 * a.Wo, jo = rem >> 1, h = rem & 1;
+      const int g = k / (NCH * a.Wo), rem = k - g * NCH * a.Wo, jo = rem / NCH, h = rem - jo * NCH;
       // the window's first pixel (2io, 2jo) is always in the frame
-      const uint8_t* p0 = a.in + ((((size_t)t * a.H + 2 * io) * gin + g) * a.W + 2 * jo) * 32 + 16 * h;
-      const size_t row_step = (size_t)gin * a.W * 32;
+      const uint8_t* p0 = a.in + ((((size_t)t * a.H + 2 * io) * gin + g) * a.W + 2 * jo) * RB + 16 * h;
+      const size_t row_step = (size_t)gin * a.W * RB;
       const bool right = 2 * jo + 1 < a.W, down = 2 * io + 1 < a.H;
+      auto mx = [](uint4 x, uint4 y) { return NCH == 2 ? max4_bf16(x, y) : max16_e4m3(x, y); };
       uint4 m = __ldg(reinterpret_cast<const uint4*>(p0));
-      if (right) m = max4_bf16(m, __ldg(reinterpret_cast<const uint4*>(p0 + 32)));
-      if (down) m = max4_bf16(m, __ldg(reinterpret_cast<const uint4*>(p0 + row_step)));
-      if (right && down) m = max4_bf16(m, __ldg(reinterpret_cast<const uint4*>(p0 + row_step + 32)));
-      *reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.Ho + io) * gout + g0 + g) * a.Wo + jo) * 32 + 16 * h) = m;
+      if (right) m = mx(m, __ldg(reinterpret_cast<const uint4*>(p0 + RB)));
+      if (down) m = mx(m, __ldg(reinterpret_cast<const uint4*>(p0 + row_step)));
+      if (right && down) m = mx(m, __ldg(reinterpret_cast<const uint4*>(p0 + row_step + RB)));
+      *reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.Ho + io) * gout + g0 + g) * a.Wo + jo) * RB + 16 * h) = m;
     }
   }
 }
@@ -82,17 +93,19 @@ __global__ void __launch_bounds__(kResampleThreads) k_pool2_f32(const ResampleAr
   }
 }
 
-// BF16 row-planar, nearest 2x: out(i, j) = in(i / 2, j / 2).
-__global__ void __launch_bounds__(kResampleThreads) k_up2_bf16(const ResampleArgs a) {
+// Row-planar (NCH chunks per group row), nearest 2x: out(i, j) = in(i / 2, j / 2).
+template <int NCH>
+__global__ void __launch_bounds__(kResampleThreads) k_up2_rp(const ResampleArgs a) {
+  constexpr int RB = 16 * NCH;
   const int G = a.C / 16, gin = a.in_ct / 16, gout = a.out_ct / 16, g0 = a.out_off / 16;
-  const int per_row = G * a.Wo * 2;
+  const int per_row = G * a.Wo * NCH;
   for (long long row = blockIdx.y; row < (long long)a.T * a.Ho; row += gridDim.y) {
     const int t = (int)(row / a.Ho), io = (int)(row - (long long)t * a.Ho);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < per_row; k += gridDim.x * blockDim.x) {
-      const int g = k / (2 * a.Wo), rem = k - g * 2 * a.Wo, jo = rem >> 1, h = rem & 1;
+      const int g = k / (NCH * a.Wo), rem = k - g * NCH * a.Wo, jo = rem / NCH, h = rem - jo * NCH;
       const uint4 v = __ldg(reinterpret_cast<const uint4*>(
-          a.in + ((((size_t)t * a.H + (io >> 1)) * gin + g) * a.W + (jo >> 1)) * 32 + 16 * h));
-      *reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.Ho + io) * gout + g0 + g) * a.Wo + jo) * 32 + 16 * h) = v;
+          a.in + ((((size_t)t * a.H + (io >> 1)) * gin + g) * a.W + (jo >> 1)) * RB + 16 * h));
+      *reinterpret_cast<uint4*>(a.out + ((((size_t)t * a.Ho + io) * gout + g0 + g) * a.Wo + jo) * RB + 16 * h) = v;
     }
   }
 }
@@ -130,11 +143,13 @@ cudaError_t launch_pool2(const void* in, int in_ct, void* out, int out_ct, int o
                          int prec, cudaStream_t s) {
   ResampleArgs a{static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), T, H, W, (H + 1) / 2, (W + 1) / 2,
                  in_ct, out_ct, C, out_off};
-  if (prec != kFP32 && prec != kBF16) return cudaErrorInvalidValue;
+  if (prec != kFP32 && prec != kBF16 && prec != kFP8) return cudaErrorInvalidValue;
   if (!resample_ok(a, prec)) return cudaErrorInvalidValue;
   if (T == 0) return cudaSuccess;
   if (prec == kBF16)
-    k_pool2_bf16<<<resample_grid(a, (C / 16) * a.Wo * 2), kResampleThreads, 0, s>>>(a);
+    k_pool2_rp<2><<<resample_grid(a, (C / 16) * a.Wo * 2), kResampleThreads, 0, s>>>(a);
+  else if (prec == kFP8)
+    k_pool2_rp<1><<<resample_grid(a, (C / 16) * a.Wo), kResampleThreads, 0, s>>>(a);
   else
     k_pool2_f32<<<resample_grid(a, a.Wo * (C / 4)), kResampleThreads, 0, s>>>(a);
   return cudaGetLastError();
@@ -143,11 +158,13 @@ cudaError_t launch_pool2(const void* in, int in_ct, void* out, int out_ct, int o
 cudaError_t launch_upsample2(const void* in, int in_ct, int h, int w, void* out, int out_ct, int out_off, int C, int T,
                              int H, int W, int prec, cudaStream_t s) {
   ResampleArgs a{static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), T, h, w, H, W, in_ct, out_ct, C, out_off};
-  if (prec != kFP32 && prec != kBF16) return cudaErrorInvalidValue;
+  if (prec != kFP32 && prec != kBF16 && prec != kFP8) return cudaErrorInvalidValue;
   if (!resample_ok(a, prec) || (H + 1) / 2 != h || (W + 1) / 2 != w) return cudaErrorInvalidValue;
   if (T == 0) return cudaSuccess;
   if (prec == kBF16)
-    k_up2_bf16<<<resample_grid(a, (C / 16) * W * 2), kResampleThreads, 0, s>>>(a);
+    k_up2_rp<2><<<resample_grid(a, (C / 16) * W * 2), kResampleThreads, 0, s>>>(a);
+  else if (prec == kFP8)
+    k_up2_rp<1><<<resample_grid(a, (C / 16) * W), kResampleThreads, 0, s>>>(a);
   else
     k_up2_f32<<<resample_grid(a, W * (C / 4)), kResampleThreads, 0, s>>>(a);
   return cudaGetLastError();

@@ -437,12 +437,18 @@ __global__ void __launch_bounds__(kSimtThreads) k_dconv_f32(const F32LayerArgs a
   }
 }
 
-// Maximum of post-ReLU activations (all >= 0, so float bit patterns order like unsigned).
+// Maximum of post-ReLU activations (all >= 0, so float bit patterns order like unsigned) over
+// rows of seg consecutive elements, stride elements apart: one layer's output channels inside
+// a wider buffer (BF16 row-planar: its groups of every pixel row; FP32 NHWC: its channels of
+// every pixel).
 template <bool BF16>
-__global__ void __launch_bounds__(256) k_amax(const void* __restrict__ x, size_t n, unsigned* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_amax(const void* __restrict__ x, size_t rows, size_t seg, size_t stride,
+                                              unsigned* __restrict__ out) {
   float m = 0.0f;
+  const size_t n = rows * seg;
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    float v = BF16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(x)[k]) : static_cast<const float*>(x)[k];
+    const size_t r = k / seg, e = r * stride + (k - r * seg);
+    float v = BF16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(x)[e]) : static_cast<const float*>(x)[e];
     m = fmaxf(m, v);
   }
 #pragma unroll
@@ -548,11 +554,19 @@ cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d,
   }
 }
 
-cudaError_t launch_amax(const void* x, size_t n, int prec, unsigned* out, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  if (prec == kFP32) k_amax<false><<<1024, 256, 0, s>>>(x, n, out);
-  else if (prec == kBF16) k_amax<true><<<1024, 256, 0, s>>>(x, n, out);
-  else return cudaErrorInvalidValue;
+cudaError_t launch_amax(const void* x, int prec, int T, int H, int W, int ct, int off, int cnt, unsigned* out,
+                        cudaStream_t s) {
+  if (T <= 0 || cnt <= 0) return cudaSuccess;
+  if (off < 0 || off + cnt > ct) return cudaErrorInvalidValue;
+  if (prec == kFP32) {  // NHWC: channels [off, off + cnt) of every pixel
+    k_amax<false><<<1024, 256, 0, s>>>(static_cast<const float*>(x) + off, (size_t)T * H * W, (size_t)cnt, (size_t)ct, out);
+  } else if (prec == kBF16) {  // row-planar: groups [off / 16, (off + cnt) / 16) of every pixel row
+    if (off % 16 || cnt % 16 || ct % 16) return cudaErrorInvalidValue;
+    k_amax<true><<<1024, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(x) + (size_t)(off / 16) * W * 16, (size_t)T * H,
+                                      (size_t)(cnt / 16) * W * 16, (size_t)(ct / 16) * W * 16, out);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

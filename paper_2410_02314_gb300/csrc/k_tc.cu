@@ -869,8 +869,8 @@ void tc_pack_bimg(const float* w /*[9][CI][CO] tap, ci, co*/, int CI, int CO, in
 }
 
 // Plain layers (ci == co, output filling whole pixel rows of its buffer) and every last layer
-// run the compile-time instances; layers of dense blocks (ci != co, or an output that is a
-// channel range of a wider buffer) run the runtime-K instances (BF16 only).
+// run the compile-time instances; layers of dense blocks and of the U-Net (ci != co, or an
+// output that is a channel range of a wider buffer) run the runtime-K instances.
 cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaStream_t s) {
   const bool plain = a.ci == a.co && a.out_g0 == 0 && a.out_gt == a.co / 16;
   if (last || plain) {
@@ -890,12 +890,12 @@ cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaSt
 #undef SML_TC
     return cudaErrorInvalidValue;
   }
-  if (a.prec != kBF16) return cudaErrorInvalidValue;
+  const bool bf = a.prec == kBF16;
   switch (a.co) {
-    case 16: return launch_tc_impl<0, 16, kBF16, false>(a, num_sms, s);
-    case 32: return launch_tc_impl<0, 32, kBF16, false>(a, num_sms, s);
-    case 48: return launch_tc_impl<0, 48, kBF16, false>(a, num_sms, s);
-    case 64: return launch_tc_impl<0, 64, kBF16, false>(a, num_sms, s);
+    case 16: return bf ? launch_tc_impl<0, 16, kBF16, false>(a, num_sms, s) : launch_tc_impl<0, 16, kFP8, false>(a, num_sms, s);
+    case 32: return bf ? launch_tc_impl<0, 32, kBF16, false>(a, num_sms, s) : launch_tc_impl<0, 32, kFP8, false>(a, num_sms, s);
+    case 48: return bf ? launch_tc_impl<0, 48, kBF16, false>(a, num_sms, s) : launch_tc_impl<0, 48, kFP8, false>(a, num_sms, s);
+    case 64: return bf ? launch_tc_impl<0, 64, kBF16, false>(a, num_sms, s) : launch_tc_impl<0, 64, kFP8, false>(a, num_sms, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -80,8 +80,10 @@ cudaError_t launch_ingest_l1(const uint16_t* frames, int T, int H, int W, int d,
 cudaError_t launch_ingest_l1_devw(const uint16_t* frames, int T, int H, int W, int d, CamArgs cam, const float* w1_dev,
                                   const float* b1_dev, int C, void* out, cudaStream_t s);
 
-// Max of n post-ReLU activations (fp32 or bf16 buffer) into *out (float bits, atomicMax).
-cudaError_t launch_amax(const void* x, size_t n, int prec, unsigned* out, cudaStream_t s);
+// Maximum of one layer's stored output: channels [off, off + cnt) of a buffer of ct channels
+// per pixel holding T frames of H x W (atomicMax of the float bits into *out).
+cudaError_t launch_amax(const void* x, int prec, int T, int H, int W, int ct, int off, int cnt, unsigned* out,
+                        cudaStream_t s);
 
 // --- SIMT FP32 path (NHWC float activations) ------------------------------------------
 // Reads channels 0..ci-1 of pixels in_ct floats apart; writes channels out_off..out_off+co-1

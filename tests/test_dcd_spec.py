@@ -59,7 +59,8 @@ def test_layer_plan_of_the_dcd_spec():
     (dict(dilations=[1]), sml.SML_ERR_BAD_SPEC),                            # no plain layer for the heads
     (dict(dcd={"growth": 32, "blocks": [[1, 2, 4, 8]]}), sml.SML_ERR_BAD_SPEC),  # 160-channel concatenation
     (dict(dcd={"blocks": [[1]] * 16}), sml.SML_ERR_BAD_SPEC),              # 35 conv layers (at most 32)
-    (dict(precision="fp8", act_scales=[1.0] * 10), sml.SML_ERR_UNSUPPORTED),  # fp8 with dense blocks
+    (dict(precision="fp8"), sml.SML_ERR_BAD_SPEC),                          # fp8 without activation scales
+    (dict(precision="fp8", act_scales=[1.0] * 9), sml.SML_ERR_BAD_SPEC),   # one scale short of the 10 layers
 ])
 def test_bad_dcd_specs_are_refused(edit, code):
     _, js, blob = _net()
@@ -98,6 +99,8 @@ def test_valid_dcd_net_reaches_the_device_check():
     for prec in ("bf16", "fp32"):
         _, js, blob = _net(prec=prec)
         assert _code(js, blob) == sml.SML_ERR_CUDA
+    _, js, blob = _net()
+    assert _code(_edit(js, precision="fp8", act_scales=[0.01] * 10), blob) == sml.SML_ERR_CUDA
     spec = synth.spec_dcd()
     assert _code(spec.to_json(), synth.pack_blob(spec, synth.init_weights(spec, 1))) == sml.SML_ERR_CUDA
 
@@ -161,7 +164,7 @@ def test_unet_layer_plan():
     (dict(unet={"levels": 0}), sml.SML_ERR_BAD_SPEC),
     (dict(unet={}), sml.SML_ERR_BAD_SPEC),
     (dict(unet=2), sml.SML_ERR_BAD_SPEC),
-    (dict(precision="fp8", act_scales=[1.0] * 7), sml.SML_ERR_UNSUPPORTED),
+    (dict(precision="fp8", act_scales=[1.0] * 6), sml.SML_ERR_BAD_SPEC),  # one scale short of the 7 layers
 ])
 def test_bad_unet_specs_are_refused(edit, code):
     _, js, blob = _unet(2)
@@ -190,6 +193,8 @@ def test_valid_unet_nets_reach_the_device_check():
                dict(levels=2, C=48)):
         _, js, blob = _unet(**kw)
         assert _code(js, blob) == sml.SML_ERR_CUDA, kw
+    _, js, blob = _unet(2)
+    assert _code(json.dumps(dict(json.loads(js), precision="fp8", act_scales=[0.01] * 7)), blob) == sml.SML_ERR_CUDA
 
 
 # ----------------------------------------------------------------------------- deep plain stacks
