@@ -98,11 +98,16 @@ typedef struct {
  *   dense layer per listed dilation (input: the block input and every earlier output of the
  *   block, concatenated; g outputs) and a transition (d = 1, C + k g -> C), then the plain
  *   layers dilations[1:] (at least one); concatenations up to 128 channels, at most 32 conv
- *   layers, fp32 or bf16 (fp8: SML_ERR_UNSUPPORTED; so is a layer whose weights do not fit
- *   one CTA's shared memory);
+ *   layers (SML_ERR_UNSUPPORTED for a layer whose weights do not fit one CTA's shared
+ *   memory);
  *   precision "fp32" (SIMT FP32 FMA), "bf16" (tensor cores, FP32 accumulation) or
  *   "fp8" (e4m3 activations and weights, FP32 accumulation; needs "act_scales": one
- *   positive float per conv layer, the scale of that layer's input activations).
+ *   positive float per conv layer in execution order, act_scales[l] for l >= 1 being the
+ *   scale of the activations layer l-1 stores (act_scales[0] is unused); layer l stores
+ *   e4m3(a / act_scales[l+1]); weights are rounded per output channel, w / s[co] with
+ *   s[co] = max |w[co,:,:,:]| / 448; in nets with dense blocks or a U-Net, whose layers read
+ *   channels stored by several layers, each weight is first multiplied by the scale of its
+ *   input channel and s[co] is taken over those products).
  *   Optional tuning: "chunk_px": pixels per device chunk (default 2^24); "tc_stages": TMA
  *   ring depth of the tensor-core conv (0 = as deep as shared memory allows, else 4..16);
  *   "fp8_pair_rows": 1 (default) loads FP8 activations of even-width frames as 32-byte pixel
@@ -233,8 +238,9 @@ int sml_decode_maps(sml_ctx* ctx, const float* d_maps, int T, int H, int W, cons
  * sml_activation_amax -- calibration for the "fp8" precision.  Runs the network of an fp32 or
  * bf16 context over d_frames (device [T][H][W] uint16, camera as in sml_localize with device
  * maps) and writes to amax (host float[L]): amax[l], l = 1..L-1, is the largest activation
- * that enters conv layer l (the ReLU output of layer l-1); amax[0] = 0.  An fp8 net spec
- * then uses act_scales[l] = amax[l] / 448 (the largest finite e4m3 value).  Synchronous.
+ * that layer l-1 stores (its ReLU output, over its output channels; for a plain stack the
+ * input of layer l); amax[0] = 0.  An fp8 net spec then uses act_scales[l] = amax[l] / 448
+ * (the largest finite e4m3 value).  Synchronous.
  * Errors: SML_ERR_UNSUPPORTED on an fp8 context, SML_ERR_BAD_ARG, SML_ERR_CUDA.
  */
 int sml_activation_amax(sml_ctx* ctx, const uint16_t* d_frames, int T, int H, int W, const sml_camera* cam,

@@ -75,7 +75,7 @@ class NetSpec:
     in_scale: float = 1e-3
     z_scale: float = 1000.0
     ph_scale: float = 10000.0
-    act_scales: tuple = ()  # fp8 only: one activation scale per conv layer input
+    act_scales: tuple = ()  # fp8 only, one per conv layer: [l] = scale of what layer l-1 stores
     # Dense connection dilated blocks, or None for the plain stack: {"growth": g, "blocks":
     # [[d, ...], ...]}.  The net is then: stem conv (dilations[0], in_ch -> C); per block, one
     # dense layer per listed dilation (input: the block input and every earlier layer's
