@@ -56,7 +56,8 @@ namespace {
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = 224;
 constexpr int kMinStages = 4;  // the handoff protocol needs a ring of at least 2 handoff groups
-constexpr int kTmemCols = 512;
+constexpr int kTmemCols = 512;  // TMEM columns of a CTA that has its SM to itself
+constexpr int kPairTmemCols = 256;  // of each of two CTAs sharing an SM (PAIR instances)
 constexpr int kMaxSeg = 10;
 constexpr int kMaxStages = 16;
 
@@ -100,7 +101,11 @@ struct TcKArgs {
 // Compile-time shape of one layer: CI input channels (K = 9 taps x CI), CO output channels
 // (N = 3 CO per MMA).  CI = 0 is the runtime-K instance: the K-dependent sizes come from the
 // kernel arguments instead (dense-block layers, whose CI grows along the block).
-template <int CI, int CO, int PREC>
+// PAIR: two CTAs share each SM, each with half of its TMEM and shared memory, so that two MMA
+// issue streams feed one tensor pipe (one CTA's MMA warp leaves the pipe idle while it
+// commits, hands over and keeps its books; measured in FP8 layers and last layers: see the
+// launcher).
+template <int CI, int CO, int PREC, bool PAIR = false>
 struct TcCfg {
   static constexpr int G = CI / 16;                       // 16-channel input groups stored in HBM
   static constexpr int GO = CO / 16;                      // output groups
@@ -111,10 +116,15 @@ struct TcCfg {
   static constexpr int BIMG = 3 * NKS * BBLK;
   // S = output rows per unit.  Output row k accumulates at columns BASE0 - CO*k .. + CO, and an
   // input row's MMA only writes the columns of the unit's rows it feeds, so a unit spans
-  // columns [BASE0 - CO*(S-1), BASE0 + CO) = [2 CO, (S+2) CO): S <= 512/CO - 2
-  static constexpr int SEG = (512 / CO - 2) < kMaxSeg ? (512 / CO - 2) : kMaxSeg;
-  static constexpr uint32_t BASE0 = (uint32_t)(SEG + 1) * CO;  // TMEM column of output row 0
-  static_assert((SEG + 2) * CO <= 512, "a unit's accumulators fit the 512 TMEM columns");
+  // columns [BASE0 - CO*(S-1), BASE0 + CO).  With the whole TMEM: BASE0 = (S+1) CO, i.e.
+  // [2 CO, (S+2) CO), S <= 512/CO - 2; with half of it (PAIR): BASE0 = (S-1) CO, i.e.
+  // [0, S CO), S <= 256/CO.
+  static constexpr int TMEM_COLS = PAIR ? kPairTmemCols : kTmemCols;
+  static constexpr int SEG_FIT = PAIR ? kPairTmemCols / CO : kTmemCols / CO - 2;
+  static constexpr int SEG = SEG_FIT < kMaxSeg ? SEG_FIT : kMaxSeg;
+  static constexpr uint32_t BASE0 = (uint32_t)(PAIR ? SEG - 1 : SEG + 1) * CO;  // TMEM column of output row 0
+  static_assert(BASE0 + CO <= (uint32_t)TMEM_COLS && BASE0 >= (uint32_t)(CO * (SEG - 1)),
+                "a unit's accumulators fit the CTA's TMEM columns");
   static constexpr uint32_t IDESC1 = instr_desc(PREC, kTileM, CO);
   static constexpr uint32_t IDESC2 = instr_desc(PREC, kTileM, 2 * CO);
   static constexpr uint32_t IDESC3 = instr_desc(PREC, kTileM, 3 * CO);
@@ -195,9 +205,10 @@ __device__ __forceinline__ void heads_out(const TcKArgs& a, const float (&v)[CO]
   }
 }
 
-template <int CI, int CO, int PREC, bool LAST, bool DGRAD = false>
-__global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant__ CUtensorMap tmap, const TcKArgs a) {
-  using Cfg = TcCfg<CI, CO, PREC>;
+template <int CI, int CO, int PREC, bool LAST, bool DGRAD = false, bool PAIR = false>
+__global__ void __launch_bounds__(kThreads, PAIR ? 2 : 1) k_dconv_tc(const __grid_constant__ CUtensorMap tmap,
+                                                                      const TcKArgs a) {
+  using Cfg = TcCfg<CI, CO, PREC, PAIR>;
   // K-dependent sizes: compile-time constants, or the arguments' values for CI = 0
   const int nks = CI > 0 ? Cfg::NKS : a.nks;
   const int g_in = CI > 0 ? Cfg::G : a.g_in;
@@ -255,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
     }
     if (warp == 5) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void*)s_tmem)),
-                   "r"(kTmemCols)
+                   "r"(Cfg::TMEM_COLS)
                    : "memory");
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -575,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dconv_tc(const __grid_constant_
   __syncthreads();
   if (warp == 5) {
     fence_after_sync();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS) : "memory");
   }
 }
 
@@ -730,6 +741,7 @@ size_t tc_smem_bytes(uint32_t bimg_bytes, int seg, int nstages, uint32_t stage_b
 }
 
 constexpr size_t kSmemBudget = 227 * 1024;
+constexpr size_t kPairSmemBudget = 112 * 1024;  // per CTA when two CTAs share an SM
 std::mutex g_tc_launch_mutex;  // serialises attribute-set + launch of the conv kernels
 
 // Row sizes of a layer with ci input channels at dilation d.
@@ -752,9 +764,10 @@ TcSizes tc_sizes(int ci, int co, int d, int prec) {
 
 int tc_seg(int co) { return (512 / co - 2) < kMaxSeg ? (512 / co - 2) : kMaxSeg; }
 
-template <int CI, int CO, int PREC, bool LAST, bool DGRAD = false>
+template <int CI, int CO, int PREC, bool LAST, bool DGRAD = false, bool PAIR = false>
 cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
-  using Cfg = TcCfg<CI, CO, PREC>;
+  using Cfg = TcCfg<CI, CO, PREC, PAIR>;
+  constexpr size_t budget = PAIR ? kPairSmemBudget : kSmemBudget;
   const int ci = CI > 0 ? CI : la.ci;
   if (la.co != CO || ci != la.ci || ci < 16 || ci > kTcMaxCin || ci % 16) return cudaErrorInvalidValue;
   TcKArgs a{};
@@ -807,19 +820,20 @@ cudaError_t launch_tc_impl(const TcLayerArgs& la, int num_sms, cudaStream_t s) {
   if (a.units == 0) return cudaSuccess;
   int nst = la.stages > 0 ? la.stages : kMaxStages;
   if (nst < kMinStages) return cudaErrorInvalidValue;
-  while (nst > kMinStages && tc_smem_bytes(z.bimg_bytes, Cfg::SEG, nst, z.stage_bytes) > kSmemBudget) --nst;
+  while (nst > kMinStages && tc_smem_bytes(z.bimg_bytes, Cfg::SEG, nst, z.stage_bytes) > budget) --nst;
   a.nstages = nst;
   size_t smem = tc_smem_bytes(z.bimg_bytes, Cfg::SEG, nst, z.stage_bytes);
-  if (smem > kSmemBudget) return cudaErrorInvalidConfiguration;
+  if (smem > budget) return cudaErrorInvalidConfiguration;
   // the limit is this launch's size, which differs between the layers that share the
   // runtime-K instance: set and launch under one lock, so that contexts on several host
   // threads never launch under another launch's smaller limit
   std::lock_guard<std::mutex> lock(g_tc_launch_mutex);
-  cudaError_t e = cudaFuncSetAttribute(k_dconv_tc<CI, CO, PREC, LAST, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_dconv_tc<CI, CO, PREC, LAST, DGRAD, PAIR>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  long long grid = (long long)a.units < (long long)num_sms ? (long long)a.units : (long long)num_sms;
-  k_dconv_tc<CI, CO, PREC, LAST, DGRAD><<<(unsigned)grid, kThreads, smem, s>>>(*la.tmap, a);
+  const long long ctas = (PAIR ? 2LL : 1LL) * num_sms;  // persistent: every CTA resident at once
+  const long long grid = (long long)a.units < ctas ? (long long)a.units : ctas;
+  k_dconv_tc<CI, CO, PREC, LAST, DGRAD, PAIR><<<(unsigned)grid, kThreads, smem, s>>>(*la.tmap, a);
   return cudaGetLastError();
 }
 
@@ -871,16 +885,38 @@ void tc_pack_bimg(const float* w /*[9][CI][CO] tap, ci, co*/, int CI, int CO, in
 // Plain layers (ci == co, output filling whole pixel rows of its buffer) and every last layer
 // run the compile-time instances; layers of dense blocks and of the U-Net (ci != co, or an
 // output that is a channel range of a wider buffer) run the runtime-K instances.
+// Two CTAs per SM (PAIR instances, 32 or 48 channels) for the FP8 layers and every last layer,
+// when a ring of kMinStages stages fits half of the shared memory.  Measured on the 256-frame
+// batch of the 48-channel net: FP8 middle layers 0.429 -> 0.365 ms, last layer 0.590 -> 0.515
+// ms (FP8) and 0.606 -> 0.529 ms (BF16).  The BF16 middle layers keep one CTA per SM: at half
+// the shared memory their ring shrinks to 4 stages and the launch went 0.618 -> 0.702 ms.
+static bool tc_use_pair(const TcLayerArgs& a, bool last) {
+  if ((a.prec != kFP8 && !last) || (a.co != 32 && a.co != 48) || a.ci != a.co) return false;
+  const TcSizes z = tc_sizes(a.ci, a.co, a.d, a.prec);
+  const int seg = kPairTmemCols / a.co < kMaxSeg ? kPairTmemCols / a.co : kMaxSeg;
+  return tc_smem_bytes(z.bimg_bytes, seg, kMinStages, z.stage_bytes) <= kPairSmemBudget;
+}
+
 cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaStream_t s) {
   const bool plain = a.ci == a.co && a.out_g0 == 0 && a.out_gt == a.co / 16;
   if (last || plain) {
+    if (a.ci != a.co) return cudaErrorInvalidValue;
+    if (tc_use_pair(a, last)) {
+      const bool bf = a.prec == kBF16;
+      if (a.co == 32)
+        return bf ? launch_tc_impl<32, 32, kBF16, true, false, true>(a, num_sms, s)
+                  : (last ? launch_tc_impl<32, 32, kFP8, true, false, true>(a, num_sms, s)
+                          : launch_tc_impl<32, 32, kFP8, false, false, true>(a, num_sms, s));
+      return bf ? launch_tc_impl<48, 48, kBF16, true, false, true>(a, num_sms, s)
+                : (last ? launch_tc_impl<48, 48, kFP8, true, false, true>(a, num_sms, s)
+                        : launch_tc_impl<48, 48, kFP8, false, false, true>(a, num_sms, s));
+    }
 #define SML_TC(CC)                                                                                          \
   case CC:                                                                                                  \
     if (a.prec == kBF16)                                                                                    \
       return last ? launch_tc_impl<CC, CC, kBF16, true>(a, num_sms, s) : launch_tc_impl<CC, CC, kBF16, false>(a, num_sms, s); \
     else                                                                                                    \
       return last ? launch_tc_impl<CC, CC, kFP8, true>(a, num_sms, s) : launch_tc_impl<CC, CC, kFP8, false>(a, num_sms, s);
-    if (a.ci != a.co) return cudaErrorInvalidValue;
     switch (a.co) {
       SML_TC(16)
       SML_TC(32)
