@@ -885,13 +885,20 @@ void tc_pack_bimg(const float* w /*[9][CI][CO] tap, ci, co*/, int CI, int CO, in
 // Plain layers (ci == co, output filling whole pixel rows of its buffer) and every last layer
 // run the compile-time instances; layers of dense blocks and of the U-Net (ci != co, or an
 // output that is a channel range of a wider buffer) run the runtime-K instances.
-// Two CTAs per SM (PAIR instances, 32 or 48 channels) for the FP8 layers and every last layer,
-// when a ring of kMinStages stages fits half of the shared memory.  Measured on the 256-frame
+// Two CTAs per SM (PAIR instances) for the 32- and 48-channel FP8 layers, every 32- or
+// 48-channel last layer and the runtime-K layers with 16 or 32 output channels (dense blocks,
+// U-Net; measured: FP8 dense-block net 27.9k -> 37.1k frames/s), when a ring of kMinStages
+// stages fits half of the shared memory.  Measured on the 256-frame
 // batch of the 48-channel net: FP8 middle layers 0.429 -> 0.365 ms, last layer 0.590 -> 0.515
 // ms (FP8) and 0.606 -> 0.529 ms (BF16).  The BF16 middle layers keep one CTA per SM: at half
 // the shared memory their ring shrinks to 4 stages and the launch went 0.618 -> 0.702 ms.
 static bool tc_use_pair(const TcLayerArgs& a, bool last) {
-  if ((a.prec != kFP8 && !last) || (a.co != 32 && a.co != 48) || a.ci != a.co) return false;
+  const bool plain = a.ci == a.co && a.out_g0 == 0 && a.out_gt == a.co / 16;
+  if (!last && !plain) {  // runtime-K layers (dense blocks, U-Net): 16 or 32 output channels
+    if (a.co != 16 && a.co != 32) return false;
+  } else if ((a.prec != kFP8 && !last) || (a.co != 32 && a.co != 48) || a.ci != a.co) {
+    return false;
+  }
   const TcSizes z = tc_sizes(a.ci, a.co, a.d, a.prec);
   const int seg = kPairTmemCols / a.co < kMaxSeg ? kPairTmemCols / a.co : kMaxSeg;
   return tc_smem_bytes(z.bimg_bytes, seg, kMinStages, z.stage_bytes) <= kPairSmemBudget;
@@ -927,6 +934,13 @@ cudaError_t launch_dconv_tc(const TcLayerArgs& a, bool last, int num_sms, cudaSt
     return cudaErrorInvalidValue;
   }
   const bool bf = a.prec == kBF16;
+  if (tc_use_pair(a, false)) {
+    if (a.co == 16)
+      return bf ? launch_tc_impl<0, 16, kBF16, false, false, true>(a, num_sms, s)
+                : launch_tc_impl<0, 16, kFP8, false, false, true>(a, num_sms, s);
+    return bf ? launch_tc_impl<0, 32, kBF16, false, false, true>(a, num_sms, s)
+              : launch_tc_impl<0, 32, kFP8, false, false, true>(a, num_sms, s);
+  }
   switch (a.co) {
     case 16: return bf ? launch_tc_impl<0, 16, kBF16, false>(a, num_sms, s) : launch_tc_impl<0, 16, kFP8, false>(a, num_sms, s);
     case 32: return bf ? launch_tc_impl<0, 32, kBF16, false>(a, num_sms, s) : launch_tc_impl<0, 32, kFP8, false>(a, num_sms, s);
