@@ -8,7 +8,8 @@ per-output-channel rounding.  Pinned by:
   * a net with dense blocks of no layers, which is a plain stack: with power-of-two scales the
     fold changes no rounding, so it must equal the plain-stack e4m3 oracle (the C forward);
   * an independent torch emulation of a dense + U-Net net: torch's own e4m3 cast at the same
-    points, torch conv2d, max_pool2d, interpolate and cat.
+    points, torch conv2d, max_pool2d, interpolate and cat;
+  * the activation scales: each layer's largest output in an independent torch forward.
 """
 from __future__ import annotations
 
@@ -121,3 +122,37 @@ def test_dense_fp8_mode_needs_the_scales():
         oracle.quantized(net, "fp8")
     with pytest.raises(ValueError):
         oracle.forward_x(net, np.zeros((1, 1, 5, 5)), quant="fp8")
+
+
+def test_dense_unet_activation_scales_are_the_layer_output_maxima():
+    """act_scales of a dense + U-Net net: 1 for the frames, then each conv layer's largest
+    stored output / 448, in execution order (layers 0..L-2), from an independent torch
+    forward of the same net."""
+    spec = synth.NetSpec(in_ch=1, channels=16, dilations=(1, 2, 1), unet=2, dcd={"growth": 16, "blocks": [[2, 4]]})
+    blob = synth.pack_blob(spec, synth.init_weights(spec, 9))
+    net = oracle.Net(spec.to_json(), blob)
+    w = synth.blob_f32_weights(blob, spec)
+    frames = np.random.default_rng(6).integers(100, 900, (2, 13, 14)).astype(np.uint16)
+    x0 = torch.from_numpy(oracle.ingest(frames, 1.0, 100.0, in_scale=net.in_scale)[:, None])
+    outs = []
+
+    def conv(t, d):
+        li = len(outs)
+        out = torch.relu(F.conv2d(t, torch.from_numpy(w.conv_w[li]), torch.from_numpy(w.conv_b[li]), padding=d,
+                                  dilation=d))
+        outs.append(out)
+        return out
+
+    stem = conv(x0, 1)
+    d1 = conv(stem, 2)
+    d2 = conv(torch.cat([stem, d1], 1), 4)
+    a = conv(conv(torch.cat([stem, d1, d2], 1), 1), 2)
+    s1 = conv(F.max_pool2d(a, 2, 2, ceil_mode=True), 1)
+    s2 = conv(F.max_pool2d(s1, 2, 2, ceil_mode=True), 1)
+    up = lambda t, like: F.interpolate(t, scale_factor=2, mode="nearest")[:, :, : like.shape[2], : like.shape[3]]
+    u1 = conv(torch.cat([s1, up(s2, s1)], 1), 1)
+    conv(conv(torch.cat([a, up(u1, a)], 1), 1), 1)
+    assert len(outs) == net.L
+    want = [1.0] + [float(o.max()) / 448.0 for o in outs[:-1]]
+    got = oracle.act_scales(net, frames, 1.0, 100.0)
+    np.testing.assert_allclose(got, want, rtol=1e-12)
