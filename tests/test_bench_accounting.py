@@ -40,6 +40,9 @@ def test_dense_block_net(bench):
     assert flops == 4 * (18 * 16 * (32 + 48 + 64 + 80) + 18 * 96 * 32) * PX  # 479 232 per px
     assert nbytes == 4 * ((48 + 64 + 80 + 96) + (96 + 32)) * 2 * PX  # 3 328 B per px
     assert nbytes == 55834574848
+    # e4m3 activations: one byte per channel, the same FLOPs
+    f8, b8, l8 = bench.conv_class_work(synth.spec_dcd(), PX, 1)
+    assert (f8, b8, l8) == (flops, nbytes // 2, launches)
 
 
 def test_full_topology_adds_the_unet_stage(bench):
